@@ -1,0 +1,374 @@
+"""Benchmark of the cascading FP64x2 GEMM on GB300.
+
+One step = one pass of the whole hot path over one problem: the split of A
+(four pieces), the split of B (seven panels) and the ten FP64 products with
+the fused bin assembly, through the C ABI (ddgemm).  Default workload: the
+4096^3 cascade with hi log-uniform over 2^-20..2^20 (random signs) and
+lo = hi 2^-53 U[-1, 1], seed 0.  The inputs (512 MiB), the cascaded panels
+(1.4 GiB) and C are all larger than the 129 MB L2, so no flush is needed
+between steps.
+
+Metric: effective FP64x2 GFLOP/s = 2 m n k / time (the work of the FP64x2
+product, not of the ten FP64 products), next to the fraction of the FP64
+tensor-path peak that the ten products reach, and the largest error against
+the double-double oracle on sampled entries.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica of the problem (the
+cascade needs no exchange between GPUs): value = all ranks' work / the
+slowest rank's time.  `--impl reference` times the CPU oracle (the scalar
+double-double triple loop) on the host cores on a bounded sample of rows.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from workloads import gemm_inputs  # noqa: E402
+
+METRIC = "effective FP64x2 GFLOP/s at 4096^3 & % FP64-TC peak; max err vs dd oracle"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Nominal GB300 dense rates (TFLOP/s) for the FP64-from-bf16 ratio.
+NOMINAL_FP64_TFLOPS = 1.25
+NOMINAL_BF16_TFLOPS = 2250.0
+
+WORKLOADS = {
+    "4096": dict(m=4096, n=4096, k=4096, kind="wide",
+                 name="ddgemm 4096x4096x4096 FP64x2, hi log-uniform 2^-20..2^20, seed 0"),
+    "rect": dict(m=8192, n=1024, k=4096, kind="wide",
+                 name="ddgemm 8192x1024x4096 FP64x2, hi log-uniform 2^-20..2^20, seed 0"),
+    "2048": dict(m=2048, n=2048, k=2048, kind="wide",
+                 name="ddgemm 2048x2048x2048 FP64x2, hi log-uniform 2^-20..2^20, seed 0"),
+    "256": dict(m=256, n=256, k=256, kind="uniform",
+                name="ddgemm 256x256x256 FP64x2, hi U[-1,1], seed 0"),
+}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def physical_index(local: int) -> int:
+    """nvidia-smi index of this rank's GPU."""
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    if local < len(vis) and vis[local].isdigit():
+        return int(vis[local])
+    return local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.proc = subprocess.Popen(
+            [exe, "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+             "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+            stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for name, val in zip(self.NAMES, parts[3:7]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.remove(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def fp64_peak_rule():
+    """FP64 tensor peak from the measured bf16 peak x the nominal
+    FP64/bf16 ratio (sustained figure: the kernel runs inside a long step)."""
+    try:
+        with open(MEASURED_PEAKS) as f:
+            mp = json.load(f)
+        return (mp["bf16_tflops_sustained"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS,
+                "MEASURED_PEAKS.json bf16_tflops_sustained x nominal FP64/bf16 (1.25/2250)")
+    except (OSError, KeyError, ValueError):
+        return (1700.0 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS,
+                "fallback sustained bf16 1.7 PFLOP/s x nominal FP64/bf16 (1.25/2250)")
+
+
+def oracle_rows_rate(a_hi, a_lo, b_hi, b_lo, rows):
+    """Time the double-double oracle on full rows of C; returns (seconds, threads)."""
+    from oracle import dd
+    n = b_hi.shape[1]
+    rr = np.repeat(np.asarray(rows, dtype=np.int32), n)
+    cc = np.tile(np.arange(n, dtype=np.int32), len(rows))
+    t0 = time.perf_counter()
+    dd.ddgemm_entries(a_hi, a_lo, b_hi, b_lo, rr, cc)
+    return time.perf_counter() - t0, dd.num_threads()
+
+
+def cpu_baseline(a_hi, a_lo, b_hi, b_lo, target_s=12.0):
+    """The oracle as it stands on the host cores, on a bounded row sample."""
+    m, k = a_hi.shape
+    n = b_hi.shape[1]
+    probe_rows = 2
+    t, _ = oracle_rows_rate(a_hi, a_lo, b_hi, b_lo, list(range(probe_rows)))
+    rows = int(max(1, min(m, probe_rows * target_s / max(t, 1e-6))))
+    sel = np.linspace(0, m - 1, rows).astype(np.int64)
+    t, threads = oracle_rows_rate(a_hi, a_lo, b_hi, b_lo, sel)
+    value = 2.0 * rows * n * k / t / 1e9
+    return {"value": round(value, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"{rows} of {m} rows of C ({rows * n} entries, k = {k}), "
+                      f"scalar double-double TwoProd/TwoSum loop, {t:.1f} s"}
+
+
+def run_reference(args, wl):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(wl["m"], wl["n"], wl["k"], kind=wl["kind"], seed=0)
+    from oracle import dd
+    dd.build()
+    m, n, k = wl["m"], wl["n"], wl["k"]
+    # rows per step sized for ~2-3 s of host work
+    t, threads = oracle_rows_rate(a_hi, a_lo, b_hi, b_lo, [0])
+    rows = int(max(1, min(m, 2.5 / max(t, 1e-6))))
+    rng = np.random.default_rng(1)
+    for _ in range(args.warmup):
+        oracle_rows_rate(a_hi, a_lo, b_hi, b_lo, rng.integers(0, m, rows))
+    times = []
+    for _ in range(args.steps):
+        t, threads = oracle_rows_rate(a_hi, a_lo, b_hi, b_lo, rng.integers(0, m, rows))
+        times.append(t)
+    step_s = sum(times) / len(times)
+    value = 2.0 * rows * n * k / step_s / 1e9
+    sample = f"{rows} random rows of C per step ({rows * n} entries, k = {k})"
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl["name"], "m": m, "n": n, "k": k,
+                       "sample": sample, "l2": "host run"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, wl):
+    import torch
+
+    from paper_2303_04353_gb300 import _lib, ops
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the cascade has no CPU path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+    m, n, k = wl["m"], wl["n"], wl["k"]
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind=wl["kind"], seed=0)
+    host_in = [torch.from_numpy(x).pin_memory() for x in (a_hi, a_lo, b_hi, b_lo)]
+    d_in = [h.to(dev) for h in host_in]
+    c_hi = torch.empty((m, n), dtype=torch.float64, device=dev)
+    c_lo = torch.empty((m, n), dtype=torch.float64, device=dev)
+    ws = ops.alloc_workspace(m, n, k, dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(events=None):
+        ops.ddgemm(*d_in, out=(c_hi, c_lo), workspace=ws, status=status, stream=stream,
+                   phase_events=events)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps on device-resident inputs -------------------
+    phase = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    for evs in phase:
+        for e in evs:
+            e.record(stream)          # create the events before handing them over
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(physical_index(local))
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(phase[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    split_ms = sum(ev[0].elapsed_time(ev[1]) for ev in phase) / args.steps
+    casc_ms = sum(ev[1].elapsed_time(ev[2]) for ev in phase) / args.steps
+    if world > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([elapsed_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    flops_dd = 2.0 * m * n * k
+    value = world * flops_dd / (ms_per_step * 1e-3) / 1e9
+    st = int(status.item())
+    if st:
+        raise SystemExit(f"bench.py: device status {st:#x} (non-finite input or timeout)")
+
+    # ---- accuracy on sampled entries vs the double-double oracle -----------
+    from oracle import dd
+    rng = np.random.default_rng(7)
+    rows = rng.integers(0, m, 256)
+    cols = rng.integers(0, n, 256)
+    ch, cl = c_hi.cpu().numpy(), c_lo.cpu().numpy()
+    oh, ol = dd.ddgemm_entries(a_hi, a_lo, b_hi, b_lo, rows, cols)
+    absab = np.array([np.abs(a_hi[i]) @ np.abs(b_hi[:, j]) for i, j in zip(rows, cols)])
+    err = np.abs((ch[rows, cols] - oh) + (cl[rows, cols] - ol))
+    max_err = float(np.max(err / absab))
+
+    # ---- end to end: pinned host inputs -> C ABI -> host result ------------
+    e2e_steps = max(1, min(args.steps, 3))
+    host_out = [torch.empty((m, n), dtype=torch.float64).pin_memory() for _ in range(2)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for d, h in zip(d_in, host_in):
+            d.copy_(h, non_blocking=True)
+        step()
+        host_out[0].copy_(c_hi, non_blocking=True)
+        host_out[1].copy_(c_lo, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([e2e_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = sum(h.numel() * 8 for h in host_in)
+    d2h = 2 * m * n * 8
+
+    # ---- the FP64 tensor-path ceiling, measured on this GPU ----------------
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    best = 0.0
+    for iters in (200, 2000, 2000, 2000):
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        fl = _lib.ddgemm_probe_fp64(iters, sink.data_ptr(), stream.cuda_stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, fl / (p0.elapsed_time(p1) * 1e-3) / 1e12)
+    probe_tflops = best
+
+    if rank != 0:
+        return
+    peak, peak_src = fp64_peak_rule()
+    achieved = 10.0 * flops_dd / (casc_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "m": m, "n": n, "k": k,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs (512 MiB) and panels larger than L2; no flush"
+                         if m * k >= 1 << 22 else "small case; L2-resident"},
+        "pct_fp64_tc_peak": round(100.0 * 10.0 * flops_dd / (ms_per_step * 1e-3) / 1e12
+                                  / probe_tflops, 2),
+        "max_err_vs_dd_oracle": max_err,
+        "phases_ms": {"split": round(split_ms, 3), "ten_products_and_assembly": round(casc_ms, 3)},
+        "roofline": {"bound": "tensor", "kernel": "cascade_fp64_kernel",
+                     "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": peak_src,
+                     "probe_peak": round(probe_tflops, 4),
+                     "frac_vs_probe": round(achieved / probe_tflops, 4),
+                     "algorithmic": f"10 x 2mnk = {10 * flops_dd:.4g} FP64 flops per launch"},
+        "e2e": {"value": round(world * flops_dd / (e2e_ms * 1e-3) / 1e9, 4), "unit": "GFLOP/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a_hi, a_lo, b_hi, b_lo)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="4096")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("bench.py: at least 3 warm-up steps")
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

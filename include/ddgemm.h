@@ -1,0 +1,166 @@
+/*
+ * ddgemm.h - cascading double-double GEMM on one GB300 GPU (sm_103a).
+ *
+ * C := A B with A, B, C in double-double (FP64x2): every matrix is a pair of
+ * FP64 arrays (hi, lo) and an entry's value is the exact real hi + lo
+ * (Parikh, van de Geijn, Henry, "Cascading GEMM: High Precision from Low
+ * Precision", Sec. "FP64 and FP64x2 numbers", eq. doubledouble).  The paper
+ * states the operation as C := A B, with no alpha or beta (Sec.
+ * "Introduction"); so does this library.
+ *
+ * Method (Sec. "Cascading matrices and GEMM", eq. Gemm10; Sec. "Simple";
+ * Appendix A): k is staged in blocks of K_C = 256.  For every k-block each
+ * row of A and each column of B is scaled by a power of two (sigma, tau)
+ * and split into four FP64 pieces holding 22, 21 and 21 fixed-point digits
+ * plus an FP64 remainder; B also gets the combined panels B4, B5, B6.  Ten
+ * FP64 products land in four bins (0, 1, 2 exact; 3-6 rounded), which are
+ * added from bin 3-6 up to bin 0 in FP64x2, scaled back by sigma tau and
+ * accumulated into C in FP64x2.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major.  Element (r, c) of a matrix with leading
+ *     dimension ld is at ptr[r * ld + c].
+ *   - Every matrix pointer is DEVICE memory owned by the caller, and the
+ *     library never allocates, frees or keeps a pointer after the call:
+ *     scratch space is the caller's `workspace`.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it and the call returns without waiting.
+ *   - The return value reports host-side checks and launch errors only.
+ *     Conditions found on the device are OR-ed into the optional word
+ *     opts->status_dev (DDGEMM_DEV_* bits), which the caller reads after
+ *     synchronising the stream.
+ *   - Inputs need not be normalised (|lo| may reach ulp(hi)); outputs are
+ *     normalised: hi == fl(hi + lo).
+ *   - Results near the FP64 overflow threshold or in the subnormal range are
+ *     outside the paper's error analysis; non-finite inputs set
+ *     DDGEMM_DEV_NONFINITE and leave the affected outputs unspecified.
+ */
+#ifndef DDGEMM_H
+#define DDGEMM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Host-side return codes. */
+#define DDGEMM_OK            0 /* work enqueued */
+#define DDGEMM_EINVAL        1 /* bad size, leading dimension, pointer or option */
+#define DDGEMM_EWORKSPACE    2 /* workspace NULL, misaligned or smaller than required */
+#define DDGEMM_ECUDA         3 /* a CUDA runtime call or kernel launch failed */
+#define DDGEMM_EUNSUPPORTED  4 /* valid request this build does not implement */
+
+/* Device status bits, OR-ed into *opts->status_dev. */
+#define DDGEMM_DEV_NONFINITE 0x1u /* an input entry was Inf or NaN */
+#define DDGEMM_DEV_TIMEOUT   0x2u /* a bounded wait inside a kernel gave up;
+                                     outputs of that call are incomplete */
+
+/* opts->variant */
+#define DDGEMM_VARIANT_FP64  0    /* ten FP64 products on the FP64 tensor path */
+
+typedef struct ddgemm_opts {
+    /* 0: A is m x k (lda >= k).  1: A is stored k x m (lda >= m) and the
+     * operation uses its transpose.  Same for B: 0 = k x n (ldb >= n),
+     * 1 = stored n x k (ldb >= k). */
+    int trans_a;
+    int trans_b;
+    /* DDGEMM_VARIANT_FP64. */
+    int variant;
+    /* Optional device word (or NULL): DDGEMM_DEV_* bits are OR-ed into it.
+     * The library never clears it. */
+    unsigned int *status_dev;
+    /* Optional device int32 array of m * n entries, row-major with leading
+     * dimension n (or NULL).  Written with, per output entry, the number of
+     * k-blocks whose bin 0 came out zero while that block's contribution
+     * did not: the paper's cheap cancellation detection (Sec. "Detecting
+     * cancellation error", Sec. "Adding detection of cancellation errors").
+     * Nothing is corrected. */
+    int *flags_dev;
+    /* Optional (or NULL): three cudaEvent_t handles, passed as void*, that
+     * ddgemm() records on `stream` before the split (phase one), between the
+     * split and the ten products (phases two and three, one kernel) and
+     * after it, so that a caller can time each phase on the device. */
+    void **phase_events;
+} ddgemm_opts;
+
+/* Bytes of device workspace ddgemm() needs for this problem (0 when m, n or
+ * k is 0).  Holds the four cascaded pieces of A (4 m k doubles), the seven
+ * cascaded panels of B (7 k n doubles) and the per-block exponents of sigma
+ * and tau.  opts may be NULL (all defaults).  Returns 0 on invalid sizes. */
+size_t ddgemm_workspace_size(int m, int n, int k, const ddgemm_opts *opts);
+
+/* C := A B in FP64x2 by the ten-GEMM cascade (eq. Gemm10).
+ *   m, n, k      sizes of op(A) (m x k), op(B) (k x n) and C (m x n); >= 0.
+ *                k = 0 writes C = 0.
+ *   A_hi, A_lo   op(A) as described for opts->trans_a, leading dim lda.
+ *   B_hi, B_lo   op(B) likewise, leading dim ldb.
+ *   C_hi, C_lo   output, m x n, leading dim ldc >= n.  Must not overlap the
+ *                inputs or the workspace.
+ *   workspace    device buffer of at least ddgemm_workspace_size() bytes,
+ *                256-byte aligned; its contents on return are the cascaded
+ *                panels (unspecified layout).
+ *   opts         may be NULL.
+ * Returns DDGEMM_OK or an error code; on error nothing was enqueued. */
+int ddgemm(int m, int n, int k,
+           const double *A_hi, const double *A_lo, int lda,
+           const double *B_hi, const double *B_lo, int ldb,
+           double *C_hi, double *C_lo, int ldc,
+           void *workspace, size_t ws_bytes, void *stream,
+           const ddgemm_opts *opts);
+
+/* The split step alone for A (Appendix A; Sec. "Cascading matrices and
+ * GEMM"): per row i and k-block p, sigma = 2^e with e the frexp exponent of
+ * max |A_hi| over the block (e = 0 for an all-zero block); every entry is
+ * scaled by 2^-e and cascaded into four pieces.
+ *   slices  device, 4 x m x ld_slices doubles: slices[(s*m + i)*ld_slices + l]
+ *           = sigma_s * A_s(i, l) with sigma_0 = 1, sigma_1 = 2^-22,
+ *           sigma_2 = 2^-43, sigma_3 = 2^-64 (the left factor of eq. Gemm10).
+ *           ld_slices >= k.  Columns l >= k are not written.
+ *   exps    device int32, ceil(k/256) x m: exps[p*m + i] = e.
+ * trans_a as in ddgemm_opts.  status_dev optional (DDGEMM_DEV_NONFINITE). */
+int ddgemm_split_a(int m, int k, const double *A_hi, const double *A_lo, int lda,
+                   int trans_a, double *slices, int ld_slices, int *exps,
+                   unsigned int *status_dev, void *stream);
+
+/* The split step alone for B: per k-block p and column j, tau = 2^e as
+ * above; seven panels [B0 | s1 B1 | s2 B2 | s3 B3 || s2 B4 | s1 B5 | B6]
+ * (the right factor of eq. Gemm10), where B4, B5, B6 are the FP64 roundings
+ * of the exact tails B2 + B3 s3/s2, B1 + B2 s2/s1 + B3 s3/s1 and
+ * B0 + s1 B1 + s2 B2 + s3 B3.
+ *   slices  device, 7 x k x ld_slices doubles: slices[(s*k + l)*ld_slices + j].
+ *           ld_slices >= n.  Columns j >= n are not written.
+ *   exps    device int32, ceil(k/256) x n: exps[p*n + j] = e. */
+int ddgemm_split_b(int k, int n, const double *B_hi, const double *B_lo, int ldb,
+                   int trans_b, double *slices, int ld_slices, int *exps,
+                   unsigned int *status_dev, void *stream);
+
+/* The ten products of one k-block without the FP64x2 assembly (for
+ * checking that bins 0-2 are exact, Sec. "Cascading vectors and dot
+ * products").  Requires 0 < k <= 256.  bins: device, 4 x m x n doubles,
+ * bins[(b*m + i)*n + j] for b = bin 0, bin 1, bin 2, bin 3-6, each in the
+ * scaled units of eq. Gemm10 (sigma tau not applied).  Other arguments as
+ * for ddgemm. */
+int ddgemm_bins(int m, int n, int k,
+                const double *A_hi, const double *A_lo, int lda,
+                const double *B_hi, const double *B_lo, int ldb,
+                double *bins, void *workspace, size_t ws_bytes, void *stream,
+                const ddgemm_opts *opts);
+
+/* Measurement aid, not part of the method: enqueue a throughput kernel of
+ * the FP64 tensor path (mma.sync m8n8k4 f64, 4 CTAs of 256 threads per SM,
+ * eight independent accumulator chains per warp, `iters` rounds) on
+ * `stream` and return the number of FP64 flops it performs (-1 on error).
+ * The caller times it; flops / time is the measured ceiling of the ten
+ * products.  sink: device pointer to one double (never written in
+ * practice). */
+double ddgemm_probe_fp64(int iters, double *sink, void *stream);
+
+/* Static text for a return code. */
+const char *ddgemm_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDGEMM_H */

@@ -1,0 +1,127 @@
+"""Thin ctypes binding of libddgemm: the C ABI of include/ddgemm.h under the
+same names, with argument marshalling only (every step of the computation
+runs in the library's CUDA kernels).  Device memory and streams come from
+PyTorch; pointers and sizes go through unchanged.
+
+There is no fallback: if the library is missing or fails to load, every
+call raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+DDGEMM_OK = 0
+DDGEMM_EINVAL = 1
+DDGEMM_EWORKSPACE = 2
+DDGEMM_ECUDA = 3
+DDGEMM_EUNSUPPORTED = 4
+DDGEMM_DEV_NONFINITE = 0x1
+DDGEMM_DEV_TIMEOUT = 0x2
+DDGEMM_VARIANT_FP64 = 0
+
+
+class DdgemmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (code {code})")
+
+
+class ddgemm_opts(ctypes.Structure):
+    _fields_ = [("trans_a", ctypes.c_int), ("trans_b", ctypes.c_int),
+                ("variant", ctypes.c_int), ("status_dev", ctypes.c_void_p),
+                ("flags_dev", ctypes.c_void_p), ("phase_events", ctypes.c_void_p)]
+
+
+_LIB = None
+
+_I, _Z, _P = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
+_SIGS = {
+    "ddgemm_workspace_size": (_Z, [_I, _I, _I, _P]),
+    "ddgemm": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _Z, _P, _P]),
+    "ddgemm_split_a": (_I, [_I, _I, _P, _P, _I, _I, _P, _I, _P, _P, _P]),
+    "ddgemm_split_b": (_I, [_I, _I, _P, _P, _I, _I, _P, _I, _P, _P, _P]),
+    "ddgemm_bins": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _Z, _P, _P]),
+    "ddgemm_status_string": (ctypes.c_char_p, [_I]),
+    "ddgemm_probe_fp64": (ctypes.c_double, [_I, _P, _P]),
+}
+
+
+def load(build_if_missing: bool = True):
+    """Load libddgemm (building it first if allowed and needed)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.lib_path()
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise RuntimeError(f"libddgemm is not built ({path}); run "
+                                   "paper_2303_04353_gb300.build.build()")
+            path = _build.build()
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def lib_file() -> str:
+    return _build.lib_path()
+
+
+def status_string(code: int) -> str:
+    return load().ddgemm_status_string(code).decode()
+
+
+def _check(code: int, where: str) -> None:
+    if code != DDGEMM_OK:
+        raise DdgemmError(code, where)
+
+
+def make_opts(trans_a=False, trans_b=False, variant=DDGEMM_VARIANT_FP64, status_dev=0,
+              flags_dev=0, phase_events=None) -> ddgemm_opts:
+    """phase_events: None or a ctypes array of three cudaEvent_t handles
+    (the caller keeps it alive until the call returns)."""
+    ev = ctypes.cast(phase_events, ctypes.c_void_p) if phase_events is not None else None
+    return ddgemm_opts(int(trans_a), int(trans_b), int(variant), status_dev or None,
+                       flags_dev or None, ev)
+
+
+def ddgemm_workspace_size(m: int, n: int, k: int, opts: ddgemm_opts | None = None) -> int:
+    return load().ddgemm_workspace_size(m, n, k, ctypes.byref(opts) if opts else None)
+
+
+def ddgemm(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo, ldc, workspace, ws_bytes,
+           stream, opts: ddgemm_opts | None = None) -> None:
+    """C := A B (raw pointers; see include/ddgemm.h).  Raises on error."""
+    _check(load().ddgemm(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo, ldc, workspace,
+                         ws_bytes, stream, ctypes.byref(opts) if opts else None), "ddgemm")
+
+
+def ddgemm_split_a(m, k, a_hi, a_lo, lda, trans_a, slices, ld_slices, exps, status_dev,
+                   stream) -> None:
+    _check(load().ddgemm_split_a(m, k, a_hi, a_lo, lda, int(trans_a), slices, ld_slices, exps,
+                                 status_dev or None, stream), "ddgemm_split_a")
+
+
+def ddgemm_split_b(k, n, b_hi, b_lo, ldb, trans_b, slices, ld_slices, exps, status_dev,
+                   stream) -> None:
+    _check(load().ddgemm_split_b(k, n, b_hi, b_lo, ldb, int(trans_b), slices, ld_slices, exps,
+                                 status_dev or None, stream), "ddgemm_split_b")
+
+
+def ddgemm_bins(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, bins, workspace, ws_bytes, stream,
+                opts: ddgemm_opts | None = None) -> None:
+    _check(load().ddgemm_bins(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, bins, workspace,
+                              ws_bytes, stream, ctypes.byref(opts) if opts else None),
+           "ddgemm_bins")
+
+
+def ddgemm_probe_fp64(iters: int, sink: int, stream: int) -> float:
+    """Enqueue the FP64 tensor-path throughput probe; returns its flop count."""
+    flops = load().ddgemm_probe_fp64(iters, sink, stream)
+    if flops < 0:
+        raise DdgemmError(DDGEMM_ECUDA, "ddgemm_probe_fp64")
+    return flops

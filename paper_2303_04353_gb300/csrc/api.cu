@@ -1,0 +1,188 @@
+// The C ABI of libddgemm (declared in include/ddgemm.h): argument checks,
+// workspace carving and the launches of the split and cascade kernels.
+// Nothing here allocates device memory.
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/ddgemm.h"
+#include "ddgemm_internal.h"
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Workspace carve: A pieces, B panels, exponents of A, exponents of B.
+struct Layout {
+    long long lda_s, ldb_s;
+    size_t off_a, off_b, off_ea, off_eb, total;
+};
+
+Layout layout_for(int m, int n, int k) {
+    Layout L;
+    const long long kb = (k + ddg::KC - 1) / ddg::KC;
+    L.lda_s = (long long)round_up((size_t)k, 8);
+    L.ldb_s = (long long)round_up((size_t)n, 8);
+    L.off_a = 0;
+    L.off_b = L.off_a + round_up((size_t)4 * m * L.lda_s * sizeof(double), ALIGN);
+    L.off_ea = L.off_b + round_up((size_t)7 * k * L.ldb_s * sizeof(double), ALIGN);
+    L.off_eb = L.off_ea + round_up((size_t)kb * m * sizeof(int), ALIGN);
+    L.total = L.off_eb + round_up((size_t)kb * n * sizeof(int), ALIGN);
+    return L;
+}
+
+struct Parsed {
+    int trans_a = 0, trans_b = 0, variant = DDGEMM_VARIANT_FP64;
+    unsigned int *status = nullptr;
+    int *flags = nullptr;
+    void **events = nullptr;
+};
+
+bool parse(const ddgemm_opts *o, Parsed &p) {
+    if (o) {
+        p.trans_a = o->trans_a;
+        p.trans_b = o->trans_b;
+        p.variant = o->variant;
+        p.status = o->status_dev;
+        p.flags = o->flags_dev;
+        p.events = o->phase_events;
+    }
+    return (p.trans_a == 0 || p.trans_a == 1) && (p.trans_b == 0 || p.trans_b == 1);
+}
+
+bool dims_ok(int m, int n, int k) {
+    if (m < 0 || n < 0 || k < 0) return false;
+    // tensor-map extents and grid limits
+    return (long long)m <= (1LL << 31) - 1 && (long long)n <= (1LL << 31) - 1;
+}
+
+int check_operands(int m, int n, int k, const void *ah, const void *al, int lda, const void *bh,
+                   const void *bl, int ldb, const Parsed &p) {
+    if (m > 0 && k > 0) {
+        if (!ah || !al) return DDGEMM_EINVAL;
+        if (lda < (p.trans_a ? m : k)) return DDGEMM_EINVAL;
+    }
+    if (n > 0 && k > 0) {
+        if (!bh || !bl) return DDGEMM_EINVAL;
+        if (ldb < (p.trans_b ? k : n)) return DDGEMM_EINVAL;
+    }
+    return DDGEMM_OK;
+}
+
+int run(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
+        const double *B_hi, const double *B_lo, int ldb, double *C_hi, double *C_lo, int ldc,
+        double *bins, void *workspace, size_t ws_bytes, cudaStream_t stream, const Parsed &p) {
+    const Layout L = layout_for(m, n, k);
+    if (!workspace || ws_bytes < L.total || (uintptr_t)workspace % ALIGN) return DDGEMM_EWORKSPACE;
+    char *ws = static_cast<char *>(workspace);
+    double *a_s = reinterpret_cast<double *>(ws + L.off_a);
+    double *b_s = reinterpret_cast<double *>(ws + L.off_b);
+    int *e_a = reinterpret_cast<int *>(ws + L.off_ea);
+    int *e_b = reinterpret_cast<int *>(ws + L.off_eb);
+    auto mark = [&](int i) {
+        return !p.events || cudaEventRecord(static_cast<cudaEvent_t>(p.events[i]), stream) ==
+                                cudaSuccess;
+    };
+    if (!mark(0)) return DDGEMM_ECUDA;
+    // A: a row of op(A) is a vector; it runs along memory unless trans_a.
+    cudaError_t e = ddg::launch_split(4, m, k, A_hi, A_lo, lda, !p.trans_a, a_s, L.lda_s,
+                                      ddg::PanelLayout::VEC_MAJOR, e_a, p.status, stream);
+    if (e != cudaSuccess) return DDGEMM_ECUDA;
+    // B: a column of op(B) is a vector; it runs along memory only if trans_b.
+    e = ddg::launch_split(7, n, k, B_hi, B_lo, ldb, p.trans_b != 0, b_s, L.ldb_s,
+                          ddg::PanelLayout::K_MAJOR, e_b, p.status, stream);
+    if (e != cudaSuccess || !mark(1)) return DDGEMM_ECUDA;
+    ddg::CascadeArgs ca{m, n, k, a_s, L.lda_s, b_s, L.ldb_s, e_a, e_b, C_hi, C_lo,
+                        (long long)ldc, p.flags, p.status, bins};
+    e = ddg::launch_cascade_fp64(ca, stream);
+    return e == cudaSuccess && mark(2) ? DDGEMM_OK : DDGEMM_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ddgemm_workspace_size(int m, int n, int k, const ddgemm_opts *opts) {
+    Parsed p;
+    if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
+    if (m == 0 || n == 0 || k == 0) return 0;
+    return layout_for(m, n, k).total;
+}
+
+int ddgemm(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
+           const double *B_hi, const double *B_lo, int ldb, double *C_hi, double *C_lo, int ldc,
+           void *workspace, size_t ws_bytes, void *stream, const ddgemm_opts *opts) {
+    Parsed p;
+    if (!parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
+    if (p.variant != DDGEMM_VARIANT_FP64) return DDGEMM_EUNSUPPORTED;
+    if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;
+    if (m == 0 || n == 0) return DDGEMM_OK;
+    if (!C_hi || !C_lo || ldc < n) return DDGEMM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (k == 0) {
+        // C := A B with k = 0 is the zero matrix
+        if (cudaMemset2DAsync(C_hi, (size_t)ldc * 8, 0, (size_t)n * 8, m, s) != cudaSuccess ||
+            cudaMemset2DAsync(C_lo, (size_t)ldc * 8, 0, (size_t)n * 8, m, s) != cudaSuccess ||
+            (p.flags && cudaMemsetAsync(p.flags, 0, (size_t)m * n * sizeof(int), s) != cudaSuccess))
+            return DDGEMM_ECUDA;
+        return DDGEMM_OK;
+    }
+    return run(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, C_hi, C_lo, ldc, nullptr, workspace,
+               ws_bytes, s, p);
+}
+
+int ddgemm_bins(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
+                const double *B_hi, const double *B_lo, int ldb, double *bins, void *workspace,
+                size_t ws_bytes, void *stream, const ddgemm_opts *opts) {
+    Parsed p;
+    if (!parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
+    if (k <= 0 || k > ddg::KC || m <= 0 || n <= 0 || !bins) return DDGEMM_EINVAL;
+    if (p.variant != DDGEMM_VARIANT_FP64) return DDGEMM_EUNSUPPORTED;
+    if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;
+    p.flags = nullptr;
+    return run(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, nullptr, nullptr, n, bins, workspace,
+               ws_bytes, static_cast<cudaStream_t>(stream), p);
+}
+
+int ddgemm_split_a(int m, int k, const double *A_hi, const double *A_lo, int lda, int trans_a,
+                   double *slices, int ld_slices, int *exps, unsigned int *status_dev,
+                   void *stream) {
+    if (m < 0 || k < 0 || (trans_a != 0 && trans_a != 1)) return DDGEMM_EINVAL;
+    if (m == 0 || k == 0) return DDGEMM_OK;
+    if (!A_hi || !A_lo || !slices || !exps || lda < (trans_a ? m : k) || ld_slices < k)
+        return DDGEMM_EINVAL;
+    const cudaError_t e =
+        ddg::launch_split(4, m, k, A_hi, A_lo, lda, !trans_a, slices, ld_slices,
+                          ddg::PanelLayout::VEC_MAJOR, exps, status_dev,
+                          static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
+}
+
+int ddgemm_split_b(int k, int n, const double *B_hi, const double *B_lo, int ldb, int trans_b,
+                   double *slices, int ld_slices, int *exps, unsigned int *status_dev,
+                   void *stream) {
+    if (n < 0 || k < 0 || (trans_b != 0 && trans_b != 1)) return DDGEMM_EINVAL;
+    if (n == 0 || k == 0) return DDGEMM_OK;
+    if (!B_hi || !B_lo || !slices || !exps || ldb < (trans_b ? k : n) || ld_slices < n)
+        return DDGEMM_EINVAL;
+    const cudaError_t e =
+        ddg::launch_split(7, n, k, B_hi, B_lo, ldb, trans_b != 0, slices, ld_slices,
+                          ddg::PanelLayout::K_MAJOR, exps, status_dev,
+                          static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
+}
+
+const char *ddgemm_status_string(int code) {
+    switch (code) {
+        case DDGEMM_OK: return "ok";
+        case DDGEMM_EINVAL: return "invalid argument";
+        case DDGEMM_EWORKSPACE: return "workspace missing, misaligned or too small";
+        case DDGEMM_ECUDA: return "CUDA error";
+        case DDGEMM_EUNSUPPORTED: return "unsupported option";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

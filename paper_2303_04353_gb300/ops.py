@@ -1,0 +1,123 @@
+"""PyTorch-facing wrappers of the C ABI.  PyTorch supplies device memory
+(outputs, workspace) and the stream; every step of the computation runs in
+libddgemm's kernels.  Inputs must be float64 CUDA tensors with unit stride
+in their last dimension; a (hi, lo) pair must share shape and strides."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+
+def _check_pair(hi: torch.Tensor, lo: torch.Tensor, name: str) -> int:
+    if hi.dtype != torch.float64 or lo.dtype != torch.float64:
+        raise TypeError(f"{name}: hi and lo must be float64")
+    if not (hi.is_cuda and lo.is_cuda):
+        raise ValueError(f"{name}: hi and lo must be CUDA tensors (there is no CPU path)")
+    if hi.dim() != 2 or hi.shape != lo.shape or hi.stride() != lo.stride():
+        raise ValueError(f"{name}: hi and lo must be 2-D with equal shape and strides")
+    if hi.shape[1] > 1 and hi.stride(1) != 1:
+        raise ValueError(f"{name}: the last dimension must be contiguous")
+    return max(hi.stride(0), hi.shape[1], 1)
+
+
+def current_stream_ptr(stream: torch.cuda.Stream | None = None) -> int:
+    return (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+
+
+def workspace_bytes(m: int, n: int, k: int) -> int:
+    return _lib.ddgemm_workspace_size(m, n, k, None)
+
+
+def alloc_workspace(m: int, n: int, k: int, device=None) -> torch.Tensor:
+    nbytes = workspace_bytes(m, n, k)
+    # torch's caching allocator hands out 512-byte aligned blocks
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device or "cuda")
+
+
+def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, workspace=None,
+           status=None, flags=None, stream=None, phase_events=None):
+    """C := op(A) op(B) in FP64x2 by the ten-GEMM cascade.  Returns (c_hi, c_lo).
+
+    trans_a: A is stored k x m and op(A) = A^T (likewise trans_b: B stored n x k).
+    out: optional (c_hi, c_lo) float64 tensors, m x n, unit last stride.
+    status: optional int32 CUDA tensor of one element; DDGEMM_DEV_* bits are OR-ed in.
+    flags: optional int32 CUDA tensor (m x n, contiguous) for cancellation counts.
+    phase_events: optional three recorded torch.cuda.Event objects; the library
+    re-records them around the split and the cascade kernel on the stream."""
+    lda = _check_pair(a_hi, a_lo, "A")
+    ldb = _check_pair(b_hi, b_lo, "B")
+    m, k = (a_hi.shape[1], a_hi.shape[0]) if trans_a else tuple(a_hi.shape)
+    kb, n = (b_hi.shape[1], b_hi.shape[0]) if trans_b else tuple(b_hi.shape)
+    if k != kb:
+        raise ValueError(f"inner dimensions differ: {k} vs {kb}")
+    dev = a_hi.device
+    if out is None:
+        c_hi = torch.empty((m, n), dtype=torch.float64, device=dev)
+        c_lo = torch.empty((m, n), dtype=torch.float64, device=dev)
+    else:
+        c_hi, c_lo = out
+        if tuple(c_hi.shape) != (m, n):
+            raise ValueError("out has the wrong shape")
+    ldc = _check_pair(c_hi, c_lo, "C")
+    if workspace is None:
+        workspace = alloc_workspace(m, n, k, dev)
+    if status is not None and (status.dtype != torch.int32 or not status.is_cuda):
+        raise TypeError("status must be an int32 CUDA tensor")
+    if flags is not None and (flags.dtype != torch.int32 or not flags.is_contiguous()
+                              or flags.numel() < m * n):
+        raise TypeError("flags must be a contiguous int32 CUDA tensor with m*n entries")
+    evs = None
+    if phase_events is not None:
+        if len(phase_events) != 3 or not all(e.cuda_event for e in phase_events):
+            raise ValueError("phase_events: three torch.cuda.Event, each recorded once")
+        evs = (ctypes.c_void_p * 3)(*[e.cuda_event for e in phase_events])
+    opts = _lib.make_opts(trans_a, trans_b, _lib.DDGEMM_VARIANT_FP64,
+                          status.data_ptr() if status is not None else 0,
+                          flags.data_ptr() if flags is not None else 0, evs)
+    _lib.ddgemm(m, n, k, a_hi.data_ptr(), a_lo.data_ptr(), lda, b_hi.data_ptr(),
+                b_lo.data_ptr(), ldb, c_hi.data_ptr(), c_lo.data_ptr(), ldc,
+                workspace.data_ptr(), workspace.numel(), current_stream_ptr(stream), opts)
+    return c_hi, c_lo
+
+
+def split_a(a_hi, a_lo, *, trans_a=False, stream=None, status=None):
+    """The split step for A: returns (slices [4, m, k], exps [ceil(k/256), m])."""
+    lda = _check_pair(a_hi, a_lo, "A")
+    m, k = (a_hi.shape[1], a_hi.shape[0]) if trans_a else tuple(a_hi.shape)
+    slices = torch.zeros((4, m, k), dtype=torch.float64, device=a_hi.device)
+    exps = torch.zeros(((k + 255) // 256, m), dtype=torch.int32, device=a_hi.device)
+    _lib.ddgemm_split_a(m, k, a_hi.data_ptr(), a_lo.data_ptr(), lda, trans_a,
+                        slices.data_ptr(), max(k, 1), exps.data_ptr(),
+                        status.data_ptr() if status is not None else 0,
+                        current_stream_ptr(stream))
+    return slices, exps
+
+
+def split_b(b_hi, b_lo, *, trans_b=False, stream=None, status=None):
+    """The split step for B: returns (panels [7, k, n], exps [ceil(k/256), n])."""
+    ldb = _check_pair(b_hi, b_lo, "B")
+    k, n = (b_hi.shape[1], b_hi.shape[0]) if trans_b else tuple(b_hi.shape)
+    slices = torch.zeros((7, k, n), dtype=torch.float64, device=b_hi.device)
+    exps = torch.zeros(((k + 255) // 256, n), dtype=torch.int32, device=b_hi.device)
+    _lib.ddgemm_split_b(k, n, b_hi.data_ptr(), b_lo.data_ptr(), ldb, trans_b,
+                        slices.data_ptr(), max(n, 1), exps.data_ptr(),
+                        status.data_ptr() if status is not None else 0,
+                        current_stream_ptr(stream))
+    return slices, exps
+
+
+def bins(a_hi, a_lo, b_hi, b_lo, *, stream=None):
+    """The four bins of the single k-block (k <= 256), shape [4, m, n]."""
+    lda = _check_pair(a_hi, a_lo, "A")
+    ldb = _check_pair(b_hi, b_lo, "B")
+    m, k = a_hi.shape
+    n = b_hi.shape[1]
+    out = torch.empty((4, m, n), dtype=torch.float64, device=a_hi.device)
+    ws = alloc_workspace(m, n, k, a_hi.device)
+    _lib.ddgemm_bins(m, n, k, a_hi.data_ptr(), a_lo.data_ptr(), lda, b_hi.data_ptr(),
+                     b_lo.data_ptr(), ldb, out.data_ptr(), ws.data_ptr(), ws.numel(),
+                     current_stream_ptr(stream), None)
+    return out

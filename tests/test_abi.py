@@ -1,0 +1,91 @@
+"""The C ABI without a GPU: the library builds and loads, exports every
+function include/ddgemm.h declares, and its host-side checks answer before
+any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2303_04353_gb300 import _lib
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "ddgemm.h")
+FAKE = 0x10000  # never dereferenced: every call below returns before a CUDA call
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ddgemm\w*)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("ddgemm", "ddgemm_workspace_size", "ddgemm_split_a", "ddgemm_split_b",
+                 "ddgemm_bins", "ddgemm_status_string"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    raw = ctypes.CDLL(_lib.lib_file())
+    for name in declared_functions():
+        assert hasattr(raw, name), name
+    assert set(_lib._SIGS) >= set(declared_functions())
+    assert lib is _lib.load()
+
+
+def test_status_strings():
+    assert _lib.status_string(0) == "ok"
+    assert "workspace" in _lib.status_string(2)
+    assert _lib.status_string(99) == "unknown status"
+
+
+def test_workspace_size():
+    ws = _lib.ddgemm_workspace_size
+    assert ws(0, 5, 5) == 0 and ws(5, 0, 5) == 0 and ws(5, 5, 0) == 0
+    assert ws(-1, 5, 5) == 0
+    m, n, k = 4096, 4096, 4096
+    # 4 m k + 7 k n doubles of cascaded pieces plus the block exponents
+    assert ws(m, n, k) >= (4 * m * k + 7 * k * n) * 8
+    assert ws(m, n, k) < (4 * m * k + 7 * k * n) * 8 * 1.01
+    assert ws(3, 5, 7) % 256 == 0
+
+
+def call(m, n, k, lda, ldb, ldc, ws=FAKE, ws_bytes=1 << 40, opts=None):
+    lib = _lib.load()
+    return lib.ddgemm(m, n, k, FAKE, FAKE, lda, FAKE, FAKE, ldb, FAKE, FAKE, ldc, ws, ws_bytes,
+                      None, ctypes.byref(opts) if opts else None)
+
+
+def test_host_checks():
+    assert call(-1, 4, 4, 4, 4, 4) == _lib.DDGEMM_EINVAL
+    assert call(4, 4, 4, 3, 4, 4) == _lib.DDGEMM_EINVAL          # lda < k
+    assert call(4, 4, 4, 4, 3, 4) == _lib.DDGEMM_EINVAL          # ldb < n
+    assert call(4, 4, 4, 4, 4, 3) == _lib.DDGEMM_EINVAL          # ldc < n
+    assert call(4, 4, 4, 4, 4, 4, ws=0) == _lib.DDGEMM_EWORKSPACE
+    assert call(4, 4, 4, 4, 4, 4, ws=FAKE + 8) == _lib.DDGEMM_EWORKSPACE  # misaligned
+    assert call(4, 4, 4, 4, 4, 4, ws_bytes=16) == _lib.DDGEMM_EWORKSPACE
+    assert call(0, 4, 4, 4, 4, 4) == _lib.DDGEMM_OK              # empty: nothing to do
+    assert call(4, 4, 4, 4, 4, 4, opts=_lib.make_opts(variant=7)) == _lib.DDGEMM_EUNSUPPORTED
+    bad = _lib.ddgemm_opts(2, 0, 0, None, None)
+    assert call(4, 4, 4, 4, 4, 4, opts=bad) == _lib.DDGEMM_EINVAL
+    # trans_a: A stored k x m needs lda >= m
+    assert call(8, 4, 2, 2, 4, 4, opts=_lib.make_opts(trans_a=True)) == _lib.DDGEMM_EINVAL
+
+
+def test_bins_and_split_host_checks():
+    lib = _lib.load()
+    assert lib.ddgemm_bins(4, 4, 300, FAKE, FAKE, 300, FAKE, FAKE, 4, FAKE, FAKE, 1 << 40,
+                           None, None) == _lib.DDGEMM_EINVAL  # one k-block at most
+    assert lib.ddgemm_split_a(4, 8, FAKE, FAKE, 7, 0, FAKE, 8, FAKE, None, None) == _lib.DDGEMM_EINVAL
+    assert lib.ddgemm_split_b(8, 4, FAKE, FAKE, 4, 0, FAKE, 3, FAKE, None, None) == _lib.DDGEMM_EINVAL
+    assert lib.ddgemm_split_a(0, 8, None, None, 8, 0, None, 8, None, None, None) == _lib.DDGEMM_OK
+
+
+def test_ops_refuse_cpu_tensors():
+    torch = pytest.importorskip("torch")
+    from paper_2303_04353_gb300 import ops
+    a = torch.zeros(2, 2, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA"):
+        ops.ddgemm(a, a, a, a)

@@ -1,0 +1,250 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+* The split (scales, four A pieces, seven B panels) is bit-identical to the
+  oracle's restatement of Appendix A.
+* Bins 0-2 of one k-block are bit-identical to the oracle's (they are exact
+  integers in their units); bin 3-6 agrees up to FP64 summation order.
+* C agrees with the double-double oracle within |C - C_dd| <= 1e-28 (|A||B|)
+  componentwise, and with the cascade restatement within the rounding that
+  the order of bin 3-6's sum allows.
+* Edge cases: k = 0, empty m or n, ragged tiles, one element, transposed
+  operands, integer matrices (exact), identity, the paper's worked example,
+  non-finite inputs, cancellation flags, and the full 4096^3 and
+  8192 x 1024 x 4096 sizes on sampled entries."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import cascade as cs  # noqa: E402
+from oracle import dd  # noqa: E402
+from tests import exact  # noqa: E402
+from tests.bounds import paper_bound  # noqa: E402
+from workloads import gemm_inputs, integer_inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+CONTRACT = 1e-28
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ops():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_04353_gb300 import ops as _ops
+    return _ops
+
+
+def dev(*arrays):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrays]
+
+
+def host(*tensors):
+    torch.cuda.synchronize()
+    return [t.cpu().numpy() for t in tensors]
+
+
+def oracle_split_a(a_hi, a_lo):
+    e = cs.block_exponents_rows(a_hi)
+    kb = e.shape[1]
+    parts = [cs.cascade_a(a_hi, a_lo, e, p) for p in range(kb)]
+    return np.stack([np.concatenate([pp[s] for pp in parts], axis=1) for s in range(4)]), e.T
+
+
+def oracle_split_b(b_hi, b_lo):
+    e = cs.block_exponents_cols(b_hi)
+    kb = e.shape[0]
+    parts = [cs.cascade_b(b_hi, b_lo, e, p) for p in range(kb)]
+    return np.stack([np.concatenate([pp[s] for pp in parts], axis=0) for s in range(7)]), e
+
+
+@pytest.mark.parametrize("m,k", [(37, 300), (64, 256), (5, 1), (130, 520), (1, 1000)])
+@pytest.mark.parametrize("kind", ["uniform", "wide"])
+@pytest.mark.parametrize("trans", [False, True])
+def test_split_a_bitwise(ops, m, k, kind, trans):
+    a_hi, a_lo, _, _ = gemm_inputs(m, 1, k, kind=kind, seed=m + k)
+    want_s, want_e = oracle_split_a(a_hi, a_lo)
+    src = (a_hi.T, a_lo.T) if trans else (a_hi, a_lo)
+    th, tl = dev(*src)
+    s, e = ops.split_a(th, tl, trans_a=trans)
+    s, e = host(s, e)
+    assert np.array_equal(e, want_e)
+    assert np.array_equal(s, want_s)
+
+
+@pytest.mark.parametrize("k,n", [(300, 37), (256, 64), (1, 5), (520, 130), (1000, 1)])
+@pytest.mark.parametrize("kind", ["uniform", "wide"])
+@pytest.mark.parametrize("trans", [False, True])
+def test_split_b_bitwise(ops, k, n, kind, trans):
+    _, _, b_hi, b_lo = gemm_inputs(1, n, k, kind=kind, seed=n + 3 * k)
+    want_s, want_e = oracle_split_b(b_hi, b_lo)
+    src = (b_hi.T, b_lo.T) if trans else (b_hi, b_lo)
+    th, tl = dev(*src)
+    s, e = ops.split_b(th, tl, trans_b=trans)
+    s, e = host(s, e)
+    assert np.array_equal(e, want_e)
+    assert np.array_equal(s, want_s)
+
+
+@pytest.mark.parametrize("m,n,k", [(64, 64, 256), (70, 33, 200), (1, 1, 1), (130, 65, 255)])
+@pytest.mark.parametrize("kind", ["uniform", "wide"])
+def test_bins_bitwise(ops, m, n, k, kind):
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind=kind, seed=m * n + k)
+    _, _, bins, _ = cs.cascade_ddgemm(a_hi, a_lo, b_hi, b_lo, return_bins=True)
+    w0, w1, w2, w36 = bins[0]
+    (got,) = host(ops.bins(*dev(a_hi, a_lo, b_hi, b_lo)))
+    assert np.array_equal(got[0], w0)
+    assert np.array_equal(got[1], w1)
+    assert np.array_equal(got[2], w2)
+    # bin 3-6: |bin36| <= 4 k 2^-64 in the scaled units; two summation
+    # orders of 4k terms differ by at most ~2 (4k) 2^-53 of that
+    tol = 2 * (4 * k) * 2.0 ** -53 * (4 * k * 2.0 ** -64)
+    assert np.max(np.abs(got[3] - w36)) <= tol
+
+
+def cascade_tolerance(a_hi, b_hi, c_ref):
+    """|C_gpu - C_cascade_oracle|: the two differ only in the FP64 summation
+    order of bin 3-6 (<= 2 (4 k_p) 2^-53 |bin36| <= 2^-94 sigma tau per
+    block) and the FP64x2 roundings that follow (a few 2^-106 |C|)."""
+    e_a = cs.block_exponents_rows(a_hi)
+    e_b = cs.block_exponents_cols(b_hi)
+    tol = np.zeros((a_hi.shape[0], b_hi.shape[1]))
+    for p in range(e_a.shape[1]):
+        tol += np.ldexp(2.0 ** -92, e_a[:, p][:, None] + e_b[p, :][None, :])
+    return tol + 8 * e_a.shape[1] * 2.0 ** -106 * np.abs(c_ref)
+
+
+def check_against_oracles(ops, a_hi, a_lo, b_hi, b_lo, trans_a=False, trans_b=False,
+                          contract=True):
+    src_a = (a_hi.T, a_lo.T) if trans_a else (a_hi, a_lo)
+    src_b = (b_hi.T, b_lo.T) if trans_b else (b_hi, b_lo)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    c_hi, c_lo = ops.ddgemm(*dev(*src_a), *dev(*src_b), trans_a=trans_a, trans_b=trans_b,
+                            status=status)
+    c_hi, c_lo, st = host(c_hi, c_lo, status)
+    assert st[0] == 0
+    assert exact.dd_is_normalised(c_hi, c_lo)
+    o_hi, o_lo = dd.ddgemm(a_hi, a_lo, b_hi, b_lo)
+    absab = exact.abs_product(a_hi, b_hi)
+    diff = np.abs((c_hi - o_hi) + (c_lo - o_lo))
+    # the paper's bound always, plus the double-double oracle's own error
+    k = a_hi.shape[1]
+    assert np.all(diff <= paper_bound(a_hi, b_hi) + 4 * (k + 2) * 2.0 ** -106 * absab)
+    if contract:
+        assert np.all(diff <= CONTRACT * absab), float(np.max(diff / np.maximum(absab, 1e-300)))
+    s_hi, s_lo = cs.cascade_ddgemm(a_hi, a_lo, b_hi, b_lo)
+    dcs = np.abs((c_hi - s_hi) + (c_lo - s_lo))
+    assert np.all(dcs <= cascade_tolerance(a_hi, b_hi, s_hi))
+    return c_hi, c_lo
+
+
+@pytest.mark.parametrize("m,n,k", [(256, 256, 256), (100, 70, 300), (65, 129, 513),
+                                   (1, 1, 1), (3, 200, 17), (128, 64, 1024)])
+@pytest.mark.parametrize("kind", ["uniform", "wide"])
+def test_ddgemm_parity(ops, m, n, k, kind):
+    """The 1e-28 |A||B| contract is stated for the named workloads (uniform
+    entries; wide entries at 4096^3): it is not a theorem of the method.  A
+    small wide-range case can hold an entry whose ||x|| ||y|| exceeds |x|^T |y|
+    by 1e8, where eq. (cascerr) allows more (the CPU restatement misses 1e-28
+    there too).  Those are judged by the paper's bound and by the cascade
+    restatement."""
+    a = gemm_inputs(m, n, k, kind=kind, seed=0 if (m, n, k) == (256, 256, 256) else m + n + k)
+    check_against_oracles(ops, *a, contract=kind == "uniform")
+
+
+@pytest.mark.parametrize("ta,tb", [(True, False), (False, True), (True, True)])
+def test_ddgemm_transposed(ops, ta, tb):
+    a = gemm_inputs(70, 90, 300, kind="wide", seed=5)
+    check_against_oracles(ops, *a, trans_a=ta, trans_b=tb, contract=False)
+    a = gemm_inputs(70, 90, 300, kind="uniform", seed=6)
+    check_against_oracles(ops, *a, trans_a=ta, trans_b=tb)
+
+
+def test_integer_matrices_exact(ops):
+    a_hi, a_lo, b_hi, b_lo = integer_inputs(128, 96, 1000, bits=10, seed=1)
+    c_hi, c_lo = host(*ops.ddgemm(*dev(a_hi, a_lo, b_hi, b_lo)))
+    ref = a_hi.astype(np.int64) @ b_hi.astype(np.int64)
+    assert np.array_equal(c_hi, ref.astype(np.float64)) and np.all(c_lo == 0)
+
+
+def test_identity(ops):
+    _, _, b_hi, b_lo = gemm_inputs(1, 50, 300, seed=12)
+    eye = np.eye(300)
+    c_hi, c_lo = host(*ops.ddgemm(*dev(eye, np.zeros_like(eye), b_hi, b_lo)))
+    for x, y, u, v in zip(c_hi.ravel(), c_lo.ravel(), b_hi.ravel(), b_lo.ravel()):
+        assert abs(exact.dd_fixed(x, y) - exact.dd_fixed(u, v)) <= exact.fixed(abs(u)) >> 104
+
+
+def test_worked_example(ops):
+    g = {}
+    for line in open(os.path.join(GOLDEN, "worked_example.txt")):
+        if line.strip() and not line.startswith("#"):
+            key, *vals = line.split()
+            g[key] = np.array([float.fromhex(v) for v in vals])
+    c_hi, c_lo = host(*ops.ddgemm(*dev(g["x_hi"][None, :], g["x_lo"][None, :],
+                                       g["y_hi"][:, None], g["y_lo"][:, None])))
+    assert c_hi[0, 0] == g["cascade_hi"][0] and c_lo[0, 0] == g["cascade_lo"][0]
+
+
+def test_k_zero_and_empty(ops):
+    a = torch.zeros((5, 0), dtype=torch.float64, device="cuda")
+    b = torch.zeros((0, 7), dtype=torch.float64, device="cuda")
+    out = (torch.full((5, 7), 3.0, dtype=torch.float64, device="cuda"),
+           torch.full((5, 7), 3.0, dtype=torch.float64, device="cuda"))
+    c_hi, c_lo = host(*ops.ddgemm(a, a, b, b, out=out))
+    assert not c_hi.any() and not c_lo.any()
+    e = torch.zeros((0, 4), dtype=torch.float64, device="cuda")
+    bb = torch.ones((4, 3), dtype=torch.float64, device="cuda")
+    c_hi, _ = ops.ddgemm(e, e, bb, bb * 0)
+    assert tuple(c_hi.shape) == (0, 3)
+
+
+def test_nonfinite_sets_status(ops):
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(20, 20, 40, seed=3)
+    a_hi[3, 5] = np.inf
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ops.ddgemm(*dev(a_hi, a_lo, b_hi, b_lo), status=status)
+    (st,) = host(status)
+    assert st[0] & 0x1
+
+
+def test_cancellation_flags(ops):
+    """Sec. "Detecting cancellation error": bin 0 of x^T y with x = (1, 1 + 2^-40),
+    y = (1, -1) cancels to zero although x^T y = -2^-40 does not."""
+    a_hi = np.array([[1.0, 1.0 + 2.0 ** -40], [1.0, 0.5]])
+    b_hi = np.array([[1.0], [-1.0]])
+    flags = torch.full((2, 1), -5, dtype=torch.int32, device="cuda")
+    c_hi, c_lo = ops.ddgemm(*dev(a_hi, np.zeros_like(a_hi), b_hi, np.zeros_like(b_hi)),
+                            flags=flags)
+    c_hi, f = host(c_hi, flags)
+    assert c_hi[0, 0] == -(2.0 ** -40) and c_hi[1, 0] == 0.5
+    assert f[0, 0] == 1 and f[1, 0] == 0
+    _, _, bins, _ = cs.cascade_ddgemm(a_hi, np.zeros_like(a_hi), b_hi, np.zeros_like(b_hi),
+                                      return_bins=True)
+    assert bins[0][0][0, 0] == 0.0 and bins[0][0][1, 0] != 0.0
+
+
+@pytest.mark.parametrize("m,n,k", [(4096, 4096, 4096), (8192, 1024, 4096)])
+def test_full_size_sampled(ops, m, n, k):
+    """The full workloads (log-uniform magnitudes over 2^-20..2^20) in the
+    launch configuration the benchmark times; 96 sampled entries against
+    the double-double oracle, and exact rationals on 8 of them."""
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind="wide", seed=0)
+    c_hi, c_lo = ops.ddgemm(*dev(a_hi, a_lo, b_hi, b_lo))
+    c_hi, c_lo = host(c_hi, c_lo)
+    rng = np.random.default_rng(42)
+    rows = np.concatenate([rng.integers(0, m, 94), [0, m - 1]])
+    cols = np.concatenate([rng.integers(0, n, 94), [n - 1, 0]])
+    o_hi, o_lo = dd.ddgemm_entries(a_hi, a_lo, b_hi, b_lo, rows, cols)
+    absab = np.array([np.abs(a_hi[i]) @ np.abs(b_hi[:, j]) for i, j in zip(rows, cols)])
+    got_hi, got_lo = c_hi[rows, cols], c_lo[rows, cols]
+    diff = np.abs((got_hi - o_hi) + (got_lo - o_lo))
+    assert np.all(diff <= CONTRACT * absab)
+    assert exact.dd_is_normalised(c_hi, c_lo)
+    for t in range(8):
+        ex = exact.exact_dot(a_hi[rows[t]], a_lo[rows[t]], b_hi[:, cols[t]], b_lo[:, cols[t]])
+        assert exact.err_vs_exact(got_hi[t], got_lo[t], ex) <= CONTRACT * absab[t]

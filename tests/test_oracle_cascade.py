@@ -26,6 +26,7 @@ import pytest
 from oracle import cascade as cs
 from oracle import dd
 from tests import exact
+from tests.bounds import paper_bound
 from workloads import gemm_inputs, integer_inputs
 
 EPS_DD = 2.0 ** -106
@@ -153,7 +154,6 @@ def test_bins_0_to_2_are_exact_integer_dots(kind):
         for j in range(10):
             b0 = dot(A0[i], B0[j])                                  # units 2^-42
             b1 = dot(A0[i], B1[j]) + dot(A1[i], B0[j])              # units 2^-63
-            b2 = (dot(A0[i], B2[j]) << 21) + dot(A1[i], B1[j]) + (dot(A2[i], B0[j]) << 21)  # 2^-105+...
             assert abs(b0) < 2 ** 53 and abs(b1) < 2 ** 53
             assert bin0[i, j] == math.ldexp(b0, -42)
             assert bin1[i, j] == math.ldexp(b1, -63)
@@ -161,28 +161,6 @@ def test_bins_0_to_2_are_exact_integer_dots(kind):
             b2u = dot(A0[i], B2[j]) + dot(A1[i], B1[j]) + dot(A2[i], B0[j])
             assert abs(b2u) < 2 ** 53
             assert bin2[i, j] == math.ldexp(b2u, -84)
-            del b2
-
-
-def paper_bound(a_hi, b_hi, kc=cs.KC):
-    """Eq. (cascerr) per k-block, summed over blocks, plus the FP64x2
-    accumulation of the block results: sum_p [2 eps_dd |A_p||B_p| +
-    2 * 40 k_p^2 eps_casc ||a_ip||_inf ||b_pj||_inf] + K_B eps_dd |A||B|.
-    (The factor 2 covers the paper's "approximately".)"""
-    m, k = a_hi.shape
-    n = b_hi.shape[1]
-    tot = np.zeros((m, n))
-    kb = max(1, (k + kc - 1) // kc)
-    for p in range(kb):
-        sl = slice(p * kc, (p + 1) * kc)
-        ap, bp = np.abs(a_hi[:, sl]), np.abs(b_hi[sl, :])
-        kp = ap.shape[1]
-        if kp == 0:
-            continue
-        tot += 2 * EPS_DD * (ap @ bp)
-        tot += 2 * 40 * kp * kp * EPS_CASC * np.outer(ap.max(axis=1), bp.max(axis=0))
-    tot += kb * EPS_DD * (np.abs(a_hi) @ np.abs(b_hi))
-    return tot
 
 
 def max_bound_ratio(fn, m, n, k, kind, seed):
