@@ -128,16 +128,19 @@ class ClockSampler:
 
 
 def fp64_peak_rule():
-    """FP64 tensor peak from the measured bf16 peak x the nominal
-    FP64/bf16 ratio (sustained figure: the kernel runs inside a long step)."""
+    """FP64 tensor-path peak = the measured bf16 peak x the nominal
+    FP64/bf16 ratio.  The burst bf16 figure is used: the FP64 pipe runs at
+    the maximum SM clock for the whole step (see "clocks"), so the
+    power-capped sustained bf16 figure does not describe it."""
     try:
         with open(MEASURED_PEAKS) as f:
             mp = json.load(f)
-        return (mp["bf16_tflops_sustained"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS,
-                "MEASURED_PEAKS.json bf16_tflops_sustained x nominal FP64/bf16 (1.25/2250)")
+        return (mp["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS,
+                "of measured: MEASURED_PEAKS.json bf16_tflops (burst) x nominal FP64/bf16 "
+                "(1.25/2250)")
     except (OSError, KeyError, ValueError):
-        return (1700.0 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS,
-                "fallback sustained bf16 1.7 PFLOP/s x nominal FP64/bf16 (1.25/2250)")
+        return (1900.0 * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS,
+                "of fallback: bf16 1.9 PFLOP/s burst x nominal FP64/bf16 (1.25/2250)")
 
 
 def oracle_rows_rate(a_hi, a_lo, b_hi, b_lo, rows):
