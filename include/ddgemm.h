@@ -109,6 +109,40 @@ int ddgemm(int m, int n, int k,
            void *workspace, size_t ws_bytes, void *stream,
            const ddgemm_opts *opts);
 
+/* Size of the static device scratch array that ddgemm_noalloc() uses. */
+#define DDGEMM_NOALLOC_SCRATCH_BYTES (64u << 20) /* 64 MiB */
+
+/* ddgemm() for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a packaging of ddgemm(), not part of the method.
+ *
+ * Who needs it: code that runs while a stream is being captured into a CUDA
+ * graph (allocation is not allowed there), plug-ins inside a framework whose
+ * memory pool owns the GPU, latency-bound paths that cannot afford
+ * cudaMalloc's implicit device synchronisation, and callers from other
+ * languages with no GPU allocator.  They pass inputs and outputs only; the
+ * scratch space is a file-scope __device__ array of
+ * DDGEMM_NOALLOC_SCRATCH_BYTES that every GPU loading this library keeps
+ * until the process exits.
+ *
+ *   - Arguments, layouts and results are those of ddgemm() (opts may be
+ *     NULL); the work is enqueued on `stream` and the call does not wait.
+ *   - Problems with ddgemm_workspace_size(m, n, k, opts) above
+ *     DDGEMM_NOALLOC_SCRATCH_BYTES are rejected with DDGEMM_EWORKSPACE
+ *     (872 x 872 x 872 is the largest cube that fits).
+ *   - The first call on each device looks up the array's device address
+ *     with cudaGetSymbolAddress (with that device current) and caches it;
+ *     make that first call before any stream capture.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - Every call on a device shares the one array, which keeps the last
+ *     call's contents (nothing in it needs clearing between calls): calls
+ *     whose work overlaps on the GPU (different streams, no ordering) race
+ *     and give wrong results.  Serialise them, e.g. on one stream. */
+int ddgemm_noalloc(int m, int n, int k,
+                   const double *A_hi, const double *A_lo, int lda,
+                   const double *B_hi, const double *B_lo, int ldb,
+                   double *C_hi, double *C_lo, int ldc,
+                   void *stream, const ddgemm_opts *opts);
+
 /* The split step alone for A (Appendix A; Sec. "Cascading matrices and
  * GEMM"): per row i and k-block p, sigma = 2^e with e the frexp exponent of
  * max |A_hi| over the block (e = 0 for an all-zero block); every entry is

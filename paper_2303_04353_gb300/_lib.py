@@ -45,7 +45,9 @@ _SIGS = {
     "ddgemm_bins": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _Z, _P, _P]),
     "ddgemm_status_string": (ctypes.c_char_p, [_I]),
     "ddgemm_probe_fp64": (ctypes.c_double, [_I, _P, _P]),
+    "ddgemm_noalloc": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P]),
 }
+DDGEMM_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 def load(build_if_missing: bool = True):
@@ -125,3 +127,11 @@ def ddgemm_probe_fp64(iters: int, sink: int, stream: int) -> float:
     if flops < 0:
         raise DdgemmError(DDGEMM_ECUDA, "ddgemm_probe_fp64")
     return flops
+
+
+def ddgemm_noalloc(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo, ldc, stream,
+                   opts: ddgemm_opts | None = None) -> None:
+    """ddgemm with the library's static scratch array instead of a workspace
+    (for callers that cannot allocate; see include/ddgemm.h).  Raises on error."""
+    _check(load().ddgemm_noalloc(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo, ldc,
+                                 stream, ctypes.byref(opts) if opts else None), "ddgemm_noalloc")
