@@ -109,6 +109,29 @@ int ddgemm(int m, int n, int k,
            void *workspace, size_t ws_bytes, void *stream,
            const ddgemm_opts *opts);
 
+/* Backward pass of C = op(A) op(B) for a loss L with dL/dC = dC (all FP64x2):
+ * dA = dC op(B)^T and dB = op(A)^T dC, each computed by the same cascade
+ * (two ddgemm() calls on `stream`).  The paper has no backward pass; this is
+ * the chain rule applied to its product.
+ *   A, B, opts   as passed to the forward ddgemm() (trans flags included).
+ *   dC_hi/lo     m x n, leading dim lddc >= n.
+ *   dA_hi/lo     op(A)'s storage shape: m x k (ldda >= k) if trans_a = 0,
+ *                else k x m (ldda >= m).
+ *   dB_hi/lo     B's storage shape: k x n (lddb >= n) if trans_b = 0, else
+ *                n x k (lddb >= k).
+ *   workspace    at least ddgemm_backward_workspace_size() bytes, reused by
+ *                both products.
+ * opts->flags_dev and opts->phase_events are ignored. */
+size_t ddgemm_backward_workspace_size(int m, int n, int k, const ddgemm_opts *opts);
+int ddgemm_backward(int m, int n, int k,
+                    const double *A_hi, const double *A_lo, int lda,
+                    const double *B_hi, const double *B_lo, int ldb,
+                    const double *dC_hi, const double *dC_lo, int lddc,
+                    double *dA_hi, double *dA_lo, int ldda,
+                    double *dB_hi, double *dB_lo, int lddb,
+                    void *workspace, size_t ws_bytes, void *stream,
+                    const ddgemm_opts *opts);
+
 /* Size of the static device scratch array that ddgemm_noalloc() uses. */
 #define DDGEMM_NOALLOC_SCRATCH_BYTES (64u << 20) /* 64 MiB */
 

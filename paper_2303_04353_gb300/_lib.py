@@ -46,6 +46,9 @@ _SIGS = {
     "ddgemm_status_string": (ctypes.c_char_p, [_I]),
     "ddgemm_probe_fp64": (ctypes.c_double, [_I, _P, _P]),
     "ddgemm_noalloc": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P]),
+    "ddgemm_backward_workspace_size": (_Z, [_I, _I, _I, _P]),
+    "ddgemm_backward": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P,
+                             _I, _P, _Z, _P, _P]),
 }
 DDGEMM_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -135,3 +138,17 @@ def ddgemm_noalloc(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo, ldc, s
     (for callers that cannot allocate; see include/ddgemm.h).  Raises on error."""
     _check(load().ddgemm_noalloc(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo, ldc,
                                  stream, ctypes.byref(opts) if opts else None), "ddgemm_noalloc")
+
+
+def ddgemm_backward_workspace_size(m: int, n: int, k: int, opts: ddgemm_opts | None = None) -> int:
+    return load().ddgemm_backward_workspace_size(m, n, k, ctypes.byref(opts) if opts else None)
+
+
+def ddgemm_backward(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, dc_hi, dc_lo, lddc, da_hi, da_lo,
+                    ldda, db_hi, db_lo, lddb, workspace, ws_bytes, stream,
+                    opts: ddgemm_opts | None = None) -> None:
+    """dA = dC op(B)^T, dB = op(A)^T dC through the cascade.  Raises on error."""
+    _check(load().ddgemm_backward(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, dc_hi, dc_lo, lddc,
+                                  da_hi, da_lo, ldda, db_hi, db_lo, lddb, workspace, ws_bytes,
+                                  stream, ctypes.byref(opts) if opts else None),
+           "ddgemm_backward")

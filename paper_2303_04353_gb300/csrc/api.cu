@@ -174,6 +174,65 @@ int ddgemm_split_b(int k, int n, const double *B_hi, const double *B_lo, int ldb
     return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }
 
+// The two products of the backward pass, each a plain ddgemm on the stream.
+// With C = op(A) op(B) and dC given:
+//   dA: trans_a = 0 -> dA (m x k) = dC op(B)^T;  trans_a = 1 -> dA (k x m) = op(B) dC^T
+//   dB: trans_b = 0 -> dB (k x n) = op(A)^T dC;  trans_b = 1 -> dB (n x k) = dC^T op(A)
+struct BwdCall {
+    int m, n, k;
+    const double *ah, *al;
+    int lda, ta;
+    const double *bh, *bl;
+    int ldb, tb;
+};
+
+static void backward_calls(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
+                           const double *B_hi, const double *B_lo, int ldb, const double *dC_hi,
+                           const double *dC_lo, int lddc, const Parsed &p, BwdCall &ca,
+                           BwdCall &cb) {
+    if (!p.trans_a)
+        ca = {m, k, n, dC_hi, dC_lo, lddc, 0, B_hi, B_lo, ldb, !p.trans_b};
+    else
+        ca = {k, m, n, B_hi, B_lo, ldb, p.trans_b, dC_hi, dC_lo, lddc, 1};
+    if (!p.trans_b)
+        cb = {k, n, m, A_hi, A_lo, lda, !p.trans_a, dC_hi, dC_lo, lddc, 0};
+    else
+        cb = {n, k, m, dC_hi, dC_lo, lddc, 1, A_hi, A_lo, lda, p.trans_a};
+}
+
+size_t ddgemm_backward_workspace_size(int m, int n, int k, const ddgemm_opts *opts) {
+    Parsed p;
+    if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
+    const size_t a = ddgemm_workspace_size(p.trans_a ? k : m, p.trans_a ? m : k, n, nullptr);
+    const size_t b = ddgemm_workspace_size(p.trans_b ? n : k, p.trans_b ? k : n, m, nullptr);
+    return a > b ? a : b;
+}
+
+int ddgemm_backward(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
+                    const double *B_hi, const double *B_lo, int ldb, const double *dC_hi,
+                    const double *dC_lo, int lddc, double *dA_hi, double *dA_lo, int ldda,
+                    double *dB_hi, double *dB_lo, int lddb, void *workspace, size_t ws_bytes,
+                    void *stream, const ddgemm_opts *opts) {
+    Parsed p;
+    if (!parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
+    if (p.variant != DDGEMM_VARIANT_FP64) return DDGEMM_EUNSUPPORTED;
+    if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;
+    if (m > 0 && n > 0 && (!dC_hi || !dC_lo || lddc < n)) return DDGEMM_EINVAL;
+    BwdCall ca, cb;
+    backward_calls(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, dC_hi, dC_lo, lddc, p, ca, cb);
+    if (ca.m > 0 && ca.n > 0 && (!dA_hi || !dA_lo || ldda < ca.n)) return DDGEMM_EINVAL;
+    if (cb.m > 0 && cb.n > 0 && (!dB_hi || !dB_lo || lddb < cb.n)) return DDGEMM_EINVAL;
+    if (ws_bytes < ddgemm_backward_workspace_size(m, n, k, opts)) return DDGEMM_EWORKSPACE;
+    ddgemm_opts oa{ca.ta, ca.tb, DDGEMM_VARIANT_FP64, p.status, nullptr, nullptr};
+    ddgemm_opts ob{cb.ta, cb.tb, DDGEMM_VARIANT_FP64, p.status, nullptr, nullptr};
+    // both products run on one stream, so the second may reuse the workspace
+    int r = ddgemm(ca.m, ca.n, ca.k, ca.ah, ca.al, ca.lda, ca.bh, ca.bl, ca.ldb, dA_hi, dA_lo,
+                   ldda, workspace, ws_bytes, stream, &oa);
+    if (r != DDGEMM_OK) return r;
+    return ddgemm(cb.m, cb.n, cb.k, cb.ah, cb.al, cb.lda, cb.bh, cb.bl, cb.ldb, dB_hi, dB_lo, lddb,
+                  workspace, ws_bytes, stream, &ob);
+}
+
 const char *ddgemm_status_string(int code) {
     switch (code) {
         case DDGEMM_OK: return "ok";

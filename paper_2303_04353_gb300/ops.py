@@ -121,3 +121,31 @@ def bins(a_hi, a_lo, b_hi, b_lo, *, stream=None):
                      b_lo.data_ptr(), ldb, out.data_ptr(), ws.data_ptr(), ws.numel(),
                      current_stream_ptr(stream), None)
     return out
+
+
+def ddgemm_backward(a_hi, a_lo, b_hi, b_lo, dc_hi, dc_lo, *, trans_a=False, trans_b=False,
+                    workspace=None, status=None, stream=None):
+    """dA = dC op(B)^T and dB = op(A)^T dC through the cascade; returns
+    (dA_hi, dA_lo, dB_hi, dB_lo) in the storage shapes of A and B."""
+    lda = _check_pair(a_hi, a_lo, "A")
+    ldb = _check_pair(b_hi, b_lo, "B")
+    lddc = _check_pair(dc_hi, dc_lo, "dC")
+    m, k = (a_hi.shape[1], a_hi.shape[0]) if trans_a else tuple(a_hi.shape)
+    kb, n = (b_hi.shape[1], b_hi.shape[0]) if trans_b else tuple(b_hi.shape)
+    if k != kb or tuple(dc_hi.shape) != (m, n):
+        raise ValueError("shapes of A, B and dC do not match")
+    dev = a_hi.device
+    da = [torch.empty(a_hi.shape, dtype=torch.float64, device=dev) for _ in range(2)]
+    db = [torch.empty(b_hi.shape, dtype=torch.float64, device=dev) for _ in range(2)]
+    opts = _lib.make_opts(trans_a, trans_b, _lib.DDGEMM_VARIANT_FP64,
+                          status.data_ptr() if status is not None else 0)
+    if workspace is None:
+        nbytes = _lib.ddgemm_backward_workspace_size(m, n, k, opts)
+        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+    _lib.ddgemm_backward(m, n, k, a_hi.data_ptr(), a_lo.data_ptr(), lda, b_hi.data_ptr(),
+                         b_lo.data_ptr(), ldb, dc_hi.data_ptr(), dc_lo.data_ptr(), lddc,
+                         da[0].data_ptr(), da[1].data_ptr(), max(da[0].shape[1], 1),
+                         db[0].data_ptr(), db[1].data_ptr(), max(db[0].shape[1], 1),
+                         workspace.data_ptr(), workspace.numel(), current_stream_ptr(stream),
+                         opts)
+    return da[0], da[1], db[0], db[1]
