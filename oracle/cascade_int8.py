@@ -1,0 +1,137 @@
+"""The cascade re-sliced into INT8 pieces, step by step (plain Python ints
+and numpy int64; exact).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The paper sketches this form in Sec. "FP64x2 in terms of INT8": convert each
+operand to fixed point, store it as about 15 INT8 pieces, compute the
+pair-products that matter (the triangle i + j <= s - 1, Sec. "Safely dropping
+lower order bins") with 32-bit integer accumulation, and add the results
+across bins in FP64x2.  The paper gives no further detail; the readings
+below (listed in the design doc) fill it in.
+
+  * Scale: sigma = 2^e per (row of A, k-block) and per (k-block, column of
+    B), e the frexp exponent of max |hi| in the block, as in the FP64 form.
+    The k-block is KB8 = 16384 entries: the longest block whose diagonal
+    sums stay inside int32 for up to 32 pieces (|digit| <= 64).
+  * Fixed point: X = rne(x_hi 2^(F-e)) + rne(x_lo 2^(F-e)), an integer,
+    with F = 6 + 7 (s - 1) fraction bits (rne = round to nearest, ties to
+    even).
+  * Pieces: the balanced base-2^7 digits of X, most significant first:
+    X = sum_i d_i 128^(s-1-i), d_i in [-64, 64], so x / sigma ~ sum_i d_i
+    2^(-6-7i).  Each piece fits INT8.
+  * Products: for every diagonal t = i + j <= s - 1 the integer sum
+    S_t = sum_{i+j=t} sum_l dA_i[l] dB_j[l] (exact in int32).
+  * Assembly: for t = s-1 down to 0 (smallest first), v = S_t 2^(-12-7t)
+    (exact in FP64) is added into an FP64x2 sum (TwoSum, add lo,
+    FastTwoSum); the block result is scaled by sigma tau and added into C
+    with the FP64x2 add, as in the FP64 form.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import cascade as _fp64
+
+KB8 = 16384
+DIGIT = 7
+
+
+def frac_bits(s: int) -> int:
+    return 6 + DIGIT * (s - 1)
+
+
+def rne_scaled(x: float, sh: int) -> int:
+    """round-half-even(x * 2^sh) as a Python int (exact)."""
+    num, den = float(x).as_integer_ratio()     # den is a power of two
+    p = sh - (den.bit_length() - 1)
+    if p >= 0:
+        return num << p
+    q, r = divmod(num, 1 << -p)                # floor division, 0 <= r < 2^-p
+    half = 1 << (-p - 1)
+    if r > half or (r == half and q & 1):
+        q += 1
+    return q
+
+
+def to_fixed(hi: float, lo: float, e: int, s: int) -> int:
+    f = frac_bits(s)
+    return rne_scaled(hi, f - e) + rne_scaled(lo, f - e)
+
+
+def digits(x: int, s: int) -> list[int]:
+    """Balanced base-128 digits of x, most significant first."""
+    out = [0] * s
+    for i in range(s - 1, 0, -1):
+        d = ((x + 64) & 127) - 64
+        out[i] = d
+        x = (x - d) >> 7
+    out[0] = x
+    return out
+
+
+def block_exponents(x_hi: np.ndarray, kb: int = KB8) -> np.ndarray:
+    """e[v, p] for vectors along the rows of x_hi (reuses the FP64 form's
+    rule; only the block length differs)."""
+    return _fp64.block_exponents_rows(x_hi, kb)
+
+
+def digit_planes(x_hi, x_lo, e, s, kb=KB8):
+    """Pieces of every row of x (vectors along rows): int64 [s][rows][k]."""
+    rows, k = x_hi.shape
+    out = np.zeros((s, rows, k), dtype=np.int64)
+    for v in range(rows):
+        for l in range(k):
+            ds = digits(to_fixed(x_hi[v, l], x_lo[v, l], int(e[v, l // kb]), s), s)
+            out[:, v, l] = ds
+    return out
+
+
+def diagonal_sums(da: np.ndarray, db: np.ndarray, s: int) -> np.ndarray:
+    """S_t = sum_{i+j=t} dA_i dB_j^T for t = 0..s-1 (int64, exact).
+    da: [s][m][k], db: [s][n][k]."""
+    m, n = da.shape[1], db.shape[1]
+    out = np.zeros((s, m, n), dtype=np.int64)
+    for i in range(s):
+        for j in range(s - i):
+            out[i + j] += da[i] @ db[j].T
+    return out
+
+
+def assemble(diag: np.ndarray, s: int):
+    """Add v_t = S_t 2^(-12-7t) for t = s-1 .. 0 into an FP64x2 sum."""
+    h = np.zeros(diag.shape[1:])
+    l = np.zeros(diag.shape[1:])
+    for t in range(s - 1, -1, -1):
+        v = np.ldexp(diag[t].astype(np.float64), -12 - DIGIT * t)
+        h, l = _fp64.dd_add_d(h, l, v)
+    return h, l
+
+
+def cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16, kb=KB8, return_parts=False):
+    """C := A B through s INT8 pieces per entry.  Returns (C_hi, C_lo)."""
+    a_hi = np.asarray(a_hi, np.float64)
+    a_lo = np.asarray(a_lo, np.float64)
+    bt_hi = np.ascontiguousarray(np.asarray(b_hi, np.float64).T)   # columns of B as rows
+    bt_lo = np.ascontiguousarray(np.asarray(b_lo, np.float64).T)
+    m, k = a_hi.shape
+    n = bt_hi.shape[0]
+    e_a = block_exponents(a_hi, kb)
+    e_b = block_exponents(bt_hi, kb)
+    c_hi = np.zeros((m, n))
+    c_lo = np.zeros((m, n))
+    parts = []
+    for p in range((k + kb - 1) // kb):
+        sl = slice(p * kb, (p + 1) * kb)
+        da = digit_planes(a_hi[:, sl], a_lo[:, sl], e_a[:, p:p + 1], s, kb=k + 1)
+        db = digit_planes(bt_hi[:, sl], bt_lo[:, sl], e_b[:, p:p + 1], s, kb=k + 1)
+        diag = diagonal_sums(da, db, s)
+        h, l = assemble(diag, s)
+        sc = e_a[:, p][:, None] + e_b[:, p][None, :]
+        h, l = np.ldexp(h, sc), np.ldexp(l, sc)
+        c_hi, c_lo = _fp64.dd_add(c_hi, c_lo, h, l)
+        if return_parts:
+            parts.append((da, db, diag))
+    if return_parts:
+        return c_hi, c_lo, parts, (e_a, e_b)
+    return c_hi, c_lo

@@ -1,0 +1,163 @@
+"""Pins for the INT8 restatement (oracle/cascade_int8.py).
+
+  * rne_scaled equals round-half-even of the exact rational x 2^sh;
+  * the digits reconstruct X exactly and lie in [-64, 64] (they fit INT8);
+  * the fixed-point value is within 2^-F sigma of the FP64x2 entry;
+  * diagonal sums equal brute-force integer dot products;
+  * the whole INT8 cascade meets the error bound derived below against
+    exact rationals, integer matrices come out exact, and the worked example
+    of Sec. "Forward Error Analysis" gives fl_FP64(eps) like the FP64 form;
+  * planted mistakes (a dropped diagonal, a digit off by one position, the
+    wrong rounding) fail a pin.
+
+Bound (per entry, per k-block p with scales sigma_p, tau_p and length k_p):
+  conversion  2 k_p sigma tau 2^-F               (|delta x| <= 2^-F sigma)
+  dropped     1.01 (s-1) k_p 2^-7s sigma tau     (diagonals i+j >= s, |digit| <= 64)
+  assembly    4 s 2^-106 k_p sigma tau, and 4 K_B 2^-106 |A||B| across blocks."""
+import math
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import cascade_int8 as c8
+from oracle import dd
+from tests import exact
+from workloads import gemm_inputs, integer_inputs
+
+
+def int8_bound(a_hi, b_hi, s, kb=c8.KB8):
+    m, k = a_hi.shape
+    n = b_hi.shape[1]
+    e_a = c8.block_exponents(a_hi, kb)
+    e_b = c8.block_exponents(np.ascontiguousarray(b_hi.T), kb)
+    f = c8.frac_bits(s)
+    tot = np.zeros((m, n))
+    for p in range(e_a.shape[1]):
+        kp = min(kb, k - p * kb)
+        st = np.exp2(e_a[:, p][:, None] + e_b[:, p][None, :])
+        tot += kp * st * (2.0 ** (1 - f) + 1.01 * (s - 1) * 2.0 ** (-7 * s) + 4 * s * 2.0 ** -106)
+    return tot + 4 * e_a.shape[1] * 2.0 ** -106 * (np.abs(a_hi) @ np.abs(b_hi))
+
+
+def test_rne_scaled_is_round_half_even():
+    rng = np.random.default_rng(0)
+    xs = list(rng.standard_normal(400) * np.exp2(rng.integers(-40, 40, 400)))
+    xs += [0.5, 1.5, 2.5, -0.5, -1.5, 3 * 2.0 ** -10, 2.0 ** -1074, -(2.0 ** -60)]
+    for x in xs:
+        for sh in (-5, 0, 3, 60, 111):
+            assert c8.rne_scaled(x, sh) == round(Fraction(x) * Fraction(2) ** sh)
+
+
+@pytest.mark.parametrize("s", [8, 16, 18])
+def test_digits_reconstruct_and_fit_int8(s):
+    rnd = random.Random(s)
+    f = c8.frac_bits(s)
+    for _ in range(500):
+        x = rnd.randint(-(2 ** f), 2 ** f) >> rnd.randint(0, f)
+        ds = c8.digits(x, s)
+        assert all(-64 <= d <= 64 for d in ds)
+        assert sum(d * 128 ** (s - 1 - i) for i, d in enumerate(ds)) == x
+    for x in (2 ** f, -(2 ** f), 0, 1, -1, 64, -64, 63):
+        ds = c8.digits(x, s)
+        assert all(-64 <= d <= 64 for d in ds)
+        assert sum(d * 128 ** (s - 1 - i) for i, d in enumerate(ds)) == x
+
+
+def test_fixed_point_conversion_error():
+    a_hi, a_lo, _, _ = gemm_inputs(6, 1, 300, kind="wide", seed=2)
+    e = c8.block_exponents(a_hi)
+    s = 16
+    f = c8.frac_bits(s)
+    for i in range(6):
+        assert 2.0 ** (e[i, 0] - 1) <= np.abs(a_hi[i]).max() < 2.0 ** e[i, 0]
+        for l in range(300):
+            x = c8.to_fixed(a_hi[i, l], a_lo[i, l], int(e[i, 0]), s)
+            exact_scaled = (Fraction(a_hi[i, l]) + Fraction(a_lo[i, l])) * Fraction(2) ** (f - int(e[i, 0]))
+            assert abs(x - exact_scaled) <= 1
+            assert abs(x) <= 2 ** f
+
+
+def test_diagonal_sums_brute_force():
+    rng = np.random.default_rng(3)
+    s, m, n, k = 5, 3, 4, 7
+    da = rng.integers(-64, 65, (s, m, k))
+    db = rng.integers(-64, 65, (s, n, k))
+    got = c8.diagonal_sums(da, db, s)
+    for t in range(s):
+        for i in range(m):
+            for j in range(n):
+                want = sum(int(da[u, i, l]) * int(db[t - u, j, l]) for u in range(t + 1)
+                           for l in range(k))
+                assert got[t, i, j] == want
+
+
+def max_ratio(fn, m, n, k, kind, seed, s):
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind=kind, seed=seed)
+    c_hi, c_lo = fn(a_hi, a_lo, b_hi, b_lo, s=s)
+    bound = int8_bound(a_hi, b_hi, s)
+    worst = 0.0
+    for i in range(m):
+        for j in range(n):
+            ex = exact.exact_dot(a_hi[i], a_lo[i], b_hi[:, j], b_lo[:, j])
+            worst = max(worst, exact.err_vs_exact(c_hi[i, j], c_lo[i, j], ex) / bound[i, j])
+    return worst
+
+
+@pytest.mark.parametrize("m,n,k,kind,s", [(5, 6, 200, "uniform", 16), (4, 5, 300, "wide", 16),
+                                          (3, 3, 64, "uniform", 12), (4, 4, 100, "wide", 18)])
+def test_int8_cascade_meets_bound(m, n, k, kind, s):
+    assert max_ratio(c8.cascade_int8_ddgemm, m, n, k, kind, k, s) <= 1.0
+
+
+def test_int8_cascade_near_fp64x2_on_uniform():
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(8, 8, 256, seed=4)
+    c_hi, c_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16)
+    o_hi, o_lo = dd.ddgemm(a_hi, a_lo, b_hi, b_lo)
+    assert np.all(np.abs((c_hi - o_hi) + (c_lo - o_lo)) <= 1e-28 * (np.abs(a_hi) @ np.abs(b_hi)))
+    assert exact.dd_is_normalised(c_hi, c_lo)
+
+
+def test_int8_integers_exact():
+    a_hi, a_lo, b_hi, b_lo = integer_inputs(5, 4, 120, bits=10, seed=5)
+    c_hi, c_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=6)
+    ref = a_hi.astype(np.int64) @ b_hi.astype(np.int64)
+    assert np.array_equal(c_hi, ref.astype(np.float64)) and np.all(c_lo == 0)
+
+
+def test_int8_worked_example():
+    eps_hi, eps_lo = 1.5 * 2.0 ** -71, 2.0 ** -130
+    c_hi, c_lo = c8.cascade_int8_ddgemm(np.array([[1.0, eps_hi]]), np.array([[0.0, eps_lo]]),
+                                        np.array([[0.0], [1.0]]), np.zeros((2, 1)), s=16)
+    assert c_hi[0, 0] == eps_hi and c_lo[0, 0] == 0.0
+
+
+# ---- planted mistakes ------------------------------------------------------
+
+def test_planted_dropped_diagonal_is_caught(monkeypatch):
+    real = c8.diagonal_sums
+
+    def drop_two(da, db, s):
+        out = real(da, db, s)
+        out[2] = 0
+        return out
+    monkeypatch.setattr(c8, "diagonal_sums", drop_two)
+    assert max_ratio(c8.cascade_int8_ddgemm, 4, 4, 100, "uniform", 6, 16) > 1.0
+
+
+def test_planted_digit_weight_is_caught(monkeypatch):
+    real = c8.digits
+
+    def shifted(x, s):
+        d = real(x, s)
+        return d[1:] + [0]      # every digit one place too high
+    monkeypatch.setattr(c8, "digits", shifted)
+    with pytest.raises(AssertionError):
+        test_digits_reconstruct_and_fit_int8(16)
+
+
+def test_planted_rounding_is_caught(monkeypatch):
+    monkeypatch.setattr(c8, "rne_scaled", lambda x, sh: math.floor(Fraction(x) * Fraction(2) ** sh))
+    with pytest.raises(AssertionError):
+        test_rne_scaled_is_round_half_even()
