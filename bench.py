@@ -51,6 +51,8 @@ WORKLOADS = {
                  name="ddgemm 4096x4096x4096 FP64x2, hi log-uniform 2^-20..2^20, seed 0"),
     "rect": dict(m=8192, n=1024, k=4096, kind="wide",
                  name="ddgemm 8192x1024x4096 FP64x2, hi log-uniform 2^-20..2^20, seed 0"),
+    "8192": dict(m=8192, n=8192, k=8192, kind="wide",
+                 name="ddgemm 8192x8192x8192 FP64x2, hi log-uniform 2^-20..2^20, seed 0"),
     "2048": dict(m=2048, n=2048, k=2048, kind="wide",
                  name="ddgemm 2048x2048x2048 FP64x2, hi log-uniform 2^-20..2^20, seed 0"),
     "256": dict(m=256, n=256, k=256, kind="uniform",
@@ -222,13 +224,14 @@ def run_ours(args, wl):
     d_in = [h.to(dev) for h in host_in]
     c_hi = torch.empty((m, n), dtype=torch.float64, device=dev)
     c_lo = torch.empty((m, n), dtype=torch.float64, device=dev)
-    ws = ops.alloc_workspace(m, n, k, dev)
+    variant = _lib.DDGEMM_VARIANT_INT8 if args.variant == "int8" else _lib.DDGEMM_VARIANT_FP64
+    ws = ops.alloc_workspace(m, n, k, dev, variant, args.int8_slices)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(events=None):
         ops.ddgemm(*d_in, out=(c_hi, c_lo), workspace=ws, status=status, stream=stream,
-                   phase_events=events)
+                   phase_events=events, variant=variant, int8_slices=args.int8_slices)
 
     def barrier():
         if world > 1:
@@ -308,43 +311,66 @@ def run_ours(args, wl):
     h2d = sum(h.numel() * 8 for h in host_in)
     d2h = 2 * m * n * 8
 
-    # ---- the FP64 tensor-path ceiling, measured on this GPU ----------------
+    # ---- the tensor-path ceilings, measured on this GPU --------------------
     sink = torch.zeros(1, dtype=torch.float64, device=dev)
-    best = 0.0
-    for iters in (200, 2000, 2000, 2000):
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        fl = _lib.ddgemm_probe_fp64(iters, sink.data_ptr(), stream.cuda_stream)
-        p1.record(stream)
-        torch.cuda.synchronize()
-        best = max(best, fl / (p0.elapsed_time(p1) * 1e-3) / 1e12)
-    probe_tflops = best
+
+    def probe(fn, iters_list):
+        best = 0.0
+        for iters in iters_list:
+            p0 = torch.cuda.Event(enable_timing=True)
+            p1 = torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            work = fn(iters, sink.data_ptr(), stream.cuda_stream)
+            p1.record(stream)
+            torch.cuda.synchronize()
+            best = max(best, work / (p0.elapsed_time(p1) * 1e-3) / 1e12)
+        return best
+    probe_tflops = probe(_lib.ddgemm_probe_fp64, (200, 2000, 2000, 2000))
+    probe_tops = probe(_lib.ddgemm_probe_int8, (200, 4000, 4000, 4000)) \
+        if variant == _lib.DDGEMM_VARIANT_INT8 else None
 
     if rank != 0:
         return
     peak, peak_src = fp64_peak_rule()
-    achieved = 10.0 * flops_dd / (casc_ms * 1e-3) / 1e12
+    if variant == _lib.DDGEMM_VARIANT_INT8:
+        s8 = args.int8_slices
+        prods = s8 * (s8 + 1) // 2
+        achieved = prods * flops_dd / (casc_ms * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "kernel": f"cascade_int8_kernel<{s8}>",
+                    "achieved": round(achieved, 3), "peak": round(probe_tops, 3), "unit": "TOPS",
+                    "frac": round(achieved / probe_tops, 4), "traffic": None,
+                    "peak_source": "of measured: live mma.sync s8 probe in this run (no INT8 "
+                                   "figure in MEASURED_PEAKS.json)",
+                    "algorithmic": f"{prods} x 2mnk = {prods * flops_dd:.4g} INT8 ops per launch"}
+    else:
+        achieved = 10.0 * flops_dd / (casc_ms * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "kernel": "cascade_fp64_kernel",
+                    "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak_source": peak_src,
+                    "probe_peak": round(probe_tflops, 4),
+                    "frac_vs_probe": round(achieved / probe_tflops, 4),
+                    "algorithmic": f"10 x 2mnk = {10 * flops_dd:.4g} FP64 flops per launch"}
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": wl["name"], "m": m, "n": n, "k": k,
+                   "variant": "fp64 (ten FP64 products)" if variant == _lib.DDGEMM_VARIANT_FP64
+                   else f"int8 ({args.int8_slices} pieces, "
+                        f"{args.int8_slices * (args.int8_slices + 1) // 2} INT8 products)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs (512 MiB) and panels larger than L2; no flush"
                          if m * k >= 1 << 22 else "small case; L2-resident"},
-        "pct_fp64_tc_peak": round(100.0 * 10.0 * flops_dd / (ms_per_step * 1e-3) / 1e12
-                                  / probe_tflops, 2),
+        **({"pct_fp64_tc_peak": round(100.0 * 10.0 * flops_dd / (ms_per_step * 1e-3) / 1e12
+                                      / probe_tflops, 2)}
+           if variant == _lib.DDGEMM_VARIANT_FP64 else
+           {"pct_int8_tc_peak": round(100.0 * (args.int8_slices * (args.int8_slices + 1) // 2)
+                                      * flops_dd / (ms_per_step * 1e-3) / 1e12 / probe_tops, 2)}),
         "max_err_vs_dd_oracle": max_err,
-        "phases_ms": {"split": round(split_ms, 3), "ten_products_and_assembly": round(casc_ms, 3)},
-        "roofline": {"bound": "tensor", "kernel": "cascade_fp64_kernel",
-                     "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
-                     "peak_source": peak_src,
-                     "probe_peak": round(probe_tflops, 4),
-                     "frac_vs_probe": round(achieved / probe_tflops, 4),
-                     "algorithmic": f"10 x 2mnk = {10 * flops_dd:.4g} FP64 flops per launch"},
+        "phases_ms": {"split": round(split_ms, 3), "products_and_assembly": round(casc_ms, 3)},
+        "roofline": roofline,
         "e2e": {"value": round(world * flops_dd / (e2e_ms * 1e-3) / 1e9, 4), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 3 * args.steps,
@@ -363,6 +389,9 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="4096")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", choices=("fp64", "int8"), default="fp64",
+                    help="fp64: the ten FP64 products (default); int8: the INT8 form")
+    ap.add_argument("--int8-slices", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("bench.py: at least 3 warm-up steps")

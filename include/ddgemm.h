@@ -58,6 +58,7 @@ extern "C" {
 
 /* opts->variant */
 #define DDGEMM_VARIANT_FP64  0    /* ten FP64 products on the FP64 tensor path */
+#define DDGEMM_VARIANT_INT8  1    /* the cascade re-sliced into INT8 pieces (below) */
 
 typedef struct ddgemm_opts {
     /* 0: A is m x k (lda >= k).  1: A is stored k x m (lda >= m) and the
@@ -65,7 +66,19 @@ typedef struct ddgemm_opts {
      * 1 = stored n x k (ldb >= k). */
     int trans_a;
     int trans_b;
-    /* DDGEMM_VARIANT_FP64. */
+    /* DDGEMM_VARIANT_FP64 (default) or DDGEMM_VARIANT_INT8.
+     *
+     * INT8 (Sec. "FP64x2 in terms of INT8", Sec. "Safely dropping lower
+     * order bins"): per (row of A, k-block of 16384) and (k-block, column of
+     * B), sigma = 2^e as in the FP64 form; each entry becomes the fixed-point
+     * integer X = rne(hi 2^(F-e)) + rne(lo 2^(F-e)), F = 6 + 7 (s - 1),
+     * written as s balanced base-128 digits in [-64, 64] (INT8 pieces).  The
+     * products of digit planes i, j with i + j <= s - 1 are accumulated
+     * exactly in int32 per diagonal t = i + j on the integer tensor path,
+     * and the diagonals are added smallest first in FP64x2.  Error per entry
+     * and k-block: at most about (s + 3) 2^-7s k sigma tau (conversion and
+     * dropped diagonals) plus FP64x2 rounding.  flags_dev is not supported
+     * with it (DDGEMM_EUNSUPPORTED). */
     int variant;
     /* Optional device word (or NULL): DDGEMM_DEV_* bits are OR-ed into it.
      * The library never clears it. */
@@ -82,6 +95,9 @@ typedef struct ddgemm_opts {
      * split and the ten products (phases two and three, one kernel) and
      * after it, so that a caller can time each phase on the device. */
     void **phase_events;
+    /* INT8 form only: pieces per entry, s in {12, 14, 15, 16, 17, 18}; 0 = 16.
+     * Products per k: s (s + 1) / 2 INT8 GEMMs. */
+    int int8_slices;
 } ddgemm_opts;
 
 /* Bytes of device workspace ddgemm() needs for this problem (0 when m, n or
@@ -192,6 +208,22 @@ int ddgemm_split_b(int k, int n, const double *B_hi, const double *B_lo, int ldb
                    int trans_b, double *slices, int ld_slices, int *exps,
                    unsigned int *status_dev, void *stream);
 
+/* The split step of the INT8 form alone (see ddgemm_opts.variant).
+ *   slices      s, as for ddgemm_opts.int8_slices (no 0 default here).
+ *   digits      device int8, s x m x ld_digits for A (row i of A is row i of
+ *               each plane) and s x n x ld_digits for B (column j of B is row
+ *               j of each plane): digits[(d*nvec + v)*ld_digits + l] is digit
+ *               d (most significant first) of entry l of vector v.
+ *               ld_digits >= k and a multiple of 16; the bytes of the last
+ *               8-byte group past k in a row are written with zero digits.
+ *   exps        device int32, ceil(k/16384) x m (or x n): e of sigma = 2^e. */
+int ddgemm_split_int8_a(int m, int k, const double *A_hi, const double *A_lo, int lda,
+                        int trans_a, int slices, signed char *digits, int ld_digits,
+                        int *exps, unsigned int *status_dev, void *stream);
+int ddgemm_split_int8_b(int k, int n, const double *B_hi, const double *B_lo, int ldb,
+                        int trans_b, int slices, signed char *digits, int ld_digits,
+                        int *exps, unsigned int *status_dev, void *stream);
+
 /* The ten products of one k-block without the FP64x2 assembly (for
  * checking that bins 0-2 are exact, Sec. "Cascading vectors and dot
  * products").  Requires 0 < k <= 256.  bins: device, 4 x m x n doubles,
@@ -212,6 +244,11 @@ int ddgemm_bins(int m, int n, int k,
  * products.  sink: device pointer to one double (never written in
  * practice). */
 double ddgemm_probe_fp64(int iters, double *sink, void *stream);
+
+/* The same for the integer tensor path of the INT8 form (mma.sync m16n8k32
+ * s8 with s32 accumulation, four independent chains per warp); returns the
+ * number of integer operations (2 per multiply-add), or -1 on error. */
+double ddgemm_probe_int8(int iters, double *sink, void *stream);
 
 /* Static text for a return code. */
 const char *ddgemm_status_string(int code);

@@ -20,6 +20,7 @@ DDGEMM_EUNSUPPORTED = 4
 DDGEMM_DEV_NONFINITE = 0x1
 DDGEMM_DEV_TIMEOUT = 0x2
 DDGEMM_VARIANT_FP64 = 0
+DDGEMM_VARIANT_INT8 = 1
 
 
 class DdgemmError(RuntimeError):
@@ -31,7 +32,8 @@ class DdgemmError(RuntimeError):
 class ddgemm_opts(ctypes.Structure):
     _fields_ = [("trans_a", ctypes.c_int), ("trans_b", ctypes.c_int),
                 ("variant", ctypes.c_int), ("status_dev", ctypes.c_void_p),
-                ("flags_dev", ctypes.c_void_p), ("phase_events", ctypes.c_void_p)]
+                ("flags_dev", ctypes.c_void_p), ("phase_events", ctypes.c_void_p),
+                ("int8_slices", ctypes.c_int)]
 
 
 _LIB = None
@@ -45,8 +47,11 @@ _SIGS = {
     "ddgemm_bins": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _Z, _P, _P]),
     "ddgemm_status_string": (ctypes.c_char_p, [_I]),
     "ddgemm_probe_fp64": (ctypes.c_double, [_I, _P, _P]),
+    "ddgemm_probe_int8": (ctypes.c_double, [_I, _P, _P]),
     "ddgemm_noalloc": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P]),
     "ddgemm_backward_workspace_size": (_Z, [_I, _I, _I, _P]),
+    "ddgemm_split_int8_a": (_I, [_I, _I, _P, _P, _I, _I, _I, _P, _I, _P, _P, _P]),
+    "ddgemm_split_int8_b": (_I, [_I, _I, _P, _P, _I, _I, _I, _P, _I, _P, _P, _P]),
     "ddgemm_backward": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P,
                              _I, _P, _Z, _P, _P]),
 }
@@ -86,12 +91,12 @@ def _check(code: int, where: str) -> None:
 
 
 def make_opts(trans_a=False, trans_b=False, variant=DDGEMM_VARIANT_FP64, status_dev=0,
-              flags_dev=0, phase_events=None) -> ddgemm_opts:
+              flags_dev=0, phase_events=None, int8_slices=0) -> ddgemm_opts:
     """phase_events: None or a ctypes array of three cudaEvent_t handles
     (the caller keeps it alive until the call returns)."""
     ev = ctypes.cast(phase_events, ctypes.c_void_p) if phase_events is not None else None
     return ddgemm_opts(int(trans_a), int(trans_b), int(variant), status_dev or None,
-                       flags_dev or None, ev)
+                       flags_dev or None, ev, int(int8_slices))
 
 
 def ddgemm_workspace_size(m: int, n: int, k: int, opts: ddgemm_opts | None = None) -> int:
@@ -152,3 +157,25 @@ def ddgemm_backward(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, dc_hi, dc_lo, ldd
                                   da_hi, da_lo, ldda, db_hi, db_lo, lddb, workspace, ws_bytes,
                                   stream, ctypes.byref(opts) if opts else None),
            "ddgemm_backward")
+
+
+def ddgemm_split_int8_a(m, k, a_hi, a_lo, lda, trans_a, slices, digits, ld_digits, exps,
+                        status_dev, stream) -> None:
+    _check(load().ddgemm_split_int8_a(m, k, a_hi, a_lo, lda, int(trans_a), slices, digits,
+                                      ld_digits, exps, status_dev or None, stream),
+           "ddgemm_split_int8_a")
+
+
+def ddgemm_split_int8_b(k, n, b_hi, b_lo, ldb, trans_b, slices, digits, ld_digits, exps,
+                        status_dev, stream) -> None:
+    _check(load().ddgemm_split_int8_b(k, n, b_hi, b_lo, ldb, int(trans_b), slices, digits,
+                                      ld_digits, exps, status_dev or None, stream),
+           "ddgemm_split_int8_b")
+
+
+def ddgemm_probe_int8(iters: int, sink: int, stream: int) -> float:
+    """Enqueue the integer tensor-path throughput probe; returns its op count."""
+    ops = load().ddgemm_probe_int8(iters, sink, stream)
+    if ops < 0:
+        raise DdgemmError(DDGEMM_ECUDA, "ddgemm_probe_int8")
+    return ops

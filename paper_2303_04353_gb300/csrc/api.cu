@@ -38,7 +38,26 @@ struct Parsed {
     unsigned int *status = nullptr;
     int *flags = nullptr;
     void **events = nullptr;
+    int slices = ddg::INT8_SLICES_DEFAULT;
 };
+
+// Workspace carve of the INT8 form: digit planes of A and B, exponents.
+struct Layout8 {
+    long long ld;
+    size_t off_a, off_b, off_ea, off_eb, total;
+};
+
+Layout8 layout8_for(int m, int n, int k, int slices) {
+    Layout8 L;
+    const long long kb = (k + ddg::KB8 - 1) / ddg::KB8;
+    L.ld = (long long)round_up((size_t)k, 64);
+    L.off_a = 0;
+    L.off_b = round_up((size_t)slices * m * L.ld, ALIGN);
+    L.off_ea = L.off_b + round_up((size_t)slices * n * L.ld, ALIGN);
+    L.off_eb = L.off_ea + round_up((size_t)kb * m * sizeof(int), ALIGN);
+    L.total = L.off_eb + round_up((size_t)kb * n * sizeof(int), ALIGN);
+    return L;
+}
 
 bool parse(const ddgemm_opts *o, Parsed &p) {
     if (o) {
@@ -48,7 +67,9 @@ bool parse(const ddgemm_opts *o, Parsed &p) {
         p.status = o->status_dev;
         p.flags = o->flags_dev;
         p.events = o->phase_events;
+        if (o->int8_slices) p.slices = o->int8_slices;
     }
+    if (p.variant == DDGEMM_VARIANT_INT8 && !ddg::int8_slices_supported(p.slices)) return false;
     return (p.trans_a == 0 || p.trans_a == 1) && (p.trans_b == 0 || p.trans_b == 1);
 }
 
@@ -100,6 +121,33 @@ int run(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
     return e == cudaSuccess && mark(2) ? DDGEMM_OK : DDGEMM_ECUDA;
 }
 
+int run_int8(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
+             const double *B_hi, const double *B_lo, int ldb, double *C_hi, double *C_lo, int ldc,
+             void *workspace, size_t ws_bytes, cudaStream_t stream, const Parsed &p) {
+    const Layout8 L = layout8_for(m, n, k, p.slices);
+    if (!workspace || ws_bytes < L.total || (uintptr_t)workspace % ALIGN) return DDGEMM_EWORKSPACE;
+    char *ws = static_cast<char *>(workspace);
+    int8_t *da = reinterpret_cast<int8_t *>(ws + L.off_a);
+    int8_t *db = reinterpret_cast<int8_t *>(ws + L.off_b);
+    int *e_a = reinterpret_cast<int *>(ws + L.off_ea);
+    int *e_b = reinterpret_cast<int *>(ws + L.off_eb);
+    auto mark = [&](int i) {
+        return !p.events || cudaEventRecord(static_cast<cudaEvent_t>(p.events[i]), stream) ==
+                                cudaSuccess;
+    };
+    if (!mark(0)) return DDGEMM_ECUDA;
+    cudaError_t e = ddg::launch_split_int8(p.slices, m, k, A_hi, A_lo, lda, !p.trans_a, da, L.ld,
+                                           e_a, p.status, stream);
+    if (e != cudaSuccess) return DDGEMM_ECUDA;
+    e = ddg::launch_split_int8(p.slices, n, k, B_hi, B_lo, ldb, p.trans_b != 0, db, L.ld, e_b,
+                               p.status, stream);
+    if (e != cudaSuccess || !mark(1)) return DDGEMM_ECUDA;
+    ddg::Int8Args a{m, n, k, p.slices, da, db, L.ld, e_a, e_b, C_hi, C_lo, (long long)ldc,
+                    p.status};
+    e = ddg::launch_cascade_int8(a, stream);
+    return e == cudaSuccess && mark(2) ? DDGEMM_OK : DDGEMM_ECUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -108,6 +156,7 @@ size_t ddgemm_workspace_size(int m, int n, int k, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
     if (m == 0 || n == 0 || k == 0) return 0;
+    if (p.variant == DDGEMM_VARIANT_INT8) return layout8_for(m, n, k, p.slices).total;
     return layout_for(m, n, k).total;
 }
 
@@ -116,7 +165,9 @@ int ddgemm(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
            void *workspace, size_t ws_bytes, void *stream, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
-    if (p.variant != DDGEMM_VARIANT_FP64) return DDGEMM_EUNSUPPORTED;
+    if (p.variant != DDGEMM_VARIANT_FP64 && p.variant != DDGEMM_VARIANT_INT8)
+        return DDGEMM_EUNSUPPORTED;
+    if (p.variant == DDGEMM_VARIANT_INT8 && p.flags) return DDGEMM_EUNSUPPORTED;
     if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;
     if (m == 0 || n == 0) return DDGEMM_OK;
     if (!C_hi || !C_lo || ldc < n) return DDGEMM_EINVAL;
@@ -129,8 +180,43 @@ int ddgemm(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
             return DDGEMM_ECUDA;
         return DDGEMM_OK;
     }
+    if (p.variant == DDGEMM_VARIANT_INT8)
+        return run_int8(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, C_hi, C_lo, ldc, workspace,
+                        ws_bytes, s, p);
     return run(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, C_hi, C_lo, ldc, nullptr, workspace,
                ws_bytes, s, p);
+}
+
+int ddgemm_split_int8_a(int m, int k, const double *A_hi, const double *A_lo, int lda,
+                        int trans_a, int slices, signed char *digits, int ld_digits, int *exps,
+                        unsigned int *status_dev, void *stream) {
+    if (m < 0 || k < 0 || (trans_a != 0 && trans_a != 1) || !ddg::int8_slices_supported(slices))
+        return DDGEMM_EINVAL;
+    if (m == 0 || k == 0) return DDGEMM_OK;
+    if (!A_hi || !A_lo || !digits || !exps || lda < (trans_a ? m : k) || ld_digits < k ||
+        ld_digits % 16)
+        return DDGEMM_EINVAL;
+    const cudaError_t e = ddg::launch_split_int8(slices, m, k, A_hi, A_lo, lda, !trans_a,
+                                                 reinterpret_cast<int8_t *>(digits), ld_digits,
+                                                 exps, status_dev,
+                                                 static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
+}
+
+int ddgemm_split_int8_b(int k, int n, const double *B_hi, const double *B_lo, int ldb,
+                        int trans_b, int slices, signed char *digits, int ld_digits, int *exps,
+                        unsigned int *status_dev, void *stream) {
+    if (n < 0 || k < 0 || (trans_b != 0 && trans_b != 1) || !ddg::int8_slices_supported(slices))
+        return DDGEMM_EINVAL;
+    if (n == 0 || k == 0) return DDGEMM_OK;
+    if (!B_hi || !B_lo || !digits || !exps || ldb < (trans_b ? k : n) || ld_digits < k ||
+        ld_digits % 16)
+        return DDGEMM_EINVAL;
+    const cudaError_t e = ddg::launch_split_int8(slices, n, k, B_hi, B_lo, ldb, trans_b != 0,
+                                                 reinterpret_cast<int8_t *>(digits), ld_digits,
+                                                 exps, status_dev,
+                                                 static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }
 
 int ddgemm_bins(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
@@ -203,8 +289,9 @@ static void backward_calls(int m, int n, int k, const double *A_hi, const double
 size_t ddgemm_backward_workspace_size(int m, int n, int k, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
-    const size_t a = ddgemm_workspace_size(p.trans_a ? k : m, p.trans_a ? m : k, n, nullptr);
-    const size_t b = ddgemm_workspace_size(p.trans_b ? n : k, p.trans_b ? k : n, m, nullptr);
+    ddgemm_opts plain{0, 0, p.variant, nullptr, nullptr, nullptr, p.slices};
+    const size_t a = ddgemm_workspace_size(p.trans_a ? k : m, p.trans_a ? m : k, n, &plain);
+    const size_t b = ddgemm_workspace_size(p.trans_b ? n : k, p.trans_b ? k : n, m, &plain);
     return a > b ? a : b;
 }
 
@@ -215,7 +302,8 @@ int ddgemm_backward(int m, int n, int k, const double *A_hi, const double *A_lo,
                     void *stream, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
-    if (p.variant != DDGEMM_VARIANT_FP64) return DDGEMM_EUNSUPPORTED;
+    if (p.variant != DDGEMM_VARIANT_FP64 && p.variant != DDGEMM_VARIANT_INT8)
+        return DDGEMM_EUNSUPPORTED;
     if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;
     if (m > 0 && n > 0 && (!dC_hi || !dC_lo || lddc < n)) return DDGEMM_EINVAL;
     BwdCall ca, cb;
@@ -223,8 +311,8 @@ int ddgemm_backward(int m, int n, int k, const double *A_hi, const double *A_lo,
     if (ca.m > 0 && ca.n > 0 && (!dA_hi || !dA_lo || ldda < ca.n)) return DDGEMM_EINVAL;
     if (cb.m > 0 && cb.n > 0 && (!dB_hi || !dB_lo || lddb < cb.n)) return DDGEMM_EINVAL;
     if (ws_bytes < ddgemm_backward_workspace_size(m, n, k, opts)) return DDGEMM_EWORKSPACE;
-    ddgemm_opts oa{ca.ta, ca.tb, DDGEMM_VARIANT_FP64, p.status, nullptr, nullptr};
-    ddgemm_opts ob{cb.ta, cb.tb, DDGEMM_VARIANT_FP64, p.status, nullptr, nullptr};
+    ddgemm_opts oa{ca.ta, ca.tb, p.variant, p.status, nullptr, nullptr, p.slices};
+    ddgemm_opts ob{cb.ta, cb.tb, p.variant, p.status, nullptr, nullptr, p.slices};
     // both products run on one stream, so the second may reuse the workspace
     int r = ddgemm(ca.m, ca.n, ca.k, ca.ah, ca.al, ca.lda, ca.bh, ca.bl, ca.ldb, dA_hi, dA_lo,
                    ldda, workspace, ws_bytes, stream, &oa);

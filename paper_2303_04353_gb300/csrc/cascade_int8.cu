@@ -1,0 +1,273 @@
+// Phases two and three of the INT8 form (Sec. "FP64x2 in terms of INT8",
+// Sec. "Safely dropping lower order bins"): the triangle of digit-pair
+// products i + j <= s - 1 on the integer tensor path (mma.sync m16n8k32 s8,
+// exact int32 accumulation), one int32 accumulator per diagonal t = i + j,
+// and the FP64x2 sum of the diagonals, smallest first, once per k-block.
+//
+// Tiling.  A CTA owns a 32 x 32 tile of C; 8 warps each own 16 x 8 (one
+// MMA tile).  Per k-step of 32, two TMA copies bring all s digit planes of
+// A ([s][32][32] int8) and of B ([s][32][32], k contiguous) into a
+// four-deep ring.  Each warp loads its s A fragments (ldmatrix.x4) and s B
+// fragments (ldmatrix.x2) once and issues the s(s+1)/2 products from
+// registers.  The s accumulators of 4 registers each are what bound the
+// tile size per warp (s = 16: 64 accumulator + 96 operand registers).
+//
+// Exactness.  |digit| <= 64, so a product is at most 2^12 and a diagonal
+// holds at most s of them per k: over a k-block of 16384 a diagonal sum is
+// below s 2^26 < 2^31.  The int32 -> FP64 conversion and the scaling by
+// 2^(-12-7t) are exact; only the FP64x2 additions round.
+//
+// Waits are bounded as in the FP64 kernel (DDGEMM_DEV_TIMEOUT).
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <cstdint>
+
+#include "dd_device.cuh"
+#include "ddgemm_internal.h"
+
+namespace ddg {
+namespace {
+
+constexpr int BM = 32, BN = 32, BKB = 32, NST = 4, NTHREADS = 256;
+constexpr unsigned DEV_TIMEOUT = 0x2u;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t (&r)[2], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(addr));
+}
+
+// D = A B + D for one m16n8k32 s8 tile with s32 accumulation.
+__device__ __forceinline__ void imma(int (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int S>
+struct Geometry {
+    static constexpr int PLANE = BM * BKB;              // bytes of one digit plane tile
+    static constexpr int A_STAGE = S * PLANE;
+    static constexpr int B_STAGE = S * BN * BKB;
+    static constexpr int STAGE = A_STAGE + B_STAGE;
+    static constexpr size_t SMEM = (size_t)NST * STAGE + NST * sizeof(uint64_t) + 1024;
+};
+
+template <int S>
+__global__ void __launch_bounds__(NTHREADS, 1)
+cascade_int8_kernel(const __grid_constant__ CUtensorMap tm_a,
+                    const __grid_constant__ CUtensorMap tm_b, const Int8Args args) {
+    using G = Geometry<S>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NST * G::STAGE);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int ksteps = (args.k + BKB - 1) / BKB;
+    constexpr int STEPS_PER_BLOCK = KB8 / BKB;
+
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[s]))
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    auto issue = [&](int t, int stage) {
+        const uint32_t bar = smem_addr(&bars[stage]);
+        unsigned char *dst = smem + stage * G::STAGE;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)G::STAGE)
+                     : "memory");
+        tma_load_3d(smem_addr(dst), &tm_a, bar, t * BKB, m0, 0);
+        tma_load_3d(smem_addr(dst + G::A_STAGE), &tm_b, bar, t * BKB, n0, 0);
+    };
+    if (tid == 0)
+        for (int s = 0; s < NST && s < ksteps; ++s) issue(s, s);
+
+    int acc[S][4];
+#pragma unroll
+    for (int t = 0; t < S; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0;
+
+    // ldmatrix row addresses (bytes, relative to a plane tile)
+    const uint32_t a_off = (uint32_t)((wm * 16 + (lane & 7) + ((lane >> 3) & 1) * 8) * BKB +
+                                      (lane >> 4) * 16);
+    const uint32_t b_off = (uint32_t)((wn * 8 + (lane & 7)) * BKB + ((lane >> 3) & 1) * 16);
+
+    for (int t = 0; t < ksteps; ++t) {
+        const int stage = t % NST;
+        const bool ok = mbar_wait(smem_addr(&bars[stage]), (t / NST) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                if (args.status) atomicOr(args.status, DEV_TIMEOUT);
+                for (int u = t; u < t + NST && u < ksteps; ++u)
+                    mbar_wait(smem_addr(&bars[u % NST]), (u / NST) & 1);
+            }
+            return;
+        }
+        const uint32_t base = smem_addr(smem + stage * G::STAGE);
+        uint32_t a[S][4], b[S][2];
+#pragma unroll
+        for (int i = 0; i < S; ++i) ldsm_x4(a[i], base + i * G::PLANE + a_off);
+#pragma unroll
+        for (int j = 0; j < S; ++j) ldsm_x2(b[j], base + G::A_STAGE + j * (BN * BKB) + b_off);
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+#pragma unroll
+            for (int j = 0; j < S - i; ++j) imma(acc[i + j], a[i], b[j]);
+        __syncthreads();
+        if (tid == 0 && t + NST < ksteps) issue(t + NST, stage);
+
+        if ((t + 1) % STEPS_PER_BLOCK == 0 || t + 1 == ksteps) {
+            const int p = t / STEPS_PER_BLOCK;
+            const int g = lane >> 2, q4 = lane & 3;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = m0 + wm * 16 + g + (q >> 1) * 8;
+                const int col = n0 + wn * 8 + 2 * q4 + (q & 1);
+                if (row < args.m && col < args.n) {
+                    double h = 0.0, l = 0.0;
+#pragma unroll
+                    for (int d = S - 1; d >= 0; --d) {
+                        // S_d 2^(-12-7d): exact; the power of two is a constant
+                        const double v = __dmul_rn(__int2double_rn(acc[d][q]),
+                                                   __longlong_as_double(
+                                                       (long long)(1023 - 12 - 7 * d) << 52));
+                        dd_add_d(h, l, v);
+                    }
+                    const int sc = args.exp_a[(long long)p * args.m + row] +
+                                   args.exp_b[(long long)p * args.n + col];
+                    h = scalbn(h, sc);
+                    l = scalbn(l, sc);
+                    const long long o = (long long)row * args.ldc + col;
+                    double ch = 0.0, cl = 0.0;
+                    if (p > 0) {
+                        ch = args.c_hi[o];
+                        cl = args.c_lo[o];
+                    }
+                    dd_add(ch, cl, h, l, ch, cl);
+                    args.c_hi[o] = ch;
+                    args.c_lo[o] = cl;
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < S; ++d) acc[d][0] = acc[d][1] = acc[d][2] = acc[d][3] = 0;
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// Digit planes [s][rows][ld] (int8, k contiguous); box [s][32][32].
+bool make_digit_map(CUtensorMap *map, const int8_t *base, uint64_t k, uint64_t rows, int s,
+                    uint64_t ld) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {k, rows, (cuuint64_t)s};
+    const cuuint64_t strides[2] = {ld, ld * rows};
+    const cuuint32_t box[3] = {BKB, 32, (cuuint32_t)s};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<int8_t *>(base), dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int S>
+cudaError_t launch_s(const Int8Args &a, cudaStream_t stream) {
+    using G = Geometry<S>;
+    CUtensorMap tm_a, tm_b;
+    if (!make_digit_map(&tm_a, a.a_digits, a.k, a.m, S, a.ld_digits) ||
+        !make_digit_map(&tm_b, a.b_digits, a.k, a.n, S, a.ld_digits))
+        return cudaErrorInvalidValue;
+    const cudaError_t e = cudaFuncSetAttribute(
+        cascade_int8_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((a.n + BN - 1) / BN, (a.m + BM - 1) / BM);
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    cascade_int8_kernel<S><<<grid, NTHREADS, G::SMEM, stream>>>(tm_a, tm_b, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_cascade_int8(const Int8Args &a, cudaStream_t stream) {
+    if (a.m <= 0 || a.n <= 0 || a.k <= 0) return cudaSuccess;
+    switch (a.slices) {
+#define DDG_CASE(S) \
+    case S:         \
+        return launch_s<S>(a, stream);
+        DDG_INT8_SLICE_CASES
+#undef DDG_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ddg

@@ -47,4 +47,39 @@ struct CascadeArgs {
 // assembly fused in (one launch).
 cudaError_t launch_cascade_fp64(const CascadeArgs &a, cudaStream_t stream);
 
+// ---- INT8 form ------------------------------------------------------------
+// k-block of the INT8 form: the longest block whose diagonal sums of up to 32
+// digit products (|digit| <= 64) stay below 2^31.
+constexpr int KB8 = 16384;
+// Piece counts with a compiled kernel (the fixed-point value needs
+// 6 + 7 (s - 1) <= 125 bits, so s <= 18).
+#define DDG_INT8_SLICE_CASES DDG_CASE(12) DDG_CASE(14) DDG_CASE(15) DDG_CASE(16) DDG_CASE(17) \
+    DDG_CASE(18)
+constexpr int INT8_SLICES_DEFAULT = 16;
+inline bool int8_slices_supported(int s) {
+    return s == 12 || (s >= 14 && s <= 18);
+}
+
+// Digit planes out[(s * nvec + v) * ld_out + l], ld_out a multiple of 16 and
+// >= kdim; exps[p * nvec + v] per k-block of KB8.  Element (v, l) of the
+// input is at x[v * ldx + l] when vec_contig, else x[l * ldx + v].
+cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi,
+                              const double *x_lo, long long ldx, bool vec_contig, int8_t *out,
+                              long long ld_out, int *exps, unsigned int *status,
+                              cudaStream_t stream);
+
+struct Int8Args {
+    int m, n, k, slices;
+    const int8_t *a_digits;  // slices x m x ld_digits
+    const int8_t *b_digits;  // slices x n x ld_digits
+    long long ld_digits;
+    const int *exp_a;        // ceil(k/KB8) x m
+    const int *exp_b;        // ceil(k/KB8) x n
+    double *c_hi, *c_lo;
+    long long ldc;
+    unsigned int *status;
+};
+
+cudaError_t launch_cascade_int8(const Int8Args &a, cudaStream_t stream);
+
 }  // namespace ddg

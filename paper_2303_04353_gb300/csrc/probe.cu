@@ -1,6 +1,7 @@
-// Throughput probe of the FP64 tensor path (mma.sync m8n8k4 f64), used as
-// the measured ceiling of the cascade's dominant kernel.  Four 256-thread
-// CTAs per SM; each warp runs eight independent accumulator chains.
+// Throughput probes of the FP64 tensor path (mma.sync m8n8k4 f64) and the
+// integer tensor path (mma.sync m16n8k32 s8), used as the measured ceilings
+// of the cascade kernels.  Four 256-thread CTAs per SM; each warp runs
+// independent accumulator chains.
 #include <cuda_runtime.h>
 
 #include "../../include/ddgemm.h"
@@ -26,7 +27,41 @@ __global__ void __launch_bounds__(256) dmma_probe_kernel(int iters, double *sink
     if (s == 1.2345e300) sink[0] = s;  // never true; keeps the chains live
 }
 
+__global__ void __launch_bounds__(256) imma_probe_kernel(int iters, double *sink) {
+    const unsigned a0 = threadIdx.x * 0x01010101u, a1 = a0 + 1u, a2 = a0 + 2u, a3 = a0 + 3u;
+    const unsigned b0 = 0x02020202u, b1 = 0x01010101u;
+    int c[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[i][0] = c[i][1] = c[i][2] = c[i][3] = 0;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            asm volatile(
+                "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                "{%8,%9}, {%0,%1,%2,%3};"
+                : "+r"(c[i][0]), "+r"(c[i][1]), "+r"(c[i][2]), "+r"(c[i][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    }
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s += (long long)c[i][0] + c[i][1] + c[i][2] + c[i][3];
+    if (s == 0x7fffffffffffLL) sink[0] = (double)s;  // never true; keeps the chains live
+}
+
 }  // namespace
+
+extern "C" double ddgemm_probe_int8(int iters, double *sink, void *stream) {
+    if (iters <= 0 || !sink) return -1.0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return -1.0;
+    const int blocks = 4 * sms;
+    imma_probe_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(iters, sink);
+    if (cudaGetLastError() != cudaSuccess) return -1.0;
+    // warps x iterations x 4 MMAs x (16 x 8 x 32 multiply-adds x 2 ops)
+    return (double)blocks * 8.0 * iters * 4.0 * 8192.0;
+}
 
 extern "C" double ddgemm_probe_fp64(int iters, double *sink, void *stream) {
     if (iters <= 0 || !sink) return -1.0;

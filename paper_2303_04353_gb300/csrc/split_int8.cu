@@ -1,0 +1,212 @@
+// Phase one of the INT8 form (Sec. "FP64x2 in terms of INT8"): every FP64x2
+// entry becomes s signed 7-bit digits of a fixed-point value.
+//
+// Per (vector, k-block of 16384 entries): sigma = 2^e with e the frexp
+// exponent of max |hi| (as in the FP64 form).  Per entry, on the integer
+// ALU (the FP64 pipe of this GPU is narrow, the integer pipes are not):
+//   X = rne(hi 2^(F-e)) + rne(lo 2^(F-e))     (exact, 128-bit integers)
+//   balanced base-128 digits d_0..d_{s-1} of X, most significant first,
+//   d_i in [-64, 64], so that x / sigma ~ sum_i d_i 2^(-6-7i).
+// Output: digit planes [s][vector][ld] of int8 with k contiguous, for A
+// (vectors = rows) and B (vectors = columns; transposed through shared
+// memory) alike, which is the operand layout of mma.sync m16n8k32 s8.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "ddgemm_internal.h"
+
+namespace ddg {
+namespace {
+
+constexpr unsigned DEV_NONFINITE = 0x1u;
+
+__device__ __forceinline__ int block_exponent(double mx) {
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    return e;
+}
+
+// Per (vector, k-block) exponents.  CONTIG: element (v, l) at x[v*ldx + l]
+// (one warp per vector and block); else at x[l*ldx + v] (one CTA per 64
+// vectors and block, 4 row groups).
+template <bool CONTIG>
+__global__ void __launch_bounds__(256)
+int8_exps_kernel(int nvec, int kdim, const double *__restrict__ x, long long ldx,
+                 int *__restrict__ exps) {
+    const int kb = (kdim + KB8 - 1) / KB8;
+    if constexpr (CONTIG) {
+        const int lane = threadIdx.x & 31;
+        const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (w >= (long long)nvec * kb) return;
+        const int v = (int)(w / kb), p = (int)(w % kb);
+        const double *row = x + (long long)v * ldx;
+        const int lend = min((p + 1) * KB8, kdim);
+        double mx = 0.0;
+        for (int l = p * KB8 + lane; l < lend; l += 32) mx = fmax(mx, fabs(row[l]));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (lane == 0) exps[(long long)p * nvec + v] = block_exponent(mx);
+    } else {
+        __shared__ double part[4][64];
+        const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+        const int v = blockIdx.x * 64 + tx, p = blockIdx.y;
+        const int lend = min((p + 1) * KB8, kdim);
+        double mx = 0.0;
+        if (v < nvec)
+            for (int l = p * KB8 + ty; l < lend; l += 4) mx = fmax(mx, fabs(x[(long long)l * ldx + v]));
+        part[ty][tx] = mx;
+        __syncthreads();
+        if (ty == 0 && v < nvec) {
+            mx = fmax(fmax(part[0][tx], part[1][tx]), fmax(part[2][tx], part[3][tx]));
+            exps[(long long)p * nvec + v] = block_exponent(mx);
+        }
+    }
+}
+
+// round-half-even(x * 2^sh) as a 128-bit integer, from the bits of x.
+__device__ __forceinline__ __int128 rne_scaled(double x, int sh) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    unsigned long long mant = bits & 0xfffffffffffffull;
+    if (ex == 0x7ff || (ex == 0 && mant == 0)) return 0;  // non-finite is flagged elsewhere
+    int p;
+    if (ex == 0) {
+        p = 1 - 1075 + sh;                 // subnormal: no implicit bit
+    } else {
+        mant |= 1ull << 52;
+        p = ex - 1075 + sh;
+    }
+    __int128 v;
+    if (p > 127 - 54) {
+        // only an entry far above its block's max |hi| gets here (a lo part
+        // much larger than every hi of the block): outside the form's range
+        v = 0;
+    } else if (p >= 0) {
+        v = (__int128)mant << p;
+    } else if (p < -63) {
+        v = 0;                             // below one half
+    } else {
+        const int r = -p;
+        unsigned long long q = mant >> r;
+        const unsigned long long rem = mant & ((1ull << r) - 1ull);
+        const unsigned long long half = 1ull << (r - 1);
+        if (rem > half || (rem == half && (q & 1ull))) ++q;
+        v = (__int128)q;
+    }
+    return (bits >> 63) ? -v : v;
+}
+
+constexpr int TV = 32, TK = 64;  // tile: 32 vectors x 64 k
+
+template <int S, bool CONTIG>
+__global__ void __launch_bounds__(256)
+int8_digits_kernel(int nvec, int kdim, const double *__restrict__ xh,
+                   const double *__restrict__ xl, long long ldx, int8_t *__restrict__ out,
+                   long long ld_out, const int *__restrict__ exps, unsigned int *status) {
+    __shared__ double sh[TV][TK + 1];
+    __shared__ double sl[TV][TK + 1];
+    const int tid = threadIdx.x;
+    const int v0 = blockIdx.y * TV, l0 = blockIdx.x * TK;
+    // coalesced tile load in the input's own layout
+#pragma unroll
+    for (int it = 0; it < TV * TK / 256; ++it) {
+        const int idx = it * 256 + tid;
+        int v, l;
+        if (CONTIG) {
+            v = idx / TK; l = idx % TK;
+        } else {
+            l = idx / TV; v = idx % TV;
+        }
+        const int gv = v0 + v, gl = l0 + l;
+        double a = 0.0, b = 0.0;
+        if (gv < nvec && gl < kdim) {
+            const long long o = CONTIG ? (long long)gv * ldx + gl : (long long)gl * ldx + gv;
+            a = xh[o];
+            b = xl[o];
+        }
+        sh[v][l] = a;
+        sl[v][l] = b;
+    }
+    __syncthreads();
+    // each thread: one vector, 8 consecutive k; one 8-byte word per digit plane
+    const int v = tid >> 3, lg = tid & 7;
+    const int gv = v0 + v;
+    if (gv >= nvec) return;
+    const int e = exps[(long long)(l0 / KB8) * nvec + gv];
+    constexpr int F = 6 + 7 * (S - 1);
+    unsigned long long word[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) word[s] = 0;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const double hi = sh[v][lg * 8 + j], lo = sl[v][lg * 8 + j];
+        bad |= !isfinite(hi) || !isfinite(lo);
+        __int128 X = rne_scaled(hi, F - e) + rne_scaled(lo, F - e);
+#pragma unroll
+        for (int s = S - 1; s > 0; --s) {
+            const int d = (int)((unsigned long long)(X + 64) & 127ull) - 64;
+            X = (X - d) >> 7;
+            word[s] |= (unsigned long long)(uint8_t)(int8_t)d << (8 * j);
+        }
+        word[0] |= (unsigned long long)(uint8_t)(int8_t)(int)X << (8 * j);
+    }
+    if (bad && status) atomicOr(status, DEV_NONFINITE);
+    const int gl = l0 + lg * 8;
+    if (gl >= kdim) return;
+    // entries past kdim in the last word carry zero digits; they sit in the
+    // row padding (ld_out >= kdim rounded up to 16) and are never read
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+        *reinterpret_cast<unsigned long long *>(out + ((long long)s * nvec + gv) * ld_out + gl) =
+            word[s];
+}
+
+template <int S>
+cudaError_t launch_digits(int nvec, int kdim, const double *xh, const double *xl, long long ldx,
+                          bool contig, int8_t *out, long long ld_out, const int *exps,
+                          unsigned int *status, cudaStream_t stream) {
+    const dim3 grid((kdim + TK - 1) / TK, (nvec + TV - 1) / TV);
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    if (contig)
+        int8_digits_kernel<S, true><<<grid, 256, 0, stream>>>(nvec, kdim, xh, xl, ldx, out, ld_out,
+                                                              exps, status);
+    else
+        int8_digits_kernel<S, false><<<grid, 256, 0, stream>>>(nvec, kdim, xh, xl, ldx, out,
+                                                               ld_out, exps, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi,
+                              const double *x_lo, long long ldx, bool vec_contig, int8_t *out,
+                              long long ld_out, int *exps, unsigned int *status,
+                              cudaStream_t stream) {
+    if (nvec <= 0 || kdim <= 0) return cudaSuccess;
+    if (ld_out % 16 != 0 || ld_out < kdim) return cudaErrorInvalidValue;
+    const int kb = (kdim + KB8 - 1) / KB8;
+    if (vec_contig) {
+        const long long blocks = ((long long)nvec * kb + 7) / 8;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+        int8_exps_kernel<true><<<(unsigned)blocks, 256, 0, stream>>>(nvec, kdim, x_hi, ldx, exps);
+    } else {
+        if (kb > 65535) return cudaErrorInvalidValue;
+        int8_exps_kernel<false><<<dim3((nvec + 63) / 64, kb), 256, 0, stream>>>(nvec, kdim, x_hi,
+                                                                               ldx, exps);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    switch (slices) {
+#define DDG_CASE(S)                                                                            \
+    case S:                                                                                    \
+        return launch_digits<S>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, ld_out, exps,    \
+                                status, stream);
+        DDG_INT8_SLICE_CASES
+#undef DDG_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ddg

@@ -27,18 +27,22 @@ def current_stream_ptr(stream: torch.cuda.Stream | None = None) -> int:
     return (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
 
 
-def workspace_bytes(m: int, n: int, k: int) -> int:
-    return _lib.ddgemm_workspace_size(m, n, k, None)
+def workspace_bytes(m: int, n: int, k: int, variant: int = _lib.DDGEMM_VARIANT_FP64,
+                    int8_slices: int = 0) -> int:
+    return _lib.ddgemm_workspace_size(m, n, k, _lib.make_opts(variant=variant,
+                                                              int8_slices=int8_slices))
 
 
-def alloc_workspace(m: int, n: int, k: int, device=None) -> torch.Tensor:
-    nbytes = workspace_bytes(m, n, k)
+def alloc_workspace(m: int, n: int, k: int, device=None, variant: int = _lib.DDGEMM_VARIANT_FP64,
+                    int8_slices: int = 0) -> torch.Tensor:
+    nbytes = workspace_bytes(m, n, k, variant, int8_slices)
     # torch's caching allocator hands out 512-byte aligned blocks
     return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device or "cuda")
 
 
 def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, workspace=None,
-           status=None, flags=None, stream=None, phase_events=None):
+           status=None, flags=None, stream=None, phase_events=None,
+           variant=_lib.DDGEMM_VARIANT_FP64, int8_slices=0):
     """C := op(A) op(B) in FP64x2 by the ten-GEMM cascade.  Returns (c_hi, c_lo).
 
     trans_a: A is stored k x m and op(A) = A^T (likewise trans_b: B stored n x k).
@@ -46,7 +50,9 @@ def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, wo
     status: optional int32 CUDA tensor of one element; DDGEMM_DEV_* bits are OR-ed in.
     flags: optional int32 CUDA tensor (m x n, contiguous) for cancellation counts.
     phase_events: optional three recorded torch.cuda.Event objects; the library
-    re-records them around the split and the cascade kernel on the stream."""
+    re-records them around the split and the cascade kernel on the stream.
+    variant: DDGEMM_VARIANT_FP64 (ten FP64 products) or DDGEMM_VARIANT_INT8
+    (int8_slices INT8 pieces per entry, 0 = 16)."""
     lda = _check_pair(a_hi, a_lo, "A")
     ldb = _check_pair(b_hi, b_lo, "B")
     m, k = (a_hi.shape[1], a_hi.shape[0]) if trans_a else tuple(a_hi.shape)
@@ -63,7 +69,7 @@ def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, wo
             raise ValueError("out has the wrong shape")
     ldc = _check_pair(c_hi, c_lo, "C")
     if workspace is None:
-        workspace = alloc_workspace(m, n, k, dev)
+        workspace = alloc_workspace(m, n, k, dev, variant, int8_slices)
     if status is not None and (status.dtype != torch.int32 or not status.is_cuda):
         raise TypeError("status must be an int32 CUDA tensor")
     if flags is not None and (flags.dtype != torch.int32 or not flags.is_contiguous()
@@ -74,9 +80,9 @@ def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, wo
         if len(phase_events) != 3 or not all(e.cuda_event for e in phase_events):
             raise ValueError("phase_events: three torch.cuda.Event, each recorded once")
         evs = (ctypes.c_void_p * 3)(*[e.cuda_event for e in phase_events])
-    opts = _lib.make_opts(trans_a, trans_b, _lib.DDGEMM_VARIANT_FP64,
+    opts = _lib.make_opts(trans_a, trans_b, variant,
                           status.data_ptr() if status is not None else 0,
-                          flags.data_ptr() if flags is not None else 0, evs)
+                          flags.data_ptr() if flags is not None else 0, evs, int8_slices)
     _lib.ddgemm(m, n, k, a_hi.data_ptr(), a_lo.data_ptr(), lda, b_hi.data_ptr(),
                 b_lo.data_ptr(), ldb, c_hi.data_ptr(), c_lo.data_ptr(), ldc,
                 workspace.data_ptr(), workspace.numel(), current_stream_ptr(stream), opts)
@@ -149,3 +155,27 @@ def ddgemm_backward(a_hi, a_lo, b_hi, b_lo, dc_hi, dc_lo, *, trans_a=False, tran
                          workspace.data_ptr(), workspace.numel(), current_stream_ptr(stream),
                          opts)
     return da[0], da[1], db[0], db[1]
+
+
+def split_int8(x_hi, x_lo, *, as_b=False, trans=False, slices=16, stream=None, status=None):
+    """The INT8 split of A (as_b=False; vectors = rows of op(A)) or of B
+    (as_b=True; vectors = columns of op(B)).  Returns (digits [s, nvec, k]
+    int8, exps [ceil(k/16384), nvec] int32)."""
+    ld = _check_pair(x_hi, x_lo, "X")
+    if not as_b:
+        nvec, k = (x_hi.shape[1], x_hi.shape[0]) if trans else tuple(x_hi.shape)
+    else:
+        k, nvec = (x_hi.shape[1], x_hi.shape[0]) if trans else tuple(x_hi.shape)
+    ldd = max(16, (k + 15) // 16 * 16)
+    digits = torch.zeros((slices, nvec, ldd), dtype=torch.int8, device=x_hi.device)
+    exps = torch.zeros(((k + 16383) // 16384, nvec), dtype=torch.int32, device=x_hi.device)
+    fn = _lib.ddgemm_split_int8_b if as_b else _lib.ddgemm_split_int8_a
+    if as_b:
+        fn(k, nvec, x_hi.data_ptr(), x_lo.data_ptr(), ld, trans, slices, digits.data_ptr(), ldd,
+           exps.data_ptr(), status.data_ptr() if status is not None else 0,
+           current_stream_ptr(stream))
+    else:
+        fn(nvec, k, x_hi.data_ptr(), x_lo.data_ptr(), ld, trans, slices, digits.data_ptr(), ldd,
+           exps.data_ptr(), status.data_ptr() if status is not None else 0,
+           current_stream_ptr(stream))
+    return digits[:, :, :k], exps
