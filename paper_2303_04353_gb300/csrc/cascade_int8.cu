@@ -7,7 +7,7 @@
 // Tiling.  A CTA owns a 32 x 32 tile of C; 8 warps each own 16 x 8 (one
 // MMA tile).  Per k-step of 32, two TMA copies bring all s digit planes of
 // A ([s][32][32] int8) and of B ([s][32][32], k contiguous) into a
-// four-deep ring.  Each warp loads its s A fragments (ldmatrix.x4) and s B
+// three-deep ring (two CTAs per SM for s <= 17).  Each warp loads its s A fragments (ldmatrix.x4) and s B
 // fragments (ldmatrix.x2) once and issues the s(s+1)/2 products from
 // registers.  The s accumulators of 4 registers each are what bound the
 // tile size per warp (s = 16: 64 accumulator + 96 operand registers).
@@ -29,7 +29,7 @@
 namespace ddg {
 namespace {
 
-constexpr int BM = 32, BN = 32, BKB = 32, NST = 4, NTHREADS = 256;
+constexpr int BM = 32, BN = 32, BKB = 32, NST = 3, NTHREADS = 256;
 constexpr unsigned DEV_TIMEOUT = 0x2u;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
@@ -103,8 +103,13 @@ struct Geometry {
     static constexpr size_t SMEM = (size_t)NST * STAGE + NST * sizeof(uint64_t) + 1024;
 };
 
+// Two CTAs per SM while the registers allow it (<= 128 per thread): one
+// CTA's FP64x2 epilogue then overlaps the other's integer MMAs.
 template <int S>
-__global__ void __launch_bounds__(NTHREADS, 1)
+constexpr int ctas_per_sm() { return S <= 17 ? 2 : 1; }
+
+template <int S>
+__global__ void __launch_bounds__(NTHREADS, ctas_per_sm<S>())
 cascade_int8_kernel(const __grid_constant__ CUtensorMap tm_a,
                     const __grid_constant__ CUtensorMap tm_b, const Int8Args args) {
     using G = Geometry<S>;

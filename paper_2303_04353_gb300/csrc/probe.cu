@@ -45,7 +45,9 @@ __global__ void __launch_bounds__(256) imma_probe_kernel(int iters, double *sink
     long long s = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) s += (long long)c[i][0] + c[i][1] + c[i][2] + c[i][3];
-    if (s == 0x7fffffffffffLL) sink[0] = (double)s;  // never true; keeps the chains live
+    // compared with a runtime value the compiler cannot rule out, so the
+    // chains stay live (a constant outside the sum's range let it drop them)
+    if (s == (long long)iters * -7) sink[0] = (double)s;
 }
 
 }  // namespace
