@@ -381,6 +381,52 @@ def run_ours(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """Config-2 study: error and throughput of the FP64 form and the INT8
+    form as the exponent spread of the entries grows (hi = +-2^u,
+    u ~ U[-S/2, S/2]), at 2048^3.  One JSON line per (spread, form); these
+    are study lines, not the benchmark line."""
+    import torch
+
+    from oracle import dd
+    from paper_2303_04353_gb300 import _lib, ops
+
+    dev = torch.device("cuda", 0)
+    m = n = k = args.sweep_size
+    stream = torch.cuda.current_stream(dev)
+    rng = np.random.default_rng(3)
+    rows, cols = rng.integers(0, m, 128), rng.integers(0, n, 128)
+    forms = [("fp64", _lib.DDGEMM_VARIANT_FP64, 0)] + [
+        (f"int8 s={s8}", _lib.DDGEMM_VARIANT_INT8, s8) for s8 in (14, 16, 18)]
+    for spread in range(0, 61, 10):
+        a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind="wide", seed=0, spread=float(spread))
+        d_in = [torch.from_numpy(x).to(dev) for x in (a_hi, a_lo, b_hi, b_lo)]
+        oh, ol = dd.ddgemm_entries(a_hi, a_lo, b_hi, b_lo, rows, cols)
+        absab = np.array([np.abs(a_hi[i]) @ np.abs(b_hi[:, j]) for i, j in zip(rows, cols)])
+        for name, variant, s8 in forms:
+            ws = ops.alloc_workspace(m, n, k, dev, variant, s8)
+            out = (torch.empty((m, n), dtype=torch.float64, device=dev),
+                   torch.empty((m, n), dtype=torch.float64, device=dev))
+            for _ in range(3):
+                ops.ddgemm(*d_in, out=out, workspace=ws, variant=variant, int8_slices=s8)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            reps = 1 if variant == _lib.DDGEMM_VARIANT_FP64 else 5
+            e0.record(stream)
+            for _ in range(reps):
+                ops.ddgemm(*d_in, out=out, workspace=ws, variant=variant, int8_slices=s8)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            ch, cl = out[0].cpu().numpy(), out[1].cpu().numpy()
+            err = np.abs((ch[rows, cols] - oh) + (cl[rows, cols] - ol)) / absab
+            print(json.dumps({"study": "exponent-spread sweep", "size": m, "spread_octaves": spread,
+                              "form": name, "ms": round(ms, 3),
+                              "effective_gflops": round(2.0 * m * n * k / (ms * 1e-3) / 1e9, 2),
+                              "max_err_rel_absAabsB": float(err.max()),
+                              "median_err_rel_absAabsB": float(np.median(err))}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -392,7 +438,13 @@ def main():
     ap.add_argument("--variant", choices=("fp64", "int8"), default="fp64",
                     help="fp64: the ten FP64 products (default); int8: the INT8 form")
     ap.add_argument("--int8-slices", type=int, default=16)
+    ap.add_argument("--sweep", action="store_true",
+                    help="exponent-spread study of both forms instead of the benchmark line")
+    ap.add_argument("--sweep-size", type=int, default=2048)
     args = ap.parse_args()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.warmup < 3:
         raise SystemExit("bench.py: at least 3 warm-up steps")
     wl = WORKLOADS[args.workload]
