@@ -148,6 +148,57 @@ int ddgemm_backward(int m, int n, int k,
                     void *workspace, size_t ws_bytes, void *stream,
                     const ddgemm_opts *opts);
 
+/* ---- Batched: many independent problems in one pass ----------------------
+ * The paper has no batched form; this schedules its FP64 cascade (eq.
+ * Gemm10, Sec. "Simple") over many problems at once.  Each C is
+ * bit-identical to what ddgemm() computes for that problem alone. */
+typedef struct ddgemm_problem {
+    int m, n, k;        /* C (m x n) := A (m x k) B (k x n); any may be 0 */
+    int lda, ldb, ldc;  /* row-major leading dimensions (>= k, n, n) */
+    const double *A_hi, *A_lo, *B_hi, *B_lo;  /* device */
+    double *C_hi, *C_lo;                      /* device */
+} ddgemm_problem;
+
+#define DDGEMM_TILE_64x64 0
+#define DDGEMM_TILE_32x64 1
+#define DDGEMM_TILE_64x32 2
+#define DDGEMM_TILE_32x32 3
+#define DDGEMM_ORDER_GIVEN           0 /* tiles in problem order */
+#define DDGEMM_ORDER_LONGEST_K_FIRST 1 /* problems by k, then m n, descending */
+
+typedef struct ddgemm_batch_config {
+    int tile;   /* DDGEMM_TILE_*: C tile of the persistent kernel's CTAs */
+    int order;  /* DDGEMM_ORDER_*: order in which CTAs pull the tiles */
+} ddgemm_batch_config;
+
+/* Workspace bytes for ddgemm_batched() over these problems (host array):
+ * a plan area plus every problem's cascaded panels. */
+size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem *probs_host,
+                                     const ddgemm_opts *opts);
+
+/* C_i := A_i B_i for count problems, in four launches on `stream`:
+ *   1. a one-CTA plan kernel that reads probs_dev and writes the problems'
+ *      workspace offsets, the tile schedule and a work counter into the
+ *      workspace;
+ *   2. and 3. the split of every A and every B (grid-stride kernels);
+ *   4. one persistent cascade kernel (CTAs pull (problem, tile) items from
+ *      the counter until none are left).
+ *   probs_host  the problems, on the host: checked, and used to size the
+ *               launches and the workspace.
+ *   probs_dev   the same array in device memory (the caller uploads it); all
+ *               device-side information comes from it, so the call can be
+ *               captured into a CUDA graph once it has been uploaded.
+ *   workspace   >= ddgemm_batched_workspace_size() bytes, 256-byte aligned.
+ *   opts        NULL or: trans flags 0, variant FP64, no flags_dev
+ *               (else DDGEMM_EUNSUPPORTED); status_dev is honoured.
+ *   config      NULL = {DDGEMM_TILE_64x64, DDGEMM_ORDER_LONGEST_K_FIRST}.
+ * Problems with m or n = 0 are skipped; k = 0 writes C = 0.  The ordering
+ * by k costs count^2 / 256 comparisons in the plan kernel. */
+int ddgemm_batched(int count, const ddgemm_problem *probs_host,
+                   const ddgemm_problem *probs_dev, void *workspace, size_t ws_bytes,
+                   void *stream, const ddgemm_opts *opts,
+                   const ddgemm_batch_config *config);
+
 /* Size of the static device scratch array that ddgemm_noalloc() uses. */
 #define DDGEMM_NOALLOC_SCRATCH_BYTES (64u << 20) /* 64 MiB */
 

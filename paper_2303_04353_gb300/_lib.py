@@ -36,6 +36,21 @@ class ddgemm_opts(ctypes.Structure):
                 ("int8_slices", ctypes.c_int)]
 
 
+class ddgemm_problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("k", ctypes.c_int),
+                ("lda", ctypes.c_int), ("ldb", ctypes.c_int), ("ldc", ctypes.c_int),
+                ("A_hi", ctypes.c_void_p), ("A_lo", ctypes.c_void_p),
+                ("B_hi", ctypes.c_void_p), ("B_lo", ctypes.c_void_p),
+                ("C_hi", ctypes.c_void_p), ("C_lo", ctypes.c_void_p)]
+
+
+class ddgemm_batch_config(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("order", ctypes.c_int)]
+
+
+DDGEMM_TILE_64x64, DDGEMM_TILE_32x64, DDGEMM_TILE_64x32, DDGEMM_TILE_32x32 = 0, 1, 2, 3
+DDGEMM_ORDER_GIVEN, DDGEMM_ORDER_LONGEST_K_FIRST = 0, 1
+
 _LIB = None
 
 _I, _Z, _P = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
@@ -51,6 +66,8 @@ _SIGS = {
     "ddgemm_noalloc": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P]),
     "ddgemm_backward_workspace_size": (_Z, [_I, _I, _I, _P]),
     "ddgemm_split_int8_a": (_I, [_I, _I, _P, _P, _I, _I, _I, _P, _I, _P, _P, _P]),
+    "ddgemm_batched_workspace_size": (_Z, [_I, _P, _P]),
+    "ddgemm_batched": (_I, [_I, _P, _P, _P, _Z, _P, _P, _P]),
     "ddgemm_split_int8_b": (_I, [_I, _I, _P, _P, _I, _I, _I, _P, _I, _P, _P, _P]),
     "ddgemm_backward": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P,
                              _I, _P, _Z, _P, _P]),
@@ -179,3 +196,17 @@ def ddgemm_probe_int8(iters: int, sink: int, stream: int) -> float:
     if ops < 0:
         raise DdgemmError(DDGEMM_ECUDA, "ddgemm_probe_int8")
     return ops
+
+
+def ddgemm_batched_workspace_size(count: int, probs_host, opts: ddgemm_opts | None = None) -> int:
+    return load().ddgemm_batched_workspace_size(count, probs_host,
+                                                ctypes.byref(opts) if opts else None)
+
+
+def ddgemm_batched(count, probs_host, probs_dev, workspace, ws_bytes, stream,
+                   opts: ddgemm_opts | None = None,
+                   config: ddgemm_batch_config | None = None) -> None:
+    """Many FP64x2 GEMMs in one pass (see include/ddgemm.h).  Raises on error."""
+    _check(load().ddgemm_batched(count, probs_host, probs_dev, workspace, ws_bytes, stream,
+                                 ctypes.byref(opts) if opts else None,
+                                 ctypes.byref(config) if config else None), "ddgemm_batched")

@@ -35,16 +35,17 @@
 #include <cstdio>
 #include <mutex>
 
-#include "dd_device.cuh"
+#include "cascade_core.cuh"
 #include "ddgemm_internal.h"
 
 namespace ddg {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 8, NST = 3, NTHREADS = 256;
-constexpr int A_STAGE = 4 * BM * BK;                  // doubles
-constexpr int B_STAGE = 7 * BK * BN;                  // doubles
-constexpr int STAGE = A_STAGE + B_STAGE;
+using Tile = Fp64Tile<4, 2>;  // 64 x 64, 8 warps
+constexpr int BM = Tile::BM, BN = Tile::BN, BK = CBK, NST = 3, NTHREADS = Tile::NTHREADS;
+constexpr int A_STAGE = Tile::A_STAGE;
+constexpr int B_STAGE = Tile::B_STAGE;
+constexpr int STAGE = Tile::STAGE;
 constexpr uint32_t STAGE_BYTES = STAGE * sizeof(double);
 constexpr int STEPS_PER_BLOCK = KC / BK;
 constexpr size_t SMEM_BYTES = (size_t)NST * STAGE * sizeof(double) + NST * sizeof(uint64_t) + 1024;
@@ -101,13 +102,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// D = A B + D for one m8n8k4 f64 fragment.
-__device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
-    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
-                 : "+d"(d[0]), "+d"(d[1])
-                 : "d"(a), "d"(b));
-}
-
 template <bool DUMP_BINS>
 __global__ void __launch_bounds__(NTHREADS, 1)
 cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
@@ -140,13 +134,10 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
         for (int s = 0; s < NST && s < ksteps; ++s) issue(s, s);
     }
 
-    double acc[4][2][4][2];
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[b][i][j][0] = acc[b][i][j][1] = 0.0;
+    Acc acc;
+    zero_acc(acc);
+    const EpilogueOut out{args.m, args.n, args.exp_a, args.exp_b, args.c_hi, args.c_lo,
+                          args.ldc, args.flags, args.bins};
 
     for (int t = 0; t < ksteps; ++t) {
         const int stage = t % NST;
@@ -163,90 +154,12 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
             return;
         }
         const double *As = smem + stage * STAGE;
-        const double *Bs = As + A_STAGE;
-#pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-            double a[4][2];
-#pragma unroll
-            for (int s = 0; s < 4; ++s)
-#pragma unroll
-                for (int i = 0; i < 2; ++i)
-                    a[s][i] = As[s * BM * BK + (wm * 16 + i * 8 + (lane >> 2)) * BK + ks * 4 +
-                                 (lane & 3)];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                double b[7];
-#pragma unroll
-                for (int s = 0; s < 7; ++s)
-                    b[s] = Bs[s * BK * BN + (ks * 4 + (lane & 3)) * BN + wn * 32 + j * 8 +
-                              (lane >> 2)];
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    dmma(acc[0][i][j], a[0][i], b[0]);  // bin 0:   A0 B0
-                    dmma(acc[1][i][j], a[0][i], b[1]);  // bin 1:   A0 s1B1
-                    dmma(acc[1][i][j], a[1][i], b[0]);  //          s1A1 B0
-                    dmma(acc[2][i][j], a[0][i], b[2]);  // bin 2:   A0 s2B2
-                    dmma(acc[2][i][j], a[1][i], b[1]);  //          s1A1 s1B1
-                    dmma(acc[2][i][j], a[2][i], b[0]);  //          s2A2 B0
-                    dmma(acc[3][i][j], a[0][i], b[3]);  // bin 3-6: A0 s3B3
-                    dmma(acc[3][i][j], a[1][i], b[4]);  //          s1A1 s2B4
-                    dmma(acc[3][i][j], a[2][i], b[5]);  //          s2A2 s1B5
-                    dmma(acc[3][i][j], a[3][i], b[6]);  //          s3A3 B6
-                }
-            }
-        }
+        mma_stage<BM, BN>(acc, As, As + A_STAGE, wm, wn, lane);
         __syncthreads();  // every warp is done with this stage
         if (tid == 0 && t + NST < ksteps) issue(t + NST, stage);
 
         if ((t + 1) % STEPS_PER_BLOCK == 0 || t + 1 == ksteps) {
-            const int p = t / STEPS_PER_BLOCK;
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int row = m0 + wm * 16 + i * 8 + (lane >> 2);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int col = n0 + wn * 32 + j * 8 + 2 * (lane & 3) + h;
-                        if (row < args.m && col < args.n) {
-                            const double b0 = acc[0][i][j][h], b1 = acc[1][i][j][h];
-                            const double b2 = acc[2][i][j][h], b36 = acc[3][i][j][h];
-                            if constexpr (DUMP_BINS) {
-                                const long long mn = (long long)args.m * args.n;
-                                const long long o = (long long)row * args.n + col;
-                                args.bins[o] = b0;
-                                args.bins[mn + o] = b1;
-                                args.bins[2 * mn + o] = b2;
-                                args.bins[3 * mn + o] = b36;
-                            } else {
-                                double sh, sl;
-                                assemble_bins(b0, b1, b2, b36, sh, sl);
-                                const int sc = args.exp_a[(long long)p * args.m + row] +
-                                               args.exp_b[(long long)p * args.n + col];
-                                sh = scalbn(sh, sc);
-                                sl = scalbn(sl, sc);
-                                const long long o = (long long)row * args.ldc + col;
-                                double ch = 0.0, cl = 0.0;
-                                if (p > 0) {
-                                    ch = args.c_hi[o];
-                                    cl = args.c_lo[o];
-                                }
-                                dd_add(ch, cl, sh, sl, ch, cl);
-                                args.c_hi[o] = ch;
-                                args.c_lo[o] = cl;
-                                if (args.flags) {
-                                    const long long fo = (long long)row * args.n + col;
-                                    int f = p > 0 ? args.flags[fo] : 0;
-                                    if (b0 == 0.0 && (sh != 0.0 || sl != 0.0)) ++f;
-                                    args.flags[fo] = f;
-                                }
-                            }
-                        }
-                        acc[0][i][j][h] = acc[1][i][j][h] = 0.0;
-                        acc[2][i][j][h] = acc[3][i][j][h] = 0.0;
-                    }
-                }
-            }
+            epilogue<DUMP_BINS>(acc, t / STEPS_PER_BLOCK, m0 + wm * 16, n0 + wn * 32, lane, out);
             if constexpr (DUMP_BINS) return;
         }
     }

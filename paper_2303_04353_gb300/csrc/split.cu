@@ -1,94 +1,22 @@
 // Phase one of the cascade (Sec. "Practical considerations"): the fused
-// scale + split kernels.
+// scale + split kernels of the FP64 form.
 //
 // For every vector (a row of A or a column of B) and every k-block of
 // K_C = 256 entries, one pass finds sigma = 2^e with e the frexp exponent of
 // the largest |hi| in the block ("the smallest power of two greater than"
 // the largest element, Sec. "Cascading vectors and dot products"), and a
 // second pass over the same entries (L1/L2-resident) cascades each FP64x2
-// entry following Appendix A:
-//   scale hi and lo by 2^-e; for each of hi and lo: round to c0 digits by
-//   adding and subtracting 2^(53-c0) + 2^(52-c0), subtract, shift by 2^c0,
-//   repeat for c1 and c2, the remainder is the fourth piece; then add the
-//   hi and lo pieces (exact for pieces 0-2).
-// The pieces are written pre-multiplied by sigma_i (exact powers of two) in
-// the order of eq. Gemm10: A -> [A0, s1 A1, s2 A2, s3 A3];
-// B -> [B0, s1 B1, s2 B2, s3 B3, s2 B4, s1 B5, B6], with B4, B5, B6 the
-// FP64 roundings of the exact tails the split already holds.
-#include <cuda_runtime.h>
-#include <cmath>
-#include <cstdint>
-
-#include "dd_device.cuh"
-#include "ddgemm_internal.h"
+// entry following Appendix A (see split_device.cuh).  The pieces are written
+// pre-multiplied by sigma_i in the order of eq. Gemm10:
+// A -> [A0, s1 A1, s2 A2, s3 A3]; B -> [B0, s1 B1, s2 B2, s3 B3, s2 B4,
+// s1 B5, B6], with B4, B5, B6 the FP64 roundings of the exact tails the
+// split already holds.
+#include "split_device.cuh"
 
 namespace ddg {
 namespace {
 
-constexpr unsigned DEV_NONFINITE = 0x1u;
-
-// Appendix A round-to-d-digits constants 2^(53-d) + 2^(52-d).
-__device__ __forceinline__ double round_c0(double x) {
-    const double m = 3221225472.0;            // 2^31 + 2^30
-    return __dsub_rn(__dadd_rn(x, m), m);
-}
-__device__ __forceinline__ double round_c12(double x) {
-    const double m = 6442450944.0;            // 2^32 + 2^31
-    return __dsub_rn(__dadd_rn(x, m), m);
-}
-
-struct Pieces {
-    double x0, x1, x2, x3;  // the four splits
-    double r0, r1, r2;      // running values before each rounding stage
-};
-
-// Appendix A for one FP64 value already scaled by 2^-e.
-__device__ __forceinline__ Pieces split_fp64(double x) {
-    Pieces q;
-    q.r0 = x;
-    q.x0 = round_c0(q.r0);
-    q.r1 = __dmul_rn(__dsub_rn(q.r0, q.x0), 4194304.0);    // 2^22
-    q.x1 = round_c12(q.r1);
-    q.r2 = __dmul_rn(__dsub_rn(q.r1, q.x1), 2097152.0);    // 2^21
-    q.x2 = round_c12(q.r2);
-    q.x3 = __dmul_rn(__dsub_rn(q.r2, q.x2), 2097152.0);    // 2^21
-    return q;
-}
-
-// Cascade one FP64x2 entry with block exponent e into NS outputs.
-template <int NS>
-__device__ __forceinline__ void cascade_entry(double hi, double lo, int e, double (&o)[NS]) {
-    const Pieces h = split_fp64(scalbn(hi, -e));
-    const Pieces l = split_fp64(scalbn(lo, -e));
-    o[0] = __dadd_rn(h.x0, l.x0);
-    o[1] = __dmul_rn(__dadd_rn(h.x1, l.x1), 0x1p-22);
-    o[2] = __dmul_rn(__dadd_rn(h.x2, l.x2), 0x1p-43);
-    o[3] = __dmul_rn(__dadd_rn(h.x3, l.x3), 0x1p-64);
-    if constexpr (NS == 7) {
-        o[4] = __dmul_rn(__dadd_rn(h.r2, l.r2), 0x1p-43);  // s2 B4
-        o[5] = __dmul_rn(__dadd_rn(h.r1, l.r1), 0x1p-22);  // s1 B5
-        o[6] = __dadd_rn(h.r0, l.r0);                      // B6
-    }
-}
-
-__device__ __forceinline__ int block_exponent(double mx) {
-    int e = 0;
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
-    return e;
-}
-
-template <int NS>
-__device__ __forceinline__ void store_entry(double *out, long long ld_out, PanelLayout layout,
-                                            int nvec, int kdim, int v, int l,
-                                            const double (&o)[NS]) {
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        const long long idx = layout == PanelLayout::VEC_MAJOR
-                                  ? ((long long)s * nvec + v) * ld_out + l
-                                  : ((long long)s * kdim + l) * ld_out + v;
-        out[idx] = o[s];
-    }
-}
+using namespace split_detail;
 
 // Vectors run along memory (A not transposed, B transposed): one warp per
 // (vector, k-block); lanes read 16-byte pairs, 512 contiguous bytes per warp
@@ -103,48 +31,8 @@ split_contig_kernel(int nvec, int kdim, const double *__restrict__ xh,
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int kb = (kdim + KC - 1) / KC;
     if (warp >= (long long)nvec * kb) return;
-    const int v = (int)(warp / kb), p = (int)(warp % kb);
-    const double *rh = xh + (long long)v * ldx;
-    const double *rl = xl + (long long)v * ldx;
-    double h[8], lo[8];
-    double mx = 0.0;
-    bool bad = false;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const int l = p * KC + 64 * t + 2 * lane;
-        if (VEC && l + 1 < kdim) {
-            const double2 a = *reinterpret_cast<const double2 *>(rh + l);
-            const double2 b = *reinterpret_cast<const double2 *>(rl + l);
-            h[2 * t] = a.x; h[2 * t + 1] = a.y; lo[2 * t] = b.x; lo[2 * t + 1] = b.y;
-        } else {
-            h[2 * t] = l < kdim ? rh[l] : 0.0;
-            lo[2 * t] = l < kdim ? rl[l] : 0.0;
-            h[2 * t + 1] = l + 1 < kdim ? rh[l + 1] : 0.0;
-            lo[2 * t + 1] = l + 1 < kdim ? rl[l + 1] : 0.0;
-        }
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            mx = fmax(mx, fabs(h[2 * t + c]));
-            bad |= !isfinite(h[2 * t + c]) || !isfinite(lo[2 * t + c]);
-        }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    const int e = block_exponent(mx);
-    if (lane == 0) exps[(long long)p * nvec + v] = e;
-    if (bad && status) atomicOr(status, DEV_NONFINITE);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int l = p * KC + 64 * t + 2 * lane + c;
-            if (l < kdim) {
-                double o[NS];
-                cascade_entry<NS>(h[2 * t + c], lo[2 * t + c], e, o);
-                store_entry<NS>(out, ld_out, layout, nvec, kdim, v, l, o);
-            }
-        }
-    }
+    split_contig_unit<NS, VEC>(lane, (int)(warp / kb), (int)(warp % kb), nvec, kdim, xh, xl, ldx,
+                               out, ld_out, layout, exps, status);
 }
 
 // Vectors are strided in memory (B not transposed, A transposed): one CTA
@@ -158,60 +46,8 @@ split_strided_kernel(int nvec, int kdim, const double *__restrict__ xh,
                      unsigned int *status) {
     __shared__ double part[8][64];
     __shared__ int sexp[64];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int p = blockIdx.y;
-    const int v = blockIdx.x * 64 + 2 * tx;
-    const int lbeg = p * KC, lend = min(lbeg + KC, kdim);
-    auto load_pair = [&](const double *x, int l, double &a, double &b) {
-        const double *row = x + (long long)l * ldx;
-        if (VEC && v + 1 < nvec) {
-            const double2 q = *reinterpret_cast<const double2 *>(row + v);
-            a = q.x; b = q.y;
-        } else {
-            a = v < nvec ? row[v] : 0.0;
-            b = v + 1 < nvec ? row[v + 1] : 0.0;
-        }
-    };
-    double m0 = 0.0, m1 = 0.0;
-    for (int l = lbeg + ty; l < lend; l += 8) {
-        double a, b;
-        load_pair(xh, l, a, b);
-        m0 = fmax(m0, fabs(a));
-        m1 = fmax(m1, fabs(b));
-    }
-    part[ty][2 * tx] = m0;
-    part[ty][2 * tx + 1] = m1;
-    __syncthreads();
-    if (ty == 0) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            double mx = 0.0;
-#pragma unroll
-            for (int r = 0; r < 8; ++r) mx = fmax(mx, part[r][2 * tx + c]);
-            const int e = block_exponent(mx);
-            sexp[2 * tx + c] = e;
-            if (v + c < nvec) exps[(long long)p * nvec + v + c] = e;
-        }
-    }
-    __syncthreads();
-    const int e0 = sexp[2 * tx], e1 = sexp[2 * tx + 1];
-    bool bad = false;
-    for (int l = lbeg + ty; l < lend; l += 8) {
-        double ha, hb, la, lb;
-        load_pair(xh, l, ha, hb);
-        load_pair(xl, l, la, lb);
-        bad |= !isfinite(ha) || !isfinite(la) || !isfinite(hb) || !isfinite(lb);
-        double o[NS];
-        if (v < nvec) {
-            cascade_entry<NS>(ha, la, e0, o);
-            store_entry<NS>(out, ld_out, layout, nvec, kdim, v, l, o);
-        }
-        if (v + 1 < nvec) {
-            cascade_entry<NS>(hb, lb, e1, o);
-            store_entry<NS>(out, ld_out, layout, nvec, kdim, v + 1, l, o);
-        }
-    }
-    if (bad && status) atomicOr(status, DEV_NONFINITE);
+    split_strided_unit<NS, VEC>(blockIdx.x, blockIdx.y, nvec, kdim, xh, xl, ldx, out, ld_out,
+                                layout, exps, status, part, sexp);
 }
 
 template <int NS>

@@ -18,7 +18,7 @@ def _check_pair(hi: torch.Tensor, lo: torch.Tensor, name: str) -> int:
         raise ValueError(f"{name}: hi and lo must be CUDA tensors (there is no CPU path)")
     if hi.dim() != 2 or hi.shape != lo.shape or hi.stride() != lo.stride():
         raise ValueError(f"{name}: hi and lo must be 2-D with equal shape and strides")
-    if hi.shape[1] > 1 and hi.stride(1) != 1:
+    if hi.numel() > 0 and hi.shape[1] > 1 and hi.stride(1) != 1:
         raise ValueError(f"{name}: the last dimension must be contiguous")
     return max(hi.stride(0), hi.shape[1], 1)
 
@@ -179,3 +179,48 @@ def split_int8(x_hi, x_lo, *, as_b=False, trans=False, slices=16, stream=None, s
            exps.data_ptr(), status.data_ptr() if status is not None else 0,
            current_stream_ptr(stream))
     return digits[:, :, :k], exps
+
+
+class Batch:
+    """Many FP64x2 GEMMs C_i := A_i B_i run by one ddgemm_batched call.
+
+    ``problems`` is a list of (a_hi, a_lo, b_hi, b_lo, c_hi, c_lo) CUDA
+    tensors (row-major, unit last stride).  The constructor uploads the
+    problem descriptors and allocates the workspace (PyTorch memory), so
+    ``run()`` only enqueues the four launches and can be captured into a
+    CUDA graph.  The tensors must stay alive and in place while the batch is
+    used."""
+
+    def __init__(self, problems, device=None):
+        self.count = len(problems)
+        arr = (_lib.ddgemm_problem * max(self.count, 1))()
+        self.shapes = []
+        self._keep = []
+        for i, (a_hi, a_lo, b_hi, b_lo, c_hi, c_lo) in enumerate(problems):
+            lda = _check_pair(a_hi, a_lo, "A")
+            ldb = _check_pair(b_hi, b_lo, "B")
+            ldc = _check_pair(c_hi, c_lo, "C")
+            m, k = a_hi.shape
+            n = b_hi.shape[1]
+            if b_hi.shape[0] != k or tuple(c_hi.shape) != (m, n):
+                raise ValueError(f"problem {i}: shapes do not match")
+            arr[i] = _lib.ddgemm_problem(m, n, k, lda, ldb, ldc, a_hi.data_ptr(), a_lo.data_ptr(),
+                                         b_hi.data_ptr(), b_lo.data_ptr(), c_hi.data_ptr(),
+                                         c_lo.data_ptr())
+            self.shapes.append((m, n, k))
+            self._keep.append((a_hi, a_lo, b_hi, b_lo, c_hi, c_lo))
+        self.host = arr
+        dev = device or (problems[0][0].device if problems else "cuda")
+        raw = bytearray(ctypes.string_at(ctypes.addressof(arr), ctypes.sizeof(arr)))
+        self.dev = torch.frombuffer(raw, dtype=torch.uint8).to(dev)
+        nbytes = _lib.ddgemm_batched_workspace_size(self.count, arr, None)
+        self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+
+    def run(self, stream=None, config=None, status=None):
+        """Enqueue the batch.  config: None (library default), a
+        ddgemm_batch_config, or a (tile, order) pair."""
+        if config is not None and not isinstance(config, _lib.ddgemm_batch_config):
+            config = _lib.ddgemm_batch_config(*config)
+        opts = _lib.make_opts(status_dev=status.data_ptr()) if status is not None else None
+        _lib.ddgemm_batched(self.count, self.host, self.dev.data_ptr(), self.workspace.data_ptr(),
+                            self.workspace.numel(), current_stream_ptr(stream), opts, config)

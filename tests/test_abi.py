@@ -89,3 +89,26 @@ def test_ops_refuse_cpu_tensors():
     a = torch.zeros(2, 2, dtype=torch.float64)
     with pytest.raises(ValueError, match="CUDA"):
         ops.ddgemm(a, a, a, a)
+
+
+def test_batched_host_checks():
+    lib = _lib.load()
+    arr = (_lib.ddgemm_problem * 2)()
+    arr[0] = _lib.ddgemm_problem(4, 5, 6, 6, 5, 5, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+    arr[1] = _lib.ddgemm_problem(0, 5, 6, 6, 5, 5, 0, 0, 0, 0, 0, 0)
+    need = _lib.ddgemm_batched_workspace_size(2, arr)
+    assert need >= (4 * 4 * 8 + 7 * 6 * 8) * 8
+    # workspace too small / misaligned
+    assert lib.ddgemm_batched(2, arr, FAKE, FAKE, 16, None, None, None) == _lib.DDGEMM_EWORKSPACE
+    assert lib.ddgemm_batched(2, arr, FAKE, FAKE + 8, need, None, None, None) == _lib.DDGEMM_EWORKSPACE
+    # a bad problem (ldc < n), trans flags, bad config, empty batch
+    bad = (_lib.ddgemm_problem * 1)()
+    bad[0] = _lib.ddgemm_problem(4, 5, 6, 6, 5, 4, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+    assert lib.ddgemm_batched(1, bad, FAKE, FAKE, 1 << 30, None, None, None) == _lib.DDGEMM_EINVAL
+    o = _lib.make_opts(trans_a=True)
+    assert lib.ddgemm_batched(2, arr, FAKE, FAKE, need, None, ctypes.byref(o), None) == \
+        _lib.DDGEMM_EUNSUPPORTED
+    cfg = _lib.ddgemm_batch_config(9, 0)
+    assert lib.ddgemm_batched(2, arr, FAKE, FAKE, need, None, None, ctypes.byref(cfg)) == \
+        _lib.DDGEMM_EINVAL
+    assert lib.ddgemm_batched(0, None, None, None, 0, None, None, None) == _lib.DDGEMM_OK

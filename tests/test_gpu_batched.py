@@ -1,0 +1,151 @@
+"""The batched form: many problems in one pass (plan, two batched splits,
+one persistent cascade kernel), captured into a CUDA graph.
+
+The per-tile arithmetic is the single-problem kernel's and the k order is
+the same, so each problem's C must be bit-identical to ddgemm() on that
+problem alone, for every tile shape and schedule; ddgemm itself is checked
+against the oracles in test_gpu_parity.py, and a few problems here are
+checked against the double-double oracle directly."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import dd  # noqa: E402
+from workloads import batched_shapes, gemm_inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+MIXED = [(64, 64, 256), (100, 70, 300), (1, 1, 1), (3, 200, 17), (0, 5, 7), (6, 0, 9),
+         (9, 11, 0), (130, 65, 513), (33, 97, 64), (256, 32, 1024), (17, 300, 250), (64, 1, 65)]
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_04353_gb300 import _lib, autotune, ops
+    return _lib, ops, autotune
+
+
+def make_batch(ops, shapes, seed=0, kind="uniform"):
+    probs, host = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        a = gemm_inputs(m, n, k, kind=kind, seed=seed + i)
+        t = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in a]
+        c = [torch.full((m, n), np.nan, dtype=torch.float64, device="cuda") for _ in range(2)]
+        probs.append((*t, *c))
+        host.append(a)
+    return ops.Batch(probs), probs, host
+
+
+def reference(ops, probs):
+    out = []
+    for a_hi, a_lo, b_hi, b_lo, _, _ in probs:
+        c_hi, c_lo = ops.ddgemm(a_hi, a_lo, b_hi, b_lo)
+        out.append((c_hi, c_lo))
+    torch.cuda.synchronize()
+    return [(h.cpu().numpy(), l.cpu().numpy()) for h, l in out]
+
+
+def results(probs):
+    torch.cuda.synchronize()
+    return [(p[4].cpu().numpy(), p[5].cpu().numpy()) for p in probs]
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+@pytest.mark.parametrize("order", [0, 1])
+def test_batched_bit_identical_to_ddgemm(mods, tile, order):
+    _lib, ops, _ = mods
+    batch, probs, _ = make_batch(ops, MIXED, seed=10, kind="wide")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    batch.run(config=(tile, order), status=status)
+    got = results(probs)
+    want = reference(ops, probs)
+    assert int(status.item()) == 0
+    for (gh, gl), (wh, wl), (m, n, k) in zip(got, want, MIXED):
+        if m == 0 or n == 0:
+            continue
+        if k == 0:
+            assert not gh.any() and not gl.any()
+        assert np.array_equal(gh, wh) and np.array_equal(gl, wl), (m, n, k)
+
+
+def test_batched_against_oracle(mods):
+    _lib, ops, _ = mods
+    shapes = [(100, 70, 300), (37, 53, 600), (5, 9, 1000)]
+    batch, probs, host = make_batch(ops, shapes, seed=20)
+    batch.run()
+    for (ch, cl), a in zip(results(probs), host):
+        oh, ol = dd.ddgemm(*a)
+        absab = np.abs(a[0]) @ np.abs(a[2])
+        assert np.all(np.abs((ch - oh) + (cl - ol)) <= 1e-28 * absab)
+
+
+def test_batched_graph_capture_and_replay(mods):
+    _lib, ops, _ = mods
+    batch, probs, _ = make_batch(ops, MIXED[:8], seed=30)
+    batch.run()                      # eager once (sets kernel attributes)
+    eager = results(probs)
+    for p in probs:
+        p[4].fill_(np.nan)
+        p[5].fill_(np.nan)
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=stream):
+        batch.run(stream=torch.cuda.current_stream())
+    g.replay()
+    replayed = results(probs)
+    for (eh, el), (rh, rl), (m, n, k) in zip(eager, replayed, MIXED[:8]):
+        if m and n:
+            assert np.array_equal(eh, rh) and np.array_equal(el, rl)
+    # new values in the same buffers: the graph recomputes them
+    for p in probs:
+        for x in p[:4]:
+            x.mul_(0.5)
+    g.replay()
+    halved = results(probs)
+    want = reference(ops, probs)
+    for (hh, hl), (wh, wl), (m, n, k) in zip(halved, want, MIXED[:8]):
+        if m and n:
+            assert np.array_equal(hh, wh) and np.array_equal(hl, wl)
+
+
+def test_batched_512_uneven_problems(mods):
+    """512 problems, m, n, k each log-uniform in [64, 1024], uniform entries:
+    every problem bit-identical to ddgemm, three against the oracle."""
+    _lib, ops, _ = mods
+    shapes = [tuple(int(v) for v in s) for s in batched_shapes(512, seed=0)]
+    batch, probs, host = make_batch(ops, shapes, seed=1000)
+    batch.run()
+    got = results(probs)
+    want = reference(ops, probs)
+    for (gh, gl), (wh, wl) in zip(got, want):
+        assert np.array_equal(gh, wh) and np.array_equal(gl, wl)
+    for i in (0, 255, 511):
+        a = host[i]
+        rows = np.arange(0, shapes[i][0], max(1, shapes[i][0] // 8))
+        cols = np.arange(0, shapes[i][1], max(1, shapes[i][1] // 8))
+        rr, cc = np.meshgrid(rows, cols, indexing="ij")
+        oh, ol = dd.ddgemm_entries(*a, rr.ravel(), cc.ravel())
+        absab = np.array([np.abs(a[0][r]) @ np.abs(a[2][:, c]) for r, c in zip(rr.ravel(), cc.ravel())])
+        gh, gl = got[i]
+        assert np.all(np.abs((gh[rr.ravel(), cc.ravel()] - oh) + (gl[rr.ravel(), cc.ravel()] - ol))
+                      <= 1e-28 * absab)
+
+
+def test_autotuner_picks_and_caches(mods, tmp_path, monkeypatch):
+    _lib, ops, autotune = mods
+    monkeypatch.setenv("DDGEMM_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    batch, probs, _ = make_batch(ops, MIXED, seed=40)
+    cfg, timings = autotune.tune(batch, reps=1)
+    assert cfg in autotune.CANDIDATES and len(timings) == len(autotune.CANDIDATES)
+    assert all(v > 0 for v in timings.values())
+    cfg2, _ = autotune.tune(batch, reps=1)           # served from the cache
+    assert cfg2 == cfg and (tmp_path / "tune.json").exists()
+    batch.run(config=cfg)
+    want = reference(ops, probs)
+    for (gh, gl), (wh, wl), (m, n, k) in zip(results(probs), want, MIXED):
+        if m and n:
+            assert np.array_equal(gh, wh) and np.array_equal(gl, wl)
