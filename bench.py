@@ -67,6 +67,24 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Largest value over the ranks (the slowest replica's time); the
+    identity for one process.  Works on gloo (CPU tensors) and NCCL."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job rate of independent replicas: all ranks' units over the
+    slowest rank's time (units per second)."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
 def physical_index(local: int) -> int:
     """nvidia-smi index of this rank's GPU."""
     vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
@@ -263,14 +281,10 @@ def run_ours(args, wl):
     elapsed_ms = t_start.elapsed_time(t_end)
     split_ms = sum(ev[0].elapsed_time(ev[1]) for ev in phase) / args.steps
     casc_ms = sum(ev[1].elapsed_time(ev[2]) for ev in phase) / args.steps
-    if world > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([elapsed_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = reduce_max(elapsed_ms, world, dev)
     ms_per_step = elapsed_ms / args.steps
     flops_dd = 2.0 * m * n * k
-    value = world * flops_dd / (ms_per_step * 1e-3) / 1e9
+    value = replica_rate(flops_dd, world, ms_per_step) / 1e9
     st = int(status.item())
     if st:
         raise SystemExit(f"bench.py: device status {st:#x} (non-finite input or timeout)")
@@ -302,12 +316,7 @@ def run_ours(args, wl):
         host_out[1].copy_(c_lo, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if world > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([e2e_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = reduce_max(e0.elapsed_time(e1) / e2e_steps, world, dev)
     h2d = sum(h.numel() * 8 for h in host_in)
     d2h = 2 * m * n * 8
 
@@ -371,7 +380,7 @@ def run_ours(args, wl):
         "max_err_vs_dd_oracle": max_err,
         "phases_ms": {"split": round(split_ms, 3), "products_and_assembly": round(casc_ms, 3)},
         "roofline": roofline,
-        "e2e": {"value": round(world * flops_dd / (e2e_ms * 1e-3) / 1e9, 4), "unit": "GFLOP/s",
+        "e2e": {"value": round(replica_rate(flops_dd, world, e2e_ms) / 1e9, 4), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
