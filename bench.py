@@ -46,6 +46,12 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NOMINAL_FP64_TFLOPS = 1.25
 NOMINAL_BF16_TFLOPS = 2250.0
 
+# DRAM bytes per launch (read + write) of the dominant kernel, from one ncu
+# capture of the current kernels at 4096^3 (profiles/dram_traffic_4096.md);
+# other workloads report null.
+TRAFFIC_4096 = {"cascade_fp64_kernel": 9.884050e9 + 0.282231e9,
+                "cascade_int8_kernel<16>": 3.528115e9 + 0.269681e9}
+
 WORKLOADS = {
     "4096": dict(m=4096, n=4096, k=4096, kind="wide",
                  name="ddgemm 4096x4096x4096 FP64x2, hi log-uniform 2^-20..2^20, seed 0"),
@@ -338,6 +344,35 @@ def run_ours(args, wl):
     probe_tops = probe(_lib.ddgemm_probe_int8, (200, 4000, 4000, 4000)) \
         if variant == _lib.DDGEMM_VARIANT_INT8 else None
 
+    # ---- the INT8 form on the same inputs (one line, both forms) ----------
+    int8_form = None
+    if variant == _lib.DDGEMM_VARIANT_FP64 and not args.no_int8_form:
+        ws8 = ops.alloc_workspace(m, n, k, dev, _lib.DDGEMM_VARIANT_INT8, 16)
+        c8 = (torch.empty((m, n), dtype=torch.float64, device=dev),
+              torch.empty((m, n), dtype=torch.float64, device=dev))
+
+        def step8():
+            ops.ddgemm(*d_in, out=c8, workspace=ws8, stream=stream,
+                       variant=_lib.DDGEMM_VARIANT_INT8, int8_slices=16)
+        for _ in range(args.warmup):
+            step8()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step8()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms8 = reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
+        h8, l8 = c8[0].cpu().numpy(), c8[1].cpu().numpy()
+        err8 = np.abs((h8[rows, cols] - oh) + (l8[rows, cols] - ol))
+        int8_form = {"pieces": 16, "products": 136, "ms_per_step": round(ms8, 3),
+                     "value": round(replica_rate(flops_dd, world, ms8) / 1e9, 4),
+                     "unit": "GFLOP/s",
+                     "max_err_vs_dd_oracle": float(np.max(err8 / absab)),
+                     "speedup_vs_fp64_form": round(ms_per_step / ms8, 3)}
+
     if rank != 0:
         return
     peak, peak_src = fp64_peak_rule()
@@ -347,7 +382,9 @@ def run_ours(args, wl):
         achieved = prods * flops_dd / (casc_ms * 1e-3) / 1e12
         roofline = {"bound": "tensor", "kernel": f"cascade_int8_kernel<{s8}>",
                     "achieved": round(achieved, 3), "peak": round(probe_tops, 3), "unit": "TOPS",
-                    "frac": round(achieved / probe_tops, 4), "traffic": None,
+                    "frac": round(achieved / probe_tops, 4),
+                    "traffic": TRAFFIC_4096.get(f"cascade_int8_kernel<{s8}>")
+                    if args.workload == "4096" else None,
                     "peak_source": "of measured: live mma.sync s8 probe in this run (no INT8 "
                                    "figure in MEASURED_PEAKS.json)",
                     "algorithmic": f"{prods} x 2mnk = {prods * flops_dd:.4g} INT8 ops per launch"}
@@ -355,7 +392,9 @@ def run_ours(args, wl):
         achieved = 10.0 * flops_dd / (casc_ms * 1e-3) / 1e12
         roofline = {"bound": "tensor", "kernel": "cascade_fp64_kernel",
                     "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "frac": round(achieved / peak, 4),
+                    "traffic": TRAFFIC_4096["cascade_fp64_kernel"]
+                    if args.workload == "4096" else None,
                     "peak_source": peak_src,
                     "probe_peak": round(probe_tflops, 4),
                     "frac_vs_probe": round(achieved / probe_tflops, 4),
@@ -385,6 +424,8 @@ def run_ours(args, wl):
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
+    if int8_form is not None:
+        line["int8_form"] = int8_form
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a_hi, a_lo, b_hi, b_lo)
     print(json.dumps(line), flush=True)
@@ -538,6 +579,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default="4096")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-int8-form", action="store_true",
+                    help="skip the INT8 form's entry in the FP64 line")
     ap.add_argument("--variant", choices=("fp64", "int8"), default="fp64",
                     help="fp64: the ten FP64 products (default); int8: the INT8 form")
     ap.add_argument("--int8-slices", type=int, default=16)

@@ -113,7 +113,9 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp & 3, wn = warp >> 2;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    int tm, tn;
+    grouped_tile(blockIdx.x, (args.m + BM - 1) / BM, (args.n + BN - 1) / BN, 8, tm, tn);
+    const int m0 = tm * BM, n0 = tn * BN;
     const int ksteps = (args.k + BK - 1) / BK;
 
     if (tid == 0) {
@@ -206,9 +208,9 @@ cudaError_t launch_impl(const CascadeArgs &a, cudaStream_t stream) {
     const cudaError_t attr_err = cudaFuncSetAttribute(
         cascade_fp64_kernel<DUMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (attr_err != cudaSuccess) return attr_err;
-    const dim3 grid((a.n + BN - 1) / BN, (a.m + BM - 1) / BM);
-    if (grid.y > 65535) return cudaErrorInvalidValue;
-    cascade_fp64_kernel<DUMP><<<grid, NTHREADS, SMEM_BYTES, stream>>>(tm_a, tm_b, a);
+    const long long tiles = (long long)((a.n + BN - 1) / BN) * ((a.m + BM - 1) / BM);
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    cascade_fp64_kernel<DUMP><<<(unsigned)tiles, NTHREADS, SMEM_BYTES, stream>>>(tm_a, tm_b, a);
     return cudaGetLastError();
 }
 

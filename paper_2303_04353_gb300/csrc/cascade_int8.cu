@@ -120,7 +120,9 @@ cascade_int8_kernel(const __grid_constant__ CUtensorMap tm_a,
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp & 1, wn = warp >> 1;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    int tm, tn;
+    grouped_tile(blockIdx.x, (args.m + BM - 1) / BM, (args.n + BN - 1) / BN, 16, tm, tn);
+    const int m0 = tm * BM, n0 = tn * BN;
     const int ksteps = (args.k + BKB - 1) / BKB;
     constexpr int STEPS_PER_BLOCK = KB8 / BKB;
 
@@ -254,9 +256,9 @@ cudaError_t launch_s(const Int8Args &a, cudaStream_t stream) {
     const cudaError_t e = cudaFuncSetAttribute(
         cascade_int8_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
     if (e != cudaSuccess) return e;
-    const dim3 grid((a.n + BN - 1) / BN, (a.m + BM - 1) / BM);
-    if (grid.y > 65535) return cudaErrorInvalidValue;
-    cascade_int8_kernel<S><<<grid, NTHREADS, G::SMEM, stream>>>(tm_a, tm_b, a);
+    const long long tiles = (long long)((a.n + BN - 1) / BN) * ((a.m + BM - 1) / BM);
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    cascade_int8_kernel<S><<<(unsigned)tiles, NTHREADS, G::SMEM, stream>>>(tm_a, tm_b, a);
     return cudaGetLastError();
 }
 

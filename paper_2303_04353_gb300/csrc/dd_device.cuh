@@ -55,4 +55,18 @@ __device__ __forceinline__ void assemble_bins(double b0, double b1, double b2, d
     dd_add_d(h, l, b0);
 }
 
+// Tile order for L2 reuse: consecutive CTAs walk down `group` row tiles of
+// one column, then the next column, so a wave of CTAs shares a few row
+// panels of A and a few column panels of B.  bid in [0, tiles_m * tiles_n).
+__device__ __forceinline__ void grouped_tile(unsigned bid, int tiles_m, int tiles_n, int group,
+                                             int &tm, int &tn) {
+    const unsigned per_group = (unsigned)group * (unsigned)tiles_n;
+    const int g = (int)(bid / per_group);
+    const int first = g * group;
+    const int rows = min(group, tiles_m - first);
+    const unsigned r = bid % per_group;
+    tm = first + (int)(r % (unsigned)rows);
+    tn = (int)(r / (unsigned)rows);
+}
+
 }  // namespace ddg

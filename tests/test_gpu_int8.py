@@ -114,3 +114,42 @@ def test_int8_full_size_sampled(ops, m, n, k, kind):
         ex = exact.exact_dot(a_hi[i], a_lo[i], b_hi[:, j], b_lo[:, j])
         bound = int8_bound(a_hi[i:i + 1], b_hi[:, j:j + 1], 16)[0, 0]
         assert exact.err_vs_exact(c_hi[i, j], c_lo[i, j], ex) <= bound
+
+
+def test_int8_backward_matches_int8_forward_products(ops):
+    """ddgemm_backward with the INT8 variant: dA = W B^T and dB = A^T W are
+    the INT8 form's products of those operands, bit for bit."""
+    from paper_2303_04353_gb300 import _lib
+    m, n, k = 40, 30, 90
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind="wide", seed=50)
+    w_hi, w_lo = gemm_inputs(m, 1, n, seed=51)[0:2]          # an m x n FP64x2 matrix
+    ta = dev(a_hi, a_lo, b_hi, b_lo, w_hi, w_lo)
+    opts = _lib.make_opts(variant=INT8)
+    ws = torch.empty(_lib.ddgemm_backward_workspace_size(m, n, k, opts), dtype=torch.uint8,
+                     device="cuda")
+    da = [torch.empty((m, k), dtype=torch.float64, device="cuda") for _ in range(2)]
+    db = [torch.empty((k, n), dtype=torch.float64, device="cuda") for _ in range(2)]
+    _lib.ddgemm_backward(m, n, k, ta[0].data_ptr(), ta[1].data_ptr(), k, ta[2].data_ptr(),
+                         ta[3].data_ptr(), n, ta[4].data_ptr(), ta[5].data_ptr(), n,
+                         da[0].data_ptr(), da[1].data_ptr(), k, db[0].data_ptr(),
+                         db[1].data_ptr(), n, ws.data_ptr(), ws.numel(),
+                         torch.cuda.current_stream().cuda_stream, opts)
+    da_hi, da_lo, db_hi, db_lo = host(*da, *db)
+    want = c8.cascade_int8_ddgemm(w_hi, w_lo, b_hi.T, b_lo.T, s=16)
+    assert np.array_equal(da_hi, want[0]) and np.array_equal(da_lo, want[1])
+    want = c8.cascade_int8_ddgemm(a_hi.T, a_lo.T, w_hi, w_lo, s=16)
+    assert np.array_equal(db_hi, want[0]) and np.array_equal(db_lo, want[1])
+
+
+def test_int8_noalloc_matches_int8_ddgemm(ops):
+    from paper_2303_04353_gb300 import _lib
+    m, n, k = 120, 90, 300
+    a = gemm_inputs(m, n, k, kind="wide", seed=52)
+    t = dev(*a)
+    c = [torch.empty((m, n), dtype=torch.float64, device="cuda") for _ in range(2)]
+    _lib.ddgemm_noalloc(m, n, k, t[0].data_ptr(), t[1].data_ptr(), k, t[2].data_ptr(),
+                        t[3].data_ptr(), n, c[0].data_ptr(), c[1].data_ptr(), n,
+                        torch.cuda.current_stream().cuda_stream, _lib.make_opts(variant=INT8))
+    got = host(*c)
+    want = c8.cascade_int8_ddgemm(*a, s=16)
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])

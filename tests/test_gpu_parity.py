@@ -248,3 +248,44 @@ def test_full_size_sampled(ops, m, n, k):
     for t in range(8):
         ex = exact.exact_dot(a_hi[rows[t]], a_lo[rows[t]], b_hi[:, cols[t]], b_lo[:, cols[t]])
         assert exact.err_vs_exact(got_hi[t], got_lo[t], ex) <= CONTRACT * absab[t]
+
+
+def test_discussion_example_flags_and_exact(ops):
+    from tests.test_oracle_discussion import read_example
+    x, y, closed = read_example()
+    z = np.zeros_like(x)
+    flags = torch.full((1, 1), -1, dtype=torch.int32, device="cuda")
+    c_hi, c_lo = ops.ddgemm(*dev(x[None, :], z[None, :], y[:, None], z[:, None]), flags=flags)
+    c_hi, c_lo, f = host(c_hi, c_lo, flags)
+    from fractions import Fraction
+    assert Fraction(c_hi[0, 0]) + Fraction(c_lo[0, 0]) == closed
+    assert f[0, 0] == 1                      # bin 0 cancelled in the single k-block
+    c_hi, c_lo = host(*ops.ddgemm(*dev(x[None, :], z[None, :], y[:, None], z[:, None]),
+                                  variant=1))
+    assert Fraction(c_hi[0, 0]) + Fraction(c_lo[0, 0]) == closed
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_unaligned_strided_views(ops, variant):
+    """Operands that are column slices of wider arrays: leading dimensions
+    above the row length and base addresses off the 16-byte grid, so the
+    splits take their scalar-load path.  Same result as contiguous copies."""
+    m, n, k = 70, 45, 300
+    a = gemm_inputs(m, n, k, kind="wide", seed=60)
+    big = [np.zeros((x.shape[0], x.shape[1] + 3)) for x in a]
+    for b_, x in zip(big, a):
+        b_[:, 1:1 + x.shape[1]] = x
+    t = [torch.from_numpy(b_).cuda()[:, 1:1 + x.shape[1]] for b_, x in zip(big, a)]
+    assert t[0].stride(0) == k + 3 and t[0].data_ptr() % 16 != 0
+    got = host(*ops.ddgemm(*t, variant=variant))
+    want = host(*ops.ddgemm(*dev(*a), variant=variant))
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
+def test_nonfinite_sets_status_int8(ops):
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(20, 20, 40, seed=3)
+    b_lo[7, 2] = np.nan
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ops.ddgemm(*dev(a_hi, a_lo, b_hi, b_lo), status=status, variant=1)
+    (st,) = host(status)
+    assert st[0] & 0x1
