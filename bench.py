@@ -373,6 +373,31 @@ def run_ours(args, wl):
                      "max_err_vs_dd_oracle": float(np.max(err8 / absab)),
                      "speedup_vs_fp64_form": round(ms_per_step / ms8, 3)}
 
+    # ---- yardstick: a plain FP64 GEMM of the same shape (cuBLAS DGEMM via
+    # torch.matmul), the unit of the paper's "10-13x DGEMM time" claim ------
+    dgemm = None
+    if variant == _lib.DDGEMM_VARIANT_FP64 and not args.no_int8_form:
+        x, y = d_in[0], d_in[2]
+        z = torch.empty((m, n), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            torch.matmul(x, y, out=z)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            torch.matmul(x, y, out=z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dg_ms = e0.elapsed_time(e1) / 3
+        dgemm = {"ms": round(dg_ms, 3), "tflops": round(flops_dd / (dg_ms * 1e-3) / 1e12, 4),
+                 "fp64_form_over_dgemm": round(ms_per_step / dg_ms, 3),
+                 "what": "cuBLAS DGEMM (torch.matmul, float64) on A_hi, B_hi: a yardstick, "
+                         "not part of the path"}
+        if int8_form is not None:
+            dgemm["int8_form_over_dgemm"] = round(int8_form["ms_per_step"] / dg_ms, 3)
+        del z
+
     if rank != 0:
         return
     peak, peak_src = fp64_peak_rule()
@@ -426,6 +451,8 @@ def run_ours(args, wl):
     }
     if int8_form is not None:
         line["int8_form"] = int8_form
+    if dgemm is not None:
+        line["dgemm_yardstick"] = dgemm
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a_hi, a_lo, b_hi, b_lo)
     print(json.dumps(line), flush=True)
