@@ -552,6 +552,47 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ablation(args):
+    """Study of eq. (Gemm16) against eq. (Gemm10): the ten folded products
+    (the method), all sixteen products, and ten products with bins 4-6
+    dropped, on the same GPU and inputs: max error against the
+    double-double oracle on sampled entries, and time.  Study lines, not the
+    benchmark line."""
+    import torch
+
+    from oracle import dd
+    from paper_2303_04353_gb300 import _lib, ops
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    m = n = k = args.sweep_size
+    rng = np.random.default_rng(5)
+    rows, cols = rng.integers(0, m, 128), rng.integers(0, n, 128)
+    for kind in ("uniform", "wide"):
+        a = gemm_inputs(m, n, k, kind=kind, seed=0)
+        d_in = [torch.from_numpy(x).to(dev) for x in a]
+        oh, ol = dd.ddgemm_entries(*a, rows, cols)
+        absab = np.array([np.abs(a[0][i]) @ np.abs(a[2][:, j]) for i, j in zip(rows, cols)])
+        for name, variant in (("gemm10 (method)", _lib.DDGEMM_VARIANT_FP64),
+                              ("gemm16", _lib.DDGEMM_VARIANT_FP64_GEMM16),
+                              ("drop bins 4-6", _lib.DDGEMM_VARIANT_FP64_DROP456)):
+            out = ops.ddgemm(*d_in, variant=variant)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = ops.ddgemm(*d_in, variant=variant, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ch, cl = out[0].cpu().numpy(), out[1].cpu().numpy()
+            err = np.abs((ch[rows, cols] - oh) + (cl[rows, cols] - ol)) / absab
+            print(json.dumps({"study": "Gemm10 vs Gemm16 vs dropped bins", "size": m,
+                              "entries": kind, "form": name,
+                              "ms": round(e0.elapsed_time(e1), 3),
+                              "max_err_rel_absAabsB": float(err.max()),
+                              "median_err_rel_absAabsB": float(np.median(err))}), flush=True)
+
+
 def run_sweep(args):
     """Config-2 study: error and throughput of the FP64 form and the INT8
     form as the exponent spread of the entries grows (hi = +-2^u,
@@ -614,9 +655,14 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="exponent-spread study of both forms instead of the benchmark line")
     ap.add_argument("--sweep-size", type=int, default=2048)
+    ap.add_argument("--ablation", action="store_true",
+                    help="Gemm10 / Gemm16 / dropped-bins accuracy study instead of the line")
     args = ap.parse_args()
     if args.sweep:
         run_sweep(args)
+        return
+    if args.ablation:
+        run_ablation(args)
         return
     if args.workload == "batched":
         run_batched(args)

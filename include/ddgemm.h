@@ -59,6 +59,10 @@ extern "C" {
 /* opts->variant */
 #define DDGEMM_VARIANT_FP64  0    /* ten FP64 products on the FP64 tensor path */
 #define DDGEMM_VARIANT_INT8  1    /* the cascade re-sliced into INT8 pieces (below) */
+/* Accuracy ablations of the FP64 form (same pieces, other products): */
+#define DDGEMM_VARIANT_FP64_GEMM16  2 /* all sixteen products of eq. Gemm16 */
+#define DDGEMM_VARIANT_FP64_DROP456 3 /* bins 0-3 of eq. Gemm16 only: bins 4-6
+                                         dropped (ten products, not folded) */
 
 typedef struct ddgemm_opts {
     /* 0: A is m x k (lda >= k).  1: A is stored k x m (lda >= m) and the

@@ -161,6 +161,42 @@ def ten_products(As, Bs):
     return bin0, bin1, bin2, bin36
 
 
+def sixteen_products(As, Bs):
+    """Eq. (Gemm16): all sixteen products; bins 0-2 as in eq. (Gemm10), and
+    every lower product (bins 3-6) summed in FP64 in the order of the
+    equation's rows: s3 A0 B3; s1 s2 A1 B2, s1 s3 A1 B3; s2 s1 A2 B1,
+    s2^2 A2 B2, s2 s3 A2 B3; s3 A3 B0, s3 s1 A3 B1, s3 s2 A3 B2, s3^2 A3 B3.
+    (Accuracy ablation; the method itself is ten_products.)"""
+    a0, a1, a2, a3 = As
+    b0, b1, b2, b3 = Bs[:4]
+    bin0 = a0 @ b0
+    bin1 = a0 @ b1 + a1 @ b0
+    bin2 = (a0 @ b2 + a1 @ b1) + a2 @ b0
+    lower = [a0 @ b3, a1 @ b2, a1 @ b3, a2 @ b1, a2 @ b2, a2 @ b3, a3 @ b0, a3 @ b1, a3 @ b2,
+             a3 @ b3]
+    bin36 = lower[0]
+    for t in lower[1:]:
+        bin36 = bin36 + t
+    return bin0, bin1, bin2, bin36
+
+
+def dropped_products(As, Bs):
+    """Ten products by dropping bins 4-6 altogether: bins 0-3 of eq. (Gemm16)
+    only (the alternative the paper contrasts with folding bins 3-6 into
+    four products).  Accuracy ablation."""
+    a0, a1, a2, a3 = As
+    b0, b1, b2, b3 = Bs[:4]
+    bin0 = a0 @ b0
+    bin1 = a0 @ b1 + a1 @ b0
+    bin2 = (a0 @ b2 + a1 @ b1) + a2 @ b0
+    bin3 = ((a0 @ b3 + a1 @ b2) + a2 @ b1) + a3 @ b0
+    return bin0, bin1, bin2, bin3
+
+
+PRODUCT_RULES = {"gemm10": "ten_products", "gemm16": "sixteen_products",
+                 "drop456": "dropped_products"}
+
+
 def two_sum(a, b):
     """Knuth TwoSum, element-wise: s + e == a + b exactly."""
     s = a + b
@@ -202,13 +238,14 @@ def assemble_bins(bin0, bin1, bin2, bin36):
     return h, l
 
 
-def cascade_ddgemm(a_hi, a_lo, b_hi, b_lo, kc=KC, return_bins=False):
+def cascade_ddgemm(a_hi, a_lo, b_hi, b_lo, kc=KC, return_bins=False, products="gemm10"):
     """C := A B approximated by the ten-GEMM cascade, k staged by K_C.
 
     Sec. "Simple": C is built as a sequence of rank-K_C updates; each update
     is cascaded, computed as ten FP64 products into four bins, assembled in
     FP64x2, scaled by Sigma and T (exact powers of two), and added into C in
-    FP64x2.  Row-major float64 inputs; returns (C_hi, C_lo)."""
+    FP64x2.  Row-major float64 inputs; returns (C_hi, C_lo).  `products`
+    selects eq. (Gemm10) (the method), eq. (Gemm16) or dropping bins 4-6."""
     a_hi = np.asarray(a_hi, np.float64)
     a_lo = np.asarray(a_lo, np.float64)
     b_hi = np.asarray(b_hi, np.float64)
@@ -223,7 +260,7 @@ def cascade_ddgemm(a_hi, a_lo, b_hi, b_lo, kc=KC, return_bins=False):
     for p in range((k + kc - 1) // kc):
         As = cascade_a(a_hi, a_lo, e_a, p, kc)
         Bs = cascade_b(b_hi, b_lo, e_b, p, kc)
-        b4 = ten_products(As, Bs)
+        b4 = globals()[PRODUCT_RULES[products]](As, Bs)
         if return_bins:
             bins.append(b4)
         h, l = assemble_bins(*b4)

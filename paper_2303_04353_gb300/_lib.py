@@ -21,6 +21,8 @@ DDGEMM_DEV_NONFINITE = 0x1
 DDGEMM_DEV_TIMEOUT = 0x2
 DDGEMM_VARIANT_FP64 = 0
 DDGEMM_VARIANT_INT8 = 1
+DDGEMM_VARIANT_FP64_GEMM16 = 2
+DDGEMM_VARIANT_FP64_DROP456 = 3
 
 
 class DdgemmError(RuntimeError):

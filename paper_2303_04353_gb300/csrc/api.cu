@@ -115,8 +115,11 @@ int run(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
     e = ddg::launch_split(7, n, k, B_hi, B_lo, ldb, p.trans_b != 0, b_s, L.ldb_s,
                           ddg::PanelLayout::K_MAJOR, e_b, p.status, stream);
     if (e != cudaSuccess || !mark(1)) return DDGEMM_ECUDA;
+    const int products = p.variant == DDGEMM_VARIANT_FP64_GEMM16    ? 1
+                         : p.variant == DDGEMM_VARIANT_FP64_DROP456 ? 2
+                                                                      : 0;
     ddg::CascadeArgs ca{m, n, k, a_s, L.lda_s, b_s, L.ldb_s, e_a, e_b, C_hi, C_lo,
-                        (long long)ldc, p.flags, p.status, bins};
+                        (long long)ldc, p.flags, p.status, bins, products};
     e = ddg::launch_cascade_fp64(ca, stream);
     return e == cudaSuccess && mark(2) ? DDGEMM_OK : DDGEMM_ECUDA;
 }
@@ -165,7 +168,7 @@ int ddgemm(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
            void *workspace, size_t ws_bytes, void *stream, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
-    if (p.variant != DDGEMM_VARIANT_FP64 && p.variant != DDGEMM_VARIANT_INT8)
+    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_FP64_DROP456)
         return DDGEMM_EUNSUPPORTED;
     if (p.variant == DDGEMM_VARIANT_INT8 && p.flags) return DDGEMM_EUNSUPPORTED;
     if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;

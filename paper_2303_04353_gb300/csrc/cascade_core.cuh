@@ -42,10 +42,17 @@ __device__ __forceinline__ void zero_acc(Acc &acc) {
             for (int j = 0; j < 4; ++j) acc[b][i][j][0] = acc[b][i][j][1] = 0.0;
 }
 
-// The ten products for one k-step held in shared memory.
-template <int BM, int BN>
+// Which products feed the bins (PRODUCTS):
+//   0  eq. (Gemm10): the method, bins 3-6 folded into four products;
+//   1  eq. (Gemm16): all sixteen products (accuracy ablation);
+//   2  bins 0-3 of eq. (Gemm16) only, bins 4-6 dropped (accuracy ablation).
+constexpr int PRODUCTS_GEMM10 = 0, PRODUCTS_GEMM16 = 1, PRODUCTS_DROP456 = 2;
+
+// The products for one k-step held in shared memory.
+template <int BM, int BN, int PRODUCTS = PRODUCTS_GEMM10>
 __device__ __forceinline__ void mma_stage(Acc &acc, const double *As, const double *Bs, int wm,
                                           int wn, int lane) {
+    constexpr int NB = PRODUCTS == PRODUCTS_GEMM10 ? 7 : 4;  // B panels the products use
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
         double a[4][2];
@@ -57,9 +64,9 @@ __device__ __forceinline__ void mma_stage(Acc &acc, const double *As, const doub
                              (lane & 3)];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            double b[7];
+            double b[NB];
 #pragma unroll
-            for (int s = 0; s < 7; ++s)
+            for (int s = 0; s < NB; ++s)
                 b[s] = Bs[s * CBK * BN + (ks * 4 + (lane & 3)) * BN + wn * 32 + j * 8 + (lane >> 2)];
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
@@ -69,10 +76,28 @@ __device__ __forceinline__ void mma_stage(Acc &acc, const double *As, const doub
                 dmma(acc[2][i][j], a[0][i], b[2]);  // bin 2:   A0 s2B2
                 dmma(acc[2][i][j], a[1][i], b[1]);  //          s1A1 s1B1
                 dmma(acc[2][i][j], a[2][i], b[0]);  //          s2A2 B0
-                dmma(acc[3][i][j], a[0][i], b[3]);  // bin 3-6: A0 s3B3
-                dmma(acc[3][i][j], a[1][i], b[4]);  //          s1A1 s2B4
-                dmma(acc[3][i][j], a[2][i], b[5]);  //          s2A2 s1B5
-                dmma(acc[3][i][j], a[3][i], b[6]);  //          s3A3 B6
+                if constexpr (PRODUCTS == PRODUCTS_GEMM10) {
+                    dmma(acc[3][i][j], a[0][i], b[3]);  // bin 3-6: A0 s3B3
+                    dmma(acc[3][i][j], a[1][i], b[4]);  //          s1A1 s2B4
+                    dmma(acc[3][i][j], a[2][i], b[5]);  //          s2A2 s1B5
+                    dmma(acc[3][i][j], a[3][i], b[6]);  //          s3A3 B6
+                } else if constexpr (PRODUCTS == PRODUCTS_GEMM16) {
+                    dmma(acc[3][i][j], a[0][i], b[3]);  // bins 3-6, row by row of eq. Gemm16
+                    dmma(acc[3][i][j], a[1][i], b[2]);
+                    dmma(acc[3][i][j], a[1][i], b[3]);
+                    dmma(acc[3][i][j], a[2][i], b[1]);
+                    dmma(acc[3][i][j], a[2][i], b[2]);
+                    dmma(acc[3][i][j], a[2][i], b[3]);
+                    dmma(acc[3][i][j], a[3][i], b[0]);
+                    dmma(acc[3][i][j], a[3][i], b[1]);
+                    dmma(acc[3][i][j], a[3][i], b[2]);
+                    dmma(acc[3][i][j], a[3][i], b[3]);
+                } else {
+                    dmma(acc[3][i][j], a[0][i], b[3]);  // bin 3 only
+                    dmma(acc[3][i][j], a[1][i], b[2]);
+                    dmma(acc[3][i][j], a[2][i], b[1]);
+                    dmma(acc[3][i][j], a[3][i], b[0]);
+                }
             }
         }
     }

@@ -28,15 +28,13 @@
 // Waits.  Every mbarrier wait gives up after ~2 s of global time: the CTA
 // then sets DDGEMM_DEV_TIMEOUT, waits (again bounded) for its own copies
 // still in flight and returns.
-#include <cuda.h>
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
+
 #include <cstdint>
-#include <cstdio>
-#include <mutex>
 
 #include "cascade_core.cuh"
 #include "ddgemm_internal.h"
+#include "tma.cuh"
 
 namespace ddg {
 namespace {
@@ -49,60 +47,7 @@ constexpr int STAGE = Tile::STAGE;
 constexpr uint32_t STAGE_BYTES = STAGE * sizeof(double);
 constexpr int STEPS_PER_BLOCK = KC / BK;
 constexpr size_t SMEM_BYTES = (size_t)NST * STAGE * sizeof(double) + NST * sizeof(uint64_t) + 1024;
-constexpr unsigned DEV_TIMEOUT = 0x2u;
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on one phase of an mbarrier.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                            int x, int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
-        : "memory");
-}
-
-template <bool DUMP_BINS>
+template <bool DUMP_BINS, int PRODUCTS>
 __global__ void __launch_bounds__(NTHREADS, 1)
 cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
                     const __grid_constant__ CUtensorMap tm_b, const CascadeArgs args) {
@@ -120,8 +65,7 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
 
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) mbar_init(smem_addr(&bars[s]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_fence_init();
     }
     __syncthreads();
 
@@ -147,7 +91,7 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
         const bool ok = mbar_wait(smem_addr(&bars[stage]), parity);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
-                if (args.status) atomicOr(args.status, DEV_TIMEOUT);
+                if (args.status) atomicOr(args.status, DEV_TIMEOUT_BIT);
                 // Copies already issued for steps t .. t+NST-1 may still be in
                 // flight into this CTA's shared memory: wait for them, bounded.
                 for (int u = t; u < t + NST && u < ksteps; ++u)
@@ -156,7 +100,7 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
             return;
         }
         const double *As = smem + stage * STAGE;
-        mma_stage<BM, BN>(acc, As, As + A_STAGE, wm, wn, lane);
+        mma_stage<BM, BN, PRODUCTS>(acc, As, As + A_STAGE, wm, wn, lane);
         __syncthreads();  // every warp is done with this stage
         if (tid == 0 && t + NST < ksteps) issue(t + NST, stage);
 
@@ -167,50 +111,24 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
-// 3-D tensor map over a stack of `nz` row-major FP64 matrices of `rows` x
-// `cols` (row stride ld doubles); box = [bz][by][bx].  Reads outside the
-// extents are filled with zeros.
-bool make_map(CUtensorMap *map, const double *base, uint64_t cols, uint64_t rows, uint64_t nz,
-              uint64_t ld, uint32_t bx, uint32_t by, uint32_t bz) {
-    auto enc = get_encode_fn();
-    if (!enc) return false;
-    const cuuint64_t dims[3] = {cols, rows, nz};
-    const cuuint64_t strides[2] = {ld * sizeof(double), ld * rows * sizeof(double)};
-    const cuuint32_t box[3] = {bx, by, bz};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double *>(base),
-                           dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
-template <bool DUMP>
+template <bool DUMP, int PRODUCTS>
 cudaError_t launch_impl(const CascadeArgs &a, cudaStream_t stream) {
     CUtensorMap tm_a, tm_b;
-    if (!make_map(&tm_a, a.a_slices, a.k, a.m, 4, a.lda_s, BK, BM, 4)) return cudaErrorInvalidValue;
-    if (!make_map(&tm_b, a.b_slices, a.n, a.k, 7, a.ldb_s, BN, BK, 7)) return cudaErrorInvalidValue;
+    // A pieces [4][m][lda_s], box [4][64][8]; B panels [7][k][ldb_s], box [7][8][64]
+    if (!encode_map_3d(&tm_a, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, a.a_slices, a.k, a.m, 4,
+                       a.lda_s, BK, BM, 4) ||
+        !encode_map_3d(&tm_b, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, a.b_slices, a.n, a.k, 7,
+                       a.ldb_s, BN, BK, 7))
+        return cudaErrorInvalidValue;
     // per device and cheap: set on every launch
     const cudaError_t attr_err = cudaFuncSetAttribute(
-        cascade_fp64_kernel<DUMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cascade_fp64_kernel<DUMP, PRODUCTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)SMEM_BYTES);
     if (attr_err != cudaSuccess) return attr_err;
     const long long tiles = (long long)((a.n + BN - 1) / BN) * ((a.m + BM - 1) / BM);
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    cascade_fp64_kernel<DUMP><<<(unsigned)tiles, NTHREADS, SMEM_BYTES, stream>>>(tm_a, tm_b, a);
+    cascade_fp64_kernel<DUMP, PRODUCTS><<<(unsigned)tiles, NTHREADS, SMEM_BYTES, stream>>>(
+        tm_a, tm_b, a);
     return cudaGetLastError();
 }
 
@@ -218,7 +136,12 @@ cudaError_t launch_impl(const CascadeArgs &a, cudaStream_t stream) {
 
 cudaError_t launch_cascade_fp64(const CascadeArgs &a, cudaStream_t stream) {
     if (a.m <= 0 || a.n <= 0 || a.k <= 0) return cudaSuccess;
-    return a.bins ? launch_impl<true>(a, stream) : launch_impl<false>(a, stream);
+    if (a.bins) return launch_impl<true, PRODUCTS_GEMM10>(a, stream);
+    switch (a.products) {
+        case PRODUCTS_GEMM16: return launch_impl<false, PRODUCTS_GEMM16>(a, stream);
+        case PRODUCTS_DROP456: return launch_impl<false, PRODUCTS_DROP456>(a, stream);
+        default: return launch_impl<false, PRODUCTS_GEMM10>(a, stream);
+    }
 }
 
 }  // namespace ddg

@@ -18,61 +18,18 @@
 // 2^(-12-7t) are exact; only the FP64x2 additions round.
 //
 // Waits are bounded as in the FP64 kernel (DDGEMM_DEV_TIMEOUT).
-#include <cuda.h>
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
+
 #include <cstdint>
 
 #include "dd_device.cuh"
 #include "ddgemm_internal.h"
+#include "tma.cuh"
 
 namespace ddg {
 namespace {
 
 constexpr int BM = 32, BN = 32, BKB = 32, NST = 3, NTHREADS = 256;
-constexpr unsigned DEV_TIMEOUT = 0x2u;
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                            int x, int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
-        : "memory");
-}
-
 __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -127,20 +84,15 @@ cascade_int8_kernel(const __grid_constant__ CUtensorMap tm_a,
     constexpr int STEPS_PER_BLOCK = KB8 / BKB;
 
     if (tid == 0) {
-        for (int s = 0; s < NST; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[s]))
-                         : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int s = 0; s < NST; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        mbar_fence_init();
     }
     __syncthreads();
 
     auto issue = [&](int t, int stage) {
         const uint32_t bar = smem_addr(&bars[stage]);
         unsigned char *dst = smem + stage * G::STAGE;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"((uint32_t)G::STAGE)
-                     : "memory");
+        mbar_arrive_expect_tx(bar, (uint32_t)G::STAGE);
         tma_load_3d(smem_addr(dst), &tm_a, bar, t * BKB, m0, 0);
         tma_load_3d(smem_addr(dst + G::A_STAGE), &tm_b, bar, t * BKB, n0, 0);
     };
@@ -161,7 +113,7 @@ cascade_int8_kernel(const __grid_constant__ CUtensorMap tm_a,
         const bool ok = mbar_wait(smem_addr(&bars[stage]), (t / NST) & 1);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
-                if (args.status) atomicOr(args.status, DEV_TIMEOUT);
+                if (args.status) atomicOr(args.status, DEV_TIMEOUT_BIT);
                 for (int u = t; u < t + NST && u < ksteps; ++u)
                     mbar_wait(smem_addr(&bars[u % NST]), (u / NST) & 1);
             }
@@ -218,40 +170,15 @@ cascade_int8_kernel(const __grid_constant__ CUtensorMap tm_a,
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
-        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }();
-    return fn;
-}
-
-// Digit planes [s][rows][ld] (int8, k contiguous); box [s][32][32].
-bool make_digit_map(CUtensorMap *map, const int8_t *base, uint64_t k, uint64_t rows, int s,
-                    uint64_t ld) {
-    auto enc = encode_fn();
-    if (!enc) return false;
-    const cuuint64_t dims[3] = {k, rows, (cuuint64_t)s};
-    const cuuint64_t strides[2] = {ld, ld * rows};
-    const cuuint32_t box[3] = {BKB, 32, (cuuint32_t)s};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<int8_t *>(base), dims, strides,
-               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int S>
 cudaError_t launch_s(const Int8Args &a, cudaStream_t stream) {
     using G = Geometry<S>;
     CUtensorMap tm_a, tm_b;
-    if (!make_digit_map(&tm_a, a.a_digits, a.k, a.m, S, a.ld_digits) ||
-        !make_digit_map(&tm_b, a.b_digits, a.k, a.n, S, a.ld_digits))
+    // digit planes [S][rows][ld] (int8, k contiguous), box [S][32][32]
+    if (!encode_map_3d(&tm_a, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, a.a_digits, a.k, a.m, S,
+                       a.ld_digits, BKB, 32, S) ||
+        !encode_map_3d(&tm_b, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, a.b_digits, a.k, a.n, S,
+                       a.ld_digits, BKB, 32, S))
         return cudaErrorInvalidValue;
     const cudaError_t e = cudaFuncSetAttribute(
         cascade_int8_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);

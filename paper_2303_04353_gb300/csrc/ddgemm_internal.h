@@ -41,6 +41,7 @@ struct CascadeArgs {
     int *flags;              // optional m x n
     unsigned int *status;    // optional
     double *bins;            // when non-null: write the bins of k-block 0 instead of C
+    int products;            // 0: eq. Gemm10 (the method); 1: Gemm16; 2: bins 4-6 dropped
 };
 
 // The ten products of eq. Gemm10 on the FP64 tensor path with the bin

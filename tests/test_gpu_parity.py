@@ -289,3 +289,17 @@ def test_nonfinite_sets_status_int8(ops):
     ops.ddgemm(*dev(a_hi, a_lo, b_hi, b_lo), status=status, variant=1)
     (st,) = host(status)
     assert st[0] & 0x1
+
+
+@pytest.mark.parametrize("variant,products", [(2, "gemm16"), (3, "drop456")])
+@pytest.mark.parametrize("kind", ["uniform", "wide"])
+def test_ablation_variants_match_their_restatement(ops, variant, products, kind):
+    """The accuracy-ablation variants (eq. Gemm16; bins 4-6 dropped) against
+    the oracle's restatement of the same products: same bins 0-2, bin 3-6 up
+    to FP64 summation order."""
+    m, n, k = 80, 70, 600
+    a = gemm_inputs(m, n, k, kind=kind, seed=90 + variant)
+    c_hi, c_lo = host(*ops.ddgemm(*dev(*a), variant=variant))
+    s_hi, s_lo = cs.cascade_ddgemm(*a, products=products)
+    tol = cascade_tolerance(a[0], a[2], s_hi) * (2 if variant == 2 else 1)
+    assert np.all(np.abs((c_hi - s_hi) + (c_lo - s_lo)) <= tol)

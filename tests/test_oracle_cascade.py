@@ -300,3 +300,28 @@ def test_planted_scale_exponent_is_caught(monkeypatch):
     _planted(monkeypatch, "block_exponents_rows", off_by_one)
     with pytest.raises(AssertionError):
         test_split_fp64x2_conversion_bound("uniform")
+
+
+@pytest.mark.parametrize("kind", ["uniform", "wide"])
+def test_folding_bins_3_to_6_is_not_dropping_them(kind):
+    """Sec. "Cascading matrices and GEMM": folding bins 3-6 into four
+    products (eq. Gemm10) is not the same as dropping bins 4-6, though both
+    give ten products.  Against exact rationals the folded form matches all
+    sixteen products of eq. (Gemm16) to within FP64x2 rounding, while
+    dropping bins 4-6 is orders of magnitude worse."""
+    a = gemm_inputs(10, 10, 300, kind=kind, seed=77)
+    absab = exact.abs_product(a[0], a[2])
+    worst = {}
+    for mode in ("gemm10", "gemm16", "drop456"):
+        h, l = cs.cascade_ddgemm(*a, products=mode)
+        w = 0.0
+        for i in range(10):
+            for j in range(10):
+                ex = exact.exact_dot(a[0][i], a[1][i], a[2][:, j], a[3][:, j])
+                w = max(w, exact.err_vs_exact(h[i, j], l[i, j], ex) / absab[i, j])
+        worst[mode] = w
+    assert worst["gemm10"] <= 4 * worst["gemm16"] + 2.0 ** -104
+    assert worst["gemm16"] <= 4 * worst["gemm10"] + 2.0 ** -104
+    assert worst["drop456"] > 1e3 * worst["gemm10"]
+    assert max_bound_ratio(lambda *x: cs.cascade_ddgemm(*x, products="gemm16"),
+                           5, 6, 300, kind, seed=8) <= 1.0
