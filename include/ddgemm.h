@@ -12,7 +12,7 @@
  * Appendix A): k is staged in blocks of K_C = 256.  For every k-block each
  * row of A and each column of B is scaled by a power of two (sigma, tau)
  * and split into four FP64 pieces holding 22, 21 and 21 fixed-point digits
- * plus an FP64 remainder; B also gets the combined panels B4, B5, B6.  Ten
+ * (more for a block shorter than 256) plus an FP64 remainder; B also gets the combined panels B4, B5, B6.  Ten
  * FP64 products land in four bins (0, 1, 2 exact; 3-6 rounded), which are
  * added from bin 3-6 up to bin 0 in FP64x2, scaled back by sigma tau and
  * accumulated into C in FP64x2.
@@ -240,10 +240,15 @@ int ddgemm_noalloc(int m, int n, int k,
 /* The split step alone for A (Appendix A; Sec. "Cascading matrices and
  * GEMM"): per row i and k-block p, sigma = 2^e with e the frexp exponent of
  * max |A_hi| over the block (e = 0 for an all-zero block); every entry is
- * scaled by 2^-e and cascaded into four pieces.
+ * scaled by 2^-e and cascaded into four pieces.  The pieces hold c0, c1, c2
+ * digits from the paper's digit budget for the block's length L (ceil of
+ * log2): 2 c0 + L <= 53, c0 + c1 + L + 1 <= 53, 2 c1 + L + 2 <= 53,
+ * c0 + c2 + L + 2 <= 53, i.e. (22, 21, 21) for a full block of 256 entries
+ * and wider for a shorter last block or small k (the paper widens them too).
  *   slices  device, 4 x m x ld_slices doubles: slices[(s*m + i)*ld_slices + l]
- *           = sigma_s * A_s(i, l) with sigma_0 = 1, sigma_1 = 2^-22,
- *           sigma_2 = 2^-43, sigma_3 = 2^-64 (the left factor of eq. Gemm10).
+ *           = sigma_s * A_s(i, l) with sigma_0 = 1, sigma_1 = 2^-c0,
+ *           sigma_2 = 2^-(c0+c1), sigma_3 = 2^-(c0+c1+c2) (2^-22, 2^-43,
+ *           2^-64 for a full block): the left factor of eq. Gemm10.
  *           ld_slices >= k.  Columns l >= k are not written.
  *   exps    device int32, ceil(k/256) x m: exps[p*m + i] = e.
  * trans_a as in ddgemm_opts.  status_dev optional (DDGEMM_DEV_NONFINITE). */

@@ -31,7 +31,9 @@ Readings where the paper is silent or garbled (all listed in the design doc):
     M_d = 2**(53-d) + 2**(52-d), one add then one subtract; chunks are then
     multiples of 2**(1-d) with |chunk| <= 1.  (The appendix's "2^{53-c-1}"
     in the second stage is read as 2^{53-c_1}.)
-  * c = (22, 21, 21) for every k-block, also short ones.
+  * c follows the digit budget of the block's own length L = ceil(log2 len)
+    (the paper widens the splits for small k): (22, 21, 21) for full
+    256-entry blocks, (23, 22, 22) for 64, (26, 25, 25) for one entry.
   * B4, B5, B6 are the FP64 roundings of the exact remainders the split
     already holds (one rounding each), equal in exact arithmetic to the
     paper's B2 + B3 s3/s2, B1 + B2 s2/s1 + B3 s3/s1, B0 + s1 B1 + s2 B2 +
@@ -54,6 +56,25 @@ C0, C1, C2 = 22, 21, 21
 SIGMA1 = 2.0 ** -C0
 SIGMA2 = 2.0 ** -(C0 + C1)
 SIGMA3 = 2.0 ** -(C0 + C1 + C2)
+
+
+def digit_budget(block_len: int):
+    """(c0, c1, c2) for a k-block of `block_len` entries, from the
+    inequalities of Sec. "Cascading vectors and dot products" with
+    L = ceil(log2 block_len): 2 c0 + L <= 53 (bin 0); c0 + c1 + L + 1 <= 53
+    and 2 c1 + L + 2 <= 53 (bins 1 and 2); c0 + c2 + L + 2 <= 53 (bin 2).
+    The paper allows wider splits when k is smaller ("if k = 64 ... c0 = 23")."""
+    L = max(0, (int(block_len) - 1).bit_length())
+    c0 = (53 - L) // 2
+    c1 = min(53 - c0 - L - 1, (53 - L - 2) // 2)
+    c2 = 53 - c0 - L - 2
+    return c0, c1, c2
+
+
+def sigmas(c):
+    """sigma_1 = 2^-D0, sigma_2 = 2^-D1, sigma_3 = 2^-D2 for digits c."""
+    c0, c1, c2 = c
+    return 2.0 ** -c0, 2.0 ** -(c0 + c1), 2.0 ** -(c0 + c1 + c2)
 
 
 def _round_const(d: int) -> float:
@@ -93,42 +114,50 @@ def block_exponents_cols(y_hi: np.ndarray, kc: int = KC) -> np.ndarray:
     return block_exponents_rows(np.ascontiguousarray(y_hi.T), kc).T.copy()
 
 
-def split_fp64(x: np.ndarray):
+def split_fp64(x: np.ndarray, c=(C0, C1, C2)):
     """Appendix A for one FP64 array already scaled by 2^-e.
 
     Returns (x0, x1, x2, x3, r0, r1, r2): the four splits and the running
     values the appendix holds before each rounding stage (r0 = the scaled
     input, r1 after removing x0 and shifting by 2^c0, r2 after removing x1
     and shifting by 2^c1).  Every subtraction and shift here is exact."""
+    c0, c1, c2 = c
     r0 = np.asarray(x, dtype=np.float64)
-    x0 = round_digits(r0, C0)
-    r1 = (r0 - x0) * 2.0 ** C0
-    x1 = round_digits(r1, C1)
-    r2 = (r1 - x1) * 2.0 ** C1
-    x2 = round_digits(r2, C2)
-    x3 = (r2 - x2) * 2.0 ** C2
+    x0 = round_digits(r0, c0)
+    r1 = (r0 - x0) * 2.0 ** c0
+    x1 = round_digits(r1, c1)
+    r2 = (r1 - x1) * 2.0 ** c1
+    x2 = round_digits(r2, c2)
+    x3 = (r2 - x2) * 2.0 ** c2
     return x0, x1, x2, x3, r0, r1, r2
 
 
-def cascade_entries(hi: np.ndarray, lo: np.ndarray, e: np.ndarray):
+def cascade_entries(hi: np.ndarray, lo: np.ndarray, e: np.ndarray, c=(C0, C1, C2)):
     """Appendix A: scale hi and lo by 2^-e, split each, add the splits.
 
     chi_i = chi_hi,i + chi_lo,i (exact for i <= 2; one rounding for i = 3).
     Also returns the FP64 roundings of the exact tails used for B4, B5, B6:
     t1 = fl(r1_hi + r1_lo), t2 = fl(r2_hi + r2_lo), t0 = fl(r0_hi + r0_lo)."""
-    h = split_fp64(np.ldexp(hi, -e))
-    l = split_fp64(np.ldexp(lo, -e))
+    h = split_fp64(np.ldexp(hi, -e), c)
+    l = split_fp64(np.ldexp(lo, -e), c)
     chunks = tuple(h[i] + l[i] for i in range(4))
     t0, t1, t2 = (h[4] + l[4], h[5] + l[5], h[6] + l[6])
     return chunks, (t0, t1, t2)
+
+
+def block_digits(k, p, kc=KC):
+    """Digits of k-block p: the budget of its length."""
+    return digit_budget(min(kc, k - p * kc))
 
 
 def cascade_a(a_hi, a_lo, e_a, p, kc=KC):
     """Row panel p of A -> [A0; s1 A1; s2 A2; s3 A3] (left factor of Gemm10)."""
     sl = slice(p * kc, (p + 1) * kc)
     e = e_a[:, p:p + 1]
-    (a0, a1, a2, a3), _ = cascade_entries(a_hi[:, sl], a_lo[:, sl], e)
-    return a0, SIGMA1 * a1, SIGMA2 * a2, SIGMA3 * a3
+    c = block_digits(a_hi.shape[1], p, kc)
+    s1, s2, s3 = sigmas(c)
+    (a0, a1, a2, a3), _ = cascade_entries(a_hi[:, sl], a_lo[:, sl], e, c)
+    return a0, s1 * a1, s2 * a2, s3 * a3
 
 
 def cascade_b(b_hi, b_lo, e_b, p, kc=KC):
@@ -139,9 +168,11 @@ def cascade_b(b_hi, b_lo, e_b, p, kc=KC):
     arithmetic these are the tails t2, t1, t0 the split already holds."""
     sl = slice(p * kc, (p + 1) * kc)
     e = e_b[p:p + 1, :]
-    (b0, b1, b2, b3), (t0, t1, t2) = cascade_entries(b_hi[sl, :], b_lo[sl, :], e)
+    c = block_digits(b_hi.shape[0], p, kc)
+    s1, s2, s3 = sigmas(c)
+    (b0, b1, b2, b3), (t0, t1, t2) = cascade_entries(b_hi[sl, :], b_lo[sl, :], e, c)
     b4, b5, b6 = t2, t1, t0
-    return b0, SIGMA1 * b1, SIGMA2 * b2, SIGMA3 * b3, SIGMA2 * b4, SIGMA1 * b5, b6
+    return b0, s1 * b1, s2 * b2, s3 * b3, s2 * b4, s1 * b5, b6
 
 
 def ten_products(As, Bs):

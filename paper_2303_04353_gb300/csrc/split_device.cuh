@@ -13,13 +13,47 @@ namespace split_detail {
 
 constexpr unsigned DEV_NONFINITE = 0x1u;
 
-// Appendix A round-to-d-digits constants 2^(53-d) + 2^(52-d).
-__device__ __forceinline__ double round_c0(double x) {
-    const double m = 3221225472.0;            // 2^31 + 2^30
-    return __dsub_rn(__dadd_rn(x, m), m);
+// Exact powers of two and the Appendix A rounding constant
+// 2^(53-c) + 2^(52-c), built from their bit patterns.
+__device__ __forceinline__ double pow2(int e) {
+    return __longlong_as_double((long long)(1023 + e) << 52);
 }
-__device__ __forceinline__ double round_c12(double x) {
-    const double m = 6442450944.0;            // 2^32 + 2^31
+__device__ __forceinline__ double round_const(int c) {
+    return __longlong_as_double(((long long)(1023 + 53 - c) << 52) | (1ll << 51));
+}
+
+// The digit budget of a k-block of `len` entries (Sec. "Cascading vectors
+// and dot products", with L = ceil(log2 len) in place of log2 k):
+//   2 c0 + L <= 53;  c0 + c1 + L + 1 <= 53;  2 c1 + L + 2 <= 53;
+//   c0 + c2 + L + 2 <= 53.
+// (22, 21, 21) for a full block of 256; wider for shorter blocks, as the
+// paper allows for smaller k.  Kept with the constants the split needs.
+struct Digits {
+    double m0, m1, m2;     // rounding constants for c0, c1, c2
+    double up0, up1, up2;  // 2^c0, 2^c1, 2^c2
+    double s1, s2, s3;     // sigma_1 = 2^-c0, sigma_2 = 2^-(c0+c1), sigma_3 = 2^-(c0+c1+c2)
+};
+
+__device__ __forceinline__ Digits block_digits(int len) {
+    const int L = len > 1 ? 32 - __clz(len - 1) : 0;
+    const int c0 = (53 - L) / 2;
+    const int c1 = min(53 - c0 - L - 1, (53 - L - 2) / 2);
+    const int c2 = 53 - c0 - L - 2;
+    Digits d;
+    d.m0 = round_const(c0);
+    d.m1 = round_const(c1);
+    d.m2 = round_const(c2);
+    d.up0 = pow2(c0);
+    d.up1 = pow2(c1);
+    d.up2 = pow2(c2);
+    d.s1 = pow2(-c0);
+    d.s2 = pow2(-(c0 + c1));
+    d.s3 = pow2(-(c0 + c1 + c2));
+    return d;
+}
+
+// Appendix A: round to a digit grid by adding and subtracting the constant.
+__device__ __forceinline__ double round_to(double x, double m) {
     return __dsub_rn(__dadd_rn(x, m), m);
 }
 
@@ -29,31 +63,32 @@ struct Pieces {
 };
 
 // Appendix A for one FP64 value already scaled by 2^-e.
-__device__ __forceinline__ Pieces split_fp64(double x) {
+__device__ __forceinline__ Pieces split_fp64(double x, const Digits &d) {
     Pieces q;
     q.r0 = x;
-    q.x0 = round_c0(q.r0);
-    q.r1 = __dmul_rn(__dsub_rn(q.r0, q.x0), 4194304.0);    // 2^22
-    q.x1 = round_c12(q.r1);
-    q.r2 = __dmul_rn(__dsub_rn(q.r1, q.x1), 2097152.0);    // 2^21
-    q.x2 = round_c12(q.r2);
-    q.x3 = __dmul_rn(__dsub_rn(q.r2, q.x2), 2097152.0);    // 2^21
+    q.x0 = round_to(q.r0, d.m0);
+    q.r1 = __dmul_rn(__dsub_rn(q.r0, q.x0), d.up0);
+    q.x1 = round_to(q.r1, d.m1);
+    q.r2 = __dmul_rn(__dsub_rn(q.r1, q.x1), d.up1);
+    q.x2 = round_to(q.r2, d.m2);
+    q.x3 = __dmul_rn(__dsub_rn(q.r2, q.x2), d.up2);
     return q;
 }
 
 // Cascade one FP64x2 entry with block exponent e into NS outputs.
 template <int NS>
-__device__ __forceinline__ void cascade_entry(double hi, double lo, int e, double (&o)[NS]) {
-    const Pieces h = split_fp64(scalbn(hi, -e));
-    const Pieces l = split_fp64(scalbn(lo, -e));
+__device__ __forceinline__ void cascade_entry(double hi, double lo, int e, const Digits &d,
+                                              double (&o)[NS]) {
+    const Pieces h = split_fp64(scalbn(hi, -e), d);
+    const Pieces l = split_fp64(scalbn(lo, -e), d);
     o[0] = __dadd_rn(h.x0, l.x0);
-    o[1] = __dmul_rn(__dadd_rn(h.x1, l.x1), 0x1p-22);
-    o[2] = __dmul_rn(__dadd_rn(h.x2, l.x2), 0x1p-43);
-    o[3] = __dmul_rn(__dadd_rn(h.x3, l.x3), 0x1p-64);
+    o[1] = __dmul_rn(__dadd_rn(h.x1, l.x1), d.s1);
+    o[2] = __dmul_rn(__dadd_rn(h.x2, l.x2), d.s2);
+    o[3] = __dmul_rn(__dadd_rn(h.x3, l.x3), d.s3);
     if constexpr (NS == 7) {
-        o[4] = __dmul_rn(__dadd_rn(h.r2, l.r2), 0x1p-43);  // s2 B4
-        o[5] = __dmul_rn(__dadd_rn(h.r1, l.r1), 0x1p-22);  // s1 B5
-        o[6] = __dadd_rn(h.r0, l.r0);                      // B6
+        o[4] = __dmul_rn(__dadd_rn(h.r2, l.r2), d.s2);  // s2 B4
+        o[5] = __dmul_rn(__dadd_rn(h.r1, l.r1), d.s1);  // s1 B5
+        o[6] = __dadd_rn(h.r0, l.r0);                   // B6
     }
 }
 
@@ -88,6 +123,7 @@ __device__ __forceinline__ void split_contig_unit(int lane, int v, int p, int nv
                                                   unsigned int *status) {
     const double *rh = xh + (long long)v * ldx;
     const double *rl = xl + (long long)v * ldx;
+    const Digits dg = block_digits(min(KC, kdim - p * KC));
     double h[8], lo[8];
     double mx = 0.0;
     bool bad = false;
@@ -122,7 +158,7 @@ __device__ __forceinline__ void split_contig_unit(int lane, int v, int p, int nv
             const int l = p * KC + 64 * t + 2 * lane + c;
             if (l < kdim) {
                 double o[NS];
-                cascade_entry<NS>(h[2 * t + c], lo[2 * t + c], e, o);
+                cascade_entry<NS>(h[2 * t + c], lo[2 * t + c], e, dg, o);
                 store_entry<NS>(out, ld_out, layout, nvec, kdim, v, l, o);
             }
         }
@@ -145,6 +181,7 @@ __device__ __forceinline__ void split_strided_unit(int vt, int p, int nvec, int 
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int v = vt * 64 + 2 * tx;
     const int lbeg = p * KC, lend = min(lbeg + KC, kdim);
+    const Digits dg = block_digits(lend - lbeg);
     auto load_pair = [&](const double *x, int l, double &a, double &b) {
         const double *row = x + (long long)l * ldx;
         if (VEC && v + 1 < nvec) {
@@ -186,11 +223,11 @@ __device__ __forceinline__ void split_strided_unit(int vt, int p, int nvec, int 
         bad |= !isfinite(ha) || !isfinite(la) || !isfinite(hb) || !isfinite(lb);
         double o[NS];
         if (v < nvec) {
-            cascade_entry<NS>(ha, la, e0, o);
+            cascade_entry<NS>(ha, la, e0, dg, o);
             store_entry<NS>(out, ld_out, layout, nvec, kdim, v, l, o);
         }
         if (v + 1 < nvec) {
-            cascade_entry<NS>(hb, lb, e1, o);
+            cascade_entry<NS>(hb, lb, e1, dg, o);
             store_entry<NS>(out, ld_out, layout, nvec, kdim, v + 1, l, o);
         }
     }

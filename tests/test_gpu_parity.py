@@ -180,13 +180,10 @@ def test_identity(ops):
 
 
 def test_worked_example(ops):
-    g = {}
-    for line in open(os.path.join(GOLDEN, "worked_example.txt")):
-        if line.strip() and not line.startswith("#"):
-            key, *vals = line.split()
-            g[key] = np.array([float.fromhex(v) for v in vals])
-    c_hi, c_lo = host(*ops.ddgemm(*dev(g["x_hi"][None, :], g["x_lo"][None, :],
-                                       g["y_hi"][:, None], g["y_lo"][:, None])))
+    from tests.test_oracle_cascade import worked_example_vectors
+    g, v = worked_example_vectors()
+    c_hi, c_lo = host(*ops.ddgemm(*dev(v["x_hi"][None, :], v["x_lo"][None, :],
+                                       v["y_hi"][:, None], v["y_lo"][:, None])))
     assert c_hi[0, 0] == g["cascade_hi"][0] and c_lo[0, 0] == g["cascade_lo"][0]
 
 

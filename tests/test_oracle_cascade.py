@@ -34,6 +34,21 @@ EPS_CASC = 2.0 ** -117
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
+def test_digit_budget_for_short_blocks():
+    """Sec. "Cascading vectors and dot products": "if k = 64 ... we allow
+    c0 = 23"; every block length satisfies the four inequalities with equality
+    or one to spare, and no digit could be wider."""
+    assert cs.digit_budget(64)[0] == 23
+    assert cs.digit_budget(256) == (22, 21, 21)
+    for n in range(1, 257):
+        c0, c1, c2 = cs.digit_budget(n)
+        L = math.ceil(math.log2(n)) if n > 1 else 0
+        assert 2 * c0 + L <= 53 < 2 * (c0 + 1) + L
+        assert c0 + c1 + L + 1 <= 53 and 2 * c1 + L + 2 <= 53
+        assert c0 + c1 + 1 + L + 1 > 53 or 2 * (c1 + 1) + L + 2 > 53
+        assert c0 + c2 + L + 2 <= 53 < c0 + c2 + 1 + L + 2
+
+
 def test_digit_budget_from_paper_inequalities():
     k = 256
     lg = int(math.log2(k))
@@ -129,8 +144,9 @@ def test_tails_b4_b5_b6_within_one_rounding():
 
 
 @pytest.mark.parametrize("kind", ["uniform", "wide"])
-def test_bins_0_to_2_are_exact_integer_dots(kind):
-    a_hi, a_lo, b_hi, b_lo = gemm_inputs(12, 10, 256, kind=kind, seed=21)
+@pytest.mark.parametrize("k", [256, 100, 64, 3])
+def test_bins_0_to_2_are_exact_integer_dots(kind, k):
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(12, 10, k, kind=kind, seed=21)
     e_a = cs.block_exponents_rows(a_hi)
     e_b = cs.block_exponents_cols(b_hi)
     As = cs.cascade_a(a_hi, a_lo, e_a, 0)
@@ -142,25 +158,29 @@ def test_bins_0_to_2_are_exact_integer_dots(kind):
         assert np.all(y == np.round(y))
         return [[int(v) for v in row] for row in y.tolist()]
 
-    # scaled panels: A0 on 2^-21, s1 A1 on 2^-42, s2 A2 on 2^-63;
-    # B0 on 2^-21, s1 B1 on 2^-42, s2 B2 on 2^-63
-    A0, A1, A2 = ints(As[0], 21), ints(As[1], 42), ints(As[2], 63)
-    B0, B1, B2 = (ints(Bs[0].T, 21), ints(Bs[1].T, 42), ints(Bs[2].T, 63))
+    # scaled panels: A0 on the grid 2^(1-c0), s1 A1 on 2^(1-c0-c1), s2 A2 on
+    # 2^(1-c0-c1-c2) (2^-21, 2^-42, 2^-63 for a full block); B likewise
+    c0, c1, c2 = cs.digit_budget(k)
+    g0, g1, g2 = c0 - 1, c0 + c1 - 1, c0 + c1 + c2 - 1
+    A0, A1, A2 = ints(As[0], g0), ints(As[1], g1), ints(As[2], g2)
+    B0, B1, B2 = (ints(Bs[0].T, g0), ints(Bs[1].T, g1), ints(Bs[2].T, g2))
 
     def dot(x, y):
         return sum(p * q for p, q in zip(x, y))
 
     for i in range(12):
         for j in range(10):
-            b0 = dot(A0[i], B0[j])                                  # units 2^-42
-            b1 = dot(A0[i], B1[j]) + dot(A1[i], B0[j])              # units 2^-63
+            b0 = dot(A0[i], B0[j])                                  # units 2^-(2 g0)
+            b1 = dot(A0[i], B1[j]) + dot(A1[i], B0[j])              # units 2^-(g0 + g1)
             assert abs(b0) < 2 ** 53 and abs(b1) < 2 ** 53
-            assert bin0[i, j] == math.ldexp(b0, -42)
-            assert bin1[i, j] == math.ldexp(b1, -63)
-            # A0 B2: 2^-21 * 2^-63 = 2^-84; A1 B1: 2^-42 * 2^-42 = 2^-84; A2 B0 likewise
-            b2u = dot(A0[i], B2[j]) + dot(A1[i], B1[j]) + dot(A2[i], B0[j])
+            assert bin0[i, j] == math.ldexp(b0, -2 * g0)
+            assert bin1[i, j] == math.ldexp(b1, -(g0 + g1))
+            # A0 B2 and A2 B0 are on 2^-(g0 + g2), A1 B1 on 2^-(2 g1): common unit
+            u = max(g0 + g2, 2 * g1)
+            b2u = ((dot(A0[i], B2[j]) + dot(A2[i], B0[j])) << (u - g0 - g2)) + \
+                (dot(A1[i], B1[j]) << (u - 2 * g1))
             assert abs(b2u) < 2 ** 53
-            assert bin2[i, j] == math.ldexp(b2u, -84)
+            assert bin2[i, j] == math.ldexp(b2u, -u)
 
 
 def max_bound_ratio(fn, m, n, k, kind, seed):
@@ -201,14 +221,26 @@ def _read_golden(name):
             if not line or line.startswith("#"):
                 continue
             key, *rest = line.split()
-            vals[key] = np.array([float.fromhex(t) for t in rest])
+            vals[key] = np.array([float.fromhex(t) if key != "pad_to" else int(t) for t in rest])
     return vals
 
 
-def test_worked_example_golden():
+def worked_example_vectors():
+    """x, y of the worked example, zero-padded to the fixture's pad_to."""
     g = _read_golden("worked_example.txt")
-    a_hi, a_lo = g["x_hi"][None, :], g["x_lo"][None, :]
-    b_hi, b_lo = g["y_hi"][:, None], g["y_lo"][:, None]
+    k = int(g["pad_to"][0])
+    out = {}
+    for key in ("x_hi", "x_lo", "y_hi", "y_lo"):
+        v = np.zeros(k)
+        v[:g[key].size] = g[key]
+        out[key] = v
+    return g, out
+
+
+def test_worked_example_golden():
+    g, v = worked_example_vectors()
+    a_hi, a_lo = v["x_hi"][None, :], v["x_lo"][None, :]
+    b_hi, b_lo = v["y_hi"][:, None], v["y_lo"][:, None]
     c_hi, c_lo = cs.cascade_ddgemm(a_hi, a_lo, b_hi, b_lo)
     assert c_hi[0, 0] == g["cascade_hi"][0] and c_lo[0, 0] == g["cascade_lo"][0]
     o_hi, o_lo = dd.ddgemm(a_hi, a_lo, b_hi, b_lo)
