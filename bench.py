@@ -593,6 +593,55 @@ def run_ablation(args):
                               "median_err_rel_absAabsB": float(np.median(err))}), flush=True)
 
 
+def run_illcond(args):
+    """Study after the paper's ill-conditioned experiments: A = Q with
+    orthonormal rows, C with entries of magnitude (t, 10t) and one 1 per
+    column, B = Q^T C (workloads/illcond.py).  Max element-wise relative
+    error over sampled entries against exact rationals, for the FP64x2
+    triple loop (the CPU oracle) and the two CUDA forms; study lines, not
+    the benchmark line."""
+    from fractions import Fraction
+
+    import torch
+
+    from oracle import dd
+    from paper_2303_04353_gb300 import _lib, ops
+    from workloads.illcond import illcond_inputs
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import exact  # exact rational dot products (test helper)
+
+    dev = torch.device("cuda", 0)
+    for n in (64, 128, 256, 512):
+        for t in (1e-9, 1e-14, 1e-19):
+            a = illcond_inputs(n, t, seed=n)[:4]
+            rng = np.random.default_rng(n)
+            rows, cols = rng.integers(0, n, 256), rng.integers(0, n, 256)
+            refs = [exact.exact_dot(a[0][i], a[1][i], a[2][:, j], a[3][:, j])
+                    for i, j in zip(rows, cols)]
+
+            def worst(c_hi, c_lo):
+                return max(exact.err_vs_exact(c_hi[i, j], c_lo[i, j], r)
+                           / abs(float(Fraction(r, 1 << (2 * exact.SHIFT))))
+                           for i, j, r in zip(rows, cols, refs))
+            o_hi, o_lo = dd.ddgemm_entries(*a, rows, cols)
+            e_dd = max(exact.err_vs_exact(h, l, r) / abs(float(Fraction(r, 1 << (2 * exact.SHIFT))))
+                       for h, l, r in zip(o_hi, o_lo, refs))
+            d_in = [torch.from_numpy(x).to(dev) for x in a]
+            res = {}
+            for name, variant in (("cascade fp64", _lib.DDGEMM_VARIANT_FP64),
+                                  ("cascade int8 s=16", _lib.DDGEMM_VARIANT_INT8)):
+                c = ops.ddgemm(*d_in, variant=variant)
+                torch.cuda.synchronize()
+                res[name] = worst(c[0].cpu().numpy(), c[1].cpu().numpy())
+            print(json.dumps({"study": "ill-conditioned products", "n": n, "t": t,
+                              "max_rel_err_fp64x2_triple_loop": e_dd,
+                              **{f"max_rel_err_{k}": v for k, v in res.items()},
+                              "ratio_fp64x2_over_cascade_fp64": e_dd / max(res["cascade fp64"],
+                                                                            1e-300)}),
+                  flush=True)
+
+
 def run_sweep(args):
     """Config-2 study: error and throughput of the FP64 form and the INT8
     form as the exponent spread of the entries grows (hi = +-2^u,
@@ -655,6 +704,8 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="exponent-spread study of both forms instead of the benchmark line")
     ap.add_argument("--sweep-size", type=int, default=2048)
+    ap.add_argument("--illcond", action="store_true",
+                    help="ill-conditioned accuracy study instead of the benchmark line")
     ap.add_argument("--ablation", action="store_true",
                     help="Gemm10 / Gemm16 / dropped-bins accuracy study instead of the line")
     args = ap.parse_args()
@@ -663,6 +714,9 @@ def main():
         return
     if args.ablation:
         run_ablation(args)
+        return
+    if args.illcond:
+        run_illcond(args)
         return
     if args.workload == "batched":
         run_batched(args)

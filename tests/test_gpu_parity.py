@@ -300,3 +300,21 @@ def test_ablation_variants_match_their_restatement(ops, variant, products, kind)
     s_hi, s_lo = cs.cascade_ddgemm(*a, products=products)
     tol = cascade_tolerance(a[0], a[2], s_hi) * (2 if variant == 2 else 1)
     assert np.all(np.abs((c_hi - s_hi) + (c_lo - s_lo)) <= tol)
+
+
+def test_illconditioned_product(ops):
+    """An ill-conditioned product (condition ~ 1e19, k = 128): the CUDA path agrees
+    with the cascade restatement within its tolerance and, like it, beats the
+    FP64x2 triple loop on max relative error."""
+    from workloads.illcond import illcond_inputs
+    from tests.test_illcond import rel_errors
+    n = 128
+    a = illcond_inputs(n, 1e-19, seed=n)[:4]
+    c_hi, c_lo = host(*ops.ddgemm(*dev(*a)))
+    s_hi, s_lo = cs.cascade_ddgemm(*a)
+    assert np.all(np.abs((c_hi - s_hi) + (c_lo - s_lo)) <= cascade_tolerance(a[0], a[2], s_hi))
+    rng = np.random.default_rng(2)
+    rows, cols = rng.integers(0, n, 40), rng.integers(0, n, 40)
+    o_hi, o_lo = dd.ddgemm(*a)
+    # at k <= 128 the study (bench.py --illcond) measures 45-170x
+    assert rel_errors(c_hi, c_lo, a, rows, cols).max() * 3 < rel_errors(o_hi, o_lo, a, rows, cols).max()
