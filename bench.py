@@ -250,6 +250,7 @@ def run_ours(args, wl):
     c_lo = torch.empty((m, n), dtype=torch.float64, device=dev)
     variant = _lib.DDGEMM_VARIANT_INT8 if args.variant == "int8" else _lib.DDGEMM_VARIANT_FP64
     ws = ops.alloc_workspace(m, n, k, dev, variant, args.int8_slices)
+    groups = ops.split_groups(m, n, k, dev, ws.numel(), variant)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -433,6 +434,7 @@ def run_ours(args, wl):
                    "variant": "fp64 (ten FP64 products)" if variant == _lib.DDGEMM_VARIANT_FP64
                    else f"int8 ({args.int8_slices} pieces, "
                         f"{args.int8_slices * (args.int8_slices + 1) // 2} INT8 products)",
+                   "split_k_groups": groups,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs (512 MiB) and panels larger than L2; no flush"
                          if m * k >= 1 << 22 else "small case; L2-resident"},
@@ -446,7 +448,8 @@ def run_ours(args, wl):
         "roofline": roofline,
         "e2e": {"value": round(replica_rate(flops_dd, world, e2e_ms) / 1e9, 4), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 3 * args.steps,
+        # split A, split B, the cascade kernel, and the split-k fix-up
+        "gpu_launches": (3 + (groups > 1)) * args.steps,
         "clocks": clocks,
     }
     if int8_form is not None:
@@ -642,6 +645,47 @@ def run_illcond(args):
                   flush=True)
 
 
+def run_splitk(args):
+    """Split-k study: effective GFLOP/s of the FP64 form with no split,
+    the automatic choice and forced group counts, on shapes whose grids of
+    64 x 64 tiles fill the 152 SMs in few waves.  Study lines, not the
+    benchmark line."""
+    import torch
+
+    from paper_2303_04353_gb300 import ops
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    shapes = [(8192, 1024, 4096), (3000, 3000, 3000), (2048, 2048, 2048), (1024, 1024, 8192),
+              (1000, 1000, 1000), (512, 512, 4096), (256, 256, 16384)]
+    for m, n, k in shapes:
+        d_in = [torch.from_numpy(x).to(dev) for x in gemm_inputs(m, n, k, kind="uniform", seed=1)]
+        out = (torch.empty((m, n), dtype=torch.float64, device=dev),
+               torch.empty((m, n), dtype=torch.float64, device=dev))
+        for split_k in (1, 0, 2, 4, 8, 16):
+            ws = ops.alloc_workspace(m, n, k, dev, split_k=split_k)
+            for _ in range(3):
+                ops.ddgemm(*d_in, out=out, workspace=ws, split_k=split_k)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            reps = 5
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                ops.ddgemm(*d_in, out=out, workspace=ws, split_k=split_k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            print(json.dumps({"study": "split-k", "m": m, "n": n, "k": k,
+                              "split_k": split_k if split_k else "auto",
+                              "groups": ops.split_groups(m, n, k, dev, ws.numel(),
+                                                         split_k=split_k),
+                              "ms": round(ms, 3),
+                              "effective_gflops": round(2.0 * m * n * k / (ms * 1e-3) / 1e9, 2)}),
+                  flush=True)
+            del ws
+
+
 def run_sweep(args):
     """Config-2 study: error and throughput of the FP64 form and the INT8
     form as the exponent spread of the entries grows (hi = +-2^u,
@@ -708,7 +752,12 @@ def main():
                     help="ill-conditioned accuracy study instead of the benchmark line")
     ap.add_argument("--ablation", action="store_true",
                     help="Gemm10 / Gemm16 / dropped-bins accuracy study instead of the line")
+    ap.add_argument("--splitk", action="store_true",
+                    help="split-k study on grids of few waves instead of the line")
     args = ap.parse_args()
+    if args.splitk:
+        run_splitk(args)
+        return
     if args.sweep:
         run_sweep(args)
         return

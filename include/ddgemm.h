@@ -102,13 +102,34 @@ typedef struct ddgemm_opts {
     /* INT8 form only: pieces per entry, s in {12, 14, 15, 16, 17, 18}; 0 = 16.
      * Products per k: s (s + 1) / 2 INT8 GEMMs. */
     int int8_slices;
+    /* FP64 forms: split-k over whole 256-entry k-blocks when a grid of 64 x 64
+     * tiles would leave SMs idle.  Group g of a tile sums its run of k-blocks
+     * into C (g = 0) or into a partial buffer in the workspace, and one more
+     * kernel adds the partials into C in group order, in FP64x2.  0 = chosen
+     * per launch from the SM count (grids below 4096 tiles only, at most
+     * min(16, ceil(8192 / tiles)) groups, only as many as the workspace
+     * holds); 1 = never (C then follows the paper's k order bit for bit);
+     * 2-16 = that many groups (capped by the k-blocks and the workspace).
+     * Not used with flags_dev. */
+    int split_k;
 } ddgemm_opts;
 
-/* Bytes of device workspace ddgemm() needs for this problem (0 when m, n or
- * k is 0).  Holds the four cascaded pieces of A (4 m k doubles), the seven
- * cascaded panels of B (7 k n doubles) and the per-block exponents of sigma
- * and tau.  opts may be NULL (all defaults).  Returns 0 on invalid sizes. */
+/* Bytes of device workspace ddgemm() can use for this problem (0 when m, n
+ * or k is 0).  Holds the four cascaded pieces of A (4 m k doubles), the seven
+ * cascaded panels of B (7 k n doubles), the per-block exponents of sigma and
+ * tau, and, for grids of fewer than 4096 tiles of 64 x 64, room for split-k
+ * partial C (2 m n doubles each, at most 15 and at most about 0.5 GB in
+ * all; see split_k).  ddgemm()
+ * accepts a smaller workspace down to the size without the partials and
+ * then splits less or not at all.  opts may be NULL (all defaults).
+ * Returns 0 on invalid sizes. */
 size_t ddgemm_workspace_size(int m, int n, int k, const ddgemm_opts *opts);
+
+/* How many split-k groups ddgemm() launches for this problem (see split_k)
+ * on a GPU with `sms` multiprocessors and a workspace of ws_bytes: 1 for the
+ * INT8 form, with flags_dev, or when there is no room for partials.  Host
+ * only, no GPU needed.  Returns 0 on invalid arguments. */
+int ddgemm_split_groups(int m, int n, int k, int sms, size_t ws_bytes, const ddgemm_opts *opts);
 
 /* C := A B in FP64x2 by the ten-GEMM cascade (eq. Gemm10).
  *   m, n, k      sizes of op(A) (m x k), op(B) (k x n) and C (m x n); >= 0.
@@ -117,9 +138,10 @@ size_t ddgemm_workspace_size(int m, int n, int k, const ddgemm_opts *opts);
  *   B_hi, B_lo   op(B) likewise, leading dim ldb.
  *   C_hi, C_lo   output, m x n, leading dim ldc >= n.  Must not overlap the
  *                inputs or the workspace.
- *   workspace    device buffer of at least ddgemm_workspace_size() bytes,
- *                256-byte aligned; its contents on return are the cascaded
- *                panels (unspecified layout).
+ *   workspace    device buffer of ddgemm_workspace_size() bytes (at the
+ *                least that size less the split-k partials), 256-byte
+ *                aligned; its contents on return are the cascaded panels
+ *                (unspecified layout).
  *   opts         may be NULL.
  * Returns DDGEMM_OK or an error code; on error nothing was enqueued. */
 int ddgemm(int m, int n, int k,
@@ -220,9 +242,10 @@ int ddgemm_batched(int count, const ddgemm_problem *probs_host,
  *
  *   - Arguments, layouts and results are those of ddgemm() (opts may be
  *     NULL); the work is enqueued on `stream` and the call does not wait.
- *   - Problems with ddgemm_workspace_size(m, n, k, opts) above
- *     DDGEMM_NOALLOC_SCRATCH_BYTES are rejected with DDGEMM_EWORKSPACE
- *     (872 x 872 x 872 is the largest cube that fits).
+ *   - Problems whose workspace without the split-k partial sums (see
+ *     ddgemm_workspace_size) is above DDGEMM_NOALLOC_SCRATCH_BYTES are
+ *     rejected with DDGEMM_EWORKSPACE (872 x 872 x 872 is the largest cube
+ *     that fits); the rest of the array is used for split-k when it fits.
  *   - The first call on each device looks up the array's device address
  *     with cudaGetSymbolAddress (with that device current) and caches it;
  *     make that first call before any stream capture.

@@ -35,7 +35,7 @@ class ddgemm_opts(ctypes.Structure):
     _fields_ = [("trans_a", ctypes.c_int), ("trans_b", ctypes.c_int),
                 ("variant", ctypes.c_int), ("status_dev", ctypes.c_void_p),
                 ("flags_dev", ctypes.c_void_p), ("phase_events", ctypes.c_void_p),
-                ("int8_slices", ctypes.c_int)]
+                ("int8_slices", ctypes.c_int), ("split_k", ctypes.c_int)]
 
 
 class ddgemm_problem(ctypes.Structure):
@@ -58,6 +58,7 @@ _LIB = None
 _I, _Z, _P = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
 _SIGS = {
     "ddgemm_workspace_size": (_Z, [_I, _I, _I, _P]),
+    "ddgemm_split_groups": (_I, [_I, _I, _I, _I, _Z, _P]),
     "ddgemm": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _Z, _P, _P]),
     "ddgemm_split_a": (_I, [_I, _I, _P, _P, _I, _I, _P, _I, _P, _P, _P]),
     "ddgemm_split_b": (_I, [_I, _I, _P, _P, _I, _I, _P, _I, _P, _P, _P]),
@@ -110,12 +111,12 @@ def _check(code: int, where: str) -> None:
 
 
 def make_opts(trans_a=False, trans_b=False, variant=DDGEMM_VARIANT_FP64, status_dev=0,
-              flags_dev=0, phase_events=None, int8_slices=0) -> ddgemm_opts:
+              flags_dev=0, phase_events=None, int8_slices=0, split_k=0) -> ddgemm_opts:
     """phase_events: None or a ctypes array of three cudaEvent_t handles
     (the caller keeps it alive until the call returns)."""
     ev = ctypes.cast(phase_events, ctypes.c_void_p) if phase_events is not None else None
     return ddgemm_opts(int(trans_a), int(trans_b), int(variant), status_dev or None,
-                       flags_dev or None, ev, int(int8_slices))
+                       flags_dev or None, ev, int(int8_slices), int(split_k))
 
 
 def ddgemm_workspace_size(m: int, n: int, k: int, opts: ddgemm_opts | None = None) -> int:

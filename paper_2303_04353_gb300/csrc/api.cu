@@ -2,6 +2,7 @@
 // workspace carving and the launches of the split and cascade kernels.
 // Nothing here allocates device memory.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 
@@ -14,13 +15,39 @@ constexpr size_t ALIGN = 256;
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Workspace carve: A pieces, B panels, exponents of A, exponents of B.
+// Split-k groups the workspace has room for: one k-block each at least, at
+// most 16, and when chosen automatically only for grids below 4096 tiles of
+// 64 x 64 (bigger grids fill the GPU in many waves) and at most
+// ceil(8192 / tiles), which bounds the partial sums at (8192 + tiles) tiles'
+// worth of FP64x2 C, about 0.5 GB.  split_k = 1 in the options reserves none.
+constexpr int SPLIT_MAX = 16;
+constexpr long long SPLIT_TILE_LIMIT = 4096;
+
+long long fp64_tiles(int m, int n) { return (long long)((m + 63) / 64) * ((n + 63) / 64); }
+
+int auto_split_cap(int m, int n, int k) {
+    const long long tiles = fp64_tiles(m, n);
+    const int kb = (k + ddg::KC - 1) / ddg::KC;
+    if (tiles <= 0 || tiles >= SPLIT_TILE_LIMIT) return 1;
+    const long long by_tiles = (2 * SPLIT_TILE_LIMIT + tiles - 1) / tiles;
+    return (int)std::min<long long>(std::min<long long>(SPLIT_MAX, kb), by_tiles);
+}
+
+int split_reserve(int m, int n, int k, int split_k) {
+    const int kb = (k + ddg::KC - 1) / ddg::KC;
+    if (split_k == 1) return 1;
+    if (split_k > 1) return std::min(std::min(split_k, SPLIT_MAX), kb);
+    return auto_split_cap(m, n, k);
+}
+
+// Workspace carve: A pieces, B panels, exponents of A, exponents of B, then
+// room for the partial C of split-k groups 1..reserve-1.
 struct Layout {
     long long lda_s, ldb_s;
-    size_t off_a, off_b, off_ea, off_eb, total;
+    size_t off_a, off_b, off_ea, off_eb, base, off_part, part_bytes, total;
 };
 
-Layout layout_for(int m, int n, int k) {
+Layout layout_for(int m, int n, int k, int split_reserve_groups = 1) {
     Layout L;
     const long long kb = (k + ddg::KC - 1) / ddg::KC;
     L.lda_s = (long long)round_up((size_t)k, 8);
@@ -29,7 +56,10 @@ Layout layout_for(int m, int n, int k) {
     L.off_b = L.off_a + round_up((size_t)4 * m * L.lda_s * sizeof(double), ALIGN);
     L.off_ea = L.off_b + round_up((size_t)7 * k * L.ldb_s * sizeof(double), ALIGN);
     L.off_eb = L.off_ea + round_up((size_t)kb * m * sizeof(int), ALIGN);
-    L.total = L.off_eb + round_up((size_t)kb * n * sizeof(int), ALIGN);
+    L.base = L.off_eb + round_up((size_t)kb * n * sizeof(int), ALIGN);
+    L.off_part = L.base;
+    L.part_bytes = round_up((size_t)m * n * sizeof(double), ALIGN);   // one hi or lo plane
+    L.total = L.base + (size_t)(split_reserve_groups - 1) * 2 * L.part_bytes;
     return L;
 }
 
@@ -39,6 +69,7 @@ struct Parsed {
     int *flags = nullptr;
     void **events = nullptr;
     int slices = ddg::INT8_SLICES_DEFAULT;
+    int split_k = 0;
 };
 
 // Workspace carve of the INT8 form: digit planes of A and B, exponents.
@@ -68,7 +99,9 @@ bool parse(const ddgemm_opts *o, Parsed &p) {
         p.flags = o->flags_dev;
         p.events = o->phase_events;
         if (o->int8_slices) p.slices = o->int8_slices;
+        p.split_k = o->split_k;
     }
+    if (p.split_k < 0) return false;
     if (p.variant == DDGEMM_VARIANT_INT8 && !ddg::int8_slices_supported(p.slices)) return false;
     return (p.trans_a == 0 || p.trans_a == 1) && (p.trans_b == 0 || p.trans_b == 1);
 }
@@ -92,11 +125,37 @@ int check_operands(int m, int n, int k, const void *ah, const void *al, int lda,
     return DDGEMM_OK;
 }
 
+// split-k groups of an FP64-form launch: as many as the workspace holds,
+// within the choice for this grid
+int split_groups(int m, int n, int k, int sms, size_t ws_bytes, const Parsed &p) {
+    if (p.variant == DDGEMM_VARIANT_INT8 || p.flags || p.split_k == 1) return 1;
+    if (m <= 0 || n <= 0 || k <= 0) return 1;
+    const Layout L = layout_for(m, n, k);
+    if (ws_bytes < L.base) return 1;
+    const int kb = (k + ddg::KC - 1) / ddg::KC;
+    const int room = 1 + (int)std::min<size_t>((ws_bytes - L.base) / (2 * L.part_bytes),
+                                                SPLIT_MAX - 1);
+    int split = 1;
+    if (p.split_k > 1)
+        split = std::min(std::min(p.split_k, SPLIT_MAX), kb);
+    else
+        split = ddg::choose_split(fp64_tiles(m, n), kb, sms, auto_split_cap(m, n, k));
+    return std::min(split, room);
+}
+
 int run(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
         const double *B_hi, const double *B_lo, int ldb, double *C_hi, double *C_lo, int ldc,
         double *bins, void *workspace, size_t ws_bytes, cudaStream_t stream, const Parsed &p) {
     const Layout L = layout_for(m, n, k);
-    if (!workspace || ws_bytes < L.total || (uintptr_t)workspace % ALIGN) return DDGEMM_EWORKSPACE;
+    if (!workspace || ws_bytes < L.base || (uintptr_t)workspace % ALIGN) return DDGEMM_EWORKSPACE;
+    int split = 1;
+    if (!bins && !p.flags && p.split_k != 1) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return DDGEMM_ECUDA;
+        split = split_groups(m, n, k, sms, ws_bytes, p);
+    }
     char *ws = static_cast<char *>(workspace);
     double *a_s = reinterpret_cast<double *>(ws + L.off_a);
     double *b_s = reinterpret_cast<double *>(ws + L.off_b);
@@ -118,8 +177,10 @@ int run(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
     const int products = p.variant == DDGEMM_VARIANT_FP64_GEMM16    ? 1
                          : p.variant == DDGEMM_VARIANT_FP64_DROP456 ? 2
                                                                       : 0;
+    double *part = reinterpret_cast<double *>(ws + L.off_part);
+    double *part_lo = reinterpret_cast<double *>(ws + L.off_part + (size_t)(split - 1) * L.part_bytes);
     ddg::CascadeArgs ca{m, n, k, a_s, L.lda_s, b_s, L.ldb_s, e_a, e_b, C_hi, C_lo,
-                        (long long)ldc, p.flags, p.status, bins, products};
+                        (long long)ldc, p.flags, p.status, bins, products, split, part, part_lo};
     e = ddg::launch_cascade_fp64(ca, stream);
     return e == cudaSuccess && mark(2) ? DDGEMM_OK : DDGEMM_ECUDA;
 }
@@ -153,6 +214,18 @@ int run_int8(int m, int n, int k, const double *A_hi, const double *A_lo, int ld
 
 }  // namespace
 
+namespace ddg {
+
+size_t base_workspace_size(int m, int n, int k, const ddgemm_opts *opts) {
+    Parsed p;
+    if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
+    if (m == 0 || n == 0 || k == 0) return 0;
+    if (p.variant == DDGEMM_VARIANT_INT8) return layout8_for(m, n, k, p.slices).total;
+    return layout_for(m, n, k).base;
+}
+
+}  // namespace ddg
+
 extern "C" {
 
 size_t ddgemm_workspace_size(int m, int n, int k, const ddgemm_opts *opts) {
@@ -160,7 +233,13 @@ size_t ddgemm_workspace_size(int m, int n, int k, const ddgemm_opts *opts) {
     if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
     if (m == 0 || n == 0 || k == 0) return 0;
     if (p.variant == DDGEMM_VARIANT_INT8) return layout8_for(m, n, k, p.slices).total;
-    return layout_for(m, n, k).total;
+    return layout_for(m, n, k, split_reserve(m, n, k, p.split_k)).total;
+}
+
+int ddgemm_split_groups(int m, int n, int k, int sms, size_t ws_bytes, const ddgemm_opts *opts) {
+    Parsed p;
+    if (!parse(opts, p) || !dims_ok(m, n, k) || sms <= 0) return 0;
+    return split_groups(m, n, k, sms, ws_bytes, p);
 }
 
 int ddgemm(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
@@ -292,7 +371,7 @@ static void backward_calls(int m, int n, int k, const double *A_hi, const double
 size_t ddgemm_backward_workspace_size(int m, int n, int k, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
-    ddgemm_opts plain{0, 0, p.variant, nullptr, nullptr, nullptr, p.slices};
+    ddgemm_opts plain{0, 0, p.variant, nullptr, nullptr, nullptr, p.slices, p.split_k};
     const size_t a = ddgemm_workspace_size(p.trans_a ? k : m, p.trans_a ? m : k, n, &plain);
     const size_t b = ddgemm_workspace_size(p.trans_b ? n : k, p.trans_b ? k : n, m, &plain);
     return a > b ? a : b;
@@ -314,8 +393,8 @@ int ddgemm_backward(int m, int n, int k, const double *A_hi, const double *A_lo,
     if (ca.m > 0 && ca.n > 0 && (!dA_hi || !dA_lo || ldda < ca.n)) return DDGEMM_EINVAL;
     if (cb.m > 0 && cb.n > 0 && (!dB_hi || !dB_lo || lddb < cb.n)) return DDGEMM_EINVAL;
     if (ws_bytes < ddgemm_backward_workspace_size(m, n, k, opts)) return DDGEMM_EWORKSPACE;
-    ddgemm_opts oa{ca.ta, ca.tb, p.variant, p.status, nullptr, nullptr, p.slices};
-    ddgemm_opts ob{cb.ta, cb.tb, p.variant, p.status, nullptr, nullptr, p.slices};
+    ddgemm_opts oa{ca.ta, ca.tb, p.variant, p.status, nullptr, nullptr, p.slices, p.split_k};
+    ddgemm_opts ob{cb.ta, cb.tb, p.variant, p.status, nullptr, nullptr, p.slices, p.split_k};
     // both products run on one stream, so the second may reuse the workspace
     int r = ddgemm(ca.m, ca.n, ca.k, ca.ah, ca.al, ca.lda, ca.bh, ca.bl, ca.ldb, dA_hi, dA_lo,
                    ldda, workspace, ws_bytes, stream, &oa);

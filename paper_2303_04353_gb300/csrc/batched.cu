@@ -319,7 +319,8 @@ batched_cascade_kernel(char *ws) {
                                        smem + (nxt % NST) * T::STAGE + T::A_STAGE);
             cp_async_commit();
             if ((t + 1) % STEPS_PER_BLOCK == 0 || t + 1 == ksteps)
-                epilogue<false>(acc, t / STEPS_PER_BLOCK, m0 + wm * 16, n0 + wn * 32, lane, out);
+                epilogue<false>(acc, t / STEPS_PER_BLOCK, t < STEPS_PER_BLOCK, m0 + wm * 16,
+                                n0 + wn * 32, lane, out);
         }
         cp_async_wait<0>();
         __syncthreads();  // the next tile refills the stages

@@ -116,10 +116,11 @@ struct EpilogueOut {
 
 // End of k-block p for one warp's sub-tile at (row0, col0): bins 3-6 -> 2
 // -> 1 -> 0 in FP64x2, scale by 2^(e_a + e_b), FP64x2-add into C (C holds
-// the running sum between k-blocks), then clear the bins.
+// the running sum between k-blocks; `first` marks the first k-block summed
+// into this output, which starts from zero), then clear the bins.
 template <bool DUMP_BINS>
-__device__ __forceinline__ void epilogue(Acc &acc, int p, int row0, int col0, int lane,
-                                         const EpilogueOut &o) {
+__device__ __forceinline__ void epilogue(Acc &acc, int p, bool first, int row0, int col0,
+                                         int lane, const EpilogueOut &o) {
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const int row = row0 + i * 8 + (lane >> 2);
@@ -147,7 +148,7 @@ __device__ __forceinline__ void epilogue(Acc &acc, int p, int row0, int col0, in
                         sl = scalbn(sl, sc);
                         const long long x = (long long)row * o.ldc + col;
                         double ch = 0.0, cl = 0.0;
-                        if (p > 0) {
+                        if (!first) {
                             ch = o.c_hi[x];
                             cl = o.c_lo[x];
                         }
@@ -156,7 +157,7 @@ __device__ __forceinline__ void epilogue(Acc &acc, int p, int row0, int col0, in
                         o.c_lo[x] = cl;
                         if (o.flags) {
                             const long long fx = (long long)row * o.n + col;
-                            int f = p > 0 ? o.flags[fx] : 0;
+                            int f = first ? 0 : o.flags[fx];
                             if (b0 == 0.0 && (sh != 0.0 || sl != 0.0)) ++f;
                             o.flags[fx] = f;
                         }

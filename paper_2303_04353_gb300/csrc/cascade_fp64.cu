@@ -58,10 +58,17 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp & 3, wn = warp >> 2;
+    const int tiles_m = (args.m + BM - 1) / BM, tiles_n = (args.n + BN - 1) / BN;
+    const unsigned tiles = (unsigned)tiles_m * (unsigned)tiles_n;
+    const int part = (int)(blockIdx.x / tiles);     // k-block group (split-k)
     int tm, tn;
-    grouped_tile(blockIdx.x, (args.m + BM - 1) / BM, (args.n + BN - 1) / BN, 8, tm, tn);
+    grouped_tile(blockIdx.x % tiles, tiles_m, tiles_n, 8, tm, tn);
     const int m0 = tm * BM, n0 = tn * BN;
-    const int ksteps = (args.k + BK - 1) / BK;
+    const int total_steps = (args.k + BK - 1) / BK;
+    const int kblocks = (args.k + KC - 1) / KC;
+    const int kb_begin = part * kblocks / args.split, kb_end = (part + 1) * kblocks / args.split;
+    const int t0 = kb_begin * STEPS_PER_BLOCK;
+    const int ksteps = min(kb_end * STEPS_PER_BLOCK, total_steps) - t0;
 
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) mbar_init(smem_addr(&bars[s]), 1);
@@ -73,8 +80,8 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
         const uint32_t bar = smem_addr(&bars[stage]);
         double *dst = smem + stage * STAGE;
         mbar_arrive_expect_tx(bar, STAGE_BYTES);
-        tma_load_3d(smem_addr(dst), &tm_a, bar, t * BK, m0, 0);
-        tma_load_3d(smem_addr(dst + A_STAGE), &tm_b, bar, n0, t * BK, 0);
+        tma_load_3d(smem_addr(dst), &tm_a, bar, (t0 + t) * BK, m0, 0);
+        tma_load_3d(smem_addr(dst + A_STAGE), &tm_b, bar, n0, (t0 + t) * BK, 0);
     };
     if (tid == 0) {
         for (int s = 0; s < NST && s < ksteps; ++s) issue(s, s);
@@ -82,8 +89,14 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
 
     Acc acc;
     zero_acc(acc);
-    const EpilogueOut out{args.m, args.n, args.exp_a, args.exp_b, args.c_hi, args.c_lo,
-                          args.ldc, args.flags, args.bins};
+    // group 0 sums into C; the others into their partial buffers
+    const long long mn = (long long)args.m * args.n;
+    const EpilogueOut out =
+        part == 0 ? EpilogueOut{args.m, args.n, args.exp_a, args.exp_b, args.c_hi, args.c_lo,
+                                args.ldc, args.flags, args.bins}
+                  : EpilogueOut{args.m, args.n, args.exp_a, args.exp_b,
+                                args.part_hi + (part - 1) * mn, args.part_lo + (part - 1) * mn,
+                                args.n, nullptr, nullptr};
 
     for (int t = 0; t < ksteps; ++t) {
         const int stage = t % NST;
@@ -104,10 +117,28 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
         __syncthreads();  // every warp is done with this stage
         if (tid == 0 && t + NST < ksteps) issue(t + NST, stage);
 
-        if ((t + 1) % STEPS_PER_BLOCK == 0 || t + 1 == ksteps) {
-            epilogue<DUMP_BINS>(acc, t / STEPS_PER_BLOCK, m0 + wm * 16, n0 + wn * 32, lane, out);
+        const int ta = t0 + t;  // the k-step in the whole of k
+        if ((ta + 1) % STEPS_PER_BLOCK == 0 || ta + 1 == total_steps) {
+            const int p = ta / STEPS_PER_BLOCK;
+            epilogue<DUMP_BINS>(acc, p, p == kb_begin, m0 + wm * 16, n0 + wn * 32, lane, out);
             if constexpr (DUMP_BINS) return;
         }
+    }
+}
+
+// Split-k: C (group 0) += the partial sums of groups 1..parts-1, in order,
+// in FP64x2.
+__global__ void __launch_bounds__(256)
+split_fixup_kernel(int m, int n, double *c_hi, double *c_lo, long long ldc, const double *p_hi,
+                   const double *p_lo, int parts) {
+    const long long mn = (long long)m * n;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < mn;
+         x += (long long)gridDim.x * blockDim.x) {
+        const long long o = (x / n) * ldc + x % n;
+        double h = c_hi[o], l = c_lo[o];
+        for (int q = 0; q < parts - 1; ++q) dd_add(h, l, p_hi[q * mn + x], p_lo[q * mn + x], h, l);
+        c_hi[o] = h;
+        c_lo[o] = l;
     }
 }
 
@@ -126,13 +157,40 @@ cudaError_t launch_impl(const CascadeArgs &a, cudaStream_t stream) {
         (int)SMEM_BYTES);
     if (attr_err != cudaSuccess) return attr_err;
     const long long tiles = (long long)((a.n + BN - 1) / BN) * ((a.m + BM - 1) / BM);
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    cascade_fp64_kernel<DUMP, PRODUCTS><<<(unsigned)tiles, NTHREADS, SMEM_BYTES, stream>>>(
-        tm_a, tm_b, a);
+    if (tiles * a.split > 0x7fffffffLL || a.split < 1) return cudaErrorInvalidValue;
+    cascade_fp64_kernel<DUMP, PRODUCTS><<<(unsigned)(tiles * a.split), NTHREADS, SMEM_BYTES,
+                                          stream>>>(tm_a, tm_b, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.split == 1) return e;
+    const long long mn = (long long)a.m * a.n;
+    const long long blocks = (mn + 255) / 256;
+    split_fixup_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, stream>>>(
+        a.m, a.n, a.c_hi, a.c_lo, a.ldc, a.part_hi, a.part_lo, a.split);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+int choose_split(long long tiles, int kblocks, int slots, int cap) {
+    // Estimated span in k-block times: ceil(CTAs / slots) waves of the
+    // longest group (ceil(kblocks / s) k-blocks), plus a 0.2% charge per
+    // extra group for the partial sums and the fix-up pass (measured on
+    // GB300: a CTA's start-up and epilogue cost well under 1% of a k-block);
+    // the least wins, ties to fewer groups.
+    if (tiles <= 0 || kblocks <= 0 || slots <= 0) return 1;
+    int best = 1;
+    double best_span = 0.0;
+    for (int s = 1; s <= cap && s <= kblocks; ++s) {
+        const long long waves = (tiles * s + slots - 1) / slots;
+        const int longest = (kblocks + s - 1) / s;
+        const double span = (double)(waves * longest) * (1.0 + 0.002 * (s - 1));
+        if (s == 1 || span < best_span) {
+            best_span = span;
+            best = s;
+        }
+    }
+    return best;
+}
 
 cudaError_t launch_cascade_fp64(const CascadeArgs &a, cudaStream_t stream) {
     if (a.m <= 0 || a.n <= 0 || a.k <= 0) return cudaSuccess;

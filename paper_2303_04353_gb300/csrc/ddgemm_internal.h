@@ -5,6 +5,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "../../include/ddgemm.h"
+
 namespace ddg {
 
 // k-block of the exactness argument (Sec. "Blocking for the k dimension").
@@ -42,7 +44,17 @@ struct CascadeArgs {
     unsigned int *status;    // optional
     double *bins;            // when non-null: write the bins of k-block 0 instead of C
     int products;            // 0: eq. Gemm10 (the method); 1: Gemm16; 2: bins 4-6 dropped
+    int split;               // k-block groups per tile (1: no split)
+    double *part_hi, *part_lo;  // split > 1: partial C of groups 1..split-1, [split-1][m][n]
 };
+
+// Split-k over whole k-blocks: the number of groups for a grid of `tiles`
+// CTAs on `slots` resident CTAs, at most `cap` (and one k-block per group).
+int choose_split(long long tiles, int kblocks, int slots, int cap);
+
+// The least workspace ddgemm() accepts: ddgemm_workspace_size() without the
+// room for split-k partial sums (api.cu).
+size_t base_workspace_size(int m, int n, int k, const ddgemm_opts *opts);
 
 // The ten products of eq. Gemm10 on the FP64 tensor path with the bin
 // assembly fused in (one launch).

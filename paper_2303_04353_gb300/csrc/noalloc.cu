@@ -19,6 +19,7 @@
 #include <unordered_map>
 
 #include "../../include/ddgemm.h"
+#include "ddgemm_internal.h"
 
 namespace {
 
@@ -47,7 +48,9 @@ extern "C" int ddgemm_noalloc(int m, int n, int k, const double *A_hi, const dou
                               double *C_hi, double *C_lo, int ldc, void *stream,
                               const ddgemm_opts *opts) {
     if (m < 0 || n < 0 || k < 0) return DDGEMM_EINVAL;
-    const size_t need = ddgemm_workspace_size(m, n, k, opts);
+    // ddgemm() needs at least the base workspace; the rest of the array gives
+    // it room for split-k partial sums when they fit
+    const size_t need = ddg::base_workspace_size(m, n, k, opts);
     if (need > (size_t)DDGEMM_NOALLOC_SCRATCH_BYTES) return DDGEMM_EWORKSPACE;
     if (need == 0) {
         // empty problem or k = 0: ddgemm needs no workspace

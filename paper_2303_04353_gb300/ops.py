@@ -28,21 +28,32 @@ def current_stream_ptr(stream: torch.cuda.Stream | None = None) -> int:
 
 
 def workspace_bytes(m: int, n: int, k: int, variant: int = _lib.DDGEMM_VARIANT_FP64,
-                    int8_slices: int = 0) -> int:
-    return _lib.ddgemm_workspace_size(m, n, k, _lib.make_opts(variant=variant,
-                                                              int8_slices=int8_slices))
+                    int8_slices: int = 0, split_k: int = 0) -> int:
+    return _lib.ddgemm_workspace_size(m, n, k, _lib.make_opts(
+        variant=variant, int8_slices=int8_slices, split_k=split_k))
+
+
+def split_groups(m: int, n: int, k: int, device=None, ws_bytes: int | None = None,
+                 variant: int = _lib.DDGEMM_VARIANT_FP64, split_k: int = 0) -> int:
+    """Split-k groups ddgemm() launches on `device` with a workspace of
+    ws_bytes (default: workspace_bytes())."""
+    opts = _lib.make_opts(variant=variant, split_k=split_k)
+    if ws_bytes is None:
+        ws_bytes = _lib.ddgemm_workspace_size(m, n, k, opts)
+    sms = torch.cuda.get_device_properties(device or torch.cuda.current_device()).multi_processor_count
+    return _lib.load().ddgemm_split_groups(m, n, k, sms, ws_bytes, ctypes.byref(opts))
 
 
 def alloc_workspace(m: int, n: int, k: int, device=None, variant: int = _lib.DDGEMM_VARIANT_FP64,
-                    int8_slices: int = 0) -> torch.Tensor:
-    nbytes = workspace_bytes(m, n, k, variant, int8_slices)
+                    int8_slices: int = 0, split_k: int = 0) -> torch.Tensor:
+    nbytes = workspace_bytes(m, n, k, variant, int8_slices, split_k)
     # torch's caching allocator hands out 512-byte aligned blocks
     return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device or "cuda")
 
 
 def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, workspace=None,
            status=None, flags=None, stream=None, phase_events=None,
-           variant=_lib.DDGEMM_VARIANT_FP64, int8_slices=0):
+           variant=_lib.DDGEMM_VARIANT_FP64, int8_slices=0, split_k=0):
     """C := op(A) op(B) in FP64x2 by the ten-GEMM cascade.  Returns (c_hi, c_lo).
 
     trans_a: A is stored k x m and op(A) = A^T (likewise trans_b: B stored n x k).
@@ -52,7 +63,8 @@ def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, wo
     phase_events: optional three recorded torch.cuda.Event objects; the library
     re-records them around the split and the cascade kernel on the stream.
     variant: DDGEMM_VARIANT_FP64 (ten FP64 products) or DDGEMM_VARIANT_INT8
-    (int8_slices INT8 pieces per entry, 0 = 16)."""
+    (int8_slices INT8 pieces per entry, 0 = 16).
+    split_k: 0 = automatic split-k for small grids, 1 = never, 2-16 = forced."""
     lda = _check_pair(a_hi, a_lo, "A")
     ldb = _check_pair(b_hi, b_lo, "B")
     m, k = (a_hi.shape[1], a_hi.shape[0]) if trans_a else tuple(a_hi.shape)
@@ -69,7 +81,7 @@ def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, wo
             raise ValueError("out has the wrong shape")
     ldc = _check_pair(c_hi, c_lo, "C")
     if workspace is None:
-        workspace = alloc_workspace(m, n, k, dev, variant, int8_slices)
+        workspace = alloc_workspace(m, n, k, dev, variant, int8_slices, split_k)
     if status is not None and (status.dtype != torch.int32 or not status.is_cuda):
         raise TypeError("status must be an int32 CUDA tensor")
     if flags is not None and (flags.dtype != torch.int32 or not flags.is_contiguous()
@@ -82,7 +94,7 @@ def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, wo
         evs = (ctypes.c_void_p * 3)(*[e.cuda_event for e in phase_events])
     opts = _lib.make_opts(trans_a, trans_b, variant,
                           status.data_ptr() if status is not None else 0,
-                          flags.data_ptr() if flags is not None else 0, evs, int8_slices)
+                          flags.data_ptr() if flags is not None else 0, evs, int8_slices, split_k)
     _lib.ddgemm(m, n, k, a_hi.data_ptr(), a_lo.data_ptr(), lda, b_hi.data_ptr(),
                 b_lo.data_ptr(), ldb, c_hi.data_ptr(), c_lo.data_ptr(), ldc,
                 workspace.data_ptr(), workspace.numel(), current_stream_ptr(stream), opts)

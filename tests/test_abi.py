@@ -52,6 +52,56 @@ def test_workspace_size():
     assert ws(3, 5, 7) % 256 == 0
 
 
+def split_groups(m, n, k, sms=152, ws_bytes=None, **kw):
+    opts = _lib.make_opts(**kw)
+    if ws_bytes is None:
+        ws_bytes = _lib.ddgemm_workspace_size(m, n, k, opts)
+    return _lib.load().ddgemm_split_groups(m, n, k, sms, ws_bytes, ctypes.byref(opts))
+
+
+def test_split_k_workspace_and_choice():
+    """Split-k: room for partial C only for grids below 4096 tiles of 64 x
+    64 (at most min(16, k-blocks, ceil(8192 / tiles)) groups), as many
+    groups as give the shortest span in k-block times, none without room."""
+    ws = _lib.ddgemm_workspace_size
+    base = ws(512, 512, 4096, _lib.make_opts(split_k=1))
+    # 64 tiles, 16 k-blocks: fifteen partial C of 512 x 512 FP64x2 entries
+    assert ws(512, 512, 4096) == base + 15 * 2 * 512 * 512 * 8
+    assert ws(4096, 4096, 4096) == ws(4096, 4096, 4096, _lib.make_opts(split_k=1))
+    assert ws(512, 512, 4096, _lib.make_opts(split_k=2)) == base + 2 * 512 * 512 * 8
+    # 2048 tiles: at most ceil(8192 / 2048) = 4 groups, 3 partials
+    assert ws(8192, 1024, 4096) - ws(8192, 1024, 4096, _lib.make_opts(split_k=1)) == \
+        3 * 2 * 8192 * 1024 * 8
+    # 4096 tiles fill 152 SMs in 27 waves: no split
+    assert split_groups(4096, 4096, 4096) == 1
+    # 64 tiles on 152 SMs: 1024 CTAs of one k-block in 7 waves (span 7)
+    # beat 128 CTAs of 8 k-blocks in one wave (span 8)
+    assert split_groups(512, 512, 4096) == 16
+    # 2048 tiles, 16 k-blocks: 27 waves of 8 blocks beat 14 waves of 16
+    assert split_groups(8192, 1024, 4096) == 2
+    # 256 tiles, 4 k-blocks: 7 waves of one block beat 2 waves of four
+    assert split_groups(1000, 1000, 1000) == 4
+    # 16 tiles, 64 k-blocks: 8 groups of 8 blocks fill one wave of 128 CTAs
+    assert split_groups(256, 256, 16384) == 8
+    # 256 tiles, 32 k-blocks: 27 waves of 2 blocks (span 54) beat 7 waves
+    # of 8 (span 56)
+    assert split_groups(1024, 1024, 8192) == 16
+    # 1024 tiles, 8 k-blocks: 27 waves of 2 blocks tie 54 waves of one;
+    # the tie goes to fewer groups
+    assert split_groups(2048, 2048, 2048) == 4
+    assert split_groups(512, 512, 256) == 1                    # one k-block
+    assert split_groups(64, 64, 8192) == 16                    # at most 16
+    assert split_groups(512, 512, 4096, split_k=1) == 1
+    assert split_groups(512, 512, 4096, split_k=3) == 3
+    assert split_groups(100, 100, 600, split_k=4) == 3         # 3 k-blocks
+    assert split_groups(100, 100, 20000, split_k=40) == 16     # at most 16
+    assert split_groups(512, 512, 4096, ws_bytes=base) == 1    # no room
+    assert split_groups(512, 512, 4096, ws_bytes=base + 2 * 512 * 512 * 8, split_k=4) == 2
+    assert split_groups(512, 512, 4096, variant=_lib.DDGEMM_VARIANT_INT8) == 1
+    assert split_groups(512, 512, 4096, sms=0) == 0
+    assert split_groups(512, 512, 4096, split_k=-1) == 0
+
+
 def call(m, n, k, lda, ldb, ldc, ws=FAKE, ws_bytes=1 << 40, opts=None):
     lib = _lib.load()
     return lib.ddgemm(m, n, k, FAKE, FAKE, lda, FAKE, FAKE, ldb, FAKE, FAKE, ldc, ws, ws_bytes,

@@ -42,7 +42,9 @@ def make_batch(ops, shapes, seed=0, kind="uniform"):
 def reference(ops, probs):
     out = []
     for a_hi, a_lo, b_hi, b_lo, _, _ in probs:
-        c_hi, c_lo = ops.ddgemm(a_hi, a_lo, b_hi, b_lo)
+        # one launch per problem in the paper's k order (no split-k), which
+        # the batched kernel follows bit for bit
+        c_hi, c_lo = ops.ddgemm(a_hi, a_lo, b_hi, b_lo, split_k=1)
         out.append((c_hi, c_lo))
     torch.cuda.synchronize()
     return [(h.cpu().numpy(), l.cpu().numpy()) for h, l in out]

@@ -118,13 +118,34 @@ def cascade_tolerance(a_hi, b_hi, c_ref):
     return tol + 8 * e_a.shape[1] * 2.0 ** -106 * np.abs(c_ref)
 
 
+def split_groups(m, n, k, split_k=0):
+    """Split-k groups ddgemm() uses on this GPU with its default workspace."""
+    from paper_2303_04353_gb300 import _lib
+    import ctypes
+    opts = _lib.make_opts(split_k=split_k)
+    ws = _lib.ddgemm_workspace_size(m, n, k, opts)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return _lib.load().ddgemm_split_groups(m, n, k, sms, ws, ctypes.byref(opts))
+
+
+def split_tolerance(a_hi, b_hi, groups):
+    """Extra |C_gpu - C_cascade_oracle| when the k-blocks are summed in
+    groups: each FP64x2 addition of the per-block values, in either order,
+    errs by a few 2^-106 of a partial sum, and every partial sum is at most
+    sum_p |block p's value| <= (1 + eps) |A||B|."""
+    if groups <= 1:
+        return 0.0
+    kb = -(-a_hi.shape[1] // cs.KC)
+    return 8 * (kb + groups) * 2.0 ** -106 * exact.abs_product(a_hi, b_hi)
+
+
 def check_against_oracles(ops, a_hi, a_lo, b_hi, b_lo, trans_a=False, trans_b=False,
-                          contract=True):
+                          contract=True, split_k=0):
     src_a = (a_hi.T, a_lo.T) if trans_a else (a_hi, a_lo)
     src_b = (b_hi.T, b_lo.T) if trans_b else (b_hi, b_lo)
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     c_hi, c_lo = ops.ddgemm(*dev(*src_a), *dev(*src_b), trans_a=trans_a, trans_b=trans_b,
-                            status=status)
+                            status=status, split_k=split_k)
     c_hi, c_lo, st = host(c_hi, c_lo, status)
     assert st[0] == 0
     assert exact.dd_is_normalised(c_hi, c_lo)
@@ -138,7 +159,8 @@ def check_against_oracles(ops, a_hi, a_lo, b_hi, b_lo, trans_a=False, trans_b=Fa
         assert np.all(diff <= CONTRACT * absab), float(np.max(diff / np.maximum(absab, 1e-300)))
     s_hi, s_lo = cs.cascade_ddgemm(a_hi, a_lo, b_hi, b_lo)
     dcs = np.abs((c_hi - s_hi) + (c_lo - s_lo))
-    assert np.all(dcs <= cascade_tolerance(a_hi, b_hi, s_hi))
+    groups = split_groups(*c_hi.shape, k, split_k)
+    assert np.all(dcs <= cascade_tolerance(a_hi, b_hi, s_hi) + split_tolerance(a_hi, b_hi, groups))
     return c_hi, c_lo
 
 
@@ -162,6 +184,68 @@ def test_ddgemm_transposed(ops, ta, tb):
     check_against_oracles(ops, *a, trans_a=ta, trans_b=tb, contract=False)
     a = gemm_inputs(70, 90, 300, kind="uniform", seed=6)
     check_against_oracles(ops, *a, trans_a=ta, trans_b=tb)
+
+
+@pytest.mark.parametrize("m,n,k", [(70, 33, 1000), (130, 65, 2049), (1, 1, 600),
+                                   (200, 150, 3000)])
+@pytest.mark.parametrize("split_k", [2, 3, 5, 16])
+@pytest.mark.parametrize("kind", ["uniform", "wide"])
+def test_split_k_forced(ops, m, n, k, split_k, kind):
+    """Split-k over k-blocks: each group sums its run of blocks from zero
+    and one more kernel adds the groups in order; C stays within the paper's
+    bound and the contract, and within the FP64x2 reordering of the cascade
+    restatement."""
+    assert split_groups(m, n, k, split_k) == min(split_k, -(-k // 256))
+    a = gemm_inputs(m, n, k, kind=kind, seed=7 * split_k + k)
+    check_against_oracles(ops, *a, contract=kind == "uniform", split_k=split_k)
+
+
+@pytest.mark.parametrize("ta,tb", [(True, False), (False, True)])
+def test_split_k_transposed_ragged(ops, ta, tb):
+    a = gemm_inputs(97, 61, 1300, kind="uniform", seed=31)
+    check_against_oracles(ops, *a, trans_a=ta, trans_b=tb, split_k=3)
+
+
+def test_split_k_auto_small_grid(ops):
+    """A 512 x 512 grid of 64 tiles leaves most SMs idle: the automatic
+    choice splits it."""
+    m = n = 512
+    k = 2048
+    assert split_groups(m, n, k) > 1
+    a = gemm_inputs(m, n, k, kind="uniform", seed=3)
+    check_against_oracles(ops, *a)
+
+
+def test_split_k_without_room_is_unsplit(ops):
+    """A workspace of the size without partials gives the unsplit order,
+    bit for bit, and so does split_k = 1."""
+    from paper_2303_04353_gb300 import _lib
+    m, n, k = 256, 192, 1500
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind="wide", seed=8)
+    A = dev(a_hi, a_lo, b_hi, b_lo)
+    base = _lib.ddgemm_workspace_size(m, n, k, _lib.make_opts(split_k=1))
+    assert base < _lib.ddgemm_workspace_size(m, n, k)
+    ws = torch.empty(base, dtype=torch.uint8, device="cuda")
+    outs = []
+    stream = torch.cuda.current_stream().cuda_stream
+    for split_k, nbytes in [(0, base), (1, base)]:
+        c = [torch.full((m, n), np.nan, dtype=torch.float64, device="cuda") for _ in range(2)]
+        _lib.ddgemm(m, n, k, A[0].data_ptr(), A[1].data_ptr(), k, A[2].data_ptr(),
+                    A[3].data_ptr(), n, c[0].data_ptr(), c[1].data_ptr(), n, ws.data_ptr(),
+                    nbytes, stream, _lib.make_opts(split_k=split_k))
+        outs.append(host(*c))
+    c_auto = host(*ops.ddgemm(*A, split_k=1))
+    for got in outs:
+        assert np.array_equal(got[0], c_auto[0]) and np.array_equal(got[1], c_auto[1])
+
+
+def test_split_k_identical_across_calls(ops):
+    """Same inputs, same grouping: the same bits on every call."""
+    a = dev(*gemm_inputs(300, 200, 2500, kind="wide", seed=4))
+    first = host(*ops.ddgemm(*a, split_k=4))
+    for _ in range(3):
+        again = host(*ops.ddgemm(*a, split_k=4))
+        assert np.array_equal(first[0], again[0]) and np.array_equal(first[1], again[1])
 
 
 def test_integer_matrices_exact(ops):
@@ -296,7 +380,7 @@ def test_ablation_variants_match_their_restatement(ops, variant, products, kind)
     to FP64 summation order."""
     m, n, k = 80, 70, 600
     a = gemm_inputs(m, n, k, kind=kind, seed=90 + variant)
-    c_hi, c_lo = host(*ops.ddgemm(*dev(*a), variant=variant))
+    c_hi, c_lo = host(*ops.ddgemm(*dev(*a), variant=variant, split_k=1))
     s_hi, s_lo = cs.cascade_ddgemm(*a, products=products)
     tol = cascade_tolerance(a[0], a[2], s_hi) * (2 if variant == 2 else 1)
     assert np.all(np.abs((c_hi - s_hi) + (c_lo - s_lo)) <= tol)

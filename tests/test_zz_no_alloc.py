@@ -25,7 +25,10 @@ FAKE = 0x10000  # never dereferenced: the size check answers before any CUDA cal
 def test_noalloc_rejects_problems_beyond_its_scratch():
     lib = _lib.load()
     big = 873  # 873^3 needs 64.5 MiB of scratch, more than the 64 MiB array
-    assert _lib.ddgemm_workspace_size(big, big, big) > _lib.DDGEMM_NOALLOC_SCRATCH_BYTES
+    no_split = _lib.make_opts(split_k=1)   # the least workspace ddgemm takes
+    assert _lib.ddgemm_workspace_size(big, big, big, no_split) > _lib.DDGEMM_NOALLOC_SCRATCH_BYTES
+    assert (_lib.ddgemm_workspace_size(big - 1, big - 1, big - 1, no_split)
+            <= _lib.DDGEMM_NOALLOC_SCRATCH_BYTES)
     rc = lib.ddgemm_noalloc(big, big, big, FAKE, FAKE, big, FAKE, FAKE, big, FAKE, FAKE, big,
                             None, None)
     assert rc == _lib.DDGEMM_EWORKSPACE
