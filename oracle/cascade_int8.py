@@ -26,8 +26,15 @@ below (listed in the design doc) fill it in.
     (exact in FP64) is added into an FP64x2 sum (TwoSum, add lo,
     FastTwoSum); the block result is scaled by sigma tau and added into C
     with the FP64x2 add, as in the FP64 form.
+  * Exact assembly (assembly="exact"; the tensor-core form of the library
+    uses it): the diagonal sums are integers, so the block value
+    sum_t S_t 2^(-12-7t) sigma tau is formed exactly and rounded once to the
+    nearest FP64x2 (hi = RN(x), lo = RN(x - hi)); the blocks are then added
+    into C with the FP64x2 add as above.
 """
 from __future__ import annotations
+
+from fractions import Fraction
 
 import numpy as np
 
@@ -108,8 +115,38 @@ def assemble(diag: np.ndarray, s: int):
     return h, l
 
 
-def cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16, kb=KB8, return_parts=False):
-    """C := A B through s INT8 pieces per entry.  Returns (C_hi, C_lo)."""
+def round_dd(num: int, exp2: int):
+    """The nearest FP64x2 to the exact x = num 2^exp2: hi = RN(x) and
+    lo = RN(x - hi), round to nearest, ties to even (Python's int / int and
+    Fraction -> float conversions round correctly)."""
+    x = Fraction(num) * Fraction(2) ** exp2
+    hi = float(x)
+    lo = float(x - Fraction(hi))
+    return hi, lo
+
+
+def assemble_exact(diag: np.ndarray, s: int, scale: np.ndarray):
+    """The block value sum_t S_t 2^(-12-7t) 2^scale of every entry, formed
+    exactly from the integer diagonal sums and rounded once to FP64x2."""
+    m, n = diag.shape[1:]
+    h = np.zeros((m, n))
+    l = np.zeros((m, n))
+    for i in range(m):
+        for j in range(n):
+            t_sum = 0
+            for t in range(s):
+                t_sum += int(diag[t, i, j]) << (DIGIT * (s - 1 - t))
+            h[i, j], l[i, j] = round_dd(t_sum, int(scale[i, j]) - 12 - DIGIT * (s - 1))
+    return h, l
+
+
+def cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16, kb=KB8, return_parts=False,
+                        assembly="fp64x2"):
+    """C := A B through s INT8 pieces per entry.  Returns (C_hi, C_lo).
+    assembly: "fp64x2" (diagonals added smallest first in FP64x2) or
+    "exact" (the exact block value rounded once)."""
+    if assembly not in ("fp64x2", "exact"):
+        raise ValueError(assembly)
     a_hi = np.asarray(a_hi, np.float64)
     a_lo = np.asarray(a_lo, np.float64)
     bt_hi = np.ascontiguousarray(np.asarray(b_hi, np.float64).T)   # columns of B as rows
@@ -126,9 +163,12 @@ def cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16, kb=KB8, return_parts=False
         da = digit_planes(a_hi[:, sl], a_lo[:, sl], e_a[:, p:p + 1], s, kb=k + 1)
         db = digit_planes(bt_hi[:, sl], bt_lo[:, sl], e_b[:, p:p + 1], s, kb=k + 1)
         diag = diagonal_sums(da, db, s)
-        h, l = assemble(diag, s)
         sc = e_a[:, p][:, None] + e_b[:, p][None, :]
-        h, l = np.ldexp(h, sc), np.ldexp(l, sc)
+        if assembly == "exact":
+            h, l = assemble_exact(diag, s, sc)
+        else:
+            h, l = assemble(diag, s)
+            h, l = np.ldexp(h, sc), np.ldexp(l, sc)
         c_hi, c_lo = _fp64.dd_add(c_hi, c_lo, h, l)
         if return_parts:
             parts.append((da, db, diag))

@@ -133,7 +133,121 @@ def test_int8_worked_example():
     assert c_hi[0, 0] == eps_hi and c_lo[0, 0] == 0.0
 
 
+# ---- exact assembly (the tensor-core form) ---------------------------------
+
+def is_nearest(x: Fraction, v: float) -> bool:
+    """v is a round-to-nearest-even double of x: no neighbour of v is
+    closer, and an exact tie picks the even significand."""
+    if v == 0.0:
+        return abs(x) <= Fraction(2.0 ** -1075)
+    up, down = math.nextafter(v, math.inf), math.nextafter(v, -math.inf)
+    d = abs(x - Fraction(v))
+    if d > abs(x - Fraction(up)) or d > abs(x - Fraction(down)):
+        return False
+    if d == abs(x - Fraction(up)) or d == abs(x - Fraction(down)):
+        return (Fraction(v) / Fraction(math.ulp(v))).numerator % 2 == 0
+    return True
+
+
+def hard_block_values():
+    """Exact integers T (and exponents) with ties and near-ties at both
+    roundings, carries across 2^53, cancellation, and full-width values."""
+    rnd = random.Random(9)
+    out = []
+    for _ in range(300):
+        bits = rnd.randint(1, 137)
+        out.append((rnd.choice((-1, 1)) * rnd.getrandbits(bits), rnd.randint(-140, 10)))
+    for top in (2 ** 52 + 1, 2 ** 53 - 1, 2 ** 52, 3):
+        for sh in (1, 2, 30, 53, 60, 83):
+            half = 1 << (sh - 1)
+            for rem in (half, half - 1, half + 1, 0):
+                t = (top << sh) + rem
+                out += [(t, -117), (-t, -50)]
+                # a tie in the second rounding: lo = 2^54 + 1 then half an ulp
+                t2 = (top << (sh + 56)) + (((1 << 54) + 1) << 2) + 2
+                out.append((t2, -200))
+    return out
+
+
+def test_round_dd_is_the_nearest_fp64x2():
+    for t, e in hard_block_values():
+        hi, lo = c8.round_dd(t, e)
+        x = Fraction(t) * Fraction(2) ** e
+        assert is_nearest(x, hi), (t, e)
+        assert is_nearest(x - Fraction(hi), lo), (t, e)
+
+
+def test_exact_assembly_brute_force():
+    """Block value of random diagonal sums against the exact rational sum of
+    S_t 2^(-12-7t) 2^scale, entry by entry."""
+    rng = np.random.default_rng(11)
+    s = 16
+    diag = rng.integers(-(2 ** 30), 2 ** 30, (s, 3, 4))
+    diag[:, 0, 0] = 0
+    diag[5:, 1, 1] = 0                       # short expansions
+    diag[0, 2, 3] = 2 ** 30                  # the largest sum a k-block allows
+    scale = rng.integers(-30, 30, (3, 4))
+    h, l = c8.assemble_exact(diag, s, scale)
+    for i in range(3):
+        for j in range(4):
+            x = sum(Fraction(int(diag[t, i, j])) * Fraction(2) ** (-12 - 7 * t) for t in range(s))
+            x *= Fraction(2) ** int(scale[i, j])
+            assert is_nearest(x, h[i, j]) and is_nearest(x - Fraction(h[i, j]), l[i, j])
+
+
+@pytest.mark.parametrize("m,n,k,kind,s", [(5, 6, 200, "uniform", 16), (4, 5, 300, "wide", 16),
+                                          (3, 3, 64, "uniform", 12)])
+def test_exact_assembly_meets_bound(m, n, k, kind, s):
+    def fn(*a, s):
+        return c8.cascade_int8_ddgemm(*a, s=s, assembly="exact")
+    assert max_ratio(fn, m, n, k, kind, k + 1, s) <= 1.0
+
+
+def test_exact_assembly_integers_and_worked_example():
+    a_hi, a_lo, b_hi, b_lo = integer_inputs(5, 4, 120, bits=10, seed=5)
+    c_hi, c_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=6, assembly="exact")
+    ref = a_hi.astype(np.int64) @ b_hi.astype(np.int64)
+    assert np.array_equal(c_hi, ref.astype(np.float64)) and np.all(c_lo == 0)
+    eps_hi, eps_lo = 1.5 * 2.0 ** -71, 2.0 ** -130
+    c_hi, c_lo = c8.cascade_int8_ddgemm(np.array([[1.0, eps_hi]]), np.array([[0.0, eps_lo]]),
+                                        np.array([[0.0], [1.0]]), np.zeros((2, 1)), s=16,
+                                        assembly="exact")
+    assert c_hi[0, 0] == eps_hi and c_lo[0, 0] == 0.0
+
+
+def test_exact_and_fp64x2_assembly_agree_closely():
+    """Same diagonal sums, two assemblies: they differ by the FP64x2
+    roundings of the smallest-first sum only."""
+    a = gemm_inputs(6, 7, 500, kind="wide", seed=12)
+    x_hi, x_lo = c8.cascade_int8_ddgemm(*a, s=16, assembly="exact")
+    y_hi, y_lo = c8.cascade_int8_ddgemm(*a, s=16)
+    diff = np.abs((x_hi - y_hi) + (x_lo - y_lo))
+    assert np.all(diff <= 4 * 16 * 2.0 ** -106 * (np.abs(a[0]) @ np.abs(a[2])))
+
+
 # ---- planted mistakes ------------------------------------------------------
+
+def test_planted_exact_assembly_rounding_is_caught(monkeypatch):
+    def truncating(num, exp2):
+        # hi as it should be, lo rounded toward zero at 40 bits
+        x = Fraction(num) * Fraction(2) ** exp2
+        hi = float(x)
+        lo = float(x - Fraction(hi))
+        if lo:
+            e = math.frexp(lo)[1]
+            lo = math.ldexp(math.trunc(math.ldexp(lo, 40 - e)), e - 40)
+        return hi, lo
+    monkeypatch.setattr(c8, "round_dd", truncating)
+    with pytest.raises(AssertionError):
+        test_round_dd_is_the_nearest_fp64x2()
+
+
+def test_planted_exact_assembly_weight_is_caught(monkeypatch):
+    real = c8.round_dd
+    monkeypatch.setattr(c8, "round_dd", lambda num, e: real(num, e + 1))
+    with pytest.raises(AssertionError):
+        test_exact_assembly_brute_force()
+
 
 def test_planted_dropped_diagonal_is_caught(monkeypatch):
     real = c8.diagonal_sums
