@@ -63,6 +63,10 @@ extern "C" {
 #define DDGEMM_VARIANT_FP64_GEMM16  2 /* all sixteen products of eq. Gemm16 */
 #define DDGEMM_VARIANT_FP64_DROP456 3 /* bins 0-3 of eq. Gemm16 only: bins 4-6
                                          dropped (ten products, not folded) */
+/* The INT8 form with its digit products on the fifth-generation tensor
+ * cores (tcgen05.mma, bf16 digits, FP32 accumulation, exact) and the exact
+ * assembly (below): */
+#define DDGEMM_VARIANT_INT8_TC 4
 
 typedef struct ddgemm_opts {
     /* 0: A is m x k (lda >= k).  1: A is stored k x m (lda >= m) and the
@@ -82,7 +86,18 @@ typedef struct ddgemm_opts {
      * and the diagonals are added smallest first in FP64x2.  Error per entry
      * and k-block: at most about (s + 3) 2^-7s k sigma tau (conversion and
      * dropped diagonals) plus FP64x2 rounding.  flags_dev is not supported
-     * with it (DDGEMM_EUNSUPPORTED). */
+     * with it (DDGEMM_EUNSUPPORTED).
+     *
+     * INT8_TC: the same digits and the same exact diagonal sums S_t, with
+     * the digit products on the tcgen05 tensor cores: a digit (|d| <= 64)
+     * is exact in bf16, a product is at most 2^12, and over 256 entries a
+     * diagonal's FP32 accumulator holds integers of at most 2^24, so it is
+     * exact; it is read out every 256 entries into an exact integer sum.
+     * Per k-block the value sum_t S_t 2^(-12-7t) sigma tau is formed
+     * exactly and rounded once to the nearest FP64x2 (hi = RN(x), lo =
+     * RN(x - hi)) before the FP64x2 add into C: a more accurate reading of
+     * "add the results across bins in FP64x2" than the smallest-first sum.
+     * s in {12, 14, 15, 16}.  flags_dev is not supported. */
     int variant;
     /* Optional device word (or NULL): DDGEMM_DEV_* bits are OR-ed into it.
      * The library never clears it. */
@@ -99,8 +114,9 @@ typedef struct ddgemm_opts {
      * split and the ten products (phases two and three, one kernel) and
      * after it, so that a caller can time each phase on the device. */
     void **phase_events;
-    /* INT8 form only: pieces per entry, s in {12, 14, 15, 16, 17, 18}; 0 = 16.
-     * Products per k: s (s + 1) / 2 INT8 GEMMs. */
+    /* INT8 forms only: pieces per entry, s in {12, 14, 15, 16, 17, 18}
+     * (INT8_TC: {12, 14, 15, 16}); 0 = 16.  Products per k: s (s + 1) / 2
+     * INT8 GEMMs. */
     int int8_slices;
     /* FP64 forms: split-k over whole 256-entry k-blocks when a grid of 64 x 64
      * tiles would leave SMs idle.  Group g of a tile sums its run of k-blocks
@@ -306,6 +322,17 @@ int ddgemm_split_int8_a(int m, int k, const double *A_hi, const double *A_lo, in
 int ddgemm_split_int8_b(int k, int n, const double *B_hi, const double *B_lo, int ldb,
                         int trans_b, int slices, signed char *digits, int ld_digits,
                         int *exps, unsigned int *status_dev, void *stream);
+
+/* The assembly step of DDGEMM_VARIANT_INT8_TC alone, on the device: for
+ * i < count, (hi[i], lo[i]) = the FP64x2 nearest to
+ *     x_i = sum_{t < slices} diag[t*count + i] 2^(-12-7t) 2^scale[i]
+ * (hi = RN(x_i), lo = RN(x_i - hi), round to nearest, ties to even), x_i
+ * formed exactly.  diag: device int32, |diag| < 2^30 (the range of a
+ * k-block's diagonal sums); scale: device int32; hi, lo: device doubles.
+ * Results in the subnormal range are rounded twice (outside the method's
+ * range).  slices in {12, 14, 15, 16}. */
+int ddgemm_assemble_int8(int count, int slices, const int *diag, const int *scale, double *hi,
+                         double *lo, void *stream);
 
 /* The ten products of one k-block without the FP64x2 assembly (for
  * checking that bins 0-2 are exact, Sec. "Cascading vectors and dot

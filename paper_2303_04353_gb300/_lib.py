@@ -23,6 +23,7 @@ DDGEMM_VARIANT_FP64 = 0
 DDGEMM_VARIANT_INT8 = 1
 DDGEMM_VARIANT_FP64_GEMM16 = 2
 DDGEMM_VARIANT_FP64_DROP456 = 3
+DDGEMM_VARIANT_INT8_TC = 4
 
 
 class DdgemmError(RuntimeError):
@@ -59,6 +60,7 @@ _I, _Z, _P = ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
 _SIGS = {
     "ddgemm_workspace_size": (_Z, [_I, _I, _I, _P]),
     "ddgemm_split_groups": (_I, [_I, _I, _I, _I, _Z, _P]),
+    "ddgemm_assemble_int8": (_I, [_I, _I, _P, _P, _P, _P, _P]),
     "ddgemm": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _Z, _P, _P]),
     "ddgemm_split_a": (_I, [_I, _I, _P, _P, _I, _I, _P, _I, _P, _P, _P]),
     "ddgemm_split_b": (_I, [_I, _I, _P, _P, _I, _I, _P, _I, _P, _P, _P]),
@@ -191,6 +193,12 @@ def ddgemm_split_int8_b(k, n, b_hi, b_lo, ldb, trans_b, slices, digits, ld_digit
     _check(load().ddgemm_split_int8_b(k, n, b_hi, b_lo, ldb, int(trans_b), slices, digits,
                                       ld_digits, exps, status_dev or None, stream),
            "ddgemm_split_int8_b")
+
+
+def ddgemm_assemble_int8(count, slices, diag, scale, hi, lo, stream) -> None:
+    """The exact assembly step of the tensor-core INT8 form (raw pointers)."""
+    _check(load().ddgemm_assemble_int8(count, slices, diag, scale, hi, lo, stream),
+           "ddgemm_assemble_int8")
 
 
 def ddgemm_probe_int8(iters: int, sink: int, stream: int) -> float:

@@ -72,19 +72,25 @@ struct Parsed {
     int split_k = 0;
 };
 
-// Workspace carve of the INT8 form: digit planes of A and B, exponents.
+bool is_int8(int variant) {
+    return variant == DDGEMM_VARIANT_INT8 || variant == DDGEMM_VARIANT_INT8_TC;
+}
+
+// Workspace carve of the INT8 forms: digit planes of A and B (int8, or bf16
+// for the tensor-core form), exponents.
 struct Layout8 {
     long long ld;
     size_t off_a, off_b, off_ea, off_eb, total;
 };
 
-Layout8 layout8_for(int m, int n, int k, int slices) {
+Layout8 layout8_for(int m, int n, int k, int slices, int variant) {
     Layout8 L;
+    const size_t esize = variant == DDGEMM_VARIANT_INT8_TC ? 2 : 1;
     const long long kb = (k + ddg::KB8 - 1) / ddg::KB8;
     L.ld = (long long)round_up((size_t)k, 64);
     L.off_a = 0;
-    L.off_b = round_up((size_t)slices * m * L.ld, ALIGN);
-    L.off_ea = L.off_b + round_up((size_t)slices * n * L.ld, ALIGN);
+    L.off_b = round_up((size_t)slices * m * L.ld * esize, ALIGN);
+    L.off_ea = L.off_b + round_up((size_t)slices * n * L.ld * esize, ALIGN);
     L.off_eb = L.off_ea + round_up((size_t)kb * m * sizeof(int), ALIGN);
     L.total = L.off_eb + round_up((size_t)kb * n * sizeof(int), ALIGN);
     return L;
@@ -103,6 +109,8 @@ bool parse(const ddgemm_opts *o, Parsed &p) {
     }
     if (p.split_k < 0) return false;
     if (p.variant == DDGEMM_VARIANT_INT8 && !ddg::int8_slices_supported(p.slices)) return false;
+    if (p.variant == DDGEMM_VARIANT_INT8_TC && !ddg::int8_tc_slices_supported(p.slices))
+        return false;
     return (p.trans_a == 0 || p.trans_a == 1) && (p.trans_b == 0 || p.trans_b == 1);
 }
 
@@ -128,7 +136,7 @@ int check_operands(int m, int n, int k, const void *ah, const void *al, int lda,
 // split-k groups of an FP64-form launch: as many as the workspace holds,
 // within the choice for this grid
 int split_groups(int m, int n, int k, int sms, size_t ws_bytes, const Parsed &p) {
-    if (p.variant == DDGEMM_VARIANT_INT8 || p.flags || p.split_k == 1) return 1;
+    if (is_int8(p.variant) || p.flags || p.split_k == 1) return 1;
     if (m <= 0 || n <= 0 || k <= 0) return 1;
     const Layout L = layout_for(m, n, k);
     if (ws_bytes < L.base) return 1;
@@ -188,11 +196,12 @@ int run(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
 int run_int8(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
              const double *B_hi, const double *B_lo, int ldb, double *C_hi, double *C_lo, int ldc,
              void *workspace, size_t ws_bytes, cudaStream_t stream, const Parsed &p) {
-    const Layout8 L = layout8_for(m, n, k, p.slices);
+    const bool tc = p.variant == DDGEMM_VARIANT_INT8_TC;
+    const Layout8 L = layout8_for(m, n, k, p.slices, p.variant);
     if (!workspace || ws_bytes < L.total || (uintptr_t)workspace % ALIGN) return DDGEMM_EWORKSPACE;
     char *ws = static_cast<char *>(workspace);
-    int8_t *da = reinterpret_cast<int8_t *>(ws + L.off_a);
-    int8_t *db = reinterpret_cast<int8_t *>(ws + L.off_b);
+    void *da = ws + L.off_a;
+    void *db = ws + L.off_b;
     int *e_a = reinterpret_cast<int *>(ws + L.off_ea);
     int *e_b = reinterpret_cast<int *>(ws + L.off_eb);
     auto mark = [&](int i) {
@@ -200,15 +209,23 @@ int run_int8(int m, int n, int k, const double *A_hi, const double *A_lo, int ld
                                 cudaSuccess;
     };
     if (!mark(0)) return DDGEMM_ECUDA;
-    cudaError_t e = ddg::launch_split_int8(p.slices, m, k, A_hi, A_lo, lda, !p.trans_a, da, L.ld,
-                                           e_a, p.status, stream);
+    cudaError_t e = ddg::launch_split_int8(p.slices, m, k, A_hi, A_lo, lda, !p.trans_a, da, tc,
+                                           L.ld, e_a, p.status, stream);
     if (e != cudaSuccess) return DDGEMM_ECUDA;
-    e = ddg::launch_split_int8(p.slices, n, k, B_hi, B_lo, ldb, p.trans_b != 0, db, L.ld, e_b,
-                               p.status, stream);
+    e = ddg::launch_split_int8(p.slices, n, k, B_hi, B_lo, ldb, p.trans_b != 0, db, tc, L.ld,
+                               e_b, p.status, stream);
     if (e != cudaSuccess || !mark(1)) return DDGEMM_ECUDA;
-    ddg::Int8Args a{m, n, k, p.slices, da, db, L.ld, e_a, e_b, C_hi, C_lo, (long long)ldc,
-                    p.status};
-    e = ddg::launch_cascade_int8(a, stream);
+    if (tc) {
+        ddg::Int8TcArgs a{m, n, k, p.slices, static_cast<const uint16_t *>(da),
+                          static_cast<const uint16_t *>(db), L.ld, e_a, e_b, C_hi, C_lo,
+                          (long long)ldc, p.status};
+        e = ddg::launch_cascade_int8_tc(a, stream);
+    } else {
+        ddg::Int8Args a{m, n, k, p.slices, static_cast<const int8_t *>(da),
+                        static_cast<const int8_t *>(db), L.ld, e_a, e_b, C_hi, C_lo,
+                        (long long)ldc, p.status};
+        e = ddg::launch_cascade_int8(a, stream);
+    }
     return e == cudaSuccess && mark(2) ? DDGEMM_OK : DDGEMM_ECUDA;
 }
 
@@ -220,7 +237,7 @@ size_t base_workspace_size(int m, int n, int k, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
     if (m == 0 || n == 0 || k == 0) return 0;
-    if (p.variant == DDGEMM_VARIANT_INT8) return layout8_for(m, n, k, p.slices).total;
+    if (is_int8(p.variant)) return layout8_for(m, n, k, p.slices, p.variant).total;
     return layout_for(m, n, k).base;
 }
 
@@ -232,7 +249,7 @@ size_t ddgemm_workspace_size(int m, int n, int k, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
     if (m == 0 || n == 0 || k == 0) return 0;
-    if (p.variant == DDGEMM_VARIANT_INT8) return layout8_for(m, n, k, p.slices).total;
+    if (is_int8(p.variant)) return layout8_for(m, n, k, p.slices, p.variant).total;
     return layout_for(m, n, k, split_reserve(m, n, k, p.split_k)).total;
 }
 
@@ -247,9 +264,9 @@ int ddgemm(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
            void *workspace, size_t ws_bytes, void *stream, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
-    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_FP64_DROP456)
+    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_INT8_TC)
         return DDGEMM_EUNSUPPORTED;
-    if (p.variant == DDGEMM_VARIANT_INT8 && p.flags) return DDGEMM_EUNSUPPORTED;
+    if (is_int8(p.variant) && p.flags) return DDGEMM_EUNSUPPORTED;
     if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;
     if (m == 0 || n == 0) return DDGEMM_OK;
     if (!C_hi || !C_lo || ldc < n) return DDGEMM_EINVAL;
@@ -262,7 +279,7 @@ int ddgemm(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
             return DDGEMM_ECUDA;
         return DDGEMM_OK;
     }
-    if (p.variant == DDGEMM_VARIANT_INT8)
+    if (is_int8(p.variant))
         return run_int8(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, C_hi, C_lo, ldc, workspace,
                         ws_bytes, s, p);
     return run(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, C_hi, C_lo, ldc, nullptr, workspace,
@@ -278,9 +295,8 @@ int ddgemm_split_int8_a(int m, int k, const double *A_hi, const double *A_lo, in
     if (!A_hi || !A_lo || !digits || !exps || lda < (trans_a ? m : k) || ld_digits < k ||
         ld_digits % 16)
         return DDGEMM_EINVAL;
-    const cudaError_t e = ddg::launch_split_int8(slices, m, k, A_hi, A_lo, lda, !trans_a,
-                                                 reinterpret_cast<int8_t *>(digits), ld_digits,
-                                                 exps, status_dev,
+    const cudaError_t e = ddg::launch_split_int8(slices, m, k, A_hi, A_lo, lda, !trans_a, digits,
+                                                 false, ld_digits, exps, status_dev,
                                                  static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }
@@ -295,8 +311,7 @@ int ddgemm_split_int8_b(int k, int n, const double *B_hi, const double *B_lo, in
         ld_digits % 16)
         return DDGEMM_EINVAL;
     const cudaError_t e = ddg::launch_split_int8(slices, n, k, B_hi, B_lo, ldb, trans_b != 0,
-                                                 reinterpret_cast<int8_t *>(digits), ld_digits,
-                                                 exps, status_dev,
+                                                 digits, false, ld_digits, exps, status_dev,
                                                  static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }
@@ -384,7 +399,7 @@ int ddgemm_backward(int m, int n, int k, const double *A_hi, const double *A_lo,
                     void *stream, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
-    if (p.variant != DDGEMM_VARIANT_FP64 && p.variant != DDGEMM_VARIANT_INT8)
+    if (p.variant != DDGEMM_VARIANT_FP64 && !is_int8(p.variant))
         return DDGEMM_EUNSUPPORTED;
     if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;
     if (m > 0 && n > 0 && (!dC_hi || !dC_lo || lddc < n)) return DDGEMM_EINVAL;
@@ -401,6 +416,16 @@ int ddgemm_backward(int m, int n, int k, const double *A_hi, const double *A_lo,
     if (r != DDGEMM_OK) return r;
     return ddgemm(cb.m, cb.n, cb.k, cb.ah, cb.al, cb.lda, cb.bh, cb.bl, cb.ldb, dB_hi, dB_lo, lddb,
                   workspace, ws_bytes, stream, &ob);
+}
+
+int ddgemm_assemble_int8(int count, int slices, const int *diag, const int *scale, double *hi,
+                         double *lo, void *stream) {
+    if (count < 0 || !ddg::int8_tc_slices_supported(slices)) return DDGEMM_EINVAL;
+    if (count == 0) return DDGEMM_OK;
+    if (!diag || !scale || !hi || !lo) return DDGEMM_EINVAL;
+    const cudaError_t e = ddg::launch_assemble_int8(count, slices, diag, scale, hi, lo,
+                                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }
 
 const char *ddgemm_status_string(int code) {

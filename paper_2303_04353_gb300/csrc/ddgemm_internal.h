@@ -73,12 +73,20 @@ inline bool int8_slices_supported(int s) {
     return s == 12 || (s >= 14 && s <= 18);
 }
 
-// Digit planes out[(s * nvec + v) * ld_out + l], ld_out a multiple of 16 and
-// >= kdim; exps[p * nvec + v] per k-block of KB8.  Element (v, l) of the
-// input is at x[v * ldx + l] when vec_contig, else x[l * ldx + v].
+// The tcgen05 form puts the products of plane i with planes 0..s-1-i in one
+// MMA of N = 16 (s - i) <= 256 columns: s <= 16.
+constexpr int INT8_TC_MAX_SLICES = 16;
+inline bool int8_tc_slices_supported(int s) {
+    return s == 12 || (s >= 14 && s <= INT8_TC_MAX_SLICES);
+}
+
+// Digit planes out[(s * nvec + v) * ld_out + l] (int8, or bf16 when `bf16`),
+// ld_out a multiple of 16 and >= kdim; exps[p * nvec + v] per k-block of
+// KB8.  Element (v, l) of the input is at x[v * ldx + l] when vec_contig,
+// else x[l * ldx + v].
 cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi,
-                              const double *x_lo, long long ldx, bool vec_contig, int8_t *out,
-                              long long ld_out, int *exps, unsigned int *status,
+                              const double *x_lo, long long ldx, bool vec_contig, void *out,
+                              bool bf16, long long ld_out, int *exps, unsigned int *status,
                               cudaStream_t stream);
 
 struct Int8Args {
@@ -94,5 +102,27 @@ struct Int8Args {
 };
 
 cudaError_t launch_cascade_int8(const Int8Args &a, cudaStream_t stream);
+
+// The INT8 form on the fifth-generation tensor cores: bf16 digit planes,
+// tcgen05.mma with FP32 accumulation in tensor memory (exact over 256
+// entries), int32 diagonal sums, exact assembly rounded once to FP64x2.
+struct Int8TcArgs {
+    int m, n, k, slices;
+    const uint16_t *a_planes;  // slices x m x ld (bf16 bits)
+    const uint16_t *b_planes;  // slices x n x ld
+    long long ld;
+    const int *exp_a;          // ceil(k/KB8) x m
+    const int *exp_b;          // ceil(k/KB8) x n
+    double *c_hi, *c_lo;
+    long long ldc;
+    unsigned int *status;
+};
+
+cudaError_t launch_cascade_int8_tc(const Int8TcArgs &a, cudaStream_t stream);
+
+// The exact assembly alone: (hi[i], lo[i]) = the FP64x2 nearest to
+// sum_t diag[t * count + i] 2^(-12-7t) 2^scale[i].
+cudaError_t launch_assemble_int8(int count, int slices, const int *diag, const int *scale,
+                                 double *hi, double *lo, cudaStream_t stream);
 
 }  // namespace ddg

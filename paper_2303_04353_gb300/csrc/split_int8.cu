@@ -7,9 +7,10 @@
 //   X = rne(hi 2^(F-e)) + rne(lo 2^(F-e))     (exact, 128-bit integers)
 //   balanced base-128 digits d_0..d_{s-1} of X, most significant first,
 //   d_i in [-64, 64], so that x / sigma ~ sum_i d_i 2^(-6-7i).
-// Output: digit planes [s][vector][ld] of int8 with k contiguous, for A
-// (vectors = rows) and B (vectors = columns; transposed through shared
-// memory) alike, which is the operand layout of mma.sync m16n8k32 s8.
+// Output: digit planes [s][vector][ld] with k contiguous, for A (vectors =
+// rows) and B (vectors = columns; transposed through shared memory) alike:
+// int8 for mma.sync m16n8k32 s8, or bf16 for the tcgen05 form (a digit of at
+// most 7 significant bits is exact in bf16).
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -98,10 +99,16 @@ __device__ __forceinline__ __int128 rne_scaled(double x, int sh) {
 
 constexpr int TV = 32, TK = 64;  // tile: 32 vectors x 64 k
 
-template <int S, bool CONTIG>
+// bf16 encoding of a small integer: the upper half of its FP32 encoding,
+// exact because the FP32 significand of |d| <= 64 has at most 7 bits.
+__device__ __forceinline__ unsigned long long bf16_bits(int d) {
+    return (unsigned long long)(__float_as_uint((float)d) >> 16);
+}
+
+template <int S, bool CONTIG, bool BF16>
 __global__ void __launch_bounds__(256)
 int8_digits_kernel(int nvec, int kdim, const double *__restrict__ xh,
-                   const double *__restrict__ xl, long long ldx, int8_t *__restrict__ out,
+                   const double *__restrict__ xl, long long ldx, void *__restrict__ out_v,
                    long long ld_out, const int *__restrict__ exps, unsigned int *status) {
     __shared__ double sh[TV][TK + 1];
     __shared__ double sl[TV][TK + 1];
@@ -134,9 +141,13 @@ int8_digits_kernel(int nvec, int kdim, const double *__restrict__ xh,
     if (gv >= nvec) return;
     const int e = exps[(long long)(l0 / KB8) * nvec + gv];
     constexpr int F = 6 + 7 * (S - 1);
-    unsigned long long word[S];
+    // 8 entries per plane: one 8-byte word of int8, or two of bf16
+    constexpr int WORDS = BF16 ? 2 : 1;
+    unsigned long long word[S][WORDS];
 #pragma unroll
-    for (int s = 0; s < S; ++s) word[s] = 0;
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int w = 0; w < WORDS; ++w) word[s][w] = 0;
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -144,44 +155,76 @@ int8_digits_kernel(int nvec, int kdim, const double *__restrict__ xh,
         bad |= !isfinite(hi) || !isfinite(lo);
         __int128 X = rne_scaled(hi, F - e) + rne_scaled(lo, F - e);
 #pragma unroll
-        for (int s = S - 1; s > 0; --s) {
-            const int d = (int)((unsigned long long)(X + 64) & 127ull) - 64;
-            X = (X - d) >> 7;
-            word[s] |= (unsigned long long)(uint8_t)(int8_t)d << (8 * j);
+        for (int s = S - 1; s >= 0; --s) {
+            int d;
+            if (s > 0) {
+                d = (int)((unsigned long long)(X + 64) & 127ull) - 64;
+                X = (X - d) >> 7;
+            } else {
+                d = (int)X;
+            }
+            if constexpr (BF16)
+                word[s][j >> 2] |= bf16_bits(d) << (16 * (j & 3));
+            else
+                word[s][0] |= (unsigned long long)(uint8_t)(int8_t)d << (8 * j);
         }
-        word[0] |= (unsigned long long)(uint8_t)(int8_t)(int)X << (8 * j);
     }
     if (bad && status) atomicOr(status, DEV_NONFINITE);
     const int gl = l0 + lg * 8;
     if (gl >= kdim) return;
-    // entries past kdim in the last word carry zero digits; they sit in the
-    // row padding (ld_out >= kdim rounded up to 16) and are never read
+    // entries past kdim in the last group of 8 carry zero digits; they sit
+    // in the row padding (ld_out >= kdim rounded up to 16) and are never read
 #pragma unroll
-    for (int s = 0; s < S; ++s)
-        *reinterpret_cast<unsigned long long *>(out + ((long long)s * nvec + gv) * ld_out + gl) =
-            word[s];
+    for (int s = 0; s < S; ++s) {
+        const long long o = ((long long)s * nvec + gv) * ld_out + gl;
+        if constexpr (BF16) {
+            uint4 q;
+            q.x = (unsigned)word[s][0];
+            q.y = (unsigned)(word[s][0] >> 32);
+            q.z = (unsigned)word[s][1];
+            q.w = (unsigned)(word[s][1] >> 32);
+            *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(out_v) + o) = q;
+        } else {
+            *reinterpret_cast<unsigned long long *>(static_cast<int8_t *>(out_v) + o) = word[s][0];
+        }
+    }
+}
+
+template <int S, bool BF16>
+cudaError_t launch_digits_t(int nvec, int kdim, const double *xh, const double *xl, long long ldx,
+                            bool contig, void *out, long long ld_out, const int *exps,
+                            unsigned int *status, cudaStream_t stream) {
+    const dim3 grid((kdim + TK - 1) / TK, (nvec + TV - 1) / TV);
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    if (contig)
+        int8_digits_kernel<S, true, BF16><<<grid, 256, 0, stream>>>(nvec, kdim, xh, xl, ldx, out,
+                                                                    ld_out, exps, status);
+    else
+        int8_digits_kernel<S, false, BF16><<<grid, 256, 0, stream>>>(nvec, kdim, xh, xl, ldx,
+                                                                     out, ld_out, exps, status);
+    return cudaGetLastError();
 }
 
 template <int S>
 cudaError_t launch_digits(int nvec, int kdim, const double *xh, const double *xl, long long ldx,
-                          bool contig, int8_t *out, long long ld_out, const int *exps,
+                          bool contig, void *out, bool bf16, long long ld_out, const int *exps,
                           unsigned int *status, cudaStream_t stream) {
-    const dim3 grid((kdim + TK - 1) / TK, (nvec + TV - 1) / TV);
-    if (grid.y > 65535) return cudaErrorInvalidValue;
-    if (contig)
-        int8_digits_kernel<S, true><<<grid, 256, 0, stream>>>(nvec, kdim, xh, xl, ldx, out, ld_out,
-                                                              exps, status);
-    else
-        int8_digits_kernel<S, false><<<grid, 256, 0, stream>>>(nvec, kdim, xh, xl, ldx, out,
-                                                               ld_out, exps, status);
-    return cudaGetLastError();
+    if (bf16) {
+        if constexpr (S <= INT8_TC_MAX_SLICES)
+            return launch_digits_t<S, true>(nvec, kdim, xh, xl, ldx, contig, out, ld_out, exps,
+                                            status, stream);
+        else
+            return cudaErrorInvalidValue;
+    }
+    return launch_digits_t<S, false>(nvec, kdim, xh, xl, ldx, contig, out, ld_out, exps, status,
+                                     stream);
 }
 
 }  // namespace
 
 cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi,
-                              const double *x_lo, long long ldx, bool vec_contig, int8_t *out,
-                              long long ld_out, int *exps, unsigned int *status,
+                              const double *x_lo, long long ldx, bool vec_contig, void *out,
+                              bool bf16, long long ld_out, int *exps, unsigned int *status,
                               cudaStream_t stream) {
     if (nvec <= 0 || kdim <= 0) return cudaSuccess;
     if (ld_out % 16 != 0 || ld_out < kdim) return cudaErrorInvalidValue;
@@ -200,8 +243,8 @@ cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi
     switch (slices) {
 #define DDG_CASE(S)                                                                            \
     case S:                                                                                    \
-        return launch_digits<S>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, ld_out, exps,    \
-                                status, stream);
+        return launch_digits<S>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, bf16, ld_out,   \
+                                exps, status, stream);
         DDG_INT8_SLICE_CASES
 #undef DDG_CASE
         default:

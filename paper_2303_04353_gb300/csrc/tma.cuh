@@ -40,6 +40,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -87,10 +91,13 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // 3-D tiled map over a stack of `nz` row-major matrices of `rows` x `cols`
 // elements (row stride `ld` elements of `esize` bytes); box = [bz][by][bx].
-// Reads outside the extents come back as zeros.
+// Reads outside the extents come back as zeros.  `swizzle` permutes the
+// 16-byte chunks of the box rows in shared memory (the tensor-core operand
+// layouts expect the same permutation).
 inline bool encode_map_3d(CUtensorMap *map, CUtensorMapDataType dtype, size_t esize,
                           const void *base, uint64_t cols, uint64_t rows, uint64_t nz, uint64_t ld,
-                          uint32_t bx, uint32_t by, uint32_t bz) {
+                          uint32_t bx, uint32_t by, uint32_t bz,
+                          CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_NONE) {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t dims[3] = {cols, rows, nz};
@@ -98,7 +105,7 @@ inline bool encode_map_3d(CUtensorMap *map, CUtensorMapDataType dtype, size_t es
     const cuuint32_t box[3] = {bx, by, bz};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, dtype, 3, const_cast<void *>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

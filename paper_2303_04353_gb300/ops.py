@@ -101,6 +101,22 @@ def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, wo
     return c_hi, c_lo
 
 
+def assemble_int8(diag: torch.Tensor, scale: torch.Tensor, *, stream=None):
+    """The exact assembly of the tensor-core INT8 form on the device: for
+    diag [s, count] int32 and scale [count] int32, returns (hi, lo), the
+    FP64x2 nearest to sum_t diag[t] 2^(-12-7t) 2^scale."""
+    if diag.dtype != torch.int32 or scale.dtype != torch.int32 or not diag.is_cuda:
+        raise TypeError("diag and scale must be int32 CUDA tensors")
+    s, count = diag.shape
+    diag = diag.contiguous()
+    scale = scale.contiguous()
+    hi = torch.empty(count, dtype=torch.float64, device=diag.device)
+    lo = torch.empty(count, dtype=torch.float64, device=diag.device)
+    _lib.ddgemm_assemble_int8(count, s, diag.data_ptr(), scale.data_ptr(), hi.data_ptr(),
+                              lo.data_ptr(), current_stream_ptr(stream))
+    return hi, lo
+
+
 def split_a(a_hi, a_lo, *, trans_a=False, stream=None, status=None):
     """The split step for A: returns (slices [4, m, k], exps [ceil(k/256), m])."""
     lda = _check_pair(a_hi, a_lo, "A")

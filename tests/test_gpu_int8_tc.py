@@ -1,0 +1,180 @@
+"""Parity of the tensor-core INT8 form (C ABI, variant DDGEMM_VARIANT_INT8_TC)
+with its CPU restatement (oracle/cascade_int8.py, assembly="exact").
+
+The digits, the exponents and the diagonal sums are the INT8 form's, exact
+integers; the tcgen05 products are exact (bf16 digits, FP32 sums below
+2^24 per 256-entry chunk); the assembly rounds the exact block value once
+to the nearest FP64x2, and the blocks are added into C by the same FP64x2
+add as the restatement.  So C must be bit-identical to the restatement.
+The assembly step alone is checked bit for bit on hard cases (ties at both
+roundings, cancellation, the largest sums)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import cascade_int8 as c8  # noqa: E402
+from oracle import dd  # noqa: E402
+from tests import exact  # noqa: E402
+from tests.test_oracle_int8 import hard_block_values  # noqa: E402
+from workloads import gemm_inputs, integer_inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+CONTRACT = 1e-28
+TC = 4
+
+
+@pytest.fixture(scope="module")
+def ops():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_04353_gb300 import ops as _ops
+    return _ops
+
+
+def dev(*arrays):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrays]
+
+
+def host(*tensors):
+    torch.cuda.synchronize()
+    return [t.cpu().numpy() for t in tensors]
+
+
+def same(a, b):
+    return np.array_equal(a, b) and np.array_equal(np.signbit(a), np.signbit(b))
+
+
+# ---- the assembly step ----------------------------------------------------
+
+def diag_for(t_val, s):
+    """Diagonal sums whose block value is exactly t_val 2^(-12-7(s-1)):
+    balanced base-128 digits of t_val, the top one taking what is left."""
+    out = [0] * s
+    x = t_val
+    for i in range(s - 1, 0, -1):
+        d = ((x + 64) & 127) - 64
+        out[i] = d
+        x = (x - d) >> 7
+    out[0] = x
+    return out
+
+
+@pytest.mark.parametrize("s", [16, 12, 14, 15])
+def test_assemble_bitwise_on_hard_values(ops, s):
+    cases = []
+    for t_val, e in hard_block_values():
+        ds = diag_for(t_val, s)
+        if abs(ds[0]) < 2 ** 30:
+            cases.append((ds, e))
+    rng = np.random.default_rng(s)
+    for _ in range(400):      # full-range sums: every diagonal up to 2^30
+        cases.append((list(rng.integers(-(2 ** 30), 2 ** 30, s)), int(rng.integers(-150, 20))))
+    cases.append(([2 ** 30 - 1] * s, 0))
+    cases.append(([-(2 ** 30 - 1)] * s, -40))
+    cases.append(([0] * s, 0))
+    diag = np.array([c[0] for c in cases], dtype=np.int64).T
+    scale = np.array([c[1] for c in cases], dtype=np.int64)
+    hi, lo = host(*ops.assemble_int8(torch.from_numpy(diag.astype(np.int32)).cuda(),
+                                     torch.from_numpy(scale.astype(np.int32)).cuda()))
+    for i in range(len(cases)):
+        t_val = sum(int(diag[t, i]) << (7 * (s - 1 - t)) for t in range(s))
+        want = c8.round_dd(t_val, int(scale[i]) - 12 - 7 * (s - 1))
+        assert hi[i] == want[0] and lo[i] == want[1], (i, cases[i])
+        assert not np.signbit(lo[i]) or lo[i] != 0.0
+
+
+# ---- the whole form -----------------------------------------------------
+
+def tc(ops, a_hi, a_lo, b_hi, b_lo, s=16, **kw):
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    c_hi, c_lo = ops.ddgemm(*dev(a_hi, a_lo, b_hi, b_lo), variant=TC, int8_slices=s,
+                            status=status, **kw)
+    c_hi, c_lo, st = host(c_hi, c_lo, status)
+    assert st[0] == 0
+    return c_hi, c_lo
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 16, 256), (1, 1, 1), (130, 20, 300), (200, 50, 1000),
+                                   (129, 17, 16), (70, 100, 513)])
+@pytest.mark.parametrize("kind", ["uniform", "wide"])
+def test_tc_bitwise_vs_restatement(ops, m, n, k, kind):
+    a = gemm_inputs(m, n, k, kind=kind, seed=m + 3 * n + k)
+    c_hi, c_lo = tc(ops, *a)
+    w_hi, w_lo = c8.cascade_int8_ddgemm(*a, s=16, assembly="exact")
+    assert same(c_hi, w_hi) and same(c_lo, w_lo)
+
+
+@pytest.mark.parametrize("s", [12, 14, 15])
+def test_tc_other_piece_counts(ops, s):
+    a = gemm_inputs(150, 40, 700, kind="wide", seed=s)
+    c_hi, c_lo = tc(ops, *a, s=s)
+    w_hi, w_lo = c8.cascade_int8_ddgemm(*a, s=s, assembly="exact")
+    assert same(c_hi, w_hi) and same(c_lo, w_lo)
+
+
+def test_tc_two_k_blocks(ops):
+    """k > 16384: two k-blocks with their own exponents, added in FP64x2."""
+    a = gemm_inputs(5, 3, 17000, kind="wide", seed=21)
+    c_hi, c_lo = tc(ops, *a)
+    w_hi, w_lo = c8.cascade_int8_ddgemm(*a, s=16, assembly="exact")
+    assert same(c_hi, w_hi) and same(c_lo, w_lo)
+
+
+@pytest.mark.parametrize("ta,tb", [(True, False), (False, True), (True, True)])
+def test_tc_transposed(ops, ta, tb):
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(90, 40, 400, kind="wide", seed=7)
+    sa = (a_hi.T, a_lo.T) if ta else (a_hi, a_lo)
+    sb = (b_hi.T, b_lo.T) if tb else (b_hi, b_lo)
+    c_hi, c_lo = tc(ops, *sa, *sb, trans_a=ta, trans_b=tb)
+    w_hi, w_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16, assembly="exact")
+    assert same(c_hi, w_hi) and same(c_lo, w_lo)
+
+
+def test_tc_integers_exact_and_contract(ops):
+    a_hi, a_lo, b_hi, b_lo = integer_inputs(160, 48, 2000, bits=10, seed=3)
+    c_hi, c_lo = tc(ops, a_hi, a_lo, b_hi, b_lo)
+    ref = a_hi.astype(np.int64) @ b_hi.astype(np.int64)
+    assert np.array_equal(c_hi, ref.astype(np.float64)) and np.all(c_lo == 0)
+    a = gemm_inputs(300, 64, 3000, kind="uniform", seed=4)
+    c_hi, c_lo = tc(ops, *a)
+    rng = np.random.default_rng(0)
+    rows, cols = rng.integers(0, 300, 64), rng.integers(0, 64, 64)
+    o_hi, o_lo = dd.ddgemm_entries(*a, rows, cols)
+    absab = np.array([np.abs(a[0][i]) @ np.abs(a[2][:, j]) for i, j in zip(rows, cols)])
+    err = np.abs((c_hi[rows, cols] - o_hi) + (c_lo[rows, cols] - o_lo))
+    assert np.all(err <= CONTRACT * absab)
+    assert exact.dd_is_normalised(c_hi, c_lo)
+
+
+def test_tc_close_to_int8_form(ops):
+    """Same diagonal sums as the mma.sync INT8 form; the two assemblies
+    differ by that form's FP64x2 roundings only."""
+    a = gemm_inputs(256, 80, 1200, kind="wide", seed=5)
+    c_hi, c_lo = tc(ops, *a)
+    i_hi, i_lo = host(*ops.ddgemm(*dev(*a), variant=1))
+    diff = np.abs((c_hi - i_hi) + (c_lo - i_lo))
+    assert np.all(diff <= 4 * 16 * 2.0 ** -106 * (np.abs(a[0]) @ np.abs(a[2])))
+
+
+def test_tc_nonfinite_sets_status(ops):
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(20, 20, 40, seed=3)
+    a_hi[3, 5] = np.inf
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ops.ddgemm(*dev(a_hi, a_lo, b_hi, b_lo), variant=TC, status=status)
+    (st,) = host(status)
+    assert st[0] & 0x1 and not st[0] & 0x2
+
+
+def test_tc_full_size_sampled(ops):
+    """2048^3 (the accuracy sweep's size): sampled entries against the
+    double-double oracle."""
+    m = n = k = 2048
+    a = gemm_inputs(m, n, k, kind="wide", seed=0)
+    c_hi, c_lo = tc(ops, *a)
+    rng = np.random.default_rng(1)
+    rows, cols = rng.integers(0, m, 48), rng.integers(0, n, 48)
+    o_hi, o_lo = dd.ddgemm_entries(*a, rows, cols)
+    absab = np.array([np.abs(a[0][i]) @ np.abs(a[2][:, j]) for i, j in zip(rows, cols)])
+    err = np.abs((c_hi[rows, cols] - o_hi) + (c_lo[rows, cols] - o_lo))
+    assert np.all(err <= CONTRACT * absab)
