@@ -169,6 +169,19 @@ def fp64_peak_rule():
                 "of fallback: bf16 1.9 PFLOP/s burst x nominal FP64/bf16 (1.25/2250)")
 
 
+def bf16_peaks():
+    """(peak, source, sustained) of the bf16 tensor path for the tcgen05
+    INT8 form: MEASURED_PEAKS.json's burst figure (a conservative
+    denominator; the sustained power-capped figure is reported beside it)."""
+    try:
+        with open(MEASURED_PEAKS) as f:
+            mp = json.load(f)
+        return (mp["bf16_tflops"], "of measured: MEASURED_PEAKS.json bf16_tflops (burst)",
+                mp.get("bf16_tflops_sustained"))
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "of fallback: bf16 1.9 PFLOP/s burst", 1700.0
+
+
 def oracle_rows_rate(a_hi, a_lo, b_hi, b_lo, rows):
     """Time the double-double oracle on full rows of C; returns (seconds, threads)."""
     from oracle import dd
@@ -248,7 +261,8 @@ def run_ours(args, wl):
     d_in = [h.to(dev) for h in host_in]
     c_hi = torch.empty((m, n), dtype=torch.float64, device=dev)
     c_lo = torch.empty((m, n), dtype=torch.float64, device=dev)
-    variant = _lib.DDGEMM_VARIANT_INT8 if args.variant == "int8" else _lib.DDGEMM_VARIANT_FP64
+    variant = {"int8": _lib.DDGEMM_VARIANT_INT8, "int8tc": _lib.DDGEMM_VARIANT_INT8_TC}.get(
+        args.variant, _lib.DDGEMM_VARIANT_FP64)
     ws = ops.alloc_workspace(m, n, k, dev, variant, args.int8_slices)
     groups = ops.split_groups(m, n, k, dev, ws.numel(), variant)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -345,16 +359,15 @@ def run_ours(args, wl):
     probe_tops = probe(_lib.ddgemm_probe_int8, (200, 4000, 4000, 4000)) \
         if variant == _lib.DDGEMM_VARIANT_INT8 else None
 
-    # ---- the INT8 form on the same inputs (one line, both forms) ----------
-    int8_form = None
-    if variant == _lib.DDGEMM_VARIANT_FP64 and not args.no_int8_form:
-        ws8 = ops.alloc_workspace(m, n, k, dev, _lib.DDGEMM_VARIANT_INT8, 16)
+    # ---- the INT8 forms on the same inputs (one line, all forms) ----------
+    def time_form(form_variant):
+        ws8 = ops.alloc_workspace(m, n, k, dev, form_variant, 16)
         c8 = (torch.empty((m, n), dtype=torch.float64, device=dev),
               torch.empty((m, n), dtype=torch.float64, device=dev))
 
         def step8():
-            ops.ddgemm(*d_in, out=c8, workspace=ws8, stream=stream,
-                       variant=_lib.DDGEMM_VARIANT_INT8, int8_slices=16)
+            ops.ddgemm(*d_in, out=c8, workspace=ws8, stream=stream, variant=form_variant,
+                       int8_slices=16)
         for _ in range(args.warmup):
             step8()
         torch.cuda.synchronize()
@@ -368,11 +381,20 @@ def run_ours(args, wl):
         ms8 = reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
         h8, l8 = c8[0].cpu().numpy(), c8[1].cpu().numpy()
         err8 = np.abs((h8[rows, cols] - oh) + (l8[rows, cols] - ol))
-        int8_form = {"pieces": 16, "products": 136, "ms_per_step": round(ms8, 3),
-                     "value": round(replica_rate(flops_dd, world, ms8) / 1e9, 4),
-                     "unit": "GFLOP/s",
-                     "max_err_vs_dd_oracle": float(np.max(err8 / absab)),
-                     "speedup_vs_fp64_form": round(ms_per_step / ms8, 3)}
+        del ws8
+        return {"pieces": 16, "products": 136, "ms_per_step": round(ms8, 3),
+                "value": round(replica_rate(flops_dd, world, ms8) / 1e9, 4),
+                "unit": "GFLOP/s",
+                "max_err_vs_dd_oracle": float(np.max(err8 / absab)),
+                "speedup_vs_fp64_form": round(ms_per_step / ms8, 3)}
+
+    int8_form = int8_tc_form = None
+    if variant == _lib.DDGEMM_VARIANT_FP64 and not args.no_int8_form:
+        int8_form = time_form(_lib.DDGEMM_VARIANT_INT8)
+        int8_form["products_on"] = "mma.sync m16n8k32 s8 (int32 accumulation)"
+        int8_tc_form = time_form(_lib.DDGEMM_VARIANT_INT8_TC)
+        int8_tc_form["products_on"] = ("tcgen05.mma kind::f16, bf16 digits, FP32 in TMEM "
+                                       "(exact per 256 entries); exact assembly")
 
     # ---- yardstick: a plain FP64 GEMM of the same shape (cuBLAS DGEMM via
     # torch.matmul), the unit of the paper's "10-13x DGEMM time" claim ------
@@ -397,12 +419,28 @@ def run_ours(args, wl):
                          "not part of the path"}
         if int8_form is not None:
             dgemm["int8_form_over_dgemm"] = round(int8_form["ms_per_step"] / dg_ms, 3)
+        if int8_tc_form is not None:
+            dgemm["int8_tc_form_over_dgemm"] = round(int8_tc_form["ms_per_step"] / dg_ms, 3)
         del z
 
     if rank != 0:
         return
     peak, peak_src = fp64_peak_rule()
-    if variant == _lib.DDGEMM_VARIANT_INT8:
+    if variant == _lib.DDGEMM_VARIANT_INT8_TC:
+        s8 = args.int8_slices
+        prods = s8 * (s8 + 1) // 2
+        achieved = prods * flops_dd / (casc_ms * 1e-3) / 1e12
+        bpeak, bsrc, spk = bf16_peaks()
+        roofline = {"bound": "tensor", "kernel": f"cascade_int8_tc_kernel<{s8}>",
+                    "achieved": round(achieved, 3), "peak": round(bpeak, 3), "unit": "TFLOP/s",
+                    "frac": round(achieved / bpeak, 4),
+                    "traffic": TRAFFIC_4096.get(f"cascade_int8_tc_kernel<{s8}>")
+                    if args.workload == "4096" else None,
+                    "peak_source": bsrc,
+                    "frac_vs_sustained": round(achieved / spk, 4) if spk else None,
+                    "algorithmic": f"{prods} x 2mnk = {prods * flops_dd:.4g} bf16 flops "
+                                   "(digit products) per launch"}
+    elif variant == _lib.DDGEMM_VARIANT_INT8:
         s8 = args.int8_slices
         prods = s8 * (s8 + 1) // 2
         achieved = prods * flops_dd / (casc_ms * 1e-3) / 1e12
@@ -432,8 +470,9 @@ def run_ours(args, wl):
         "data": "synthetic",
         "config": {"workload": wl["name"], "m": m, "n": n, "k": k,
                    "variant": "fp64 (ten FP64 products)" if variant == _lib.DDGEMM_VARIANT_FP64
-                   else f"int8 ({args.int8_slices} pieces, "
-                        f"{args.int8_slices * (args.int8_slices + 1) // 2} INT8 products)",
+                   else f"{'int8 on tcgen05' if variant == _lib.DDGEMM_VARIANT_INT8_TC else 'int8'}"
+                        f" ({args.int8_slices} pieces, "
+                        f"{args.int8_slices * (args.int8_slices + 1) // 2} digit products)",
                    "split_k_groups": groups,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs (512 MiB) and panels larger than L2; no flush"
@@ -442,7 +481,11 @@ def run_ours(args, wl):
                                       / probe_tflops, 2)}
            if variant == _lib.DDGEMM_VARIANT_FP64 else
            {"pct_int8_tc_peak": round(100.0 * (args.int8_slices * (args.int8_slices + 1) // 2)
-                                      * flops_dd / (ms_per_step * 1e-3) / 1e12 / probe_tops, 2)}),
+                                      * flops_dd / (ms_per_step * 1e-3) / 1e12 / probe_tops, 2)}
+           if variant == _lib.DDGEMM_VARIANT_INT8 else
+           {"pct_bf16_tc_peak": round(100.0 * (args.int8_slices * (args.int8_slices + 1) // 2)
+                                      * flops_dd / (ms_per_step * 1e-3) / 1e12
+                                      / bf16_peaks()[0], 2)}),
         "max_err_vs_dd_oracle": max_err,
         "phases_ms": {"split": round(split_ms, 3), "products_and_assembly": round(casc_ms, 3)},
         "roofline": roofline,
@@ -454,6 +497,8 @@ def run_ours(args, wl):
     }
     if int8_form is not None:
         line["int8_form"] = int8_form
+    if int8_tc_form is not None:
+        line["int8_tc_form"] = int8_tc_form
     if dgemm is not None:
         line["dgemm_yardstick"] = dgemm
     if world == 1 and not args.no_cpu_baseline:
@@ -742,8 +787,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-int8-form", action="store_true",
                     help="skip the INT8 form's entry in the FP64 line")
-    ap.add_argument("--variant", choices=("fp64", "int8"), default="fp64",
-                    help="fp64: the ten FP64 products (default); int8: the INT8 form")
+    ap.add_argument("--variant", choices=("fp64", "int8", "int8tc"), default="fp64",
+                    help="fp64: the ten FP64 products (default); int8: the INT8 form on "
+                         "mma.sync s8; int8tc: the INT8 form on the tcgen05 tensor cores")
     ap.add_argument("--int8-slices", type=int, default=16)
     ap.add_argument("--sweep", action="store_true",
                     help="exponent-spread study of both forms instead of the benchmark line")

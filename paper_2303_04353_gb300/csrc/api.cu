@@ -85,12 +85,20 @@ struct Layout8 {
 
 Layout8 layout8_for(int m, int n, int k, int slices, int variant) {
     Layout8 L;
-    const size_t esize = variant == DDGEMM_VARIANT_INT8_TC ? 2 : 1;
     const long long kb = (k + ddg::KB8 - 1) / ddg::KB8;
     L.ld = (long long)round_up((size_t)k, 64);
     L.off_a = 0;
-    L.off_b = round_up((size_t)slices * m * L.ld * esize, ALIGN);
-    L.off_ea = L.off_b + round_up((size_t)slices * n * L.ld * esize, ALIGN);
+    if (variant == DDGEMM_VARIANT_INT8_TC) {
+        // bf16 digits in whole tiles of 128 rows (A) and 16 columns (B) by
+        // k-steps of 16
+        const size_t kpad = round_up((size_t)k, 16);
+        L.off_b = round_up((size_t)slices * round_up((size_t)m, ddg::INT8_TC_BM) * kpad * 2, ALIGN);
+        L.off_ea = L.off_b +
+                   round_up((size_t)slices * round_up((size_t)n, ddg::INT8_TC_BN) * kpad * 2, ALIGN);
+    } else {
+        L.off_b = round_up((size_t)slices * m * L.ld, ALIGN);
+        L.off_ea = L.off_b + round_up((size_t)slices * n * L.ld, ALIGN);
+    }
     L.off_eb = L.off_ea + round_up((size_t)kb * m * sizeof(int), ALIGN);
     L.total = L.off_eb + round_up((size_t)kb * n * sizeof(int), ALIGN);
     return L;
@@ -209,15 +217,15 @@ int run_int8(int m, int n, int k, const double *A_hi, const double *A_lo, int ld
                                 cudaSuccess;
     };
     if (!mark(0)) return DDGEMM_ECUDA;
-    cudaError_t e = ddg::launch_split_int8(p.slices, m, k, A_hi, A_lo, lda, !p.trans_a, da, tc,
-                                           L.ld, e_a, p.status, stream);
+    cudaError_t e = ddg::launch_split_int8(p.slices, m, k, A_hi, A_lo, lda, !p.trans_a, da,
+                                           tc ? ddg::INT8_TC_BM : 0, L.ld, e_a, p.status, stream);
     if (e != cudaSuccess) return DDGEMM_ECUDA;
-    e = ddg::launch_split_int8(p.slices, n, k, B_hi, B_lo, ldb, p.trans_b != 0, db, tc, L.ld,
-                               e_b, p.status, stream);
+    e = ddg::launch_split_int8(p.slices, n, k, B_hi, B_lo, ldb, p.trans_b != 0, db,
+                               tc ? ddg::INT8_TC_BN : 0, L.ld, e_b, p.status, stream);
     if (e != cudaSuccess || !mark(1)) return DDGEMM_ECUDA;
     if (tc) {
         ddg::Int8TcArgs a{m, n, k, p.slices, static_cast<const uint16_t *>(da),
-                          static_cast<const uint16_t *>(db), L.ld, e_a, e_b, C_hi, C_lo,
+                          static_cast<const uint16_t *>(db), e_a, e_b, C_hi, C_lo,
                           (long long)ldc, p.status};
         e = ddg::launch_cascade_int8_tc(a, stream);
     } else {
@@ -296,7 +304,7 @@ int ddgemm_split_int8_a(int m, int k, const double *A_hi, const double *A_lo, in
         ld_digits % 16)
         return DDGEMM_EINVAL;
     const cudaError_t e = ddg::launch_split_int8(slices, m, k, A_hi, A_lo, lda, !trans_a, digits,
-                                                 false, ld_digits, exps, status_dev,
+                                                 0, ld_digits, exps, status_dev,
                                                  static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }
@@ -311,7 +319,7 @@ int ddgemm_split_int8_b(int k, int n, const double *B_hi, const double *B_lo, in
         ld_digits % 16)
         return DDGEMM_EINVAL;
     const cudaError_t e = ddg::launch_split_int8(slices, n, k, B_hi, B_lo, ldb, trans_b != 0,
-                                                 digits, false, ld_digits, exps, status_dev,
+                                                 digits, 0, ld_digits, exps, status_dev,
                                                  static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }

@@ -18,10 +18,13 @@
 // the FP64x2 add.  This is one rounding where the paper's smallest-first
 // FP64x2 sum of the diagonals has s.
 //
-// Tiling.  A C tile is 128 rows x 16 columns; k advances by 16.  One TMA
-// copy per operand and stage brings all s digit planes of A ([s][128][16]
-// bf16, 64 KB at s = 16) and of B ([s][16][16]) into a three-deep ring with
-// 32-byte swizzling.  Per stage, one MMA per A plane i: M = 128,
+// Tiling.  A C tile is 128 rows x 16 columns; k advances by 16.  The split
+// wrote the digits tiled and pre-swizzled (split_int8.cu), so one bulk copy
+// per operand and stage brings all s digit planes of A ([s][128][16] bf16,
+// 64 KB at s = 16) and of B ([s][16][16]) into a three-deep ring, already in
+// the 32-byte-swizzled K-major layout the MMA reads (a tensor-map copy with
+// 32-byte rows would issue one request per row; the bulk copy issues few and
+// large ones).  Per stage, one MMA per A plane i: M = 128,
 // N = 16 (s - i) (B planes 0..s-1-i side by side), K = 16, accumulating
 // into tensor-memory columns 16 i .. 16 s - 1, so that the product of
 // planes i and j lands on diagonal i + j's 16 columns.  Two accumulator sets
@@ -54,7 +57,7 @@
 namespace ddg {
 namespace {
 
-constexpr int BM = 128, BN = 16, BK = 16;
+constexpr int BM = INT8_TC_BM, BN = INT8_TC_BN, BK = 16;
 constexpr int CHUNK_STEPS = 16;                       // 16 k-steps of 16: 256 entries
 constexpr int BLOCK_CHUNKS = KB8 / (BK * CHUNK_STEPS);  // chunks per k-block
 constexpr int NST = 3;
@@ -245,8 +248,7 @@ __device__ __forceinline__ void fold_group(uint32_t base, __int128 (&acc)[8]) {
 
 template <int S>
 __global__ void __launch_bounds__(NTHREADS, 1)
-cascade_int8_tc_kernel(const __grid_constant__ CUtensorMap tm_a,
-                       const __grid_constant__ CUtensorMap tm_b, const Int8TcArgs args) {
+cascade_int8_tc_kernel(const Int8TcArgs args) {
     using G = TcGeom<S>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -301,8 +303,14 @@ cascade_int8_tc_kernel(const __grid_constant__ CUtensorMap tm_a,
                     unsigned char *dst = smem + stage * G::STAGE;
                     const uint32_t bar = smem_addr(&sh->full[stage]);
                     mbar_arrive_expect_tx(bar, (uint32_t)G::TX);
-                    tma_load_3d(smem_addr(dst), &tm_a, bar, ks * BK, tm * BM, 0);
-                    tma_load_3d(smem_addr(dst + G::A_STAGE), &tm_b, bar, ks * BK, tn * BN, 0);
+                    // k-step ks of all S planes: S consecutive blocks
+                    const uint16_t *src_a =
+                        args.a_tiles + ((long long)tm * ksteps + ks) * S * (BM * BK);
+                    const uint16_t *src_b =
+                        args.b_tiles + ((long long)tn * ksteps + ks) * S * (BN * BK);
+                    bulk_load(smem_addr(dst), src_a, (uint32_t)G::A_STAGE, bar);
+                    bulk_load(smem_addr(dst + G::A_STAGE), src_b, (uint32_t)(S * G::B_PLANE),
+                              bar);
                 }
             }
             if (!ok) {
@@ -433,13 +441,7 @@ cascade_int8_tc_kernel(const __grid_constant__ CUtensorMap tm_a,
 template <int S>
 cudaError_t launch_tc(const Int8TcArgs &a, cudaStream_t stream) {
     using G = TcGeom<S>;
-    CUtensorMap tm_a, tm_b;
-    // bf16 digit planes [S][rows][ld], boxes [S][128][16] and [S][16][16]
-    if (!encode_map_3d(&tm_a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.a_planes, a.k, a.m, S, a.ld,
-                       BK, BM, S, CU_TENSOR_MAP_SWIZZLE_32B) ||
-        !encode_map_3d(&tm_b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a.b_planes, a.k, a.n, S, a.ld,
-                       BK, BN, S, CU_TENSOR_MAP_SWIZZLE_32B))
-        return cudaErrorInvalidValue;
+    if ((uintptr_t)a.a_tiles % 16 || (uintptr_t)a.b_tiles % 16) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(cascade_int8_tc_kernel<S>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)G::SMEM);
@@ -451,7 +453,7 @@ cudaError_t launch_tc(const Int8TcArgs &a, cudaStream_t stream) {
     const long long tiles = (long long)((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    cascade_int8_tc_kernel<S><<<grid, NTHREADS, G::SMEM, stream>>>(tm_a, tm_b, a);
+    cascade_int8_tc_kernel<S><<<grid, NTHREADS, G::SMEM, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -471,7 +473,6 @@ assemble_kernel(int count, const int *__restrict__ diag, const int *__restrict__
 
 cudaError_t launch_cascade_int8_tc(const Int8TcArgs &a, cudaStream_t stream) {
     if (a.m <= 0 || a.n <= 0 || a.k <= 0) return cudaSuccess;
-    if (a.ld % 8 != 0) return cudaErrorInvalidValue;
     switch (a.slices) {
         case 12: return launch_tc<12>(a, stream);
         case 14: return launch_tc<14>(a, stream);

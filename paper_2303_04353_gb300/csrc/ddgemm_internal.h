@@ -80,13 +80,16 @@ inline bool int8_tc_slices_supported(int s) {
     return s == 12 || (s >= 14 && s <= INT8_TC_MAX_SLICES);
 }
 
-// Digit planes out[(s * nvec + v) * ld_out + l] (int8, or bf16 when `bf16`),
-// ld_out a multiple of 16 and >= kdim; exps[p * nvec + v] per k-block of
-// KB8.  Element (v, l) of the input is at x[v * ldx + l] when vec_contig,
-// else x[l * ldx + v].
+// tile_rows = 0: int8 digit planes out[(s * nvec + v) * ld_out + l], ld_out
+// a multiple of 16 and >= kdim.  tile_rows = TH (a multiple of 8): bf16
+// digits in the tcgen05 form's tiled, pre-swizzled order (split_int8.cu),
+// ceil(nvec / TH) * ceil(kdim / 16) * s blocks of TH x 16; entries past
+// kdim up to a multiple of 16 are zero, rows past nvec are not written.
+// exps[p * nvec + v] per k-block of KB8.  Element (v, l) of the input is at
+// x[v * ldx + l] when vec_contig, else x[l * ldx + v].
 cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi,
                               const double *x_lo, long long ldx, bool vec_contig, void *out,
-                              bool bf16, long long ld_out, int *exps, unsigned int *status,
+                              int tile_rows, long long ld_out, int *exps, unsigned int *status,
                               cudaStream_t stream);
 
 struct Int8Args {
@@ -106,11 +109,14 @@ cudaError_t launch_cascade_int8(const Int8Args &a, cudaStream_t stream);
 // The INT8 form on the fifth-generation tensor cores: bf16 digit planes,
 // tcgen05.mma with FP32 accumulation in tensor memory (exact over 256
 // entries), int32 diagonal sums, exact assembly rounded once to FP64x2.
+// Tile heights of the tcgen05 form's tiled digit order: rows of C per tile
+// (A) and columns (B).
+constexpr int INT8_TC_BM = 128, INT8_TC_BN = 16;
+
 struct Int8TcArgs {
     int m, n, k, slices;
-    const uint16_t *a_planes;  // slices x m x ld (bf16 bits)
-    const uint16_t *b_planes;  // slices x n x ld
-    long long ld;
+    const uint16_t *a_tiles;   // bf16, tiled order with TH = INT8_TC_BM
+    const uint16_t *b_tiles;   // bf16, tiled order with TH = INT8_TC_BN
     const int *exp_a;          // ceil(k/KB8) x m
     const int *exp_b;          // ceil(k/KB8) x n
     double *c_hi, *c_lo;

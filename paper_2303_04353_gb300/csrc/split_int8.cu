@@ -7,10 +7,17 @@
 //   X = rne(hi 2^(F-e)) + rne(lo 2^(F-e))     (exact, 128-bit integers)
 //   balanced base-128 digits d_0..d_{s-1} of X, most significant first,
 //   d_i in [-64, 64], so that x / sigma ~ sum_i d_i 2^(-6-7i).
-// Output: digit planes [s][vector][ld] with k contiguous, for A (vectors =
-// rows) and B (vectors = columns; transposed through shared memory) alike:
-// int8 for mma.sync m16n8k32 s8, or bf16 for the tcgen05 form (a digit of at
-// most 7 significant bits is exact in bf16).
+// Output, for A (vectors = rows) and B (vectors = columns; transposed
+// through shared memory) alike, either
+//   * int8 digit planes [s][vector][ld] with k contiguous (mma.sync
+//     m16n8k32 s8), or
+//   * bf16 digits (a digit of at most 7 significant bits is exact in bf16)
+//     in the tcgen05 form's tiled order: for every tile of TH vectors
+//     (TH = 128 for A, 16 for B) and every k-step of 16 entries, the s
+//     planes' TH x 16 blocks follow one another, each block being the
+//     shared-memory image of a K-major operand with 32-byte swizzling (row r
+//     at byte 32 r, its two 16-byte halves exchanged when bit 2 of r is
+//     set).  One contiguous copy then stages a whole k-step of all planes.
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -105,11 +112,20 @@ __device__ __forceinline__ unsigned long long bf16_bits(int d) {
     return (unsigned long long)(__float_as_uint((float)d) >> 16);
 }
 
+// Element offset of the 8-entry group (v, l .. l+7) of plane s in the tiled
+// bf16 order (l a multiple of 8).
+template <int S>
+__device__ __forceinline__ long long tiled_offset(int v, int l, int s, int th, int ksteps) {
+    const int r = v % th;
+    const long long block = ((long long)(v / th) * ksteps + l / 16) * S + s;
+    return block * th * 16 + r * 16 + ((((l >> 3) & 1) ^ ((r >> 2) & 1)) << 3);
+}
+
 template <int S, bool CONTIG, bool BF16>
 __global__ void __launch_bounds__(256)
 int8_digits_kernel(int nvec, int kdim, const double *__restrict__ xh,
                    const double *__restrict__ xl, long long ldx, void *__restrict__ out_v,
-                   long long ld_out, const int *__restrict__ exps, unsigned int *status) {
+                   long long ld_out, int th, const int *__restrict__ exps, unsigned int *status) {
     __shared__ double sh[TV][TK + 1];
     __shared__ double sl[TV][TK + 1];
     const int tid = threadIdx.x;
@@ -171,20 +187,29 @@ int8_digits_kernel(int nvec, int kdim, const double *__restrict__ xh,
     }
     if (bad && status) atomicOr(status, DEV_NONFINITE);
     const int gl = l0 + lg * 8;
-    if (gl >= kdim) return;
-    // entries past kdim in the last group of 8 carry zero digits; they sit
-    // in the row padding (ld_out >= kdim rounded up to 16) and are never read
+    if constexpr (BF16) {
+        // the tiled order is read a whole k-step of 16 at a time: groups past
+        // kdim up to the next multiple of 16 are written with zero digits
+        if (gl >= (kdim + 15) / 16 * 16) return;
+        const int ksteps = (kdim + 15) / 16;
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const long long o = ((long long)s * nvec + gv) * ld_out + gl;
-        if constexpr (BF16) {
+        for (int s = 0; s < S; ++s) {
             uint4 q;
             q.x = (unsigned)word[s][0];
             q.y = (unsigned)(word[s][0] >> 32);
             q.z = (unsigned)word[s][1];
             q.w = (unsigned)(word[s][1] >> 32);
-            *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(out_v) + o) = q;
-        } else {
+            *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(out_v) +
+                                       tiled_offset<S>(gv, gl, s, th, ksteps)) = q;
+        }
+    } else {
+        if (gl >= kdim) return;
+        // entries past kdim in the last group of 8 carry zero digits; they
+        // sit in the row padding (ld_out >= kdim rounded up to 16) and are
+        // never read
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const long long o = ((long long)s * nvec + gv) * ld_out + gl;
             *reinterpret_cast<unsigned long long *>(static_cast<int8_t *>(out_v) + o) = word[s][0];
         }
     }
@@ -192,42 +217,44 @@ int8_digits_kernel(int nvec, int kdim, const double *__restrict__ xh,
 
 template <int S, bool BF16>
 cudaError_t launch_digits_t(int nvec, int kdim, const double *xh, const double *xl, long long ldx,
-                            bool contig, void *out, long long ld_out, const int *exps,
+                            bool contig, void *out, long long ld_out, int th, const int *exps,
                             unsigned int *status, cudaStream_t stream) {
     const dim3 grid((kdim + TK - 1) / TK, (nvec + TV - 1) / TV);
     if (grid.y > 65535) return cudaErrorInvalidValue;
     if (contig)
         int8_digits_kernel<S, true, BF16><<<grid, 256, 0, stream>>>(nvec, kdim, xh, xl, ldx, out,
-                                                                    ld_out, exps, status);
+                                                                    ld_out, th, exps, status);
     else
         int8_digits_kernel<S, false, BF16><<<grid, 256, 0, stream>>>(nvec, kdim, xh, xl, ldx,
-                                                                     out, ld_out, exps, status);
+                                                                     out, ld_out, th, exps,
+                                                                     status);
     return cudaGetLastError();
 }
 
 template <int S>
 cudaError_t launch_digits(int nvec, int kdim, const double *xh, const double *xl, long long ldx,
-                          bool contig, void *out, bool bf16, long long ld_out, const int *exps,
-                          unsigned int *status, cudaStream_t stream) {
-    if (bf16) {
+                          bool contig, void *out, int tile_rows, long long ld_out,
+                          const int *exps, unsigned int *status, cudaStream_t stream) {
+    if (tile_rows) {
         if constexpr (S <= INT8_TC_MAX_SLICES)
-            return launch_digits_t<S, true>(nvec, kdim, xh, xl, ldx, contig, out, ld_out, exps,
-                                            status, stream);
+            return launch_digits_t<S, true>(nvec, kdim, xh, xl, ldx, contig, out, 0, tile_rows,
+                                            exps, status, stream);
         else
             return cudaErrorInvalidValue;
     }
-    return launch_digits_t<S, false>(nvec, kdim, xh, xl, ldx, contig, out, ld_out, exps, status,
-                                     stream);
+    return launch_digits_t<S, false>(nvec, kdim, xh, xl, ldx, contig, out, ld_out, 0, exps,
+                                     status, stream);
 }
 
 }  // namespace
 
 cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi,
                               const double *x_lo, long long ldx, bool vec_contig, void *out,
-                              bool bf16, long long ld_out, int *exps, unsigned int *status,
+                              int tile_rows, long long ld_out, int *exps, unsigned int *status,
                               cudaStream_t stream) {
     if (nvec <= 0 || kdim <= 0) return cudaSuccess;
-    if (ld_out % 16 != 0 || ld_out < kdim) return cudaErrorInvalidValue;
+    if (tile_rows == 0 && (ld_out % 16 != 0 || ld_out < kdim)) return cudaErrorInvalidValue;
+    if (tile_rows != 0 && tile_rows % 8 != 0) return cudaErrorInvalidValue;
     const int kb = (kdim + KB8 - 1) / KB8;
     if (vec_contig) {
         const long long blocks = ((long long)nvec * kb + 7) / 8;
@@ -243,8 +270,8 @@ cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi
     switch (slices) {
 #define DDG_CASE(S)                                                                            \
     case S:                                                                                    \
-        return launch_digits<S>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, bf16, ld_out,   \
-                                exps, status, stream);
+        return launch_digits<S>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,      \
+                                ld_out, exps, status, stream);
         DDG_INT8_SLICE_CASES
 #undef DDG_CASE
         default:
