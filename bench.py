@@ -47,10 +47,12 @@ NOMINAL_FP64_TFLOPS = 1.25
 NOMINAL_BF16_TFLOPS = 2250.0
 
 # DRAM bytes per launch (read + write) of the dominant kernel, from one ncu
-# capture of the current kernels at 4096^3 (profiles/dram_traffic_4096.md);
+# capture of the current kernels at 4096^3 (profiles/dram_traffic_4096.md, and
+# profiles/cascade_int8_tc_kernel_2048.md for the tcgen05 kernel);
 # other workloads report null.
 TRAFFIC_4096 = {"cascade_fp64_kernel": 9.884050e9 + 0.282231e9,
-                "cascade_int8_kernel<16>": 3.528115e9 + 0.269681e9}
+                "cascade_int8_kernel<16>": 3.528115e9 + 0.269681e9,
+                "cascade_int8_tc_kernel<16>": 9.281074e9 + 0.339288e9}
 
 WORKLOADS = {
     "4096": dict(m=4096, n=4096, k=4096, kind="wide",
@@ -491,8 +493,10 @@ def run_ours(args, wl):
         "roofline": roofline,
         "e2e": {"value": round(replica_rate(flops_dd, world, e2e_ms) / 1e9, 4), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        # split A, split B, the cascade kernel, and the split-k fix-up
-        "gpu_launches": (3 + (groups > 1)) * args.steps,
+        # FP64 form: split A, split B, the cascade kernel, the split-k fix-up;
+        # INT8 forms: exponents and digits of A and of B, the cascade kernel
+        "gpu_launches": ((3 + (groups > 1)) if variant == _lib.DDGEMM_VARIANT_FP64 else 5)
+        * args.steps,
         "clocks": clocks,
     }
     if int8_form is not None:
@@ -678,7 +682,8 @@ def run_illcond(args):
             d_in = [torch.from_numpy(x).to(dev) for x in a]
             res = {}
             for name, variant in (("cascade fp64", _lib.DDGEMM_VARIANT_FP64),
-                                  ("cascade int8 s=16", _lib.DDGEMM_VARIANT_INT8)):
+                                  ("cascade int8 s=16", _lib.DDGEMM_VARIANT_INT8),
+                                  ("cascade int8 tcgen05 s=16", _lib.DDGEMM_VARIANT_INT8_TC)):
                 c = ops.ddgemm(*d_in, variant=variant)
                 torch.cuda.synchronize()
                 res[name] = worst(c[0].cpu().numpy(), c[1].cpu().numpy())
@@ -747,7 +752,8 @@ def run_sweep(args):
     rng = np.random.default_rng(3)
     rows, cols = rng.integers(0, m, 128), rng.integers(0, n, 128)
     forms = [("fp64", _lib.DDGEMM_VARIANT_FP64, 0)] + [
-        (f"int8 s={s8}", _lib.DDGEMM_VARIANT_INT8, s8) for s8 in (14, 16, 18)]
+        (f"int8 s={s8}", _lib.DDGEMM_VARIANT_INT8, s8) for s8 in (14, 16, 18)] + [
+        (f"int8 tcgen05 s={s8}", _lib.DDGEMM_VARIANT_INT8_TC, s8) for s8 in (14, 16)]
     for spread in range(0, 61, 10):
         a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind="wide", seed=0, spread=float(spread))
         d_in = [torch.from_numpy(x).to(dev) for x in (a_hi, a_lo, b_hi, b_lo)]

@@ -60,12 +60,14 @@ namespace {
 constexpr int BM = INT8_TC_BM, BN = INT8_TC_BN, BK = 16;
 constexpr int CHUNK_STEPS = 16;                       // 16 k-steps of 16: 256 entries
 constexpr int BLOCK_CHUNKS = KB8 / (BK * CHUNK_STEPS);  // chunks per k-block
-constexpr int NST = 3;
 constexpr int EPI_WARPS = 8;
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_STRIDE = 256;                  // columns between the two sets
 constexpr int TILE_GROUP = 4;
+
+constexpr int MAX_SMEM = 227 * 1024;                  // dynamic shared memory per CTA
+constexpr int BAR_BYTES = 256;
 
 template <int S>
 struct TcGeom {
@@ -74,11 +76,15 @@ struct TcGeom {
     static constexpr int A_STAGE = S * A_PLANE;
     static constexpr int TX = S * (A_PLANE + B_PLANE);  // bytes the two copies deliver
     static constexpr int STAGE = (TX + 1023) / 1024 * 1024;
-    static constexpr int BAR_BYTES = 256;
+    // as many stages as fit, at most 4 (3 at s = 16)
+    static constexpr int NST_FIT = (MAX_SMEM - BAR_BYTES - 1024) / STAGE;
+    static constexpr int NST = NST_FIT < 4 ? NST_FIT : 4;
     static constexpr size_t SMEM = (size_t)NST * STAGE + BAR_BYTES + 1024;
+    static_assert(NST >= 2, "at least two stages");
     static_assert(S * BN <= (int)ACC_STRIDE, "one accumulator set is 16 s columns");
 };
 
+template <int NST>
 struct Shared {
     uint64_t full[NST], empty[NST], acc_full[2], acc_empty[2], mma_done;
     uint32_t tmem_base;
@@ -86,7 +92,8 @@ struct Shared {
 };
 
 // A bounded wait that also gives up when another role has aborted.
-__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, Shared *sh,
+template <class SH>
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, SH *sh,
                                               unsigned int *status) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
@@ -250,10 +257,12 @@ template <int S>
 __global__ void __launch_bounds__(NTHREADS, 1)
 cascade_int8_tc_kernel(const Int8TcArgs args) {
     using G = TcGeom<S>;
+    constexpr int NST = G::NST;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    Shared *sh = reinterpret_cast<Shared *>(smem + NST * G::STAGE);
+    auto *sh = reinterpret_cast<Shared<NST> *>(smem + NST * G::STAGE);
+    static_assert(sizeof(Shared<NST>) <= BAR_BYTES, "barriers fit their region");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_m = (args.m + BM - 1) / BM, tiles_n = (args.n + BN - 1) / BN;
