@@ -360,6 +360,15 @@ double ddgemm_probe_fp64(int iters, double *sink, void *stream);
  * number of integer operations (2 per multiply-add), or -1 on error. */
 double ddgemm_probe_int8(int iters, double *sink, void *stream);
 
+/* Check of the kernels' failure handling, not part of the method: one
+ * thread waits, with the same bounded mbarrier wait the cascade kernels
+ * use, on a barrier that nothing arrives on.  After limit_ns nanoseconds
+ * (1 .. 10^10) it gives up and ORs DDGEMM_DEV_TIMEOUT into *status_dev, as
+ * a cascade kernel does when a wait runs out; the context stays usable.
+ * Returns DDGEMM_EINVAL for a null status or a limit out of range. */
+int ddgemm_probe_wait_timeout(unsigned long long limit_ns, unsigned int *status_dev,
+                              void *stream);
+
 /* Static text for a return code. */
 const char *ddgemm_status_string(int code);
 

@@ -61,6 +61,7 @@ _SIGS = {
     "ddgemm_workspace_size": (_Z, [_I, _I, _I, _P]),
     "ddgemm_split_groups": (_I, [_I, _I, _I, _I, _Z, _P]),
     "ddgemm_assemble_int8": (_I, [_I, _I, _P, _P, _P, _P, _P]),
+    "ddgemm_probe_wait_timeout": (_I, [ctypes.c_ulonglong, _P, _P]),
     "ddgemm": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _Z, _P, _P]),
     "ddgemm_split_a": (_I, [_I, _I, _P, _P, _I, _I, _P, _I, _P, _P, _P]),
     "ddgemm_split_b": (_I, [_I, _I, _P, _P, _I, _I, _P, _I, _P, _P, _P]),

@@ -20,9 +20,10 @@ from . import ops
 
 class DDMatmul(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, a_hi, a_lo, b_hi, b_lo):
-        c_hi, c_lo = ops.ddgemm(a_hi, a_lo, b_hi, b_lo)
+    def forward(ctx, a_hi, a_lo, b_hi, b_lo, variant=0):
+        c_hi, c_lo = ops.ddgemm(a_hi, a_lo, b_hi, b_lo, variant=variant)
         ctx.save_for_backward(a_hi, a_lo, b_hi, b_lo)
+        ctx.variant = variant
         return c_hi, c_lo
 
     @staticmethod
@@ -30,13 +31,16 @@ class DDMatmul(torch.autograd.Function):
         a_hi, a_lo, b_hi, b_lo = ctx.saved_tensors
         ref = g_hi if g_hi is not None else g_lo
         if ref is None:
-            return None, None, None, None
+            return None, None, None, None, None
         g_hi = torch.zeros_like(ref) if g_hi is None else g_hi.contiguous()
         g_lo = torch.zeros_like(ref) if g_lo is None else g_lo.contiguous()
-        da_hi, da_lo, db_hi, db_lo = ops.ddgemm_backward(a_hi, a_lo, b_hi, b_lo, g_hi, g_lo)
-        return da_hi, da_lo, db_hi, db_lo
+        da_hi, da_lo, db_hi, db_lo = ops.ddgemm_backward(a_hi, a_lo, b_hi, b_lo, g_hi, g_lo,
+                                                         variant=ctx.variant)
+        return da_hi, da_lo, db_hi, db_lo, None
 
 
-def ddmatmul(a_hi, a_lo, b_hi, b_lo):
-    """C = A B in FP64x2 (differentiable); returns (c_hi, c_lo)."""
-    return DDMatmul.apply(a_hi, a_lo, b_hi, b_lo)
+def ddmatmul(a_hi, a_lo, b_hi, b_lo, variant=0):
+    """C = A B in FP64x2 (differentiable); returns (c_hi, c_lo).  variant:
+    0 the FP64 form (default), 1 the INT8 form on mma.sync, 4 the INT8 form
+    on the tcgen05 tensor cores; forward and backward use the same form."""
+    return DDMatmul.apply(a_hi, a_lo, b_hi, b_lo, variant)

@@ -5,8 +5,19 @@
 #include <cuda_runtime.h>
 
 #include "../../include/ddgemm.h"
+#include "tma.cuh"
 
 namespace {
+
+// One thread waits, with the kernels' bounded wait, on an mbarrier that
+// nothing ever arrives on, and reports DDGEMM_DEV_TIMEOUT when it gives up.
+__global__ void wait_probe_kernel(unsigned long long limit_ns, unsigned int *status) {
+    __shared__ uint64_t bar;
+    const uint32_t a = ddg::smem_addr(&bar);
+    ddg::mbar_init(a, 1);
+    ddg::mbar_fence_init();
+    if (!ddg::mbar_wait_limit(a, 0, limit_ns)) atomicOr(status, ddg::DEV_TIMEOUT_BIT);
+}
 
 __global__ void __launch_bounds__(256) dmma_probe_kernel(int iters, double *sink) {
     const double a = 1e-3 * (threadIdx.x + 1), b = 0.5;
@@ -76,4 +87,11 @@ extern "C" double ddgemm_probe_fp64(int iters, double *sink, void *stream) {
     if (cudaGetLastError() != cudaSuccess) return -1.0;
     // warps x iterations x 8 MMAs x (8 x 8 x 4 multiply-adds x 2 flops)
     return (double)blocks * 8.0 * iters * 8.0 * 512.0;
+}
+
+extern "C" int ddgemm_probe_wait_timeout(unsigned long long limit_ns, unsigned int *status_dev,
+                                         void *stream) {
+    if (!status_dev || limit_ns == 0 || limit_ns > 10000000000ull) return DDGEMM_EINVAL;
+    wait_probe_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(limit_ns, status_dev);
+    return cudaGetLastError() == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }

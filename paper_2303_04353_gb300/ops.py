@@ -158,9 +158,11 @@ def bins(a_hi, a_lo, b_hi, b_lo, *, stream=None):
 
 
 def ddgemm_backward(a_hi, a_lo, b_hi, b_lo, dc_hi, dc_lo, *, trans_a=False, trans_b=False,
-                    workspace=None, status=None, stream=None):
-    """dA = dC op(B)^T and dB = op(A)^T dC through the cascade; returns
-    (dA_hi, dA_lo, dB_hi, dB_lo) in the storage shapes of A and B."""
+                    workspace=None, status=None, stream=None,
+                    variant=_lib.DDGEMM_VARIANT_FP64, int8_slices=0):
+    """dA = dC op(B)^T and dB = op(A)^T dC through the cascade (variant: the
+    FP64 form or one of the INT8 forms); returns (dA_hi, dA_lo, dB_hi,
+    dB_lo) in the storage shapes of A and B."""
     lda = _check_pair(a_hi, a_lo, "A")
     ldb = _check_pair(b_hi, b_lo, "B")
     lddc = _check_pair(dc_hi, dc_lo, "dC")
@@ -171,8 +173,9 @@ def ddgemm_backward(a_hi, a_lo, b_hi, b_lo, dc_hi, dc_lo, *, trans_a=False, tran
     dev = a_hi.device
     da = [torch.empty(a_hi.shape, dtype=torch.float64, device=dev) for _ in range(2)]
     db = [torch.empty(b_hi.shape, dtype=torch.float64, device=dev) for _ in range(2)]
-    opts = _lib.make_opts(trans_a, trans_b, _lib.DDGEMM_VARIANT_FP64,
-                          status.data_ptr() if status is not None else 0)
+    opts = _lib.make_opts(trans_a, trans_b, variant,
+                          status.data_ptr() if status is not None else 0,
+                          int8_slices=int8_slices)
     if workspace is None:
         nbytes = _lib.ddgemm_backward_workspace_size(m, n, k, opts)
         workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)

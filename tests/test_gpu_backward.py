@@ -156,3 +156,27 @@ def test_backward_2048_sampled(mods):
     oh, ol = dd.ddgemm_entries(at_hi, at_lo, w_hi, w_lo, r, c)
     absxy = np.array([np.abs(at_hi[i]) @ np.abs(w_hi[:, j]) for i, j in zip(r, c)])
     assert np.all(np.abs((db_hi[r, c] - oh) + (db_lo[r, c] - ol)) <= CONTRACT * absxy)
+
+
+@pytest.mark.parametrize("variant", [1, 4])
+def test_backward_int8_forms_equal_their_forward_products(mods, variant):
+    """The backward of the INT8 forms is two products of the same form:
+    dA = dC B^T and dB = A^T dC, bit for bit, and close to the oracle."""
+    ops, ag = mods
+    m, n, k = 150, 40, 300
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, seed=41)
+    w_hi, w_lo = dd_matrix(np.random.default_rng(42), (m, n))
+    t = dev(a_hi, a_lo, b_hi, b_lo, w_hi, w_lo)
+    da_hi, da_lo, db_hi, db_lo = host(*ops.ddgemm_backward(*t, variant=variant))
+    fa = host(*ops.ddgemm(t[4], t[5], t[2].T.contiguous(), t[3].T.contiguous(), variant=variant))
+    fb = host(*ops.ddgemm(t[0].T.contiguous(), t[1].T.contiguous(), t[4], t[5], variant=variant))
+    assert np.array_equal(da_hi, fa[0]) and np.array_equal(da_lo, fa[1])
+    assert np.array_equal(db_hi, fb[0]) and np.array_equal(db_lo, fb[1])
+    o_hi, o_lo = dd.ddgemm(w_hi, w_lo, b_hi.T, b_lo.T)
+    close(da_hi, da_lo, o_hi, o_lo, w_hi, b_hi.T, True)
+    # through autograd
+    ta = [x.clone().requires_grad_(True) for x in t[:4]]
+    c_hi, c_lo = ag.ddmatmul(*ta, variant=variant)
+    torch.autograd.backward((c_hi, c_lo), (t[4], t[5]))
+    assert np.array_equal(ta[0].grad.cpu().numpy(), da_hi)
+    assert np.array_equal(ta[3].grad.cpu().numpy(), db_lo)

@@ -402,3 +402,18 @@ def test_illconditioned_product(ops):
     o_hi, o_lo = dd.ddgemm(*a)
     # at k <= 128 the study (bench.py --illcond) measures 45-170x
     assert rel_errors(c_hi, c_lo, a, rows, cols).max() * 3 < rel_errors(o_hi, o_lo, a, rows, cols).max()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(ops):
+    """A wait that nothing ends gives up after its limit and reports
+    DDGEMM_DEV_TIMEOUT in the status word (the kernels' failure path), and
+    the context still runs a cascade GEMM correctly afterwards."""
+    from paper_2303_04353_gb300 import _lib
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = _lib.load().ddgemm_probe_wait_timeout(20_000_000, status.data_ptr(), stream)
+    assert rc == 0
+    (st,) = host(status)
+    assert st[0] & 0x2
+    a = gemm_inputs(64, 48, 300, kind="uniform", seed=77)
+    check_against_oracles(ops, *a)
