@@ -18,6 +18,11 @@
 // the FP64x2 add.  This is one rounding where the paper's smallest-first
 // FP64x2 sum of the diagonals has s.
 //
+// Clusters (optional, default off).  CL CTAs take neighbouring column
+// tiles of one row tile; each loads S / CL of the A planes and multicasts
+// them to all, and a stage is free once every CTA's MMAs have read it
+// (multicast commits, CL arrivals per use).
+//
 // Tiling.  A C tile is 128 rows x 16 columns; k advances by 16.  The split
 // wrote the digits tiled and pre-swizzled (split_int8.cu), so one bulk copy
 // per operand and stage brings all s digit planes of A ([s][128][16] bf16,
@@ -48,6 +53,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "dd_device.cuh"
 #include "ddgemm_internal.h"
@@ -253,11 +259,12 @@ __device__ __forceinline__ void fold_group(uint32_t base, __int128 (&acc)[8]) {
     }
 }
 
-template <int S>
+template <int S, int CL>
 __global__ void __launch_bounds__(NTHREADS, 1)
 cascade_int8_tc_kernel(const Int8TcArgs args) {
     using G = TcGeom<S>;
     constexpr int NST = G::NST;
+    constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -266,14 +273,21 @@ cascade_int8_tc_kernel(const Int8TcArgs args) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_m = (args.m + BM - 1) / BM, tiles_n = (args.n + BN - 1) / BN;
-    const long long tiles = (long long)tiles_m * tiles_n;
+    // a cluster of CL CTAs takes CL neighbouring column tiles of one row
+    // tile; rank r loads A planes [r S / CL, (r+1) S / CL) for all of them
+    const int rank = CL > 1 ? (int)cluster_rank() : 0;
+    const int groups_n = (tiles_n + CL - 1) / CL;
+    const long long tiles = (long long)tiles_m * groups_n;
+    const long long first = blockIdx.x / CL, stride = gridDim.x / CL;
+    const int p0 = rank * S / CL, p1 = (rank + 1) * S / CL;
     const int ksteps = (args.k + BK - 1) / BK;
     const int nchunks = (ksteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(smem_addr(&sh->full[s]), 1);
-            mbar_init(smem_addr(&sh->empty[s]), 1);
+            // one arrival per CTA of the cluster: each one's MMAs read the stage
+            mbar_init(smem_addr(&sh->empty[s]), CL);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_addr(&sh->acc_full[b]), 1);
@@ -289,6 +303,8 @@ cascade_int8_tc_kernel(const Int8TcArgs args) {
     }
     umma::fence_before();
     __syncthreads();
+    // no peer may copy into or arrive on this CTA's barriers before they exist
+    if constexpr (CL > 1) cluster_sync();
     umma::fence_after();
     const uint32_t tmem = sh->tmem_base;
 
@@ -297,9 +313,12 @@ cascade_int8_tc_kernel(const Int8TcArgs args) {
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (long long tile = blockIdx.x; ok && tile < tiles; tile += gridDim.x) {
-                int tm, tn;
-                grouped_tile((unsigned)tile, tiles_m, tiles_n, TILE_GROUP, tm, tn);
+            for (long long tile = first; ok && tile < tiles; tile += stride) {
+                int tm, tg;
+                grouped_tile((unsigned)tile, tiles_m, groups_n, TILE_GROUP, tm, tg);
+                // a rank past the last column tile computes a copy of it and
+                // stores nothing (its share of A is still needed)
+                const int tn = min(tg * CL + rank, tiles_n - 1);
                 for (int ks = 0; ks < ksteps; ++ks, ++it) {
                     const int stage = it % NST;
                     const uint32_t use = it / NST;
@@ -314,10 +333,14 @@ cascade_int8_tc_kernel(const Int8TcArgs args) {
                     mbar_arrive_expect_tx(bar, (uint32_t)G::TX);
                     // k-step ks of all S planes: S consecutive blocks
                     const uint16_t *src_a =
-                        args.a_tiles + ((long long)tm * ksteps + ks) * S * (BM * BK);
+                        args.a_tiles + (((long long)tm * ksteps + ks) * S + p0) * (BM * BK);
                     const uint16_t *src_b =
                         args.b_tiles + ((long long)tn * ksteps + ks) * S * (BN * BK);
-                    bulk_load(smem_addr(dst), src_a, (uint32_t)G::A_STAGE, bar);
+                    if constexpr (CL > 1)
+                        bulk_load_multicast(smem_addr(dst + p0 * G::A_PLANE), src_a,
+                                            (uint32_t)((p1 - p0) * G::A_PLANE), bar, CL_MASK);
+                    else
+                        bulk_load(smem_addr(dst), src_a, (uint32_t)G::A_STAGE, bar);
                     bulk_load(smem_addr(dst + G::A_STAGE), src_b, (uint32_t)(S * G::B_PLANE),
                               bar);
                 }
@@ -326,6 +349,11 @@ cascade_int8_tc_kernel(const Int8TcArgs args) {
                 // copies issued but perhaps not consumed: let them land (bounded)
                 for (uint32_t u = it > (uint32_t)NST ? it - NST : 0; u < it; ++u)
                     mbar_wait(smem_addr(&sh->full[u % NST]), (u / NST) & 1);
+            } else if (CL > 1) {
+                // the last use of every stage: all CTAs' MMAs have arrived on
+                // this CTA's empty barriers before it may exit (bounded)
+                for (uint32_t u = it > (uint32_t)NST ? it - NST : 0; u < it; ++u)
+                    mbar_wait(smem_addr(&sh->empty[u % NST]), (u / NST) & 1);
             }
         }
         __syncwarp();
@@ -334,7 +362,7 @@ cascade_int8_tc_kernel(const Int8TcArgs args) {
         if (lane == 0) {
             uint32_t it = 0, chunk = 0;
             bool ok = true;
-            for (long long tile = blockIdx.x; ok && tile < tiles; tile += gridDim.x) {
+            for (long long tile = first; ok && tile < tiles; tile += stride) {
                 for (int c = 0; ok && c < nchunks; ++c, ++chunk) {
                     const int b = chunk & 1;
                     const uint32_t use = chunk >> 1;
@@ -363,7 +391,11 @@ cascade_int8_tc_kernel(const Int8TcArgs args) {
                                            umma::desc_k_sw32(a0 + i * G::A_PLANE), bdesc,
                                            umma::idesc_bf16_f32(BM, (S - i) * BN),
                                            (ks > ks0 || i > 0) ? 1u : 0u);
-                        umma::commit(smem_addr(&sh->empty[stage]));
+                        // the stage is free once every CTA that shares it is done
+                        if constexpr (CL > 1)
+                            umma::commit_multicast(smem_addr(&sh->empty[stage]), CL_MASK);
+                        else
+                            umma::commit(smem_addr(&sh->empty[stage]));
                     }
                     if (ok) umma::commit(smem_addr(&sh->acc_full[b]));
                 }
@@ -381,11 +413,12 @@ cascade_int8_tc_kernel(const Int8TcArgs args) {
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + half * 8;
         uint32_t chunk = 0;
         bool ok = true;
-        for (long long tile = blockIdx.x; ok && tile < tiles; tile += gridDim.x) {
-            int tm, tn;
-            grouped_tile((unsigned)tile, tiles_m, tiles_n, TILE_GROUP, tm, tn);
+        for (long long tile = first; ok && tile < tiles; tile += stride) {
+            int tm, tg;
+            grouped_tile((unsigned)tile, tiles_m, groups_n, TILE_GROUP, tm, tg);
             const int row = tm * BM + row_in_tile;
-            const int col0 = tn * BN + half * 8;
+            // past the last column tile: every col >= n, nothing is stored
+            const int col0 = (tg * CL + rank) * BN + half * 8;
             __int128 H[8], L[8];
 #pragma unroll
             for (int x = 0; x < 8; ++x) H[x] = L[x] = 0;
@@ -441,29 +474,60 @@ cascade_int8_tc_kernel(const Int8TcArgs args) {
     }
     umma::fence_before();
     __syncthreads();
+    if constexpr (CL > 1) cluster_sync();   // peers are done with this CTA's memory
     if (warp == 1) {
         umma::fence_after();
         umma::dealloc(tmem, TMEM_COLS);
     }
 }
 
-template <int S>
-cudaError_t launch_tc(const Int8TcArgs &a, cudaStream_t stream) {
+template <int S, int CL>
+cudaError_t launch_tc_cl(const Int8TcArgs &a, cudaStream_t stream) {
     using G = TcGeom<S>;
-    if ((uintptr_t)a.a_tiles % 16 || (uintptr_t)a.b_tiles % 16) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(cascade_int8_tc_kernel<S>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto kernel = cascade_int8_tc_kernel<S, CL>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)G::SMEM);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-        return e;
-    const long long tiles = (long long)((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    const int grid = (int)(tiles < sms ? tiles : sms);
-    cascade_int8_tc_kernel<S><<<grid, NTHREADS, G::SMEM, stream>>>(a);
-    return cudaGetLastError();
+    const long long tiles_n = (a.n + BN - 1) / BN;
+    const long long groups = (long long)((a.m + BM - 1) / BM) * ((tiles_n + CL - 1) / CL);
+    if (groups > 0x7fffffffLL) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cfg.stream = stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // persistent: as many clusters as can be resident at once
+    int clusters = 0;
+    cfg.gridDim = dim3(CL);
+    if ((e = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg)) != cudaSuccess) return e;
+    if (clusters <= 0) return cudaErrorInvalidConfiguration;
+    const long long use = groups < clusters ? groups : clusters;
+    cfg.gridDim = dim3((unsigned)(use * CL));
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+// Cluster size: CTAs along n that share A by multicast copies.  Measured on
+// GB300 at 2048^3 and 4096^3: 2 is as fast as 1 (the L2 reads A causes do
+// not limit the kernel) and 4 is 5-7 % slower (fewer SMs hold whole
+// clusters), so the default is 1.  DDGEMM_INT8TC_CLUSTER = 1, 2 or 4
+// overrides it, for measurement and for the tests of the shared path.
+template <int S>
+cudaError_t launch_tc(const Int8TcArgs &a, cudaStream_t stream) {
+    if ((uintptr_t)a.a_tiles % 16 || (uintptr_t)a.b_tiles % 16) return cudaErrorInvalidValue;
+    int cl = 1;
+    if (const char *env = getenv("DDGEMM_INT8TC_CLUSTER")) {
+        const int v = atoi(env);
+        if (v == 1 || v == 2 || v == 4) cl = v;
+    }
+    if (cl == 4) return launch_tc_cl<S, 4>(a, stream);
+    if (cl == 2) return launch_tc_cl<S, 2>(a, stream);
+    return launch_tc_cl<S, 1>(a, stream);
 }
 
 template <int S>

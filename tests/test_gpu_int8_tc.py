@@ -178,3 +178,16 @@ def test_tc_full_size_sampled(ops):
     absab = np.array([np.abs(a[0][i]) @ np.abs(a[2][:, j]) for i, j in zip(rows, cols)])
     err = np.abs((c_hi[rows, cols] - o_hi) + (c_lo[rows, cols] - o_lo))
     assert np.all(err <= CONTRACT * absab)
+
+
+@pytest.mark.parametrize("cl", ["2", "4"])
+def test_tc_cluster_multicast_path(ops, cl, monkeypatch):
+    """The cluster form (A shared by multicast copies across CL CTAs, the
+    last ranks past n computing a copy and storing nothing): the same bits
+    as the restatement."""
+    monkeypatch.setenv("DDGEMM_INT8TC_CLUSTER", cl)
+    for m, n, k in [(200, 50, 1000), (70, 100, 513), (130, 20, 300)]:
+        a = gemm_inputs(m, n, k, kind="wide", seed=m + n)
+        c_hi, c_lo = tc(ops, *a)
+        w_hi, w_lo = c8.cascade_int8_ddgemm(*a, s=16, assembly="exact")
+        assert same(c_hi, w_hi) and same(c_lo, w_lo)
