@@ -213,12 +213,13 @@ typedef struct ddgemm_batch_config {
     int order;  /* DDGEMM_ORDER_*: order in which CTAs pull the tiles */
 } ddgemm_batch_config;
 
-/* Workspace bytes for ddgemm_batched() over these problems (host array):
- * a plan area plus every problem's cascaded panels. */
+/* Workspace bytes for ddgemm_batched() over these problems (host array)
+ * with these opts (NULL: the FP64 form): a plan area plus every problem's
+ * cascaded panels, or digit tiles for INT8_TC. */
 size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem *probs_host,
                                      const ddgemm_opts *opts);
 
-/* C_i := A_i B_i for count problems, in four launches on `stream`:
+/* C_i := A_i B_i for count problems.  FP64 form: four launches on `stream`:
  *   1. a one-CTA plan kernel that reads probs_dev and writes the problems'
  *      workspace offsets, the tile schedule and a work counter into the
  *      workspace;
@@ -231,9 +232,17 @@ size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem *probs_host
  *               device-side information comes from it, so the call can be
  *               captured into a CUDA graph once it has been uploaded.
  *   workspace   >= ddgemm_batched_workspace_size() bytes, 256-byte aligned.
- *   opts        NULL or: trans flags 0, variant FP64, no flags_dev
- *               (else DDGEMM_EUNSUPPORTED); status_dev is honoured.
+ *   opts        NULL or: trans flags 0, variant FP64 or INT8_TC, no
+ *               flags_dev (else DDGEMM_EUNSUPPORTED); status_dev is
+ *               honoured; int8_slices for INT8_TC (12, 14, 15, 16; 0 = 16).
  *   config      NULL = {DDGEMM_TILE_64x64, DDGEMM_ORDER_LONGEST_K_FIRST}.
+ *               Not used by INT8_TC.
+ * INT8_TC (the INT8 form on the tcgen05 tensor cores, see
+ * DDGEMM_VARIANT_INT8_TC): five launches, a plan, the exponents of every A
+ * and of every B, the digits of all of them, and one persistent tcgen05
+ * kernel over the (problem, 128 x 16 tile) items, longest k first; each
+ * C_i is bit-identical to ddgemm() with that variant.  The workspace size
+ * depends on opts (pass the same opts to both calls).
  * Problems with m or n = 0 are skipped; k = 0 writes C = 0.  The ordering
  * by k costs count^2 / 256 comparisons in the plan kernel. */
 int ddgemm_batched(int count, const ddgemm_problem *probs_host,

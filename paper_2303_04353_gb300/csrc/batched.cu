@@ -371,8 +371,12 @@ bool problem_ok(const ddgemm_problem &q) {
 
 extern "C" size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem *probs_host,
                                                 const ddgemm_opts *opts) {
-    (void)opts;
     if (count <= 0 || !probs_host) return 0;
+    if (opts && opts->variant == DDGEMM_VARIANT_INT8_TC) {
+        const int s = opts->int8_slices ? opts->int8_slices : ddg::INT8_SLICES_DEFAULT;
+        if (!ddg::int8_tc_slices_supported(s)) return 0;
+        return ddg::batched_int8_tc_workspace_size(count, probs_host, s);
+    }
     size_t total = ddg::plan_layout(count).panels;
     for (int i = 0; i < count; ++i) {
         const ddgemm_problem &q = probs_host[i];
@@ -391,9 +395,15 @@ extern "C" int ddgemm_batched(int count, const ddgemm_problem *probs_host,
     unsigned int *status = nullptr;
     if (opts) {
         if (opts->trans_a || opts->trans_b || opts->flags_dev ||
-            opts->variant != DDGEMM_VARIANT_FP64)
+            (opts->variant != DDGEMM_VARIANT_FP64 && opts->variant != DDGEMM_VARIANT_INT8_TC))
             return DDGEMM_EUNSUPPORTED;
         status = opts->status_dev;
+        if (opts->variant == DDGEMM_VARIANT_INT8_TC) {
+            const int s = opts->int8_slices ? opts->int8_slices : INT8_SLICES_DEFAULT;
+            if (!int8_tc_slices_supported(s)) return DDGEMM_EINVAL;
+            return run_batched_int8_tc(count, probs_host, probs_dev, workspace, ws_bytes,
+                                       static_cast<cudaStream_t>(stream), s, status);
+        }
     }
     const int tile = config ? config->tile : DDGEMM_TILE_64x64;
     const int order = config ? config->order : DDGEMM_ORDER_LONGEST_K_FIRST;

@@ -1,0 +1,378 @@
+// Many FP64x2 GEMMs of uneven shapes with the INT8 form on the tcgen05
+// tensor cores, in five launches: a plan, the block exponents of every A
+// (one warp per row and k-block) and of every B (one CTA per 64 columns and
+// k-block), the tiled bf16 digits of every A and B (one CTA per 32 x 64
+// input tile), and one persistent tcgen05 kernel that walks the planned list
+// of (problem, 128 x 16 tile) items, longest k first.  The paper has no
+// batched form; this is the tcgen05 INT8 form (cascade_int8_tc.cu) scheduled
+// for many small problems at once.  Every unit runs the single-problem
+// form's device code on that problem's data, so each C is bit-identical to
+// what ddgemm() computes for it with DDGEMM_VARIANT_INT8_TC.
+//
+// Everything the kernels need is computed on the device from the caller's
+// device copy of the problem list (the host copy only sizes the launches),
+// so the call can be captured into a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/ddgemm.h"
+#include "cascade_int8_tc_core.cuh"
+#include "split_int8_device.cuh"
+
+namespace ddg {
+namespace {
+
+constexpr size_t TC_ALIGN = 256;
+
+__host__ __device__ inline size_t ru_tc(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// One problem as the kernels see it.
+struct TcEntry {
+    int m, n, k, kb8, lda, ldb;
+    long long ldc;
+    const double *a_hi, *a_lo, *b_hi, *b_lo;
+    double *c_hi, *c_lo;
+    uint16_t *a_tiles, *b_tiles;
+    int *e_a, *e_b;
+    int tiles_n;
+    long long tiles;
+    long long ea_units, eb_units, da_units, db_units;
+};
+
+struct TcHeader {
+    long long total_tiles, total_ea, total_eb, total_d;
+    int count;
+    unsigned int *status;
+};
+
+// Workspace: [header][entries][order][tile prefix][4 unit prefixes] | digits
+struct TcPlanLayout {
+    size_t entries, order, tile_pre, ea_pre, eb_pre, da_pre, db_pre, data;
+};
+
+__host__ __device__ inline TcPlanLayout tc_plan_layout(int count) {
+    TcPlanLayout L;
+    const size_t pre = (size_t)(count + 1) * sizeof(long long);
+    L.entries = ru_tc(sizeof(TcHeader), TC_ALIGN);
+    L.order = ru_tc(L.entries + (size_t)count * sizeof(TcEntry), TC_ALIGN);
+    L.tile_pre = ru_tc(L.order + (size_t)count * sizeof(int), TC_ALIGN);
+    L.ea_pre = ru_tc(L.tile_pre + pre, TC_ALIGN);
+    L.eb_pre = ru_tc(L.ea_pre + pre, TC_ALIGN);
+    L.da_pre = ru_tc(L.eb_pre + pre, TC_ALIGN);
+    L.db_pre = ru_tc(L.da_pre + pre, TC_ALIGN);
+    L.data = ru_tc(L.db_pre + pre, TC_ALIGN);
+    return L;
+}
+
+// Digit and exponent bytes of one problem (the single-problem layout).
+__host__ __device__ inline size_t tc_problem_bytes(int m, int n, int k, int slices) {
+    if (m <= 0 || n <= 0 || k <= 0) return 0;
+    const size_t kpad = ru_tc((size_t)k, 16), kb8 = (size_t)(k + KB8 - 1) / KB8;
+    return ru_tc((size_t)slices * ru_tc((size_t)m, INT8_TC_BM) * kpad * 2, TC_ALIGN) +
+           ru_tc((size_t)slices * ru_tc((size_t)n, INT8_TC_BN) * kpad * 2, TC_ALIGN) +
+           ru_tc(kb8 * m * 4, TC_ALIGN) + ru_tc(kb8 * n * 4, TC_ALIGN);
+}
+
+__device__ inline int find_tc(const long long *prefix, int count, long long u) {
+    int lo = 0, hi = count;  // prefix[lo] <= u < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Longest k first, then larger m n, then index.
+__device__ inline bool before_tc(const ddgemm_problem &a, int ia, const ddgemm_problem &b, int ib) {
+    if (a.k != b.k) return a.k > b.k;
+    const long long sa = (long long)a.m * a.n, sb = (long long)b.m * b.n;
+    if (sa != sb) return sa > sb;
+    return ia < ib;
+}
+
+__global__ void __launch_bounds__(256)
+tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, int slices,
+               unsigned int *status) {
+    const TcPlanLayout L = tc_plan_layout(count);
+    TcHeader *hdr = reinterpret_cast<TcHeader *>(ws);
+    TcEntry *ent = reinterpret_cast<TcEntry *>(ws + L.entries);
+    int *order = reinterpret_cast<int *>(ws + L.order);
+    long long *tile_pre = reinterpret_cast<long long *>(ws + L.tile_pre);
+    long long *ea_pre = reinterpret_cast<long long *>(ws + L.ea_pre);
+    long long *eb_pre = reinterpret_cast<long long *>(ws + L.eb_pre);
+    long long *da_pre = reinterpret_cast<long long *>(ws + L.da_pre);
+    long long *db_pre = reinterpret_cast<long long *>(ws + L.db_pre);
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const ddgemm_problem q = probs[i];
+        TcEntry e;
+        e.m = q.m; e.n = q.n; e.k = q.k;
+        e.kb8 = q.k > 0 ? (q.k + KB8 - 1) / KB8 : 0;
+        e.lda = q.lda; e.ldb = q.ldb; e.ldc = q.ldc;
+        e.a_hi = q.A_hi; e.a_lo = q.A_lo; e.b_hi = q.B_hi; e.b_lo = q.B_lo;
+        e.c_hi = q.C_hi; e.c_lo = q.C_lo;
+        const bool mn = q.m > 0 && q.n > 0, work = mn && q.k > 0;
+        e.tiles_n = mn ? (q.n + INT8_TC_BN - 1) / INT8_TC_BN : 0;
+        e.tiles = mn ? (long long)((q.m + INT8_TC_BM - 1) / INT8_TC_BM) * e.tiles_n : 0;
+        const long long ktiles = work ? (q.k + split8::TK - 1) / split8::TK : 0;
+        e.ea_units = work ? (long long)q.m * e.kb8 : 0;
+        e.eb_units = work ? (long long)((q.n + 63) / 64) * e.kb8 : 0;
+        e.da_units = work ? (long long)((q.m + split8::TV - 1) / split8::TV) * ktiles : 0;
+        e.db_units = work ? (long long)((q.n + split8::TV - 1) / split8::TV) * ktiles : 0;
+        ent[i] = e;
+        int r = 0;
+        for (int j = 0; j < count; ++j)
+            if (j != i && before_tc(probs[j], j, q, i)) ++r;
+        order[r] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        size_t off = L.data;
+        long long ta = 0, tb = 0, tda = 0, tdb = 0;
+        for (int i = 0; i < count; ++i) {
+            TcEntry &e = ent[i];
+            ea_pre[i] = ta;
+            eb_pre[i] = tb;
+            da_pre[i] = tda;
+            db_pre[i] = tdb;
+            ta += e.ea_units;
+            tb += e.eb_units;
+            tda += e.da_units;
+            tdb += e.db_units;
+            e.a_tiles = e.b_tiles = nullptr;
+            e.e_a = e.e_b = nullptr;
+            if (e.ea_units > 0) {
+                const size_t kpad = ru_tc((size_t)e.k, 16);
+                e.a_tiles = reinterpret_cast<uint16_t *>(ws + off);
+                off += ru_tc((size_t)slices * ru_tc((size_t)e.m, INT8_TC_BM) * kpad * 2, TC_ALIGN);
+                e.b_tiles = reinterpret_cast<uint16_t *>(ws + off);
+                off += ru_tc((size_t)slices * ru_tc((size_t)e.n, INT8_TC_BN) * kpad * 2, TC_ALIGN);
+                e.e_a = reinterpret_cast<int *>(ws + off);
+                off += ru_tc((size_t)e.kb8 * e.m * 4, TC_ALIGN);
+                e.e_b = reinterpret_cast<int *>(ws + off);
+                off += ru_tc((size_t)e.kb8 * e.n * 4, TC_ALIGN);
+            }
+        }
+        ea_pre[count] = ta;
+        eb_pre[count] = tb;
+        da_pre[count] = tda;
+        db_pre[count] = tdb;
+        long long tt = 0;
+        for (int r = 0; r < count; ++r) {
+            tile_pre[r] = tt;
+            tt += ent[order[r]].tiles;
+        }
+        tile_pre[count] = tt;
+        hdr->total_tiles = tt;
+        hdr->total_ea = ta;
+        hdr->total_eb = tb;
+        hdr->total_d = tda + tdb;
+        hdr->count = count;
+        hdr->status = status;
+    }
+}
+
+struct TcView {
+    const TcHeader *hdr;
+    const TcEntry *ent;
+    const int *order;
+    const long long *tile_pre, *ea_pre, *eb_pre, *da_pre, *db_pre;
+    __device__ explicit TcView(const char *ws) {
+        hdr = reinterpret_cast<const TcHeader *>(ws);
+        const TcPlanLayout L = tc_plan_layout(hdr->count);
+        ent = reinterpret_cast<const TcEntry *>(ws + L.entries);
+        order = reinterpret_cast<const int *>(ws + L.order);
+        tile_pre = reinterpret_cast<const long long *>(ws + L.tile_pre);
+        ea_pre = reinterpret_cast<const long long *>(ws + L.ea_pre);
+        eb_pre = reinterpret_cast<const long long *>(ws + L.eb_pre);
+        da_pre = reinterpret_cast<const long long *>(ws + L.da_pre);
+        db_pre = reinterpret_cast<const long long *>(ws + L.db_pre);
+    }
+};
+
+// Exponents of every A: one warp per (problem, row, k-block).
+__global__ void __launch_bounds__(256) tc_exps_a_kernel(const char *ws) {
+    const TcView V(ws);
+    const int count = V.hdr->count, lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+         u < V.hdr->total_ea; u += nw) {
+        const int i = find_tc(V.ea_pre, count, u);
+        const TcEntry &e = V.ent[i];
+        const long long local = u - V.ea_pre[i];
+        split8::exps_contig_unit(lane, (int)(local / e.kb8), (int)(local % e.kb8), e.m, e.k,
+                                 e.a_hi, e.lda, e.e_a);
+    }
+}
+
+// Exponents of every B: one CTA per (problem, 64 columns, k-block).
+__global__ void __launch_bounds__(256) tc_exps_b_kernel(const char *ws) {
+    __shared__ double part[4][64];
+    const TcView V(ws);
+    const int count = V.hdr->count;
+    for (long long u = blockIdx.x; u < V.hdr->total_eb; u += gridDim.x) {
+        const int i = find_tc(V.eb_pre, count, u);
+        const TcEntry &e = V.ent[i];
+        const long long local = u - V.eb_pre[i];
+        const int vtiles = (e.n + 63) / 64;
+        split8::exps_strided_unit((int)(local % vtiles), (int)(local / vtiles), e.n, e.k, e.b_hi,
+                                  e.ldb, e.e_b, part);
+    }
+}
+
+// Digits of every A, then of every B: one CTA per 32 x 64 input tile.
+template <int S>
+__global__ void __launch_bounds__(256) tc_digits_kernel(const char *ws) {
+    __shared__ double sh[split8::TV][split8::TK + 1];
+    __shared__ double sl[split8::TV][split8::TK + 1];
+    const TcView V(ws);
+    const int count = V.hdr->count;
+    const long long total_a = V.da_pre[count];
+    unsigned int *status = V.hdr->status;
+    for (long long u = blockIdx.x; u < V.hdr->total_d; u += gridDim.x) {
+        __syncthreads();  // the previous unit is done with sh, sl
+        if (u < total_a) {
+            const int i = find_tc(V.da_pre, count, u);
+            const TcEntry &e = V.ent[i];
+            const long long local = u - V.da_pre[i];
+            const int ktiles = (e.k + split8::TK - 1) / split8::TK;
+            split8::digits_unit<S, true, true>((int)(local / ktiles) * split8::TV,
+                                               (int)(local % ktiles) * split8::TK, e.m, e.k,
+                                               e.a_hi, e.a_lo, e.lda, e.a_tiles, 0, INT8_TC_BM,
+                                               e.e_a, status, sh, sl);
+        } else {
+            const long long ub = u - total_a;
+            const int i = find_tc(V.db_pre, count, ub);
+            const TcEntry &e = V.ent[i];
+            const long long local = ub - V.db_pre[i];
+            const int ktiles = (e.k + split8::TK - 1) / split8::TK;
+            split8::digits_unit<S, false, true>((int)(local / ktiles) * split8::TV,
+                                                (int)(local % ktiles) * split8::TK, e.n, e.k,
+                                                e.b_hi, e.b_lo, e.ldb, e.b_tiles, 0, INT8_TC_BN,
+                                                e.e_b, status, sh, sl);
+        }
+    }
+}
+
+// The planned (problem, tile) items, longest k first; within a problem the
+// tiles go in groups of TILE_GROUP row tiles.
+struct BatchSource {
+    const char *ws;
+    __device__ long long items() const {
+        return reinterpret_cast<const TcHeader *>(ws)->total_tiles;
+    }
+    __device__ unsigned int *status() const {
+        return reinterpret_cast<const TcHeader *>(ws)->status;
+    }
+    __device__ TcJob job(long long item, int) const {
+        const TcView V(ws);
+        const int r = find_tc(V.tile_pre, V.hdr->count, item);
+        const TcEntry &e = V.ent[V.order[r]];
+        const long long local = item - V.tile_pre[r];
+        int tm, tn;
+        grouped_tile((unsigned)local, (e.m + BM - 1) / BM, e.tiles_n, TILE_GROUP, tm, tn);
+        TcJob j;
+        j.m = e.m;
+        j.n = e.n;
+        j.k = e.k;
+        j.tm = tm;
+        j.tn_load = tn;
+        j.col0 = tn * BN;
+        j.a_tiles = e.a_tiles;
+        j.b_tiles = e.b_tiles;
+        j.exp_a = e.e_a;
+        j.exp_b = e.e_b;
+        j.c_hi = e.c_hi;
+        j.c_lo = e.c_lo;
+        j.ldc = e.ldc;
+        return j;
+    }
+};
+
+template <int S>
+cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, long long units_eb,
+                              long long units_d, int sms, cudaStream_t s) {
+    const long long cap = 8LL * sms;
+    if (units_ea > 0) {
+        const long long blocks = (units_ea + 7) / 8;
+        tc_exps_a_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(ws);
+    }
+    if (units_eb > 0)
+        tc_exps_b_kernel<<<(unsigned)(units_eb < cap ? units_eb : cap), 256, 0, s>>>(ws);
+    if (units_d > 0)
+        tc_digits_kernel<S><<<(unsigned)(units_d < cap ? units_d : cap), 256, 0, s>>>(ws);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || tiles == 0) return e;
+    using G = TcGeom<S>;
+    auto kernel = cascade_int8_tc_kernel<S, 1, BatchSource>;
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)G::SMEM)) != cudaSuccess)
+        return e;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    BatchSource src{ws};
+    kernel<<<grid, NTHREADS, G::SMEM, s>>>(src);
+    return cudaGetLastError();
+}
+
+bool tc_problem_ok(const ddgemm_problem &q) {
+    if (q.m < 0 || q.n < 0 || q.k < 0) return false;
+    if (q.m > 0 && q.n > 0) {
+        if (!q.C_hi || !q.C_lo || q.ldc < q.n) return false;
+        if (q.k > 0 && (!q.A_hi || !q.A_lo || !q.B_hi || !q.B_lo || q.lda < q.k || q.ldb < q.n))
+            return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+size_t batched_int8_tc_workspace_size(int count, const ddgemm_problem *probs_host, int slices) {
+    if (count <= 0 || !probs_host) return 0;
+    size_t total = tc_plan_layout(count).data;
+    for (int i = 0; i < count; ++i)
+        total += tc_problem_bytes(probs_host[i].m, probs_host[i].n, probs_host[i].k, slices);
+    return total;
+}
+
+int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
+                        const ddgemm_problem *probs_dev, void *workspace, size_t ws_bytes,
+                        cudaStream_t s, int slices, unsigned int *status) {
+    long long tiles = 0, ea = 0, eb = 0, d = 0;
+    for (int i = 0; i < count; ++i) {
+        const ddgemm_problem &q = probs_host[i];
+        if (!tc_problem_ok(q)) return DDGEMM_EINVAL;
+        if (q.m > 0 && q.n > 0) {
+            tiles += (long long)((q.m + INT8_TC_BM - 1) / INT8_TC_BM) *
+                     ((q.n + INT8_TC_BN - 1) / INT8_TC_BN);
+            if (q.k > 0) {
+                const long long kb8 = (q.k + KB8 - 1) / KB8, kt = (q.k + split8::TK - 1) / split8::TK;
+                ea += (long long)q.m * kb8;
+                eb += (long long)((q.n + 63) / 64) * kb8;
+                d += (long long)((q.m + split8::TV - 1) / split8::TV) * kt +
+                     (long long)((q.n + split8::TV - 1) / split8::TV) * kt;
+            }
+        }
+    }
+    const size_t need = batched_int8_tc_workspace_size(count, probs_host, slices);
+    if (!workspace || ws_bytes < need || (uintptr_t)workspace % TC_ALIGN) return DDGEMM_EWORKSPACE;
+    if (tiles > 0x7fffffffLL) return DDGEMM_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return DDGEMM_ECUDA;
+    char *ws = static_cast<char *>(workspace);
+    tc_plan_kernel<<<1, 256, 0, s>>>(count, probs_dev, ws, slices, status);
+    if (cudaGetLastError() != cudaSuccess) return DDGEMM_ECUDA;
+    cudaError_t e;
+    switch (slices) {
+        case 12: e = launch_batched_tc<12>(ws, tiles, ea, eb, d, sms, s); break;
+        case 14: e = launch_batched_tc<14>(ws, tiles, ea, eb, d, sms, s); break;
+        case 15: e = launch_batched_tc<15>(ws, tiles, ea, eb, d, sms, s); break;
+        case 16: e = launch_batched_tc<16>(ws, tiles, ea, eb, d, sms, s); break;
+        default: return DDGEMM_EINVAL;
+    }
+    return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
+}
+
+}  // namespace ddg

@@ -1,0 +1,482 @@
+// The tcgen05 INT8-form kernel (see cascade_int8_tc.cu for the method),
+// templated on where its tiles come from: one problem (cascade_int8_tc.cu)
+// or a planned list of (problem, tile) items (batched_int8_tc.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdlib>
+
+#include "dd_device.cuh"
+#include "ddgemm_internal.h"
+#include "tma.cuh"
+#include "umma.cuh"
+
+namespace ddg {
+namespace {
+
+constexpr int BM = INT8_TC_BM, BN = INT8_TC_BN, BK = 16;
+constexpr int CHUNK_STEPS = 16;                       // 16 k-steps of 16: 256 entries
+constexpr int BLOCK_CHUNKS = KB8 / (BK * CHUNK_STEPS);  // chunks per k-block
+constexpr int EPI_WARPS = 8;
+constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t ACC_STRIDE = 256;                  // columns between the two sets
+constexpr int TILE_GROUP = 4;
+
+constexpr int MAX_SMEM = 227 * 1024;                  // dynamic shared memory per CTA
+constexpr int BAR_BYTES = 256;
+
+template <int S>
+struct TcGeom {
+    static constexpr int A_PLANE = BM * BK * 2;       // 4 KB
+    static constexpr int B_PLANE = BN * BK * 2;       // 512 bytes
+    static constexpr int A_STAGE = S * A_PLANE;
+    static constexpr int TX = S * (A_PLANE + B_PLANE);  // bytes the two copies deliver
+    static constexpr int STAGE = (TX + 1023) / 1024 * 1024;
+    // as many stages as fit, at most 4 (3 at s = 16)
+    static constexpr int NST_FIT = (MAX_SMEM - BAR_BYTES - 1024) / STAGE;
+    static constexpr int NST = NST_FIT < 4 ? NST_FIT : 4;
+    static constexpr size_t SMEM = (size_t)NST * STAGE + BAR_BYTES + 1024;
+    static_assert(NST >= 2, "at least two stages");
+    static_assert(S * BN <= (int)ACC_STRIDE, "one accumulator set is 16 s columns");
+};
+
+template <int NST>
+struct Shared {
+    uint64_t full[NST], empty[NST], acc_full[2], acc_empty[2], mma_done;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+// A bounded wait that also gives up when another role has aborted.
+template <class SH>
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, SH *sh,
+                                              unsigned int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    volatile int *flag = &sh->abort_flag;
+    while (!mbar_try_wait(bar, parity)) {
+        if (*flag) return false;
+        if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            *flag = 1;
+            if (status) atomicOr(status, DEV_TIMEOUT_BIT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ int bitlen128(unsigned __int128 x) {
+    const unsigned long long h = (unsigned long long)(x >> 64), l = (unsigned long long)x;
+    if (h) return 128 - __clzll((long long)h);
+    return l ? 64 - __clzll((long long)l) : 0;
+}
+
+// Nearest double (ties to even) to the signed integer r times 2^e, |r| < 2^127.
+__device__ __forceinline__ double round_int(__int128 r, int e) {
+    if (r == 0) return 0.0;
+    const bool neg = r < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-r) : (unsigned __int128)r;
+    const int q = bitlen128(u);
+    double v;
+    if (q <= 53) {
+        v = scalbn((double)(unsigned long long)u, e);
+    } else {
+        const int sh = q - 53;
+        unsigned long long m = (unsigned long long)(u >> sh);
+        const unsigned __int128 rem = u & (((unsigned __int128)1 << sh) - 1);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) ++m;
+        v = scalbn((double)m, sh + e);
+    }
+    return neg ? -v : v;
+}
+
+// The FP64x2 nearest to T 2^e with T = H 2^56 + L (|H|, |L| < 2^80):
+// hi = RN(T 2^e), lo = RN(T 2^e - hi).
+__device__ __forceinline__ void round_dd(__int128 H, __int128 L, int e, double &hi, double &lo) {
+    // carry L's bits above 2^56 into H: T = H1 2^56 + L0, 0 <= L0 < 2^56
+    // (floor division by 2^56)
+    const __int128 q56 = L / ((__int128)1 << 56);
+    const __int128 carry = (L < 0 && q56 * ((__int128)1 << 56) != L) ? q56 - 1 : q56;
+    const unsigned long long L0 = (unsigned long long)(L - carry * ((__int128)1 << 56));
+    __int128 H1 = H + carry;
+    const bool neg = H1 < 0;
+    unsigned __int128 Hm;
+    unsigned long long Lm;
+    if (!neg) {
+        Hm = (unsigned __int128)H1;
+        Lm = L0;
+    } else if (L0 != 0) {  // -T = (-H1 - 1) 2^56 + (2^56 - L0)
+        Hm = (unsigned __int128)(-H1 - 1);
+        Lm = (1ull << 56) - L0;
+    } else {
+        Hm = (unsigned __int128)(-H1);
+        Lm = 0;
+    }
+    if (Hm == 0 && Lm == 0) {
+        hi = 0.0;
+        lo = 0.0;
+        return;
+    }
+    const int p = Hm ? 56 + bitlen128(Hm) : 64 - __clzll((long long)Lm);
+    if (p <= 53) {  // then Hm = 0 and |T| = Lm < 2^53
+        const double v = scalbn((double)Lm, e);
+        hi = neg ? -v : v;
+        lo = 0.0;
+        return;
+    }
+    // |T| = m 2^sh + r with m the 53-bit significand rounded to nearest even
+    const int sh = p - 53;
+    unsigned __int128 q, rem;
+    if (sh >= 56) {
+        const int s2 = sh - 56;
+        q = Hm >> s2;
+        rem = ((Hm & (((unsigned __int128)1 << s2) - 1)) << 56) | Lm;
+    } else {
+        const unsigned __int128 x = (Hm << 56) | Lm;  // p < 109: fits
+        q = x >> sh;
+        rem = x & (((unsigned __int128)1 << sh) - 1);
+    }
+    unsigned long long m = (unsigned long long)q;
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    __int128 r;
+    if (rem > half || (rem == half && (m & 1ull))) {
+        ++m;
+        r = (__int128)rem - ((__int128)1 << sh);
+    } else {
+        r = (__int128)rem;
+    }
+    const double vh = scalbn((double)m, sh + e);
+    hi = neg ? -vh : vh;
+    lo = round_int(neg ? -r : r, e);
+}
+
+// Diagonal t's term of T = sum_t S_t 2^(7 (s-1-t)) = H 2^56 + L: the eight
+// smallest diagonals go to L, the others to H (multiplications by powers of
+// two: shifts of negative values are not defined in C++17).
+template <int S>
+__device__ __forceinline__ void add_diagonal(int t, int v, __int128 &H, __int128 &L) {
+    if (t < S - 8)
+        H += (__int128)v * ((__int128)1 << (7 * (S - 9 - t)));
+    else
+        L += (__int128)v * ((__int128)1 << (7 * (S - 1 - t)));
+}
+
+// Add diagonals T0 .. T1-1 of one chunk, read from tensor memory (8
+// columns each, at base + 16 t), into acc[j] with the weights of
+// T = H 2^56 + L: the diagonal T1-1 has weight 1 in its half, each
+// earlier one 2^7 more.  Four diagonals at a time are combined exactly in
+// an int64 (|sum| <= 2^24 per diagonal, so at most 2^45), then added in.
+template <int S, int T0, int T1>
+__device__ __forceinline__ void fold_group(uint32_t base, __int128 (&acc)[8]) {
+    static_assert(T1 - T0 <= 8 && T1 > T0, "a half holds 1 to 8 diagonals");
+#pragma unroll
+    for (int g0 = T0; g0 < T1; g0 += 4) {
+        const int len = (T1 - g0) < 4 ? (T1 - g0) : 4;
+        long long g[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) g[j] = 0;
+        uint32_t r[16];
+        if (len >= 2) {
+            umma::ld_x8_x2(base + g0 * BN, base + (g0 + 1) * BN, r);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                g[j] = (long long)__float2int_rn(__uint_as_float(r[j])) * 128 +
+                       __float2int_rn(__uint_as_float(r[8 + j]));
+        } else {
+            uint32_t r1[8];
+            umma::ld_x8(base + g0 * BN, r1);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) g[j] = __float2int_rn(__uint_as_float(r1[j]));
+        }
+        if (len == 3) {
+            uint32_t r1[8];
+            umma::ld_x8(base + (g0 + 2) * BN, r1);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) g[j] = g[j] * 128 + __float2int_rn(__uint_as_float(r1[j]));
+        } else if (len == 4) {
+            umma::ld_x8_x2(base + (g0 + 2) * BN, base + (g0 + 3) * BN, r);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                g[j] = (g[j] * 128 + __float2int_rn(__uint_as_float(r[j]))) * 128 +
+                       __float2int_rn(__uint_as_float(r[8 + j]));
+        }
+        // weight of the group's last diagonal within its half
+        const int last = g0 + len - 1;
+        const int shift = 7 * (T1 - 1 - last);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += (__int128)g[j] * ((__int128)1 << shift);
+    }
+}
+
+// One output tile of one problem, as a CTA sees it.
+struct TcJob {
+    int m, n, k;
+    int tm;        // row tile
+    int tn_load;   // column tile whose B digits are loaded
+    int col0;      // first column this CTA stores (>= n: nothing is stored)
+    const uint16_t *a_tiles, *b_tiles;
+    const int *exp_a, *exp_b;
+    double *c_hi, *c_lo;
+    long long ldc;
+};
+
+// The tiles of one problem (Int8TcArgs), in groups of TILE_GROUP row tiles;
+// with clusters, an item is CL neighbouring column tiles of one row tile.
+struct SingleSource {
+    Int8TcArgs a;
+    int tiles_m, tiles_n, groups_n, cl;
+    __device__ long long items() const { return (long long)tiles_m * groups_n; }
+    __device__ unsigned int *status() const { return a.status; }
+    __device__ TcJob job(long long item, int rank) const {
+        int tm, tg;
+        grouped_tile((unsigned)item, tiles_m, groups_n, TILE_GROUP, tm, tg);
+        const int tn = tg * cl + rank;
+        TcJob j;
+        j.m = a.m;
+        j.n = a.n;
+        j.k = a.k;
+        j.tm = tm;
+        j.tn_load = min(tn, tiles_n - 1);  // a rank past the last tile loads a copy
+        j.col0 = tn * BN;
+        j.a_tiles = a.a_tiles;
+        j.b_tiles = a.b_tiles;
+        j.exp_a = a.exp_a;
+        j.exp_b = a.exp_b;
+        j.c_hi = a.c_hi;
+        j.c_lo = a.c_lo;
+        j.ldc = a.ldc;
+        return j;
+    }
+};
+
+template <int S, int CL, class Src>
+__global__ void __launch_bounds__(NTHREADS, 1)
+cascade_int8_tc_kernel(const Src src) {
+    using G = TcGeom<S>;
+    constexpr int NST = G::NST;
+    constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    auto *sh = reinterpret_cast<Shared<NST> *>(smem + NST * G::STAGE);
+    static_assert(sizeof(Shared<NST>) <= BAR_BYTES, "barriers fit their region");
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // a cluster of CL CTAs takes CL neighbouring column tiles of one row
+    // tile; rank r loads A planes [r S / CL, (r+1) S / CL) for all of them
+    const int rank = CL > 1 ? (int)cluster_rank() : 0;
+    const long long tiles = src.items();
+    const long long first = blockIdx.x / CL, stride = gridDim.x / CL;
+    const int p0 = rank * S / CL, p1 = (rank + 1) * S / CL;
+    unsigned int *status = src.status();
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(smem_addr(&sh->full[s]), 1);
+            // one arrival per CTA of the cluster: each one's MMAs read the stage
+            mbar_init(smem_addr(&sh->empty[s]), CL);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_addr(&sh->acc_full[b]), 1);
+            mbar_init(smem_addr(&sh->acc_empty[b]), EPI_WARPS);
+        }
+        mbar_init(smem_addr(&sh->mma_done), 1);
+        sh->abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        umma::alloc(smem_addr(&sh->tmem_base), TMEM_COLS);
+        umma::relinquish();
+    }
+    umma::fence_before();
+    __syncthreads();
+    // no peer may copy into or arrive on this CTA's barriers before they exist
+    if constexpr (CL > 1) cluster_sync();
+    umma::fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    if (warp == 0) {
+        // ---- TMA producer -----------------------------------------------
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (long long tile = first; ok && tile < tiles; tile += stride) {
+                const TcJob j = src.job(tile, rank);
+                const int ksteps = (j.k + BK - 1) / BK;
+                for (int ks = 0; ks < ksteps; ++ks, ++it) {
+                    const int stage = it % NST;
+                    const uint32_t use = it / NST;
+                    if (use > 0 &&
+                        !wait_or_abort(smem_addr(&sh->empty[stage]), (use - 1) & 1, sh, status)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *dst = smem + stage * G::STAGE;
+                    const uint32_t bar = smem_addr(&sh->full[stage]);
+                    mbar_arrive_expect_tx(bar, (uint32_t)G::TX);
+                    // k-step ks of all S planes: S consecutive blocks
+                    const uint16_t *src_a =
+                        j.a_tiles + (((long long)j.tm * ksteps + ks) * S + p0) * (BM * BK);
+                    const uint16_t *src_b =
+                        j.b_tiles + ((long long)j.tn_load * ksteps + ks) * S * (BN * BK);
+                    if constexpr (CL > 1)
+                        bulk_load_multicast(smem_addr(dst + p0 * G::A_PLANE), src_a,
+                                            (uint32_t)((p1 - p0) * G::A_PLANE), bar, CL_MASK);
+                    else
+                        bulk_load(smem_addr(dst), src_a, (uint32_t)G::A_STAGE, bar);
+                    bulk_load(smem_addr(dst + G::A_STAGE), src_b, (uint32_t)(S * G::B_PLANE),
+                              bar);
+                }
+            }
+            if (!ok) {
+                // copies issued but perhaps not consumed: let them land (bounded)
+                for (uint32_t u = it > (uint32_t)NST ? it - NST : 0; u < it; ++u)
+                    mbar_wait(smem_addr(&sh->full[u % NST]), (u / NST) & 1);
+            } else if (CL > 1) {
+                // the last use of every stage: all CTAs' MMAs have arrived on
+                // this CTA's empty barriers before it may exit (bounded)
+                for (uint32_t u = it > (uint32_t)NST ? it - NST : 0; u < it; ++u)
+                    mbar_wait(smem_addr(&sh->empty[u % NST]), (u / NST) & 1);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- MMA issuer ---------------------------------------------------
+        if (lane == 0) {
+            uint32_t it = 0, chunk = 0;
+            bool ok = true;
+            for (long long tile = first; ok && tile < tiles; tile += stride) {
+                const TcJob j = src.job(tile, rank);
+                const int ksteps = (j.k + BK - 1) / BK;
+                const int nchunks = (ksteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
+                for (int c = 0; ok && c < nchunks; ++c, ++chunk) {
+                    const int b = chunk & 1;
+                    const uint32_t use = chunk >> 1;
+                    if (use > 0 && !wait_or_abort(smem_addr(&sh->acc_empty[b]), (use - 1) & 1,
+                                                  sh, status)) {
+                        ok = false;
+                        break;
+                    }
+                    umma::fence_after();
+                    const uint32_t d_base = tmem + b * ACC_STRIDE;
+                    const int ks0 = c * CHUNK_STEPS;
+                    const int ks1 = min(ksteps, ks0 + CHUNK_STEPS);
+                    for (int ks = ks0; ks < ks1; ++ks, ++it) {
+                        const int stage = it % NST;
+                        if (!wait_or_abort(smem_addr(&sh->full[stage]), (it / NST) & 1, sh,
+                                           status)) {
+                            ok = false;
+                            break;
+                        }
+                        umma::fence_after();
+                        const uint32_t a0 = smem_addr(smem + stage * G::STAGE);
+                        const uint64_t bdesc = umma::desc_k_sw32(a0 + G::A_STAGE);
+#pragma unroll
+                        for (int i = 0; i < S; ++i)
+                            umma::mma_bf16(d_base + i * BN,
+                                           umma::desc_k_sw32(a0 + i * G::A_PLANE), bdesc,
+                                           umma::idesc_bf16_f32(BM, (S - i) * BN),
+                                           (ks > ks0 || i > 0) ? 1u : 0u);
+                        // the stage is free once every CTA that shares it is done
+                        if constexpr (CL > 1)
+                            umma::commit_multicast(smem_addr(&sh->empty[stage]), CL_MASK);
+                        else
+                            umma::commit(smem_addr(&sh->empty[stage]));
+                    }
+                    if (ok) umma::commit(smem_addr(&sh->acc_full[b]));
+                }
+            }
+            // every product of this CTA is done before tensor memory is freed
+            umma::commit(smem_addr(&sh->mma_done));
+            mbar_wait(smem_addr(&sh->mma_done), 0);
+        }
+        __syncwarp();
+    } else {
+        // ---- drain and assembly ---------------------------------------------
+        const int quad = warp & 3;               // tensor-memory lanes 32 quad ..
+        const int half = (warp - 2) >> 2;        // columns 8 half .. + 7 of each diagonal
+        const int row_in_tile = quad * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + half * 8;
+        uint32_t chunk = 0;
+        bool ok = true;
+        for (long long tile = first; ok && tile < tiles; tile += stride) {
+            const TcJob j = src.job(tile, rank);
+            const int ksteps = (j.k + BK - 1) / BK;
+            const int nchunks = (ksteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
+            const int row = j.tm * BM + row_in_tile;
+            // past the last column tile: every col >= n, nothing is stored
+            const int col0 = j.col0 + half * 8;
+            if (nchunks == 0 && row < j.m) {  // k = 0: C = 0 on this tile
+                for (int x = 0; x < 8; ++x)
+                    if (col0 + x < j.n) {
+                        j.c_hi[(long long)row * j.ldc + col0 + x] = 0.0;
+                        j.c_lo[(long long)row * j.ldc + col0 + x] = 0.0;
+                    }
+            }
+            __int128 H[8], L[8];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) H[x] = L[x] = 0;
+            for (int c = 0; c < nchunks; ++c, ++chunk) {
+                const int b = chunk & 1;
+                // every lane waits; the warp goes on only together (the
+                // tensor-memory loads below are warp-wide)
+                const bool lane_ok = wait_or_abort(smem_addr(&sh->acc_full[b]), (chunk >> 1) & 1,
+                                                   sh, status);
+                if (!__all_sync(0xffffffffu, lane_ok)) {
+                    ok = false;
+                    break;
+                }
+                umma::fence_after();
+                const uint32_t base = lane_base + b * ACC_STRIDE;
+                // diagonals 0 .. S-9 belong to H, S-8 .. S-1 to L
+                fold_group<S, 0, S - 8>(base, H);
+                fold_group<S, S - 8, S>(base, L);
+                umma::fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&sh->acc_empty[b]));
+
+                if ((c + 1) % BLOCK_CHUNKS == 0 || c + 1 == nchunks) {
+                    // end of a k-block: its value, rounded once, into C
+                    const int p = c / BLOCK_CHUNKS;
+                    if (row < j.m) {
+                        const int ea = j.exp_a[(long long)p * j.m + row];
+#pragma unroll
+                        for (int x = 0; x < 8; ++x) {
+                            const int col = col0 + x;
+                            if (col < j.n) {
+                                const int e = ea + j.exp_b[(long long)p * j.n + col] - 12 -
+                                              7 * (S - 1);
+                                double h, l;
+                                round_dd(H[x], L[x], e, h, l);
+                                const long long o = (long long)row * j.ldc + col;
+                                double ch = 0.0, cl = 0.0;
+                                if (p > 0) {
+                                    ch = j.c_hi[o];
+                                    cl = j.c_lo[o];
+                                }
+                                dd_add(ch, cl, h, l, ch, cl);
+                                j.c_hi[o] = ch;
+                                j.c_lo[o] = cl;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int x = 0; x < 8; ++x) H[x] = L[x] = 0;
+                }
+            }
+        }
+    }
+    umma::fence_before();
+    __syncthreads();
+    if constexpr (CL > 1) cluster_sync();   // peers are done with this CTA's memory
+    if (warp == 1) {
+        umma::fence_after();
+        umma::dealloc(tmem, TMEM_COLS);
+    }
+}
+
+}  // namespace
+}  // namespace ddg

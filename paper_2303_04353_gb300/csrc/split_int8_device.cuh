@@ -1,0 +1,205 @@
+// Device units of the INT8 split (phase one of the INT8 forms), shared by
+// the single-problem kernels (split_int8.cu) and the batched tcgen05 form
+// (batched_int8_tc.cu).  See split_int8.cu for the method.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "ddgemm_internal.h"
+
+namespace ddg {
+namespace split8 {
+
+constexpr unsigned DEV_NONFINITE = 0x1u;
+
+__device__ __forceinline__ int block_exponent(double mx) {
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    return e;
+}
+
+// One warp: the exponent of block p of vector v, whose entries are
+// contiguous (element l at row[l]).
+__device__ __forceinline__ void exps_contig_unit(int lane, int v, int p, int nvec, int kdim,
+                                                 const double *__restrict__ x, long long ldx,
+                                                 int *__restrict__ exps) {
+    const double *row = x + (long long)v * ldx;
+    const int lend = min((p + 1) * KB8, kdim);
+    double mx = 0.0;
+    for (int l = p * KB8 + lane; l < lend; l += 32) mx = fmax(mx, fabs(row[l]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) exps[(long long)p * nvec + v] = block_exponent(mx);
+}
+
+// One CTA of 256 threads: the exponents of block p of vectors
+// [64 vt, 64 vt + 64), whose entries are strided (element l at x[l*ldx + v]).
+__device__ __forceinline__ void exps_strided_unit(int vt, int p, int nvec, int kdim,
+                                                  const double *__restrict__ x, long long ldx,
+                                                  int *__restrict__ exps, double (&part)[4][64]) {
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    const int v = vt * 64 + tx;
+    const int lend = min((p + 1) * KB8, kdim);
+    double mx = 0.0;
+    if (v < nvec)
+        for (int l = p * KB8 + ty; l < lend; l += 4) mx = fmax(mx, fabs(x[(long long)l * ldx + v]));
+    part[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0 && v < nvec) {
+        mx = fmax(fmax(part[0][tx], part[1][tx]), fmax(part[2][tx], part[3][tx]));
+        exps[(long long)p * nvec + v] = block_exponent(mx);
+    }
+    __syncthreads();  // part is reused by the next unit
+}
+
+// round-half-even(x * 2^sh) as a 128-bit integer, from the bits of x.
+__device__ __forceinline__ __int128 rne_scaled(double x, int sh) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    unsigned long long mant = bits & 0xfffffffffffffull;
+    if (ex == 0x7ff || (ex == 0 && mant == 0)) return 0;  // non-finite is flagged elsewhere
+    int p;
+    if (ex == 0) {
+        p = 1 - 1075 + sh;                 // subnormal: no implicit bit
+    } else {
+        mant |= 1ull << 52;
+        p = ex - 1075 + sh;
+    }
+    __int128 v;
+    if (p > 127 - 54) {
+        // only an entry far above its block's max |hi| gets here (a lo part
+        // much larger than every hi of the block): outside the form's range
+        v = 0;
+    } else if (p >= 0) {
+        v = (__int128)mant << p;
+    } else if (p < -63) {
+        v = 0;                             // below one half
+    } else {
+        const int r = -p;
+        unsigned long long q = mant >> r;
+        const unsigned long long rem = mant & ((1ull << r) - 1ull);
+        const unsigned long long half = 1ull << (r - 1);
+        if (rem > half || (rem == half && (q & 1ull))) ++q;
+        v = (__int128)q;
+    }
+    return (bits >> 63) ? -v : v;
+}
+
+constexpr int TV = 32, TK = 64;  // tile: 32 vectors x 64 k
+
+// bf16 encoding of a small integer: the upper half of its FP32 encoding,
+// exact because the FP32 significand of |d| <= 64 has at most 7 bits.
+__device__ __forceinline__ unsigned long long bf16_bits(int d) {
+    return (unsigned long long)(__float_as_uint((float)d) >> 16);
+}
+
+// Element offset of the 8-entry group (v, l .. l+7) of plane s in the tiled
+// bf16 order (l a multiple of 8).
+template <int S>
+__device__ __forceinline__ long long tiled_offset(int v, int l, int s, int th, int ksteps) {
+    const int r = v % th;
+    const long long block = ((long long)(v / th) * ksteps + l / 16) * S + s;
+    return block * th * 16 + r * 16 + ((((l >> 3) & 1) ^ ((r >> 2) & 1)) << 3);
+}
+
+// One CTA of 256 threads: the digits of the tile of TV vectors x TK entries
+// at (v0, l0), through shared memory (sh, sl) so that both input layouts
+// are read coalesced.  CONTIG: element (v, l) at x[v*ldx + l]; else at
+// x[l*ldx + v].  BF16: the tiled bf16 order with tile height th; else int8
+// planes with leading dimension ld_out.
+template <int S, bool CONTIG, bool BF16>
+__device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
+                                            const double *__restrict__ xh,
+                                            const double *__restrict__ xl, long long ldx,
+                                            void *__restrict__ out_v, long long ld_out, int th,
+                                            const int *__restrict__ exps, unsigned int *status,
+                                            double (&sh)[TV][TK + 1], double (&sl)[TV][TK + 1]) {
+    const int tid = threadIdx.x;
+    // coalesced tile load in the input's own layout
+#pragma unroll
+    for (int it = 0; it < TV * TK / 256; ++it) {
+        const int idx = it * 256 + tid;
+        int v, l;
+        if (CONTIG) {
+            v = idx / TK; l = idx % TK;
+        } else {
+            l = idx / TV; v = idx % TV;
+        }
+        const int gv = v0 + v, gl = l0 + l;
+        double a = 0.0, b = 0.0;
+        if (gv < nvec && gl < kdim) {
+            const long long o = CONTIG ? (long long)gv * ldx + gl : (long long)gl * ldx + gv;
+            a = xh[o];
+            b = xl[o];
+        }
+        sh[v][l] = a;
+        sl[v][l] = b;
+    }
+    __syncthreads();
+    // each thread: one vector, 8 consecutive k; one 8-byte word per digit plane
+    const int v = tid >> 3, lg = tid & 7;
+    const int gv = v0 + v;
+    if (gv >= nvec) return;
+    const int e = exps[(long long)(l0 / KB8) * nvec + gv];
+    constexpr int F = 6 + 7 * (S - 1);
+    // 8 entries per plane: one 8-byte word of int8, or two of bf16
+    constexpr int WORDS = BF16 ? 2 : 1;
+    unsigned long long word[S][WORDS];
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int w = 0; w < WORDS; ++w) word[s][w] = 0;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const double hi = sh[v][lg * 8 + j], lo = sl[v][lg * 8 + j];
+        bad |= !isfinite(hi) || !isfinite(lo);
+        __int128 X = rne_scaled(hi, F - e) + rne_scaled(lo, F - e);
+#pragma unroll
+        for (int s = S - 1; s >= 0; --s) {
+            int d;
+            if (s > 0) {
+                d = (int)((unsigned long long)(X + 64) & 127ull) - 64;
+                X = (X - d) >> 7;
+            } else {
+                d = (int)X;
+            }
+            if constexpr (BF16)
+                word[s][j >> 2] |= bf16_bits(d) << (16 * (j & 3));
+            else
+                word[s][0] |= (unsigned long long)(uint8_t)(int8_t)d << (8 * j);
+        }
+    }
+    if (bad && status) atomicOr(status, DEV_NONFINITE);
+    const int gl = l0 + lg * 8;
+    if constexpr (BF16) {
+        // the tiled order is read a whole k-step of 16 at a time: groups past
+        // kdim up to the next multiple of 16 are written with zero digits
+        if (gl >= (kdim + 15) / 16 * 16) return;
+        const int ksteps = (kdim + 15) / 16;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            uint4 q;
+            q.x = (unsigned)word[s][0];
+            q.y = (unsigned)(word[s][0] >> 32);
+            q.z = (unsigned)word[s][1];
+            q.w = (unsigned)(word[s][1] >> 32);
+            *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(out_v) +
+                                       tiled_offset<S>(gv, gl, s, th, ksteps)) = q;
+        }
+    } else {
+        if (gl >= kdim) return;
+        // entries past kdim in the last group of 8 carry zero digits; they
+        // sit in the row padding (ld_out >= kdim rounded up to 16) and are
+        // never read
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const long long o = ((long long)s * nvec + gv) * ld_out + gl;
+            *reinterpret_cast<unsigned long long *>(static_cast<int8_t *>(out_v) + o) = word[s][0];
+        }
+    }
+}
+
+
+}  // namespace split8
+}  // namespace ddg

@@ -222,8 +222,12 @@ class Batch:
     CUDA graph.  The tensors must stay alive and in place while the batch is
     used."""
 
-    def __init__(self, problems, device=None):
+    def __init__(self, problems, device=None, variant=_lib.DDGEMM_VARIANT_FP64, int8_slices=0):
+        """variant: DDGEMM_VARIANT_FP64 (the persistent FP64 kernel) or
+        DDGEMM_VARIANT_INT8_TC (the INT8 form on the tcgen05 tensor cores)."""
         self.count = len(problems)
+        self.variant = variant
+        self.int8_slices = int8_slices
         arr = (_lib.ddgemm_problem * max(self.count, 1))()
         self.shapes = []
         self._keep = []
@@ -244,7 +248,8 @@ class Batch:
         dev = device or (problems[0][0].device if problems else "cuda")
         raw = bytearray(ctypes.string_at(ctypes.addressof(arr), ctypes.sizeof(arr)))
         self.dev = torch.frombuffer(raw, dtype=torch.uint8).to(dev)
-        nbytes = _lib.ddgemm_batched_workspace_size(self.count, arr, None)
+        nbytes = _lib.ddgemm_batched_workspace_size(
+            self.count, arr, _lib.make_opts(variant=variant, int8_slices=int8_slices))
         self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
 
     def run(self, stream=None, config=None, status=None):
@@ -252,6 +257,7 @@ class Batch:
         ddgemm_batch_config, or a (tile, order) pair."""
         if config is not None and not isinstance(config, _lib.ddgemm_batch_config):
             config = _lib.ddgemm_batch_config(*config)
-        opts = _lib.make_opts(status_dev=status.data_ptr()) if status is not None else None
+        opts = _lib.make_opts(variant=self.variant, int8_slices=self.int8_slices,
+                              status_dev=status.data_ptr() if status is not None else 0)
         _lib.ddgemm_batched(self.count, self.host, self.dev.data_ptr(), self.workspace.data_ptr(),
                             self.workspace.numel(), current_stream_ptr(stream), opts, config)

@@ -162,3 +162,30 @@ def test_batched_host_checks():
     assert lib.ddgemm_batched(2, arr, FAKE, FAKE, need, None, None, ctypes.byref(cfg)) == \
         _lib.DDGEMM_EINVAL
     assert lib.ddgemm_batched(0, None, None, None, 0, None, None, None) == _lib.DDGEMM_OK
+
+
+def test_batched_tc_host_checks():
+    """The tcgen05 batched form: its workspace (digit tiles of whole
+    128 x 16 tiles), and the host checks before any CUDA call."""
+    lib = _lib.load()
+    arr = (_lib.ddgemm_problem * 2)()
+    arr[0] = _lib.ddgemm_problem(4, 5, 6, 6, 5, 5, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+    arr[1] = _lib.ddgemm_problem(0, 5, 6, 6, 5, 5, 0, 0, 0, 0, 0, 0)
+    o = _lib.make_opts(variant=_lib.DDGEMM_VARIANT_INT8_TC)
+    need = _lib.ddgemm_batched_workspace_size(2, arr, o)
+    # 16 planes of a 128 x 16 A tile and a 16 x 16 B tile, bf16
+    assert need >= 16 * (128 + 16) * 16 * 2
+    assert need != _lib.ddgemm_batched_workspace_size(2, arr)
+    bad_s = _lib.make_opts(variant=_lib.DDGEMM_VARIANT_INT8_TC, int8_slices=18)
+    assert _lib.ddgemm_batched_workspace_size(2, arr, bad_s) == 0
+    assert lib.ddgemm_batched(2, arr, FAKE, FAKE, need, None, ctypes.byref(bad_s), None) == \
+        _lib.DDGEMM_EINVAL
+    assert lib.ddgemm_batched(2, arr, FAKE, FAKE, 16, None, ctypes.byref(o), None) == \
+        _lib.DDGEMM_EWORKSPACE
+    bad = (_lib.ddgemm_problem * 1)()
+    bad[0] = _lib.ddgemm_problem(4, 5, 6, 6, 5, 4, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+    assert lib.ddgemm_batched(1, bad, FAKE, FAKE, 1 << 30, None, ctypes.byref(o), None) == \
+        _lib.DDGEMM_EINVAL
+    int8 = _lib.make_opts(variant=_lib.DDGEMM_VARIANT_INT8)
+    assert lib.ddgemm_batched(2, arr, FAKE, FAKE, need, None, ctypes.byref(int8), None) == \
+        _lib.DDGEMM_EUNSUPPORTED

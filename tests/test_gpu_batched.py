@@ -28,7 +28,7 @@ def mods():
     return _lib, ops, autotune
 
 
-def make_batch(ops, shapes, seed=0, kind="uniform"):
+def make_batch(ops, shapes, seed=0, kind="uniform", variant=0):
     probs, host = [], []
     for i, (m, n, k) in enumerate(shapes):
         a = gemm_inputs(m, n, k, kind=kind, seed=seed + i)
@@ -36,7 +36,7 @@ def make_batch(ops, shapes, seed=0, kind="uniform"):
         c = [torch.full((m, n), np.nan, dtype=torch.float64, device="cuda") for _ in range(2)]
         probs.append((*t, *c))
         host.append(a)
-    return ops.Batch(probs), probs, host
+    return ops.Batch(probs, variant=variant), probs, host
 
 
 def reference(ops, probs):
@@ -151,3 +151,70 @@ def test_autotuner_picks_and_caches(mods, tmp_path, monkeypatch):
     for (gh, gl), (wh, wl), (m, n, k) in zip(results(probs), want, MIXED):
         if m and n:
             assert np.array_equal(gh, wh) and np.array_equal(gl, wl)
+
+
+# ---- the batched tcgen05 INT8 form -------------------------------------
+
+TC = 4
+
+
+def reference_tc(ops, probs):
+    out = []
+    for a_hi, a_lo, b_hi, b_lo, _, _ in probs:
+        out.append(ops.ddgemm(a_hi, a_lo, b_hi, b_lo, variant=TC))
+    torch.cuda.synchronize()
+    return [(h.cpu().numpy(), l.cpu().numpy()) for h, l in out]
+
+
+@pytest.mark.parametrize("kind", ["uniform", "wide"])
+def test_batched_tc_bit_identical_to_ddgemm(mods, kind):
+    """Every problem of a batched tcgen05 pass equals ddgemm() with the
+    tcgen05 form on that problem alone, bit for bit; k = 0 gives C = 0 and
+    empty problems are skipped."""
+    _lib, ops, _ = mods
+    batch, probs, _ = make_batch(ops, MIXED, seed=60, kind=kind, variant=TC)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    batch.run(status=status)
+    got = results(probs)
+    want = reference_tc(ops, probs)
+    assert int(status.item()) == 0
+    for (gh, gl), (wh, wl), (m, n, k) in zip(got, want, MIXED):
+        if m and n:
+            assert np.array_equal(gh, wh) and np.array_equal(gl, wl), (m, n, k)
+        if m and n and not k:
+            assert not gh.any() and not gl.any()
+
+
+def test_batched_tc_512_uneven_graph_replay(mods):
+    """The 512-problem workload through the tcgen05 form, captured into a
+    CUDA graph and replayed: bit-identical to ddgemm per problem, and within
+    1e-28 (|A||B|) of the double-double oracle on sampled entries."""
+    _lib, ops, _ = mods
+    shapes = [tuple(int(v) for v in s) for s in batched_shapes(512, seed=0)]
+    batch, probs, host = make_batch(ops, shapes, seed=1000, variant=TC)
+    batch.run()
+    torch.cuda.synchronize()
+    for p in probs:
+        p[4].fill_(np.nan)
+        p[5].fill_(np.nan)
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=stream):
+        batch.run(stream=torch.cuda.current_stream())
+    g.replay()
+    got = results(probs)
+    want = reference_tc(ops, probs)
+    for (gh, gl), (wh, wl) in zip(got, want):
+        assert np.array_equal(gh, wh) and np.array_equal(gl, wl)
+    for i in (0, 511):
+        a = host[i]
+        rows = np.arange(0, shapes[i][0], max(1, shapes[i][0] // 6))
+        cols = np.arange(0, shapes[i][1], max(1, shapes[i][1] // 6))
+        rr, cc = np.meshgrid(rows, cols, indexing="ij")
+        oh, ol = dd.ddgemm_entries(*a, rr.ravel(), cc.ravel())
+        absab = np.array([np.abs(a[0][r]) @ np.abs(a[2][:, c])
+                          for r, c in zip(rr.ravel(), cc.ravel())])
+        gh, gl = got[i]
+        assert np.all(np.abs((gh[rr.ravel(), cc.ravel()] - oh) + (gl[rr.ravel(), cc.ravel()] - ol))
+                      <= 1e-28 * absab)

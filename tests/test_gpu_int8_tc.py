@@ -166,10 +166,14 @@ def test_tc_nonfinite_sets_status(ops):
     assert st[0] & 0x1 and not st[0] & 0x2
 
 
-def test_tc_full_size_sampled(ops):
-    """2048^3 (the accuracy sweep's size): sampled entries against the
-    double-double oracle."""
-    m = n = k = 2048
+@pytest.mark.parametrize("m", [2048, 4096, 8192])
+def test_tc_full_size_sampled(ops, m):
+    """The sweep's size and the benchmark workloads (4096^3, 8192^3, wide
+    entries), in the bench's launch configuration: sampled entries within
+    1e-28 (|A||B|) of the double-double oracle, a few within the INT8 bound
+    of exact rationals."""
+    from tests.test_oracle_int8 import int8_bound
+    n = k = m
     a = gemm_inputs(m, n, k, kind="wide", seed=0)
     c_hi, c_lo = tc(ops, *a)
     rng = np.random.default_rng(1)
@@ -178,6 +182,43 @@ def test_tc_full_size_sampled(ops):
     absab = np.array([np.abs(a[0][i]) @ np.abs(a[2][:, j]) for i, j in zip(rows, cols)])
     err = np.abs((c_hi[rows, cols] - o_hi) + (c_lo[rows, cols] - o_lo))
     assert np.all(err <= CONTRACT * absab)
+    for t in range(3):
+        i, j = rows[t], cols[t]
+        ex = exact.exact_dot(a[0][i], a[1][i], a[2][:, j], a[3][:, j])
+        bound = int8_bound(a[0][i:i + 1], a[2][:, j:j + 1], 16)[0, 0]
+        assert exact.err_vs_exact(c_hi[i, j], c_lo[i, j], ex) <= bound
+
+
+def test_tc_k_zero_empty_and_worked_example(ops):
+    a = torch.zeros((5, 0), dtype=torch.float64, device="cuda")
+    b = torch.zeros((0, 7), dtype=torch.float64, device="cuda")
+    out = (torch.full((5, 7), 3.0, dtype=torch.float64, device="cuda"),
+           torch.full((5, 7), 3.0, dtype=torch.float64, device="cuda"))
+    c_hi, c_lo = host(*ops.ddgemm(a, a, b, b, out=out, variant=TC))
+    assert not c_hi.any() and not c_lo.any()
+    e = torch.zeros((0, 4), dtype=torch.float64, device="cuda")
+    bb = torch.ones((4, 3), dtype=torch.float64, device="cuda")
+    c_hi, _ = ops.ddgemm(e, e, bb, bb * 0, variant=TC)
+    assert tuple(c_hi.shape) == (0, 3)
+    # Sec. "Forward Error Analysis": x = (1, eps), y = (0, 1) gives eps exactly
+    eps_hi, eps_lo = 1.5 * 2.0 ** -71, 2.0 ** -130
+    c_hi, c_lo = tc(ops, np.array([[1.0, eps_hi]]), np.array([[0.0, eps_lo]]),
+                    np.array([[0.0], [1.0]]), np.zeros((2, 1)))
+    assert c_hi[0, 0] == eps_hi and c_lo[0, 0] == 0.0
+
+
+def test_tc_noalloc_matches_tc_ddgemm(ops):
+    from paper_2303_04353_gb300 import _lib
+    m, n, k = 120, 90, 300
+    a = gemm_inputs(m, n, k, kind="wide", seed=53)
+    t = dev(*a)
+    c = [torch.empty((m, n), dtype=torch.float64, device="cuda") for _ in range(2)]
+    _lib.ddgemm_noalloc(m, n, k, t[0].data_ptr(), t[1].data_ptr(), k, t[2].data_ptr(),
+                        t[3].data_ptr(), n, c[0].data_ptr(), c[1].data_ptr(), n,
+                        torch.cuda.current_stream().cuda_stream, _lib.make_opts(variant=TC))
+    got = host(*c)
+    want = c8.cascade_int8_ddgemm(*a, s=16, assembly="exact")
+    assert same(got[0], want[0]) and same(got[1], want[1])
 
 
 @pytest.mark.parametrize("cl", ["2", "4"])

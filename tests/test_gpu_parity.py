@@ -346,7 +346,7 @@ def test_discussion_example_flags_and_exact(ops):
     assert Fraction(c_hi[0, 0]) + Fraction(c_lo[0, 0]) == closed
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 4])
 def test_unaligned_strided_views(ops, variant):
     """Operands that are column slices of wider arrays: leading dimensions
     above the row length and base addresses off the 16-byte grid, so the
