@@ -87,6 +87,15 @@ __device__ __forceinline__ __int128 rne_scaled(double x, int sh) {
 
 constexpr int TV = 32, TK = 64;  // tile: 32 vectors x 64 k
 
+// sum_{i < S-1} 64 128^i: adding it turns the balanced digits of X into
+// plain 7-bit fields offset by 64.
+template <int S>
+__host__ __device__ constexpr __int128 digit_offset() {
+    __int128 c = 0;
+    for (int i = 0; i < S - 1; ++i) c = c * 128 + 64;
+    return c;
+}
+
 // bf16 encoding of a small integer: the upper half of its FP32 encoding,
 // exact because the FP32 significand of |d| <= 64 has at most 7 bits.
 __device__ __forceinline__ unsigned long long bf16_bits(int d) {
@@ -154,15 +163,29 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
     for (int j = 0; j < 8; ++j) {
         const double hi = sh[v][lg * 8 + j], lo = sl[v][lg * 8 + j];
         bad |= !isfinite(hi) || !isfinite(lo);
-        __int128 X = rne_scaled(hi, F - e) + rne_scaled(lo, F - e);
+        // Balanced base-128 digits as bit fields: with Y = X + sum_{i<s-1}
+        // 64 128^i, digit i (least significant first) is bits 7i..7i+6 of
+        // Y minus 64, and the top digit is Y >> 7(s-1).  The same digits as
+        // peeling d = ((X + 64) mod 128) - 64, X = (X - d) / 128, one
+        // 128-bit subtract and shift at a time, in a few operations each.
+        const __int128 Y = rne_scaled(hi, F - e) + rne_scaled(lo, F - e) + digit_offset<S>();
+        const unsigned long long y_lo = (unsigned long long)Y;
+        const unsigned long long y_hi = (unsigned long long)(Y >> 64);
 #pragma unroll
         for (int s = S - 1; s >= 0; --s) {
+            const int i = S - 1 - s;  // digit position, least significant first
             int d;
             if (s > 0) {
-                d = (int)((unsigned long long)(X + 64) & 127ull) - 64;
-                X = (X - d) >> 7;
+                unsigned long long field;
+                if (7 * i + 7 <= 64)
+                    field = y_lo >> (7 * i);
+                else if (7 * i >= 64)
+                    field = y_hi >> (7 * i - 64);
+                else
+                    field = (y_lo >> (7 * i)) | (y_hi << (64 - 7 * i));
+                d = (int)(field & 127ull) - 64;
             } else {
-                d = (int)X;
+                d = (int)(Y >> (7 * (S - 1)));
             }
             if constexpr (BF16)
                 word[s][j >> 2] |= bf16_bits(d) << (16 * (j & 3));
