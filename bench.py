@@ -50,9 +50,9 @@ NOMINAL_BF16_TFLOPS = 2250.0
 # capture of the current kernels at 4096^3 (profiles/dram_traffic_4096.md, and
 # profiles/cascade_int8_tc_kernel_2048.md for the tcgen05 kernel);
 # other workloads report null.
-TRAFFIC_4096 = {"cascade_fp64_kernel": 9.884050e9 + 0.282231e9,
+TRAFFIC_4096 = {"cascade_fp64_kernel": 9.879882e9 + 0.281523e9,
                 "cascade_int8_kernel<16>": 3.528115e9 + 0.269681e9,
-                "cascade_int8_tc_kernel<16>": 9.281074e9 + 0.339288e9}
+                "cascade_int8_tc_kernel<16>": 9.123969e9 + 0.347044e9}
 
 WORKLOADS = {
     "4096": dict(m=4096, n=4096, k=4096, kind="wide",
