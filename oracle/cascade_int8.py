@@ -12,23 +12,25 @@ below (listed in the design doc) fill it in.
 
   * Scale: sigma = 2^e per (row of A, k-block) and per (k-block, column of
     B), e the frexp exponent of max |hi| in the block, as in the FP64 form.
-    The k-block is KB8 = 16384 entries: the longest block whose diagonal
-    sums stay inside int32 for up to 32 pieces (|digit| <= 64).
+    The k-block is KB8 = 8192 entries: the longest power of two whose
+    diagonal sums stay inside int32 for up to 15 pieces (|digit| <= 128:
+    15 * 8192 * 2^14 < 2^31).
   * Fixed point: X = rne(x_hi 2^(F-e)) + rne(x_lo 2^(F-e)), an integer,
-    with F = 6 + 7 (s - 1) fraction bits (rne = round to nearest, ties to
-    even).
-  * Pieces: the balanced base-2^7 digits of X, most significant first:
-    X = sum_i d_i 128^(s-1-i), d_i in [-64, 64], so x / sigma ~ sum_i d_i
-    2^(-6-7i).  Each piece fits INT8.
+    with F = 6 + 8 (s - 1) fraction bits (rne = round to nearest, ties to
+    even); |X| <= 2^F + 1 fits a signed 128-bit integer for s <= 15.
+  * Pieces: the balanced base-2^8 digits of X, most significant first:
+    X = sum_i d_i 256^(s-1-i), d_i in [-128, 127] (the first one in
+    [-65, 65]), so x / sigma ~ sum_i d_i 2^(-6-8i).  Each piece fits INT8:
+    the paper's "about 15 INT8 pieces" of eight bits each.
   * Products: for every diagonal t = i + j <= s - 1 the integer sum
     S_t = sum_{i+j=t} sum_l dA_i[l] dB_j[l] (exact in int32).
-  * Assembly: for t = s-1 down to 0 (smallest first), v = S_t 2^(-12-7t)
+  * Assembly: for t = s-1 down to 0 (smallest first), v = S_t 2^(-12-8t)
     (exact in FP64) is added into an FP64x2 sum (TwoSum, add lo,
     FastTwoSum); the block result is scaled by sigma tau and added into C
     with the FP64x2 add, as in the FP64 form.
   * Exact assembly (assembly="exact"; the tensor-core form of the library
     uses it): the diagonal sums are integers, so the block value
-    sum_t S_t 2^(-12-7t) sigma tau is formed exactly and rounded once to the
+    sum_t S_t 2^(-12-8t) sigma tau is formed exactly and rounded once to the
     nearest FP64x2 (hi = RN(x), lo = RN(x - hi)); the blocks are then added
     into C with the FP64x2 add as above.
 """
@@ -40,8 +42,9 @@ import numpy as np
 
 from . import cascade as _fp64
 
-KB8 = 16384
-DIGIT = 7
+KB8 = 8192
+DIGIT = 8
+SLICES = (12, 13, 14, 15)     # piece counts: F + 2 <= 127 bits
 
 
 def frac_bits(s: int) -> int:
@@ -67,12 +70,12 @@ def to_fixed(hi: float, lo: float, e: int, s: int) -> int:
 
 
 def digits(x: int, s: int) -> list[int]:
-    """Balanced base-128 digits of x, most significant first."""
+    """Balanced base-256 digits of x, most significant first."""
     out = [0] * s
     for i in range(s - 1, 0, -1):
-        d = ((x + 64) & 127) - 64
+        d = ((x + 128) & 255) - 128
         out[i] = d
-        x = (x - d) >> 7
+        x = (x - d) >> 8
     out[0] = x
     return out
 
@@ -106,7 +109,7 @@ def diagonal_sums(da: np.ndarray, db: np.ndarray, s: int) -> np.ndarray:
 
 
 def assemble(diag: np.ndarray, s: int):
-    """Add v_t = S_t 2^(-12-7t) for t = s-1 .. 0 into an FP64x2 sum."""
+    """Add v_t = S_t 2^(-12-8t) for t = s-1 .. 0 into an FP64x2 sum."""
     h = np.zeros(diag.shape[1:])
     l = np.zeros(diag.shape[1:])
     for t in range(s - 1, -1, -1):
@@ -126,7 +129,7 @@ def round_dd(num: int, exp2: int):
 
 
 def assemble_exact(diag: np.ndarray, s: int, scale: np.ndarray):
-    """The block value sum_t S_t 2^(-12-7t) 2^scale of every entry, formed
+    """The block value sum_t S_t 2^(-12-8t) 2^scale of every entry, formed
     exactly from the integer diagonal sums and rounded once to FP64x2."""
     m, n = diag.shape[1:]
     h = np.zeros((m, n))
@@ -140,7 +143,7 @@ def assemble_exact(diag: np.ndarray, s: int, scale: np.ndarray):
     return h, l
 
 
-def cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16, kb=KB8, return_parts=False,
+def cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=15, kb=KB8, return_parts=False,
                         assembly="fp64x2"):
     """C := A B through s INT8 pieces per entry.  Returns (C_hi, C_lo).
     assembly: "fp64x2" (diagonals added smallest first in FP64x2) or

@@ -1,7 +1,8 @@
 """Pins for the INT8 restatement (oracle/cascade_int8.py).
 
   * rne_scaled equals round-half-even of the exact rational x 2^sh;
-  * the digits reconstruct X exactly and lie in [-64, 64] (they fit INT8);
+  * the digits reconstruct X exactly and lie in [-128, 127], the first in
+    [-65, 65] (they fit INT8);
   * the fixed-point value is within 2^-F sigma of the FP64x2 entry;
   * diagonal sums equal brute-force integer dot products;
   * the whole INT8 cascade meets the error bound derived below against
@@ -12,7 +13,7 @@
 
 Bound (per entry, per k-block p with scales sigma_p, tau_p and length k_p):
   conversion  2 k_p sigma tau 2^-F               (|delta x| <= 2^-F sigma)
-  dropped     1.01 (s-1) k_p 2^-7s sigma tau     (diagonals i+j >= s, |digit| <= 64)
+  dropped     4.02 (s-1) k_p 2^-8s sigma tau     (diagonals i+j >= s, |digit| <= 128)
   assembly    4 s 2^-106 k_p sigma tau, and 4 K_B 2^-106 |A||B| across blocks."""
 import math
 import random
@@ -37,7 +38,7 @@ def int8_bound(a_hi, b_hi, s, kb=c8.KB8):
     for p in range(e_a.shape[1]):
         kp = min(kb, k - p * kb)
         st = np.exp2(e_a[:, p][:, None] + e_b[:, p][None, :])
-        tot += kp * st * (2.0 ** (1 - f) + 1.01 * (s - 1) * 2.0 ** (-7 * s) + 4 * s * 2.0 ** -106)
+        tot += kp * st * (2.0 ** (1 - f) + 4.02 * (s - 1) * 2.0 ** (-8 * s) + 4 * s * 2.0 ** -106)
     return tot + 4 * e_a.shape[1] * 2.0 ** -106 * (np.abs(a_hi) @ np.abs(b_hi))
 
 
@@ -50,25 +51,24 @@ def test_rne_scaled_is_round_half_even():
             assert c8.rne_scaled(x, sh) == round(Fraction(x) * Fraction(2) ** sh)
 
 
-@pytest.mark.parametrize("s", [8, 16, 18])
+@pytest.mark.parametrize("s", [8, 12, 15])
 def test_digits_reconstruct_and_fit_int8(s):
+    """Every X the conversion produces (|X| <= 2^F + 1) has digits that fit
+    INT8: balanced base-256, the first within [-65, 65]."""
     rnd = random.Random(s)
     f = c8.frac_bits(s)
-    for _ in range(500):
-        x = rnd.randint(-(2 ** f), 2 ** f) >> rnd.randint(0, f)
+    xs = [rnd.randint(-(2 ** f) - 1, 2 ** f + 1) >> rnd.randint(0, f) for _ in range(500)]
+    xs += [2 ** f + 1, -(2 ** f) - 1, 2 ** f, -(2 ** f), 0, 1, -1, 128, -128, 127, -129, 255]
+    for x in xs:
         ds = c8.digits(x, s)
-        assert all(-64 <= d <= 64 for d in ds)
-        assert sum(d * 128 ** (s - 1 - i) for i, d in enumerate(ds)) == x
-    for x in (2 ** f, -(2 ** f), 0, 1, -1, 64, -64, 63):
-        ds = c8.digits(x, s)
-        assert all(-64 <= d <= 64 for d in ds)
-        assert sum(d * 128 ** (s - 1 - i) for i, d in enumerate(ds)) == x
+        assert all(-128 <= d <= 127 for d in ds[1:]) and -65 <= ds[0] <= 65, (x, ds)
+        assert sum(d * 256 ** (s - 1 - i) for i, d in enumerate(ds)) == x
 
 
 def test_fixed_point_conversion_error():
     a_hi, a_lo, _, _ = gemm_inputs(6, 1, 300, kind="wide", seed=2)
     e = c8.block_exponents(a_hi)
-    s = 16
+    s = 15
     f = c8.frac_bits(s)
     for i in range(6):
         assert 2.0 ** (e[i, 0] - 1) <= np.abs(a_hi[i]).max() < 2.0 ** e[i, 0]
@@ -82,8 +82,8 @@ def test_fixed_point_conversion_error():
 def test_diagonal_sums_brute_force():
     rng = np.random.default_rng(3)
     s, m, n, k = 5, 3, 4, 7
-    da = rng.integers(-64, 65, (s, m, k))
-    db = rng.integers(-64, 65, (s, n, k))
+    da = rng.integers(-128, 128, (s, m, k))
+    db = rng.integers(-128, 128, (s, n, k))
     got = c8.diagonal_sums(da, db, s)
     for t in range(s):
         for i in range(m):
@@ -105,15 +105,16 @@ def max_ratio(fn, m, n, k, kind, seed, s):
     return worst
 
 
-@pytest.mark.parametrize("m,n,k,kind,s", [(5, 6, 200, "uniform", 16), (4, 5, 300, "wide", 16),
-                                          (3, 3, 64, "uniform", 12), (4, 4, 100, "wide", 18)])
+@pytest.mark.parametrize("m,n,k,kind,s", [(5, 6, 200, "uniform", 15), (4, 5, 300, "wide", 15),
+                                          (3, 3, 64, "uniform", 12), (4, 4, 100, "wide", 13),
+                                          (4, 4, 120, "wide", 14)])
 def test_int8_cascade_meets_bound(m, n, k, kind, s):
     assert max_ratio(c8.cascade_int8_ddgemm, m, n, k, kind, k, s) <= 1.0
 
 
 def test_int8_cascade_near_fp64x2_on_uniform():
     a_hi, a_lo, b_hi, b_lo = gemm_inputs(8, 8, 256, seed=4)
-    c_hi, c_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16)
+    c_hi, c_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=15)
     o_hi, o_lo = dd.ddgemm(a_hi, a_lo, b_hi, b_lo)
     assert np.all(np.abs((c_hi - o_hi) + (c_lo - o_lo)) <= 1e-28 * (np.abs(a_hi) @ np.abs(b_hi)))
     assert exact.dd_is_normalised(c_hi, c_lo)
@@ -129,7 +130,7 @@ def test_int8_integers_exact():
 def test_int8_worked_example():
     eps_hi, eps_lo = 1.5 * 2.0 ** -71, 2.0 ** -130
     c_hi, c_lo = c8.cascade_int8_ddgemm(np.array([[1.0, eps_hi]]), np.array([[0.0, eps_lo]]),
-                                        np.array([[0.0], [1.0]]), np.zeros((2, 1)), s=16)
+                                        np.array([[0.0], [1.0]]), np.zeros((2, 1)), s=15)
     assert c_hi[0, 0] == eps_hi and c_lo[0, 0] == 0.0
 
 
@@ -155,17 +156,18 @@ def hard_block_values():
     rnd = random.Random(9)
     out = []
     for _ in range(300):
-        bits = rnd.randint(1, 137)
+        bits = rnd.randint(1, 143)
         out.append((rnd.choice((-1, 1)) * rnd.getrandbits(bits), rnd.randint(-140, 10)))
     for top in (2 ** 52 + 1, 2 ** 53 - 1, 2 ** 52, 3):
-        for sh in (1, 2, 30, 53, 60, 83):
+        for sh in (1, 2, 30, 53, 60, 64, 83, 90):
             half = 1 << (sh - 1)
             for rem in (half, half - 1, half + 1, 0):
                 t = (top << sh) + rem
                 out += [(t, -117), (-t, -50)]
                 # a tie in the second rounding: lo = 2^54 + 1 then half an ulp
                 t2 = (top << (sh + 56)) + (((1 << 54) + 1) << 2) + 2
-                out.append((t2, -200))
+                t3 = (top << (sh + 64)) + (((1 << 54) + 1) << 9) + (1 << 8)
+                out += [(t2, -200), (t3, -230)]
     return out
 
 
@@ -181,21 +183,21 @@ def test_exact_assembly_brute_force():
     """Block value of random diagonal sums against the exact rational sum of
     S_t 2^(-12-7t) 2^scale, entry by entry."""
     rng = np.random.default_rng(11)
-    s = 16
-    diag = rng.integers(-(2 ** 30), 2 ** 30, (s, 3, 4))
+    s = 15
+    diag = rng.integers(-(2 ** 31) + 1, 2 ** 31, (s, 3, 4))
     diag[:, 0, 0] = 0
     diag[5:, 1, 1] = 0                       # short expansions
-    diag[0, 2, 3] = 2 ** 30                  # the largest sum a k-block allows
+    diag[0, 2, 3] = 15 * 2 ** 27             # the largest sum a k-block allows
     scale = rng.integers(-30, 30, (3, 4))
     h, l = c8.assemble_exact(diag, s, scale)
     for i in range(3):
         for j in range(4):
-            x = sum(Fraction(int(diag[t, i, j])) * Fraction(2) ** (-12 - 7 * t) for t in range(s))
+            x = sum(Fraction(int(diag[t, i, j])) * Fraction(2) ** (-12 - 8 * t) for t in range(s))
             x *= Fraction(2) ** int(scale[i, j])
             assert is_nearest(x, h[i, j]) and is_nearest(x - Fraction(h[i, j]), l[i, j])
 
 
-@pytest.mark.parametrize("m,n,k,kind,s", [(5, 6, 200, "uniform", 16), (4, 5, 300, "wide", 16),
+@pytest.mark.parametrize("m,n,k,kind,s", [(5, 6, 200, "uniform", 15), (4, 5, 300, "wide", 14),
                                           (3, 3, 64, "uniform", 12)])
 def test_exact_assembly_meets_bound(m, n, k, kind, s):
     def fn(*a, s):
@@ -210,7 +212,7 @@ def test_exact_assembly_integers_and_worked_example():
     assert np.array_equal(c_hi, ref.astype(np.float64)) and np.all(c_lo == 0)
     eps_hi, eps_lo = 1.5 * 2.0 ** -71, 2.0 ** -130
     c_hi, c_lo = c8.cascade_int8_ddgemm(np.array([[1.0, eps_hi]]), np.array([[0.0, eps_lo]]),
-                                        np.array([[0.0], [1.0]]), np.zeros((2, 1)), s=16,
+                                        np.array([[0.0], [1.0]]), np.zeros((2, 1)), s=15,
                                         assembly="exact")
     assert c_hi[0, 0] == eps_hi and c_lo[0, 0] == 0.0
 
@@ -219,10 +221,10 @@ def test_exact_and_fp64x2_assembly_agree_closely():
     """Same diagonal sums, two assemblies: they differ by the FP64x2
     roundings of the smallest-first sum only."""
     a = gemm_inputs(6, 7, 500, kind="wide", seed=12)
-    x_hi, x_lo = c8.cascade_int8_ddgemm(*a, s=16, assembly="exact")
-    y_hi, y_lo = c8.cascade_int8_ddgemm(*a, s=16)
+    x_hi, x_lo = c8.cascade_int8_ddgemm(*a, s=15, assembly="exact")
+    y_hi, y_lo = c8.cascade_int8_ddgemm(*a, s=15)
     diff = np.abs((x_hi - y_hi) + (x_lo - y_lo))
-    assert np.all(diff <= 4 * 16 * 2.0 ** -106 * (np.abs(a[0]) @ np.abs(a[2])))
+    assert np.all(diff <= 4 * 15 * 2.0 ** -106 * (np.abs(a[0]) @ np.abs(a[2])))
 
 
 # ---- planted mistakes ------------------------------------------------------
@@ -257,7 +259,7 @@ def test_planted_dropped_diagonal_is_caught(monkeypatch):
         out[2] = 0
         return out
     monkeypatch.setattr(c8, "diagonal_sums", drop_two)
-    assert max_ratio(c8.cascade_int8_ddgemm, 4, 4, 100, "uniform", 6, 16) > 1.0
+    assert max_ratio(c8.cascade_int8_ddgemm, 4, 4, 100, "uniform", 6, 15) > 1.0
 
 
 def test_planted_digit_weight_is_caught(monkeypatch):
@@ -268,7 +270,7 @@ def test_planted_digit_weight_is_caught(monkeypatch):
         return d[1:] + [0]      # every digit one place too high
     monkeypatch.setattr(c8, "digits", shifted)
     with pytest.raises(AssertionError):
-        test_digits_reconstruct_and_fit_int8(16)
+        test_digits_reconstruct_and_fit_int8(15)
 
 
 def test_planted_rounding_is_caught(monkeypatch):
