@@ -33,6 +33,11 @@ below (listed in the design doc) fill it in.
     sum_t S_t 2^(-12-8t) sigma tau is formed exactly and rounded once to the
     nearest FP64x2 (hi = RN(x), lo = RN(x - hi)); the blocks are then added
     into C with the FP64x2 add as above.
+  * Digit width (bits): the mma.sync form takes eight-bit pieces; the
+    tcgen05 form takes seven-bit pieces (balanced base 128, d in [-64, 64],
+    F = 6 + 7 (s - 1), k-blocks of 16384, s up to 16), whose products its FP32
+    accumulators sum exactly over 256 entries instead of 64.  Every formula
+    above holds with 8 replaced by bits.
 """
 from __future__ import annotations
 
@@ -42,13 +47,23 @@ import numpy as np
 
 from . import cascade as _fp64
 
-KB8 = 8192
-DIGIT = 8
-SLICES = (12, 13, 14, 15)     # piece counts: F + 2 <= 127 bits
+BITS = 8                      # digit width of the INT8 form (mma.sync)
+BITS_TC = 7                   # digit width of its tcgen05 form (see below)
 
 
-def frac_bits(s: int) -> int:
-    return 6 + DIGIT * (s - 1)
+def kblock(bits: int = BITS) -> int:
+    """Longest power-of-two k-block whose int32 diagonal sums stay exact:
+    8192 for eight-bit pieces (15 * 8192 * 2^14 < 2^31), 16384 for seven-bit
+    ones (up to 18 pieces: 18 * 16384 * 2^12 < 2^31)."""
+    return 8192 if bits == 8 else 16384
+
+
+KB8 = kblock(BITS)
+SLICES = {8: (12, 13, 14, 15), 7: (12, 13, 14, 15, 16)}   # F + 2 <= 127 bits
+
+
+def frac_bits(s: int, bits: int = BITS) -> int:
+    return 6 + bits * (s - 1)
 
 
 def rne_scaled(x: float, sh: int) -> int:
@@ -64,18 +79,19 @@ def rne_scaled(x: float, sh: int) -> int:
     return q
 
 
-def to_fixed(hi: float, lo: float, e: int, s: int) -> int:
-    f = frac_bits(s)
+def to_fixed(hi: float, lo: float, e: int, s: int, bits: int = BITS) -> int:
+    f = frac_bits(s, bits)
     return rne_scaled(hi, f - e) + rne_scaled(lo, f - e)
 
 
-def digits(x: int, s: int) -> list[int]:
-    """Balanced base-256 digits of x, most significant first."""
+def digits(x: int, s: int, bits: int = BITS) -> list[int]:
+    """Balanced base-2^bits digits of x, most significant first."""
+    base, half = 1 << bits, 1 << (bits - 1)
     out = [0] * s
     for i in range(s - 1, 0, -1):
-        d = ((x + 128) & 255) - 128
+        d = ((x + half) & (base - 1)) - half
         out[i] = d
-        x = (x - d) >> 8
+        x = (x - d) >> bits
     out[0] = x
     return out
 
@@ -86,13 +102,13 @@ def block_exponents(x_hi: np.ndarray, kb: int = KB8) -> np.ndarray:
     return _fp64.block_exponents_rows(x_hi, kb)
 
 
-def digit_planes(x_hi, x_lo, e, s, kb=KB8):
+def digit_planes(x_hi, x_lo, e, s, kb=KB8, bits=BITS):
     """Pieces of every row of x (vectors along rows): int64 [s][rows][k]."""
     rows, k = x_hi.shape
     out = np.zeros((s, rows, k), dtype=np.int64)
     for v in range(rows):
         for l in range(k):
-            ds = digits(to_fixed(x_hi[v, l], x_lo[v, l], int(e[v, l // kb]), s), s)
+            ds = digits(to_fixed(x_hi[v, l], x_lo[v, l], int(e[v, l // kb]), s, bits), s, bits)
             out[:, v, l] = ds
     return out
 
@@ -108,12 +124,12 @@ def diagonal_sums(da: np.ndarray, db: np.ndarray, s: int) -> np.ndarray:
     return out
 
 
-def assemble(diag: np.ndarray, s: int):
-    """Add v_t = S_t 2^(-12-8t) for t = s-1 .. 0 into an FP64x2 sum."""
+def assemble(diag: np.ndarray, s: int, bits: int = BITS):
+    """Add v_t = S_t 2^(-12-bits t) for t = s-1 .. 0 into an FP64x2 sum."""
     h = np.zeros(diag.shape[1:])
     l = np.zeros(diag.shape[1:])
     for t in range(s - 1, -1, -1):
-        v = np.ldexp(diag[t].astype(np.float64), -12 - DIGIT * t)
+        v = np.ldexp(diag[t].astype(np.float64), -12 - bits * t)
         h, l = _fp64.dd_add_d(h, l, v)
     return h, l
 
@@ -128,9 +144,10 @@ def round_dd(num: int, exp2: int):
     return hi, lo
 
 
-def assemble_exact(diag: np.ndarray, s: int, scale: np.ndarray):
-    """The block value sum_t S_t 2^(-12-8t) 2^scale of every entry, formed
-    exactly from the integer diagonal sums and rounded once to FP64x2."""
+def assemble_exact(diag: np.ndarray, s: int, scale: np.ndarray, bits: int = BITS):
+    """The block value sum_t S_t 2^(-12-bits t) 2^scale of every entry,
+    formed exactly from the integer diagonal sums and rounded once to
+    FP64x2."""
     m, n = diag.shape[1:]
     h = np.zeros((m, n))
     l = np.zeros((m, n))
@@ -138,18 +155,21 @@ def assemble_exact(diag: np.ndarray, s: int, scale: np.ndarray):
         for j in range(n):
             t_sum = 0
             for t in range(s):
-                t_sum += int(diag[t, i, j]) << (DIGIT * (s - 1 - t))
-            h[i, j], l[i, j] = round_dd(t_sum, int(scale[i, j]) - 12 - DIGIT * (s - 1))
+                t_sum += int(diag[t, i, j]) << (bits * (s - 1 - t))
+            h[i, j], l[i, j] = round_dd(t_sum, int(scale[i, j]) - 12 - bits * (s - 1))
     return h, l
 
 
-def cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=15, kb=KB8, return_parts=False,
-                        assembly="fp64x2"):
-    """C := A B through s INT8 pieces per entry.  Returns (C_hi, C_lo).
-    assembly: "fp64x2" (diagonals added smallest first in FP64x2) or
-    "exact" (the exact block value rounded once)."""
+def cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=15, kb=None, return_parts=False,
+                        assembly="fp64x2", bits=BITS):
+    """C := A B through s INT8 pieces of `bits` bits per entry.  Returns
+    (C_hi, C_lo).  kb: the k-block (default kblock(bits)).  assembly:
+    "fp64x2" (diagonals added smallest first in FP64x2) or "exact" (the
+    exact block value rounded once)."""
     if assembly not in ("fp64x2", "exact"):
         raise ValueError(assembly)
+    if kb is None:
+        kb = kblock(bits)
     a_hi = np.asarray(a_hi, np.float64)
     a_lo = np.asarray(a_lo, np.float64)
     bt_hi = np.ascontiguousarray(np.asarray(b_hi, np.float64).T)   # columns of B as rows
@@ -163,14 +183,14 @@ def cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=15, kb=KB8, return_parts=False
     parts = []
     for p in range((k + kb - 1) // kb):
         sl = slice(p * kb, (p + 1) * kb)
-        da = digit_planes(a_hi[:, sl], a_lo[:, sl], e_a[:, p:p + 1], s, kb=k + 1)
-        db = digit_planes(bt_hi[:, sl], bt_lo[:, sl], e_b[:, p:p + 1], s, kb=k + 1)
+        da = digit_planes(a_hi[:, sl], a_lo[:, sl], e_a[:, p:p + 1], s, kb=k + 1, bits=bits)
+        db = digit_planes(bt_hi[:, sl], bt_lo[:, sl], e_b[:, p:p + 1], s, kb=k + 1, bits=bits)
         diag = diagonal_sums(da, db, s)
         sc = e_a[:, p][:, None] + e_b[:, p][None, :]
         if assembly == "exact":
-            h, l = assemble_exact(diag, s, sc)
+            h, l = assemble_exact(diag, s, sc, bits)
         else:
-            h, l = assemble(diag, s)
+            h, l = assemble(diag, s, bits)
             h, l = np.ldexp(h, sc), np.ldexp(l, sc)
         c_hi, c_lo = _fp64.dd_add(c_hi, c_lo, h, l)
         if return_parts:
@@ -178,3 +198,9 @@ def cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=15, kb=KB8, return_parts=False
     if return_parts:
         return c_hi, c_lo, parts, (e_a, e_b)
     return c_hi, c_lo
+
+
+def cascade_int8_tc_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16):
+    """The tcgen05 form's product: seven-bit pieces (k-blocks of 16384) and
+    the exact assembly."""
+    return cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=s, assembly="exact", bits=BITS_TC)

@@ -28,17 +28,23 @@ from tests import exact
 from workloads import gemm_inputs, integer_inputs
 
 
-def int8_bound(a_hi, b_hi, s, kb=c8.KB8):
+def int8_bound(a_hi, b_hi, s, kb=None, bits=c8.BITS):
+    """Per-entry bound of the INT8 form with s pieces of `bits` bits: the
+    dropped-diagonal term is (s-1) k 2^(2 bits - 14) (1 + 2^(1-bits))
+    2^(-bits s) sigma tau (|digit| <= 2^(bits-1)): 4.02 (s-1) k 2^-8s for
+    eight bits, 1.01 (s-1) k 2^-7s for seven."""
+    kb = kb or c8.kblock(bits)
     m, k = a_hi.shape
     n = b_hi.shape[1]
     e_a = c8.block_exponents(a_hi, kb)
     e_b = c8.block_exponents(np.ascontiguousarray(b_hi.T), kb)
-    f = c8.frac_bits(s)
+    f = c8.frac_bits(s, bits)
+    dropped = (s - 1) * 2.0 ** (2 * bits - 14) * (1 + 2.0 ** (1 - bits)) * 2.0 ** (-bits * s)
     tot = np.zeros((m, n))
     for p in range(e_a.shape[1]):
         kp = min(kb, k - p * kb)
         st = np.exp2(e_a[:, p][:, None] + e_b[:, p][None, :])
-        tot += kp * st * (2.0 ** (1 - f) + 4.02 * (s - 1) * 2.0 ** (-8 * s) + 4 * s * 2.0 ** -106)
+        tot += kp * st * (2.0 ** (1 - f) + dropped + 4 * s * 2.0 ** -106)
     return tot + 4 * e_a.shape[1] * 2.0 ** -106 * (np.abs(a_hi) @ np.abs(b_hi))
 
 
@@ -51,18 +57,20 @@ def test_rne_scaled_is_round_half_even():
             assert c8.rne_scaled(x, sh) == round(Fraction(x) * Fraction(2) ** sh)
 
 
-@pytest.mark.parametrize("s", [8, 12, 15])
-def test_digits_reconstruct_and_fit_int8(s):
+@pytest.mark.parametrize("s,bits", [(8, 8), (12, 8), (15, 8), (12, 7), (16, 7)])
+def test_digits_reconstruct_and_fit_int8(s, bits):
     """Every X the conversion produces (|X| <= 2^F + 1) has digits that fit
-    INT8: balanced base-256, the first within [-65, 65]."""
+    INT8: balanced base 2^bits, the first within [-65, 65]."""
     rnd = random.Random(s)
-    f = c8.frac_bits(s)
+    f = c8.frac_bits(s, bits)
+    base, half = 1 << bits, 1 << (bits - 1)
     xs = [rnd.randint(-(2 ** f) - 1, 2 ** f + 1) >> rnd.randint(0, f) for _ in range(500)]
-    xs += [2 ** f + 1, -(2 ** f) - 1, 2 ** f, -(2 ** f), 0, 1, -1, 128, -128, 127, -129, 255]
+    xs += [2 ** f + 1, -(2 ** f) - 1, 2 ** f, -(2 ** f), 0, 1, -1, half, -half, half - 1,
+           -half - 1, base - 1]
     for x in xs:
-        ds = c8.digits(x, s)
-        assert all(-128 <= d <= 127 for d in ds[1:]) and -65 <= ds[0] <= 65, (x, ds)
-        assert sum(d * 256 ** (s - 1 - i) for i, d in enumerate(ds)) == x
+        ds = c8.digits(x, s, bits)
+        assert all(-half <= d < half for d in ds[1:]) and -65 <= ds[0] <= 65, (x, ds)
+        assert sum(d * base ** (s - 1 - i) for i, d in enumerate(ds)) == x
 
 
 def test_fixed_point_conversion_error():
@@ -93,10 +101,10 @@ def test_diagonal_sums_brute_force():
                 assert got[t, i, j] == want
 
 
-def max_ratio(fn, m, n, k, kind, seed, s):
+def max_ratio(fn, m, n, k, kind, seed, s, bits=c8.BITS):
     a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind=kind, seed=seed)
     c_hi, c_lo = fn(a_hi, a_lo, b_hi, b_lo, s=s)
-    bound = int8_bound(a_hi, b_hi, s)
+    bound = int8_bound(a_hi, b_hi, s, bits=bits)
     worst = 0.0
     for i in range(m):
         for j in range(n):
@@ -105,11 +113,17 @@ def max_ratio(fn, m, n, k, kind, seed, s):
     return worst
 
 
-@pytest.mark.parametrize("m,n,k,kind,s", [(5, 6, 200, "uniform", 15), (4, 5, 300, "wide", 15),
-                                          (3, 3, 64, "uniform", 12), (4, 4, 100, "wide", 13),
-                                          (4, 4, 120, "wide", 14)])
-def test_int8_cascade_meets_bound(m, n, k, kind, s):
-    assert max_ratio(c8.cascade_int8_ddgemm, m, n, k, kind, k, s) <= 1.0
+@pytest.mark.parametrize("m,n,k,kind,s,bits", [(5, 6, 200, "uniform", 15, 8),
+                                               (4, 5, 300, "wide", 15, 8),
+                                               (3, 3, 64, "uniform", 12, 8),
+                                               (4, 4, 100, "wide", 13, 8),
+                                               (4, 4, 120, "wide", 14, 8),
+                                               (4, 5, 300, "wide", 16, 7),
+                                               (3, 4, 90, "uniform", 14, 7)])
+def test_int8_cascade_meets_bound(m, n, k, kind, s, bits):
+    def fn(*a, s):
+        return c8.cascade_int8_ddgemm(*a, s=s, bits=bits)
+    assert max_ratio(fn, m, n, k, kind, k, s, bits) <= 1.0
 
 
 def test_int8_cascade_near_fp64x2_on_uniform():
@@ -179,30 +193,33 @@ def test_round_dd_is_the_nearest_fp64x2():
         assert is_nearest(x - Fraction(hi), lo), (t, e)
 
 
-def test_exact_assembly_brute_force():
+@pytest.mark.parametrize("s,bits", [(15, 8), (16, 7)])
+def test_exact_assembly_brute_force(s, bits):
     """Block value of random diagonal sums against the exact rational sum of
-    S_t 2^(-12-7t) 2^scale, entry by entry."""
+    S_t 2^(-12-bits t) 2^scale, entry by entry."""
     rng = np.random.default_rng(11)
-    s = 15
     diag = rng.integers(-(2 ** 31) + 1, 2 ** 31, (s, 3, 4))
     diag[:, 0, 0] = 0
     diag[5:, 1, 1] = 0                       # short expansions
     diag[0, 2, 3] = 15 * 2 ** 27             # the largest sum a k-block allows
     scale = rng.integers(-30, 30, (3, 4))
-    h, l = c8.assemble_exact(diag, s, scale)
+    h, l = c8.assemble_exact(diag, s, scale, bits)
     for i in range(3):
         for j in range(4):
-            x = sum(Fraction(int(diag[t, i, j])) * Fraction(2) ** (-12 - 8 * t) for t in range(s))
+            x = sum(Fraction(int(diag[t, i, j])) * Fraction(2) ** (-12 - bits * t)
+                    for t in range(s))
             x *= Fraction(2) ** int(scale[i, j])
             assert is_nearest(x, h[i, j]) and is_nearest(x - Fraction(h[i, j]), l[i, j])
 
 
-@pytest.mark.parametrize("m,n,k,kind,s", [(5, 6, 200, "uniform", 15), (4, 5, 300, "wide", 14),
-                                          (3, 3, 64, "uniform", 12)])
-def test_exact_assembly_meets_bound(m, n, k, kind, s):
+@pytest.mark.parametrize("m,n,k,kind,s,bits", [(5, 6, 200, "uniform", 15, 8),
+                                               (4, 5, 300, "wide", 14, 8),
+                                               (3, 3, 64, "uniform", 12, 8),
+                                               (4, 5, 300, "wide", 16, 7)])
+def test_exact_assembly_meets_bound(m, n, k, kind, s, bits):
     def fn(*a, s):
-        return c8.cascade_int8_ddgemm(*a, s=s, assembly="exact")
-    assert max_ratio(fn, m, n, k, kind, k + 1, s) <= 1.0
+        return c8.cascade_int8_ddgemm(*a, s=s, assembly="exact", bits=bits)
+    assert max_ratio(fn, m, n, k, kind, k + 1, s, bits) <= 1.0
 
 
 def test_exact_assembly_integers_and_worked_example():
@@ -248,7 +265,7 @@ def test_planted_exact_assembly_weight_is_caught(monkeypatch):
     real = c8.round_dd
     monkeypatch.setattr(c8, "round_dd", lambda num, e: real(num, e + 1))
     with pytest.raises(AssertionError):
-        test_exact_assembly_brute_force()
+        test_exact_assembly_brute_force(15, 8)
 
 
 def test_planted_dropped_diagonal_is_caught(monkeypatch):
@@ -265,12 +282,12 @@ def test_planted_dropped_diagonal_is_caught(monkeypatch):
 def test_planted_digit_weight_is_caught(monkeypatch):
     real = c8.digits
 
-    def shifted(x, s):
-        d = real(x, s)
+    def shifted(x, s, bits=8):
+        d = real(x, s, bits)
         return d[1:] + [0]      # every digit one place too high
     monkeypatch.setattr(c8, "digits", shifted)
     with pytest.raises(AssertionError):
-        test_digits_reconstruct_and_fit_int8(15)
+        test_digits_reconstruct_and_fit_int8(15, 8)
 
 
 def test_planted_rounding_is_caught(monkeypatch):
