@@ -265,6 +265,8 @@ def run_ours(args, wl):
     c_lo = torch.empty((m, n), dtype=torch.float64, device=dev)
     variant = {"int8": _lib.DDGEMM_VARIANT_INT8, "int8tc": _lib.DDGEMM_VARIANT_INT8_TC}.get(
         args.variant, _lib.DDGEMM_VARIANT_FP64)
+    if not args.int8_slices:   # each form's default: 15 eight-bit / 16 seven-bit pieces
+        args.int8_slices = 16 if variant == _lib.DDGEMM_VARIANT_INT8_TC else 15
     ws = ops.alloc_workspace(m, n, k, dev, variant, args.int8_slices)
     groups = ops.split_groups(m, n, k, dev, ws.numel(), variant)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -363,13 +365,14 @@ def run_ours(args, wl):
 
     # ---- the INT8 forms on the same inputs (one line, all forms) ----------
     def time_form(form_variant):
-        ws8 = ops.alloc_workspace(m, n, k, dev, form_variant, 16)
+        s8 = 16 if form_variant == _lib.DDGEMM_VARIANT_INT8_TC else 15
+        ws8 = ops.alloc_workspace(m, n, k, dev, form_variant, s8)
         c8 = (torch.empty((m, n), dtype=torch.float64, device=dev),
               torch.empty((m, n), dtype=torch.float64, device=dev))
 
         def step8():
             ops.ddgemm(*d_in, out=c8, workspace=ws8, stream=stream, variant=form_variant,
-                       int8_slices=16)
+                       int8_slices=s8)
         for _ in range(args.warmup):
             step8()
         torch.cuda.synchronize()
@@ -384,7 +387,8 @@ def run_ours(args, wl):
         h8, l8 = c8[0].cpu().numpy(), c8[1].cpu().numpy()
         err8 = np.abs((h8[rows, cols] - oh) + (l8[rows, cols] - ol))
         del ws8
-        return {"pieces": 16, "products": 136, "ms_per_step": round(ms8, 3),
+        return {"pieces": s8, "piece_bits": 7 if form_variant == _lib.DDGEMM_VARIANT_INT8_TC else 8,
+                "products": s8 * (s8 + 1) // 2, "ms_per_step": round(ms8, 3),
                 "value": round(replica_rate(flops_dd, world, ms8) / 1e9, 4),
                 "unit": "GFLOP/s",
                 "max_err_vs_dd_oracle": float(np.max(err8 / absab)),
@@ -620,7 +624,7 @@ def run_batched(args):
                                 "gflops": round(flops / (tc_ms * 1e-3) / 1e9, 3),
                                 "launches": 5, "max_err_vs_dd_oracle": tc_worst,
                                 "what": "the same problems, batched tcgen05 INT8 form "
-                                        "(16 pieces), one CUDA-graph replay"},
+                                        "(16 seven-bit pieces), one CUDA-graph replay"},
             "roofline": {"bound": "tensor", "kernel": "whole batched pass (4 launches)",
                          "achieved": round(achieved, 4), "peak": round(peak, 4),
                          "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
@@ -707,7 +711,7 @@ def run_illcond(args):
             d_in = [torch.from_numpy(x).to(dev) for x in a]
             res = {}
             for name, variant in (("cascade fp64", _lib.DDGEMM_VARIANT_FP64),
-                                  ("cascade int8 s=16", _lib.DDGEMM_VARIANT_INT8),
+                                  ("cascade int8 s=15", _lib.DDGEMM_VARIANT_INT8),
                                   ("cascade int8 tcgen05 s=16", _lib.DDGEMM_VARIANT_INT8_TC)):
                 c = ops.ddgemm(*d_in, variant=variant)
                 torch.cuda.synchronize()
@@ -777,8 +781,8 @@ def run_sweep(args):
     rng = np.random.default_rng(3)
     rows, cols = rng.integers(0, m, 128), rng.integers(0, n, 128)
     forms = [("fp64", _lib.DDGEMM_VARIANT_FP64, 0)] + [
-        (f"int8 s={s8}", _lib.DDGEMM_VARIANT_INT8, s8) for s8 in (14, 16, 18)] + [
-        (f"int8 tcgen05 s={s8}", _lib.DDGEMM_VARIANT_INT8_TC, s8) for s8 in (14, 16)]
+        (f"int8 s={s8}", _lib.DDGEMM_VARIANT_INT8, s8) for s8 in (13, 14, 15)] + [
+        (f"int8 tcgen05 s={s8}", _lib.DDGEMM_VARIANT_INT8_TC, s8) for s8 in (14, 15, 16)]
     for spread in range(0, 61, 10):
         a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind="wide", seed=0, spread=float(spread))
         d_in = [torch.from_numpy(x).to(dev) for x in (a_hi, a_lo, b_hi, b_lo)]
@@ -821,7 +825,9 @@ def main():
     ap.add_argument("--variant", choices=("fp64", "int8", "int8tc"), default="fp64",
                     help="fp64: the ten FP64 products (default); int8: the INT8 form on "
                          "mma.sync s8; int8tc: the INT8 form on the tcgen05 tensor cores")
-    ap.add_argument("--int8-slices", type=int, default=16)
+    ap.add_argument("--int8-slices", type=int, default=0,
+                    help="pieces of the INT8 forms; 0: 15 eight-bit (mma.sync) or 16 "
+                         "seven-bit (tcgen05)")
     ap.add_argument("--sweep", action="store_true",
                     help="exponent-spread study of both forms instead of the benchmark line")
     ap.add_argument("--sweep-size", type=int, default=2048)

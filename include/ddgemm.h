@@ -77,27 +77,29 @@ typedef struct ddgemm_opts {
     /* DDGEMM_VARIANT_FP64 (default) or DDGEMM_VARIANT_INT8.
      *
      * INT8 (Sec. "FP64x2 in terms of INT8", Sec. "Safely dropping lower
-     * order bins"): per (row of A, k-block of 16384) and (k-block, column of
+     * order bins"): per (row of A, k-block of 8192) and (k-block, column of
      * B), sigma = 2^e as in the FP64 form; each entry becomes the fixed-point
-     * integer X = rne(hi 2^(F-e)) + rne(lo 2^(F-e)), F = 6 + 7 (s - 1),
-     * written as s balanced base-128 digits in [-64, 64] (INT8 pieces).  The
-     * products of digit planes i, j with i + j <= s - 1 are accumulated
-     * exactly in int32 per diagonal t = i + j on the integer tensor path,
-     * and the diagonals are added smallest first in FP64x2.  Error per entry
-     * and k-block: at most about (s + 3) 2^-7s k sigma tau (conversion and
-     * dropped diagonals) plus FP64x2 rounding.  flags_dev is not supported
-     * with it (DDGEMM_EUNSUPPORTED).
+     * integer X = rne(hi 2^(F-e)) + rne(lo 2^(F-e)), F = 6 + 8 (s - 1),
+     * written as s balanced base-256 digits in [-128, 127] (eight-bit INT8
+     * pieces, the first within +-65).  The products of digit planes i, j
+     * with i + j <= s - 1 are accumulated exactly in int32 per diagonal
+     * t = i + j on the integer tensor path, and the diagonals are added
+     * smallest first in FP64x2.  Error per entry and k-block: at most about
+     * (4 s + 2) 2^-8s k sigma tau (conversion and dropped diagonals) plus
+     * FP64x2 rounding.  flags_dev is not supported with it
+     * (DDGEMM_EUNSUPPORTED).
      *
-     * INT8_TC: the same digits and the same exact diagonal sums S_t, with
-     * the digit products on the tcgen05 tensor cores: a digit (|d| <= 64)
-     * is exact in bf16, a product is at most 2^12, and over 256 entries a
-     * diagonal's FP32 accumulator holds integers of at most 2^24, so it is
-     * exact; it is read out every 256 entries into an exact integer sum.
-     * Per k-block the value sum_t S_t 2^(-12-7t) sigma tau is formed
-     * exactly and rounded once to the nearest FP64x2 (hi = RN(x), lo =
-     * RN(x - hi)) before the FP64x2 add into C: a more accurate reading of
-     * "add the results across bins in FP64x2" than the smallest-first sum.
-     * s in {12, 14, 15, 16}.  flags_dev is not supported. */
+     * INT8_TC: the same cascade with seven-bit pieces (balanced base-128
+     * digits in [-64, 64], F = 6 + 7 (s - 1), k-blocks of 16384) and the
+     * digit products on the tcgen05 tensor cores: a digit is exact in
+     * bf16, a product is at most 2^12, and over 256 entries a diagonal's
+     * FP32 accumulator holds integers of at most 2^24, so it is exact; it
+     * is read out every 256 entries into an exact integer sum (eight-bit
+     * pieces would allow 64 entries only).  Per k-block the value
+     * sum_t S_t 2^(-12-7t) sigma tau is formed exactly and rounded once to
+     * the nearest FP64x2 (hi = RN(x), lo = RN(x - hi)) before the FP64x2
+     * add into C: a more accurate reading of "add the results across bins
+     * in FP64x2" than the smallest-first sum.  flags_dev is not supported. */
     int variant;
     /* Optional device word (or NULL): DDGEMM_DEV_* bits are OR-ed into it.
      * The library never clears it. */
@@ -114,9 +116,10 @@ typedef struct ddgemm_opts {
      * split and the ten products (phases two and three, one kernel) and
      * after it, so that a caller can time each phase on the device. */
     void **phase_events;
-    /* INT8 forms only: pieces per entry, s in {12, 14, 15, 16, 17, 18}
-     * (INT8_TC: {12, 14, 15, 16}); 0 = 16.  Products per k: s (s + 1) / 2
-     * INT8 GEMMs. */
+    /* INT8 forms only: pieces per entry, s (s + 1) / 2 digit products per k.
+     * INT8: s in {12, 13, 14, 15}, 0 = 15 (the paper estimates 14-15; 120
+     * products).  INT8_TC: s in {12, ..., 16}, 0 = 16 (seven-bit pieces;
+     * 136 products). */
     int int8_slices;
     /* FP64 forms: split-k over whole 256-entry k-blocks when a grid of 64 x 64
      * tiles would leave SMs idle.  Group g of a tile sums its run of k-blocks
@@ -234,7 +237,7 @@ size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem *probs_host
  *   workspace   >= ddgemm_batched_workspace_size() bytes, 256-byte aligned.
  *   opts        NULL or: trans flags 0, variant FP64 or INT8_TC, no
  *               flags_dev (else DDGEMM_EUNSUPPORTED); status_dev is
- *               honoured; int8_slices for INT8_TC (12, 14, 15, 16; 0 = 16).
+ *               honoured; int8_slices for INT8_TC (12-16; 0 = 16).
  *   config      NULL = {DDGEMM_TILE_64x64, DDGEMM_ORDER_LONGEST_K_FIRST}.
  *               Not used by INT8_TC.
  * INT8_TC (the INT8 form on the tcgen05 tensor cores, see
@@ -324,7 +327,8 @@ int ddgemm_split_b(int k, int n, const double *B_hi, const double *B_lo, int ldb
  *               d (most significant first) of entry l of vector v.
  *               ld_digits >= k and a multiple of 16; the bytes of the last
  *               8-byte group past k in a row are written with zero digits.
- *   exps        device int32, ceil(k/16384) x m (or x n): e of sigma = 2^e. */
+ *               Digits are in [-128, 127].
+ *   exps        device int32, ceil(k/8192) x m (or x n): e of sigma = 2^e. */
 int ddgemm_split_int8_a(int m, int k, const double *A_hi, const double *A_lo, int lda,
                         int trans_a, int slices, signed char *digits, int ld_digits,
                         int *exps, unsigned int *status_dev, void *stream);
@@ -336,10 +340,10 @@ int ddgemm_split_int8_b(int k, int n, const double *B_hi, const double *B_lo, in
  * i < count, (hi[i], lo[i]) = the FP64x2 nearest to
  *     x_i = sum_{t < slices} diag[t*count + i] 2^(-12-7t) 2^scale[i]
  * (hi = RN(x_i), lo = RN(x_i - hi), round to nearest, ties to even), x_i
- * formed exactly.  diag: device int32, |diag| < 2^30 (the range of a
- * k-block's diagonal sums); scale: device int32; hi, lo: device doubles.
- * Results in the subnormal range are rounded twice (outside the method's
- * range).  slices in {12, 14, 15, 16}. */
+ * formed exactly (the form's seven-bit pieces).  diag: device int32 (any
+ * value; a k-block's diagonal sums stay within 2^30); scale: device int32;
+ * hi, lo: device doubles.  Results in the subnormal range are rounded twice
+ * (outside the method's range).  slices in {12, ..., 16}. */
 int ddgemm_assemble_int8(int count, int slices, const int *diag, const int *scale, double *hi,
                          double *lo, void *stream);
 

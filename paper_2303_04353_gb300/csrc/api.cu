@@ -68,7 +68,7 @@ struct Parsed {
     unsigned int *status = nullptr;
     int *flags = nullptr;
     void **events = nullptr;
-    int slices = ddg::INT8_SLICES_DEFAULT;
+    int slices = 0;  // 0: the form's default
     int split_k = 0;
 };
 
@@ -85,7 +85,8 @@ struct Layout8 {
 
 Layout8 layout8_for(int m, int n, int k, int slices, int variant) {
     Layout8 L;
-    const long long kb = (k + ddg::KB8 - 1) / ddg::KB8;
+    const int blk = variant == DDGEMM_VARIANT_INT8_TC ? ddg::KB8_TC : ddg::KB8;
+    const long long kb = (k + blk - 1) / blk;
     L.ld = (long long)round_up((size_t)k, 64);
     L.off_a = 0;
     if (variant == DDGEMM_VARIANT_INT8_TC) {
@@ -116,6 +117,9 @@ bool parse(const ddgemm_opts *o, Parsed &p) {
         p.split_k = o->split_k;
     }
     if (p.split_k < 0) return false;
+    if (p.slices == 0)
+        p.slices = p.variant == DDGEMM_VARIANT_INT8_TC ? ddg::INT8_TC_SLICES_DEFAULT
+                                                       : ddg::INT8_SLICES_DEFAULT;
     if (p.variant == DDGEMM_VARIANT_INT8 && !ddg::int8_slices_supported(p.slices)) return false;
     if (p.variant == DDGEMM_VARIANT_INT8_TC && !ddg::int8_tc_slices_supported(p.slices))
         return false;

@@ -373,7 +373,7 @@ extern "C" size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem 
                                                 const ddgemm_opts *opts) {
     if (count <= 0 || !probs_host) return 0;
     if (opts && opts->variant == DDGEMM_VARIANT_INT8_TC) {
-        const int s = opts->int8_slices ? opts->int8_slices : ddg::INT8_SLICES_DEFAULT;
+        const int s = opts->int8_slices ? opts->int8_slices : ddg::INT8_TC_SLICES_DEFAULT;
         if (!ddg::int8_tc_slices_supported(s)) return 0;
         return ddg::batched_int8_tc_workspace_size(count, probs_host, s);
     }
@@ -399,7 +399,7 @@ extern "C" int ddgemm_batched(int count, const ddgemm_problem *probs_host,
             return DDGEMM_EUNSUPPORTED;
         status = opts->status_dev;
         if (opts->variant == DDGEMM_VARIANT_INT8_TC) {
-            const int s = opts->int8_slices ? opts->int8_slices : INT8_SLICES_DEFAULT;
+            const int s = opts->int8_slices ? opts->int8_slices : INT8_TC_SLICES_DEFAULT;
             if (!int8_tc_slices_supported(s)) return DDGEMM_EINVAL;
             return run_batched_int8_tc(count, probs_host, probs_dev, workspace, ws_bytes,
                                        static_cast<cudaStream_t>(stream), s, status);

@@ -69,7 +69,7 @@ __host__ __device__ inline TcPlanLayout tc_plan_layout(int count) {
 // Digit and exponent bytes of one problem (the single-problem layout).
 __host__ __device__ inline size_t tc_problem_bytes(int m, int n, int k, int slices) {
     if (m <= 0 || n <= 0 || k <= 0) return 0;
-    const size_t kpad = ru_tc((size_t)k, 16), kb8 = (size_t)(k + KB8 - 1) / KB8;
+    const size_t kpad = ru_tc((size_t)k, 16), kb8 = (size_t)(k + KB8_TC - 1) / KB8_TC;
     return ru_tc((size_t)slices * ru_tc((size_t)m, INT8_TC_BM) * kpad * 2, TC_ALIGN) +
            ru_tc((size_t)slices * ru_tc((size_t)n, INT8_TC_BN) * kpad * 2, TC_ALIGN) +
            ru_tc(kb8 * m * 4, TC_ALIGN) + ru_tc(kb8 * n * 4, TC_ALIGN);
@@ -108,7 +108,7 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
         const ddgemm_problem q = probs[i];
         TcEntry e;
         e.m = q.m; e.n = q.n; e.k = q.k;
-        e.kb8 = q.k > 0 ? (q.k + KB8 - 1) / KB8 : 0;
+        e.kb8 = q.k > 0 ? (q.k + KB8_TC - 1) / KB8_TC : 0;
         e.lda = q.lda; e.ldb = q.ldb; e.ldc = q.ldc;
         e.a_hi = q.A_hi; e.a_lo = q.A_lo; e.b_hi = q.B_hi; e.b_lo = q.B_lo;
         e.c_hi = q.C_hi; e.c_lo = q.C_lo;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256) tc_exps_a_kernel(const char *ws) {
         const TcEntry &e = V.ent[i];
         const long long local = u - V.ea_pre[i];
         split8::exps_contig_unit(lane, (int)(local / e.kb8), (int)(local % e.kb8), e.m, e.k,
-                                 e.a_hi, e.lda, e.e_a);
+                                 KB8_TC, e.a_hi, e.lda, e.e_a);
     }
 }
 
@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(256) tc_exps_b_kernel(const char *ws) {
         const TcEntry &e = V.ent[i];
         const long long local = u - V.eb_pre[i];
         const int vtiles = (e.n + 63) / 64;
-        split8::exps_strided_unit((int)(local % vtiles), (int)(local / vtiles), e.n, e.k, e.b_hi,
-                                  e.ldb, e.e_b, part);
+        split8::exps_strided_unit((int)(local % vtiles), (int)(local / vtiles), e.n, e.k, KB8_TC,
+                                  e.b_hi, e.ldb, e.e_b, part);
     }
 }
 
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) tc_digits_kernel(const char *ws) {
             const TcEntry &e = V.ent[i];
             const long long local = u - V.da_pre[i];
             const int ktiles = (e.k + split8::TK - 1) / split8::TK;
-            split8::digits_unit<S, true, true>((int)(local / ktiles) * split8::TV,
+            split8::digits_unit<S, true, true, INT8_TC_BITS>((int)(local / ktiles) * split8::TV,
                                                (int)(local % ktiles) * split8::TK, e.m, e.k,
                                                e.a_hi, e.a_lo, e.lda, e.a_tiles, 0, INT8_TC_BM,
                                                e.e_a, status, sh, sl);
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(256) tc_digits_kernel(const char *ws) {
             const TcEntry &e = V.ent[i];
             const long long local = ub - V.db_pre[i];
             const int ktiles = (e.k + split8::TK - 1) / split8::TK;
-            split8::digits_unit<S, false, true>((int)(local / ktiles) * split8::TV,
+            split8::digits_unit<S, false, true, INT8_TC_BITS>((int)(local / ktiles) * split8::TV,
                                                 (int)(local % ktiles) * split8::TK, e.n, e.k,
                                                 e.b_hi, e.b_lo, e.ldb, e.b_tiles, 0, INT8_TC_BN,
                                                 e.e_b, status, sh, sl);
@@ -346,7 +346,8 @@ int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
             tiles += (long long)((q.m + INT8_TC_BM - 1) / INT8_TC_BM) *
                      ((q.n + INT8_TC_BN - 1) / INT8_TC_BN);
             if (q.k > 0) {
-                const long long kb8 = (q.k + KB8 - 1) / KB8, kt = (q.k + split8::TK - 1) / split8::TK;
+                const long long kb8 = (q.k + KB8_TC - 1) / KB8_TC,
+                                kt = (q.k + split8::TK - 1) / split8::TK;
                 ea += (long long)q.m * kb8;
                 eb += (long long)((q.n + 63) / 64) * kb8;
                 d += (long long)((q.m + split8::TV - 1) / split8::TV) * kt +
@@ -367,6 +368,7 @@ int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
     cudaError_t e;
     switch (slices) {
         case 12: e = launch_batched_tc<12>(ws, tiles, ea, eb, d, sms, s); break;
+        case 13: e = launch_batched_tc<13>(ws, tiles, ea, eb, d, sms, s); break;
         case 14: e = launch_batched_tc<14>(ws, tiles, ea, eb, d, sms, s); break;
         case 15: e = launch_batched_tc<15>(ws, tiles, ea, eb, d, sms, s); break;
         case 16: e = launch_batched_tc<16>(ws, tiles, ea, eb, d, sms, s); break;

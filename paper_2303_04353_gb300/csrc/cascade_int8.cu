@@ -7,15 +7,15 @@
 // Tiling.  A CTA owns a 32 x 32 tile of C; 8 warps each own 16 x 8 (one
 // MMA tile).  Per k-step of 32, two TMA copies bring all s digit planes of
 // A ([s][32][32] int8) and of B ([s][32][32], k contiguous) into a
-// three-deep ring (two CTAs per SM for s <= 17).  Each warp loads its s A fragments (ldmatrix.x4) and s B
+// three-deep ring (two CTAs per SM).  Each warp loads its s A fragments (ldmatrix.x4) and s B
 // fragments (ldmatrix.x2) once and issues the s(s+1)/2 products from
 // registers.  The s accumulators of 4 registers each are what bound the
-// tile size per warp (s = 16: 64 accumulator + 96 operand registers).
+// tile size per warp (s = 15: 60 accumulator + 90 operand registers).
 //
-// Exactness.  |digit| <= 64, so a product is at most 2^12 and a diagonal
-// holds at most s of them per k: over a k-block of 16384 a diagonal sum is
-// below s 2^26 < 2^31.  The int32 -> FP64 conversion and the scaling by
-// 2^(-12-7t) are exact; only the FP64x2 additions round.
+// Exactness.  |digit| <= 128, so a product is at most 2^14 and a diagonal
+// holds at most s <= 15 of them per k: over a k-block of 8192 a diagonal sum
+// is below 15 2^27 < 2^31.  The int32 -> FP64 conversion and the scaling by
+// 2^(-12-8t) are exact; only the FP64x2 additions round.
 //
 // Waits are bounded as in the FP64 kernel (DDGEMM_DEV_TIMEOUT).
 #include <cuda_runtime.h>
@@ -143,10 +143,10 @@ cascade_int8_kernel(const __grid_constant__ CUtensorMap tm_a,
                     double h = 0.0, l = 0.0;
 #pragma unroll
                     for (int d = S - 1; d >= 0; --d) {
-                        // S_d 2^(-12-7d): exact; the power of two is a constant
+                        // S_d 2^(-12-8d): exact; the power of two is a constant
                         const double v = __dmul_rn(__int2double_rn(acc[d][q]),
                                                    __longlong_as_double(
-                                                       (long long)(1023 - 12 - 7 * d) << 52));
+                                                       (long long)(1023 - 12 - 8 * d) << 52));
                         dd_add_d(h, l, v);
                     }
                     const int sc = args.exp_a[(long long)p * args.m + row] +

@@ -4,14 +4,17 @@
 // integers, exact in bf16, and their products are summed exactly by an FP32
 // accumulator while every partial sum stays below 2^24.
 //
-// Exactness.  |digit| <= 64, a product is at most 2^12 and diagonal t holds
-// t + 1 <= 16 products per k, so over a chunk of 256 entries every partial
-// sum of a diagonal is an integer of magnitude <= 256 * 16 * 2^12 = 2^24:
-// exact in FP32.  After each chunk the FP32 sums are read out of tensor
-// memory, converted (exactly) to integers and added into each output's
-// exact k-block value; over a k-block of 16384 entries a diagonal's sum
-// stays below 2^30.  The diagonal sums are the INT8 form's S_t, bit for
-// bit.
+// Digits.  This form takes seven-bit pieces (balanced base 128, |digit| <=
+// 64; the mma.sync form takes eight-bit ones): a product is at most 2^12 and
+// diagonal t holds t + 1 <= 16 products per k, so over a chunk of 256
+// entries every partial sum of a diagonal is an integer of magnitude
+// <= 256 * 16 * 2^12 = 2^24: exact in FP32.  With eight-bit pieces the chunk
+// would be 64 entries, and four times as many read-outs starve the MMA
+// issue (measured: 13.75 ms for 15 eight-bit pieces against 12.05 ms for 16
+// seven-bit ones at 4096^3).  After each chunk the FP32 sums are read out of
+// tensor memory, converted (exactly) to integers and added into each
+// output's exact k-block value; over a k-block of 16384 entries a
+// diagonal's sum stays within 2^30.
 //
 // Assembly.  Per k-block the exact value sum_t S_t 2^(-12-7t) sigma tau is
 // formed in 128-bit integer arithmetic and rounded once to the nearest
@@ -43,8 +46,8 @@
 // the tile) and columns 8 ((w - 2) / 4) .. + 7 of every diagonal.  Per
 // output it keeps the block value exactly, as T = H 2^56 + L in two 128-bit
 // integers: each chunk's diagonal sums are folded in four at a time (four
-// consecutive diagonals make an exact int64 of at most 2^45), so a thread
-// holds 8 x 2 128-bit sums instead of 16 x 8 int32 totals.  The kernel is
+// consecutive diagonals make an exact int64 below 2^46), so a thread holds
+// 8 x 2 128-bit sums instead of 16 x 8 int32 totals.  The kernel is
 // persistent: one CTA per SM walks the tiles in groups of 4 row tiles.
 //
 // Waits.  Every wait gives up after ~2 s, sets DDGEMM_DEV_TIMEOUT and a flag
@@ -120,7 +123,7 @@ assemble_kernel(int count, const int *__restrict__ diag, const int *__restrict__
     __int128 H = 0, L = 0;
 #pragma unroll
     for (int t = 0; t < S; ++t) add_diagonal<S>(t, diag[(long long)t * count + i], H, L);
-    round_dd(H, L, scale[i] - 12 - 7 * (S - 1), hi[i], lo[i]);
+    round_dd(H, L, scale[i] - 12 - TB * (S - 1), hi[i], lo[i]);
 }
 
 }  // namespace
@@ -129,6 +132,7 @@ cudaError_t launch_cascade_int8_tc(const Int8TcArgs &a, cudaStream_t stream) {
     if (a.m <= 0 || a.n <= 0 || a.k <= 0) return cudaSuccess;
     switch (a.slices) {
         case 12: return launch_tc<12>(a, stream);
+        case 13: return launch_tc<13>(a, stream);
         case 14: return launch_tc<14>(a, stream);
         case 15: return launch_tc<15>(a, stream);
         case 16: return launch_tc<16>(a, stream);
@@ -145,7 +149,7 @@ cudaError_t launch_assemble_int8(int count, int slices, const int *diag, const i
     case S:                                                                                 \
         assemble_kernel<S><<<blocks, 256, 0, stream>>>(count, diag, scale, hi, lo);         \
         return cudaGetLastError();
-        DDG_ASM(12) DDG_ASM(14) DDG_ASM(15) DDG_ASM(16)
+        DDG_ASM(12) DDG_ASM(13) DDG_ASM(14) DDG_ASM(15) DDG_ASM(16)
 #undef DDG_ASM
         default:
             return cudaErrorInvalidValue;

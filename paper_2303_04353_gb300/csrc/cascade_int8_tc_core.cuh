@@ -16,8 +16,14 @@ namespace ddg {
 namespace {
 
 constexpr int BM = INT8_TC_BM, BN = INT8_TC_BN, BK = 16;
-constexpr int CHUNK_STEPS = 16;                       // 16 k-steps of 16: 256 entries
-constexpr int BLOCK_CHUNKS = KB8 / (BK * CHUNK_STEPS);  // chunks per k-block
+// Digit width of this form's pieces, and the chunk over which an FP32
+// accumulator stays exact: up to 16 products of |digit| <= 2^(TB-1) per
+// entry, so 2^24 / (16 2^(2 TB - 2)) entries (256 for seven bits).
+constexpr int TB = INT8_TC_BITS;
+constexpr int CHUNK_STEPS = (1 << 24) / (16 << (2 * TB - 2)) / 16;  // k-steps of 16 per chunk
+constexpr int BLOCK_CHUNKS = KB8_TC / (BK * CHUNK_STEPS);           // chunks per k-block
+constexpr int SPLIT = 8 * TB;   // T = H 2^SPLIT + L: L holds the eight smallest diagonals
+static_assert(CHUNK_STEPS >= 1 && SPLIT <= 64, "digit width");
 constexpr int EPI_WARPS = 8;
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
 constexpr uint32_t TMEM_COLS = 512;
@@ -93,14 +99,15 @@ __device__ __forceinline__ double round_int(__int128 r, int e) {
     return neg ? -v : v;
 }
 
-// The FP64x2 nearest to T 2^e with T = H 2^56 + L (|H|, |L| < 2^80):
-// hi = RN(T 2^e), lo = RN(T 2^e - hi).
+// The FP64x2 nearest to T 2^e with T = H 2^SPLIT + L (|H| < 2^80,
+// |L| < 2^90, SPLIT <= 64): hi = RN(T 2^e), lo = RN(T 2^e - hi).
 __device__ __forceinline__ void round_dd(__int128 H, __int128 L, int e, double &hi, double &lo) {
-    // carry L's bits above 2^56 into H: T = H1 2^56 + L0, 0 <= L0 < 2^56
-    // (floor division by 2^56)
-    const __int128 q56 = L / ((__int128)1 << 56);
-    const __int128 carry = (L < 0 && q56 * ((__int128)1 << 56) != L) ? q56 - 1 : q56;
-    const unsigned long long L0 = (unsigned long long)(L - carry * ((__int128)1 << 56));
+    // carry L's bits above 2^SPLIT into H: T = H1 2^SPLIT + L0,
+    // 0 <= L0 < 2^SPLIT (floor division)
+    const __int128 unit = (__int128)1 << SPLIT;
+    const __int128 qs = L / unit;
+    const __int128 carry = (L < 0 && qs * unit != L) ? qs - 1 : qs;
+    const unsigned long long L0 = (unsigned long long)(L - carry * unit);
     __int128 H1 = H + carry;
     const bool neg = H1 < 0;
     unsigned __int128 Hm;
@@ -108,9 +115,9 @@ __device__ __forceinline__ void round_dd(__int128 H, __int128 L, int e, double &
     if (!neg) {
         Hm = (unsigned __int128)H1;
         Lm = L0;
-    } else if (L0 != 0) {  // -T = (-H1 - 1) 2^56 + (2^56 - L0)
+    } else if (L0 != 0) {  // -T = (-H1 - 1) 2^SPLIT + (2^SPLIT - L0)
         Hm = (unsigned __int128)(-H1 - 1);
-        Lm = (1ull << 56) - L0;
+        Lm = (unsigned long long)(unit - (__int128)L0);
     } else {
         Hm = (unsigned __int128)(-H1);
         Lm = 0;
@@ -120,7 +127,7 @@ __device__ __forceinline__ void round_dd(__int128 H, __int128 L, int e, double &
         lo = 0.0;
         return;
     }
-    const int p = Hm ? 56 + bitlen128(Hm) : 64 - __clzll((long long)Lm);
+    const int p = Hm ? SPLIT + bitlen128(Hm) : 64 - __clzll((long long)Lm);
     if (p <= 53) {  // then Hm = 0 and |T| = Lm < 2^53
         const double v = scalbn((double)Lm, e);
         hi = neg ? -v : v;
@@ -130,12 +137,12 @@ __device__ __forceinline__ void round_dd(__int128 H, __int128 L, int e, double &
     // |T| = m 2^sh + r with m the 53-bit significand rounded to nearest even
     const int sh = p - 53;
     unsigned __int128 q, rem;
-    if (sh >= 56) {
-        const int s2 = sh - 56;
+    if (sh >= SPLIT) {
+        const int s2 = sh - SPLIT;
         q = Hm >> s2;
-        rem = ((Hm & (((unsigned __int128)1 << s2) - 1)) << 56) | Lm;
+        rem = ((Hm & (((unsigned __int128)1 << s2) - 1)) << SPLIT) | Lm;
     } else {
-        const unsigned __int128 x = (Hm << 56) | Lm;  // p < 109: fits
+        const unsigned __int128 x = (Hm << SPLIT) | Lm;  // p < 53 + SPLIT: fits
         q = x >> sh;
         rem = x & (((unsigned __int128)1 << sh) - 1);
     }
@@ -153,22 +160,23 @@ __device__ __forceinline__ void round_dd(__int128 H, __int128 L, int e, double &
     lo = round_int(neg ? -r : r, e);
 }
 
-// Diagonal t's term of T = sum_t S_t 2^(7 (s-1-t)) = H 2^56 + L: the eight
-// smallest diagonals go to L, the others to H (multiplications by powers of
-// two: shifts of negative values are not defined in C++17).
+// Diagonal t's term of T = sum_t S_t 2^(TB (s-1-t)) = H 2^SPLIT + L: the
+// eight smallest diagonals go to L, the others to H (multiplications by
+// powers of two: shifts of negative values are not defined in C++17).
 template <int S>
 __device__ __forceinline__ void add_diagonal(int t, int v, __int128 &H, __int128 &L) {
     if (t < S - 8)
-        H += (__int128)v * ((__int128)1 << (7 * (S - 9 - t)));
+        H += (__int128)v * ((__int128)1 << (TB * (S - 9 - t)));
     else
-        L += (__int128)v * ((__int128)1 << (7 * (S - 1 - t)));
+        L += (__int128)v * ((__int128)1 << (TB * (S - 1 - t)));
 }
 
 // Add diagonals T0 .. T1-1 of one chunk, read from tensor memory (8
 // columns each, at base + 16 t), into acc[j] with the weights of
-// T = H 2^56 + L: the diagonal T1-1 has weight 1 in its half, each
-// earlier one 2^7 more.  Four diagonals at a time are combined exactly in
-// an int64 (|sum| <= 2^24 per diagonal, so at most 2^45), then added in.
+// T = H 2^SPLIT + L: the diagonal T1-1 has weight 1 in its half, each
+// earlier one 2^TB more.  Four diagonals at a time are combined exactly in
+// an int64 (|sum| <= 2^24 per diagonal and chunk, so below 2^(25 + 3 TB)),
+// then added in.
 template <int S, int T0, int T1>
 __device__ __forceinline__ void fold_group(uint32_t base, __int128 (&acc)[8]) {
     static_assert(T1 - T0 <= 8 && T1 > T0, "a half holds 1 to 8 diagonals");
@@ -183,7 +191,7 @@ __device__ __forceinline__ void fold_group(uint32_t base, __int128 (&acc)[8]) {
             umma::ld_x8_x2(base + g0 * BN, base + (g0 + 1) * BN, r);
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                g[j] = (long long)__float2int_rn(__uint_as_float(r[j])) * 128 +
+                g[j] = (long long)__float2int_rn(__uint_as_float(r[j])) * (1 << TB) +
                        __float2int_rn(__uint_as_float(r[8 + j]));
         } else {
             uint32_t r1[8];
@@ -195,17 +203,18 @@ __device__ __forceinline__ void fold_group(uint32_t base, __int128 (&acc)[8]) {
             uint32_t r1[8];
             umma::ld_x8(base + (g0 + 2) * BN, r1);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) g[j] = g[j] * 128 + __float2int_rn(__uint_as_float(r1[j]));
+            for (int j = 0; j < 8; ++j)
+                g[j] = g[j] * (1 << TB) + __float2int_rn(__uint_as_float(r1[j]));
         } else if (len == 4) {
             umma::ld_x8_x2(base + (g0 + 2) * BN, base + (g0 + 3) * BN, r);
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                g[j] = (g[j] * 128 + __float2int_rn(__uint_as_float(r[j]))) * 128 +
+                g[j] = (g[j] * (1 << TB) + __float2int_rn(__uint_as_float(r[j]))) * (1 << TB) +
                        __float2int_rn(__uint_as_float(r[8 + j]));
         }
         // weight of the group's last diagonal within its half
         const int last = g0 + len - 1;
-        const int shift = 7 * (T1 - 1 - last);
+        const int shift = TB * (T1 - 1 - last);
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[j] += (__int128)g[j] * ((__int128)1 << shift);
     }
@@ -448,7 +457,7 @@ cascade_int8_tc_kernel(const Src src) {
                             const int col = col0 + x;
                             if (col < j.n) {
                                 const int e = ea + j.exp_b[(long long)p * j.n + col] - 12 -
-                                              7 * (S - 1);
+                                              TB * (S - 1);
                                 double h, l;
                                 round_dd(H[x], L[x], e, h, l);
                                 const long long o = (long long)row * j.ldc + col;

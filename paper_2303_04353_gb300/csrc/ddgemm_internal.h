@@ -61,32 +61,36 @@ size_t base_workspace_size(int m, int n, int k, const ddgemm_opts *opts);
 cudaError_t launch_cascade_fp64(const CascadeArgs &a, cudaStream_t stream);
 
 // ---- INT8 form ------------------------------------------------------------
-// k-block of the INT8 form: the longest block whose diagonal sums of up to 32
-// digit products (|digit| <= 64) stay below 2^31.
-constexpr int KB8 = 16384;
+// The INT8 pieces are balanced digits of INT8_BITS bits for the mma.sync
+// form (eight, as the paper's estimate of about 15 pieces implies) and of
+// INT8_TC_BITS bits for the tcgen05 form (seven: its FP32 accumulators then
+// stay exact over 256 entries instead of 64).
+constexpr int INT8_BITS = 8, INT8_TC_BITS = 7;
+// k-block: the longest power of two whose int32 diagonal sums stay exact
+// (8 bits: 15 * 8192 * 2^14 < 2^31; 7 bits: 16 * 16384 * 2^12 <= 2^30).
+__host__ __device__ constexpr int kblock_of_bits(int bits) { return bits == 8 ? 8192 : 16384; }
+constexpr int KB8 = kblock_of_bits(INT8_BITS);
+constexpr int KB8_TC = kblock_of_bits(INT8_TC_BITS);
 // Piece counts with a compiled kernel (the fixed-point value needs
-// 6 + 7 (s - 1) <= 125 bits, so s <= 18).
-#define DDG_INT8_SLICE_CASES DDG_CASE(12) DDG_CASE(14) DDG_CASE(15) DDG_CASE(16) DDG_CASE(17) \
-    DDG_CASE(18)
-constexpr int INT8_SLICES_DEFAULT = 16;
-inline bool int8_slices_supported(int s) {
-    return s == 12 || (s >= 14 && s <= 18);
-}
+// 6 + 8 (s - 1) + 2 <= 127 bits, so s <= 15).
+#define DDG_INT8_SLICE_CASES DDG_CASE(12) DDG_CASE(13) DDG_CASE(14) DDG_CASE(15)
+constexpr int INT8_SLICES_DEFAULT = 15;
+inline bool int8_slices_supported(int s) { return s >= 12 && s <= 15; }
 
 // The tcgen05 form puts the products of plane i with planes 0..s-1-i in one
 // MMA of N = 16 (s - i) <= 256 columns: s <= 16.
 constexpr int INT8_TC_MAX_SLICES = 16;
-inline bool int8_tc_slices_supported(int s) {
-    return s == 12 || (s >= 14 && s <= INT8_TC_MAX_SLICES);
-}
+constexpr int INT8_TC_SLICES_DEFAULT = 16;
+inline bool int8_tc_slices_supported(int s) { return s >= 12 && s <= INT8_TC_MAX_SLICES; }
 
-// tile_rows = 0: int8 digit planes out[(s * nvec + v) * ld_out + l], ld_out
-// a multiple of 16 and >= kdim.  tile_rows = TH (a multiple of 8): bf16
-// digits in the tcgen05 form's tiled, pre-swizzled order (split_int8.cu),
-// ceil(nvec / TH) * ceil(kdim / 16) * s blocks of TH x 16; entries past
-// kdim up to a multiple of 16 are zero, rows past nvec are not written.
-// exps[p * nvec + v] per k-block of KB8.  Element (v, l) of the input is at
-// x[v * ldx + l] when vec_contig, else x[l * ldx + v].
+// tile_rows = 0: int8 digit planes out[(s * nvec + v) * ld_out + l] of
+// INT8_BITS-bit digits, ld_out a multiple of 16 and >= kdim.  tile_rows = TH
+// (a multiple of 8): bf16 INT8_TC_BITS-bit digits in the tcgen05 form's
+// tiled, pre-swizzled order (split_int8.cu), ceil(nvec / TH) * ceil(kdim /
+// 16) * s blocks of TH x 16; entries past kdim up to a multiple of 16 are
+// zero, rows past nvec are not written.  exps[p * nvec + v] per k-block of
+// that width's k-block.  Element (v, l) of the input is at x[v * ldx + l]
+// when vec_contig, else x[l * ldx + v].
 cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi,
                               const double *x_lo, long long ldx, bool vec_contig, void *out,
                               int tile_rows, long long ld_out, int *exps, unsigned int *status,
@@ -110,15 +114,15 @@ cudaError_t launch_cascade_int8(const Int8Args &a, cudaStream_t stream);
 // tcgen05.mma with FP32 accumulation in tensor memory (exact over 256
 // entries), int32 diagonal sums, exact assembly rounded once to FP64x2.
 // Tile heights of the tcgen05 form's tiled digit order: rows of C per tile
-// (A) and columns (B).
+// (A) and columns (B).  Its k-blocks are KB8_TC long.
 constexpr int INT8_TC_BM = 128, INT8_TC_BN = 16;
 
 struct Int8TcArgs {
     int m, n, k, slices;
     const uint16_t *a_tiles;   // bf16, tiled order with TH = INT8_TC_BM
     const uint16_t *b_tiles;   // bf16, tiled order with TH = INT8_TC_BN
-    const int *exp_a;          // ceil(k/KB8) x m
-    const int *exp_b;          // ceil(k/KB8) x n
+    const int *exp_a;          // ceil(k/KB8_TC) x m
+    const int *exp_b;          // ceil(k/KB8_TC) x n
     double *c_hi, *c_lo;
     long long ldc;
     unsigned int *status;

@@ -4,14 +4,15 @@
 // Per (vector, k-block of 16384 entries): sigma = 2^e with e the frexp
 // exponent of max |hi| (as in the FP64 form).  Per entry, on the integer
 // ALU (the FP64 pipe of this GPU is narrow, the integer pipes are not):
-//   X = rne(hi 2^(F-e)) + rne(lo 2^(F-e))     (exact, 128-bit integers)
-//   balanced base-128 digits d_0..d_{s-1} of X, most significant first,
-//   d_i in [-64, 64], so that x / sigma ~ sum_i d_i 2^(-6-7i).
+//   X = rne(hi 2^(F-e)) + rne(lo 2^(F-e)), F = 6 + b (s-1)   (exact, 128 bits)
+//   balanced base-2^b digits d_0..d_{s-1} of X, most significant first,
+//   |d_i| <= 2^(b-1) (d_0 within +-65), so x / sigma ~ sum_i d_i 2^(-6-b i),
+//   with b = 8 for the int8 planes and b = 7 for the tcgen05 form's bf16.
 // Output, for A (vectors = rows) and B (vectors = columns; transposed
 // through shared memory) alike, either
 //   * int8 digit planes [s][vector][ld] with k contiguous (mma.sync
 //     m16n8k32 s8), or
-//   * bf16 digits (a digit of at most 7 significant bits is exact in bf16)
+//   * bf16 digits (a digit of at most 8 significant bits is exact in bf16)
 //     in the tcgen05 form's tiled order: for every tile of TH vectors
 //     (TH = 128 for A, 16 for B) and every k-step of 16 entries, the s
 //     planes' TH x 16 blocks follow one another, each block being the
@@ -34,20 +35,22 @@ using namespace split8;
 // vectors and block, 4 row groups).
 template <bool CONTIG>
 __global__ void __launch_bounds__(256)
-int8_exps_kernel(int nvec, int kdim, const double *__restrict__ x, long long ldx,
+int8_exps_kernel(int nvec, int kdim, int blk, const double *__restrict__ x, long long ldx,
                  int *__restrict__ exps) {
-    const int kb = (kdim + KB8 - 1) / KB8;
+    const int kb = (kdim + blk - 1) / blk;
     if constexpr (CONTIG) {
         const int lane = threadIdx.x & 31;
         const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         if (w >= (long long)nvec * kb) return;
-        exps_contig_unit(lane, (int)(w / kb), (int)(w % kb), nvec, kdim, x, ldx, exps);
+        exps_contig_unit(lane, (int)(w / kb), (int)(w % kb), nvec, kdim, blk, x, ldx, exps);
     } else {
         __shared__ double part[4][64];
-        exps_strided_unit(blockIdx.x, blockIdx.y, nvec, kdim, x, ldx, exps, part);
+        exps_strided_unit(blockIdx.x, blockIdx.y, nvec, kdim, blk, x, ldx, exps, part);
     }
 }
 
+// int8 planes carry INT8_BITS-bit digits, the tiled bf16 order
+// INT8_TC_BITS-bit ones.
 template <int S, bool CONTIG, bool BF16>
 __global__ void __launch_bounds__(256)
 int8_digits_kernel(int nvec, int kdim, const double *__restrict__ xh,
@@ -55,8 +58,9 @@ int8_digits_kernel(int nvec, int kdim, const double *__restrict__ xh,
                    long long ld_out, int th, const int *__restrict__ exps, unsigned int *status) {
     __shared__ double sh[TV][TK + 1];
     __shared__ double sl[TV][TK + 1];
-    digits_unit<S, CONTIG, BF16>(blockIdx.y * TV, blockIdx.x * TK, nvec, kdim, xh, xl, ldx, out_v,
-                                 ld_out, th, exps, status, sh, sl);
+    digits_unit<S, CONTIG, BF16, BF16 ? INT8_TC_BITS : INT8_BITS>(
+        blockIdx.y * TV, blockIdx.x * TK, nvec, kdim, xh, xl, ldx, out_v, ld_out, th, exps,
+        status, sh, sl);
 }
 
 template <int S, bool BF16>
@@ -75,19 +79,20 @@ cudaError_t launch_digits_t(int nvec, int kdim, const double *xh, const double *
     return cudaGetLastError();
 }
 
+// int8 planes: s in 12..15 (eight-bit digits); tiled bf16: s in 12..16
+// (seven-bit digits).
 template <int S>
 cudaError_t launch_digits(int nvec, int kdim, const double *xh, const double *xl, long long ldx,
                           bool contig, void *out, int tile_rows, long long ld_out,
                           const int *exps, unsigned int *status, cudaStream_t stream) {
-    if (tile_rows) {
-        if constexpr (S <= INT8_TC_MAX_SLICES)
-            return launch_digits_t<S, true>(nvec, kdim, xh, xl, ldx, contig, out, 0, tile_rows,
-                                            exps, status, stream);
-        else
-            return cudaErrorInvalidValue;
-    }
-    return launch_digits_t<S, false>(nvec, kdim, xh, xl, ldx, contig, out, ld_out, 0, exps,
-                                     status, stream);
+    if (tile_rows)
+        return launch_digits_t<S, true>(nvec, kdim, xh, xl, ldx, contig, out, 0, tile_rows, exps,
+                                        status, stream);
+    if constexpr (S <= 15)
+        return launch_digits_t<S, false>(nvec, kdim, xh, xl, ldx, contig, out, ld_out, 0, exps,
+                                         status, stream);
+    else
+        return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -99,27 +104,33 @@ cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi
     if (nvec <= 0 || kdim <= 0) return cudaSuccess;
     if (tile_rows == 0 && (ld_out % 16 != 0 || ld_out < kdim)) return cudaErrorInvalidValue;
     if (tile_rows != 0 && tile_rows % 8 != 0) return cudaErrorInvalidValue;
-    const int kb = (kdim + KB8 - 1) / KB8;
+    // block exponents per k-block of the digit width in use
+    const int blk = kblock_of_bits(tile_rows ? INT8_TC_BITS : INT8_BITS);
+    const int kb = (kdim + blk - 1) / blk;
     if (vec_contig) {
         const long long blocks = ((long long)nvec * kb + 7) / 8;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-        int8_exps_kernel<true><<<(unsigned)blocks, 256, 0, stream>>>(nvec, kdim, x_hi, ldx, exps);
+        int8_exps_kernel<true><<<(unsigned)blocks, 256, 0, stream>>>(nvec, kdim, blk, x_hi, ldx,
+                                                                     exps);
     } else {
         if (kb > 65535) return cudaErrorInvalidValue;
-        int8_exps_kernel<false><<<dim3((nvec + 63) / 64, kb), 256, 0, stream>>>(nvec, kdim, x_hi,
-                                                                               ldx, exps);
+        int8_exps_kernel<false><<<dim3((nvec + 63) / 64, kb), 256, 0, stream>>>(nvec, kdim, blk,
+                                                                               x_hi, ldx, exps);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     switch (slices) {
-#define DDG_CASE(S)                                                                            \
-    case S:                                                                                    \
-        return launch_digits<S>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,      \
-                                ld_out, exps, status, stream);
-        DDG_INT8_SLICE_CASES
-#undef DDG_CASE
-        default:
-            return cudaErrorInvalidValue;
+        case 12: return launch_digits<12>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,
+                                          ld_out, exps, status, stream);
+        case 13: return launch_digits<13>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,
+                                          ld_out, exps, status, stream);
+        case 14: return launch_digits<14>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,
+                                          ld_out, exps, status, stream);
+        case 15: return launch_digits<15>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,
+                                          ld_out, exps, status, stream);
+        case 16: return launch_digits<16>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,
+                                          ld_out, exps, status, stream);
+        default: return cudaErrorInvalidValue;
     }
 }
 

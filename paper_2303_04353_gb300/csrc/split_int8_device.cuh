@@ -18,31 +18,32 @@ __device__ __forceinline__ int block_exponent(double mx) {
     return e;
 }
 
-// One warp: the exponent of block p of vector v, whose entries are
-// contiguous (element l at row[l]).
+// One warp: the exponent of block p (of kb entries) of vector v, whose
+// entries are contiguous (element l at row[l]).
 __device__ __forceinline__ void exps_contig_unit(int lane, int v, int p, int nvec, int kdim,
-                                                 const double *__restrict__ x, long long ldx,
-                                                 int *__restrict__ exps) {
+                                                 int kb, const double *__restrict__ x,
+                                                 long long ldx, int *__restrict__ exps) {
     const double *row = x + (long long)v * ldx;
-    const int lend = min((p + 1) * KB8, kdim);
+    const int lend = min((p + 1) * kb, kdim);
     double mx = 0.0;
-    for (int l = p * KB8 + lane; l < lend; l += 32) mx = fmax(mx, fabs(row[l]));
+    for (int l = p * kb + lane; l < lend; l += 32) mx = fmax(mx, fabs(row[l]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     if (lane == 0) exps[(long long)p * nvec + v] = block_exponent(mx);
 }
 
-// One CTA of 256 threads: the exponents of block p of vectors
-// [64 vt, 64 vt + 64), whose entries are strided (element l at x[l*ldx + v]).
-__device__ __forceinline__ void exps_strided_unit(int vt, int p, int nvec, int kdim,
+// One CTA of 256 threads: the exponents of block p (of kb entries) of
+// vectors [64 vt, 64 vt + 64), whose entries are strided (element l at
+// x[l*ldx + v]).
+__device__ __forceinline__ void exps_strided_unit(int vt, int p, int nvec, int kdim, int kb,
                                                   const double *__restrict__ x, long long ldx,
                                                   int *__restrict__ exps, double (&part)[4][64]) {
     const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
     const int v = vt * 64 + tx;
-    const int lend = min((p + 1) * KB8, kdim);
+    const int lend = min((p + 1) * kb, kdim);
     double mx = 0.0;
     if (v < nvec)
-        for (int l = p * KB8 + ty; l < lend; l += 4) mx = fmax(mx, fabs(x[(long long)l * ldx + v]));
+        for (int l = p * kb + ty; l < lend; l += 4) mx = fmax(mx, fabs(x[(long long)l * ldx + v]));
     part[ty][tx] = mx;
     __syncthreads();
     if (ty == 0 && v < nvec) {
@@ -87,17 +88,18 @@ __device__ __forceinline__ __int128 rne_scaled(double x, int sh) {
 
 constexpr int TV = 32, TK = 64;  // tile: 32 vectors x 64 k
 
-// sum_{i < S-1} 64 128^i: adding it turns the balanced digits of X into
-// plain 7-bit fields offset by 64.
-template <int S>
+// sum_{i < S-1} 2^(BITS-1) 2^(BITS i): adding it turns the balanced digits
+// of X into plain BITS-bit fields offset by 2^(BITS-1).
+template <int S, int BITS>
 __host__ __device__ constexpr __int128 digit_offset() {
     __int128 c = 0;
-    for (int i = 0; i < S - 1; ++i) c = c * 128 + 64;
+    for (int i = 0; i < S - 1; ++i) c = c * (1 << BITS) + (1 << (BITS - 1));
     return c;
 }
 
 // bf16 encoding of a small integer: the upper half of its FP32 encoding,
-// exact because the FP32 significand of |d| <= 64 has at most 7 bits.
+// exact because the FP32 significand of |d| <= 128 has at most 8 bits (bf16
+// keeps 8).
 __device__ __forceinline__ unsigned long long bf16_bits(int d) {
     return (unsigned long long)(__float_as_uint((float)d) >> 16);
 }
@@ -111,12 +113,13 @@ __device__ __forceinline__ long long tiled_offset(int v, int l, int s, int th, i
     return block * th * 16 + r * 16 + ((((l >> 3) & 1) ^ ((r >> 2) & 1)) << 3);
 }
 
-// One CTA of 256 threads: the digits of the tile of TV vectors x TK entries
-// at (v0, l0), through shared memory (sh, sl) so that both input layouts
-// are read coalesced.  CONTIG: element (v, l) at x[v*ldx + l]; else at
-// x[l*ldx + v].  BF16: the tiled bf16 order with tile height th; else int8
-// planes with leading dimension ld_out.
-template <int S, bool CONTIG, bool BF16>
+// One CTA of 256 threads: the BITS-bit digits of the tile of TV vectors x
+// TK entries at (v0, l0), through shared memory (sh, sl) so that both input
+// layouts are read coalesced.  CONTIG: element (v, l) at x[v*ldx + l]; else
+// at x[l*ldx + v].  BF16: the tiled bf16 order with tile height th; else
+// int8 planes with leading dimension ld_out.  exps per k-block of
+// kblock_of_bits(BITS).
+template <int S, bool CONTIG, bool BF16, int BITS>
 __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
                                             const double *__restrict__ xh,
                                             const double *__restrict__ xl, long long ldx,
@@ -149,8 +152,8 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
     const int v = tid >> 3, lg = tid & 7;
     const int gv = v0 + v;
     if (gv >= nvec) return;
-    const int e = exps[(long long)(l0 / KB8) * nvec + gv];
-    constexpr int F = 6 + 7 * (S - 1);
+    const int e = exps[(long long)(l0 / kblock_of_bits(BITS)) * nvec + gv];
+    constexpr int F = 6 + BITS * (S - 1);
     // 8 entries per plane: one 8-byte word of int8, or two of bf16
     constexpr int WORDS = BF16 ? 2 : 1;
     unsigned long long word[S][WORDS];
@@ -163,12 +166,14 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
     for (int j = 0; j < 8; ++j) {
         const double hi = sh[v][lg * 8 + j], lo = sl[v][lg * 8 + j];
         bad |= !isfinite(hi) || !isfinite(lo);
-        // Balanced base-128 digits as bit fields: with Y = X + sum_{i<s-1}
-        // 64 128^i, digit i (least significant first) is bits 7i..7i+6 of
-        // Y minus 64, and the top digit is Y >> 7(s-1).  The same digits as
-        // peeling d = ((X + 64) mod 128) - 64, X = (X - d) / 128, one
-        // 128-bit subtract and shift at a time, in a few operations each.
-        const __int128 Y = rne_scaled(hi, F - e) + rne_scaled(lo, F - e) + digit_offset<S>();
+        // Balanced base-2^BITS digits as bit fields: with Y = X +
+        // sum_{i<s-1} 2^(BITS-1) 2^(BITS i), digit i (least significant
+        // first) is field i of Y minus 2^(BITS-1), and the top digit is
+        // Y >> BITS (s-1).  The same digits as peeling d = ((X + h) mod 2 h)
+        // - h, X = (X - d) / 2h (h = 2^(BITS-1)), one 128-bit subtract and
+        // shift at a time, in a few operations each.
+        const __int128 Y =
+            rne_scaled(hi, F - e) + rne_scaled(lo, F - e) + digit_offset<S, BITS>();
         const unsigned long long y_lo = (unsigned long long)Y;
         const unsigned long long y_hi = (unsigned long long)(Y >> 64);
 #pragma unroll
@@ -176,16 +181,17 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
             const int i = S - 1 - s;  // digit position, least significant first
             int d;
             if (s > 0) {
+                const int b0 = BITS * i;   // first bit of the field
                 unsigned long long field;
-                if (7 * i + 7 <= 64)
-                    field = y_lo >> (7 * i);
-                else if (7 * i >= 64)
-                    field = y_hi >> (7 * i - 64);
+                if (b0 + BITS <= 64)
+                    field = y_lo >> b0;
+                else if (b0 >= 64)
+                    field = y_hi >> (b0 - 64);
                 else
-                    field = (y_lo >> (7 * i)) | (y_hi << (64 - 7 * i));
-                d = (int)(field & 127ull) - 64;
+                    field = (y_lo >> b0) | (y_hi << (64 - b0));
+                d = (int)(field & ((1ull << BITS) - 1)) - (1 << (BITS - 1));
             } else {
-                d = (int)(Y >> (7 * (S - 1)));
+                d = (int)(Y >> (BITS * (S - 1)));
             }
             if constexpr (BF16)
                 word[s][j >> 2] |= bf16_bits(d) << (16 * (j & 3));

@@ -63,7 +63,7 @@ def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, wo
     phase_events: optional three recorded torch.cuda.Event objects; the library
     re-records them around the split and the cascade kernel on the stream.
     variant: DDGEMM_VARIANT_FP64 (ten FP64 products) or DDGEMM_VARIANT_INT8
-    (int8_slices INT8 pieces per entry, 0 = 16).
+    (int8_slices INT8 pieces per entry, 0 = 15).
     split_k: 0 = automatic split-k for small grids, 1 = never, 2-16 = forced."""
     lda = _check_pair(a_hi, a_lo, "A")
     ldb = _check_pair(b_hi, b_lo, "B")
@@ -188,7 +188,7 @@ def ddgemm_backward(a_hi, a_lo, b_hi, b_lo, dc_hi, dc_lo, *, trans_a=False, tran
     return da[0], da[1], db[0], db[1]
 
 
-def split_int8(x_hi, x_lo, *, as_b=False, trans=False, slices=16, stream=None, status=None):
+def split_int8(x_hi, x_lo, *, as_b=False, trans=False, slices=15, stream=None, status=None):
     """The INT8 split of A (as_b=False; vectors = rows of op(A)) or of B
     (as_b=True; vectors = columns of op(B)).  Returns (digits [s, nvec, k]
     int8, exps [ceil(k/16384), nvec] int32)."""

@@ -40,7 +40,7 @@ def host(*tensors):
 @pytest.mark.parametrize("nvec,k", [(37, 300), (64, 64), (5, 1), (33, 130)])
 @pytest.mark.parametrize("kind", ["uniform", "wide"])
 @pytest.mark.parametrize("as_b,trans", [(False, False), (False, True), (True, False), (True, True)])
-@pytest.mark.parametrize("s", [14, 16, 18])
+@pytest.mark.parametrize("s", [12, 14, 15])
 def test_split_int8_bitwise(ops, nvec, k, kind, as_b, trans, s):
     x_hi, x_lo, _, _ = gemm_inputs(nvec, 1, k, kind=kind, seed=nvec + k)   # vectors as rows
     e = c8.block_exponents(x_hi)
@@ -57,7 +57,7 @@ def test_split_int8_bitwise(ops, nvec, k, kind, as_b, trans, s):
 
 @pytest.mark.parametrize("m,n,k", [(64, 64, 256), (37, 45, 300), (1, 1, 1), (70, 33, 100)])
 @pytest.mark.parametrize("kind", ["uniform", "wide"])
-@pytest.mark.parametrize("s", [12, 16, 18])
+@pytest.mark.parametrize("s", [12, 13, 15])
 def test_int8_ddgemm_bit_identical(ops, m, n, k, kind, s):
     a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind=kind, seed=m * 7 + n + k)
     want_hi, want_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=s)
@@ -68,7 +68,7 @@ def test_int8_ddgemm_bit_identical(ops, m, n, k, kind, s):
 @pytest.mark.parametrize("ta,tb", [(True, False), (False, True), (True, True)])
 def test_int8_transposed(ops, ta, tb):
     a_hi, a_lo, b_hi, b_lo = gemm_inputs(40, 50, 90, kind="wide", seed=3)
-    want_hi, want_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16)
+    want_hi, want_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=15)
     sa = (a_hi.T, a_lo.T) if ta else (a_hi, a_lo)
     sb = (b_hi.T, b_lo.T) if tb else (b_hi, b_lo)
     c_hi, c_lo = host(*ops.ddgemm(*dev(*sa), *dev(*sb), trans_a=ta, trans_b=tb, variant=INT8))
@@ -78,7 +78,7 @@ def test_int8_transposed(ops, ta, tb):
 def test_int8_two_k_blocks(ops):
     """k > 16384: two INT8 k-blocks with their own scales."""
     a_hi, a_lo, b_hi, b_lo = gemm_inputs(4, 6, 17000, kind="wide", seed=4)
-    want_hi, want_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16)
+    want_hi, want_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=15)
     c_hi, c_lo = host(*ops.ddgemm(*dev(a_hi, a_lo, b_hi, b_lo), variant=INT8))
     assert np.array_equal(c_hi, want_hi) and np.array_equal(c_lo, want_lo)
 
@@ -112,7 +112,7 @@ def test_int8_full_size_sampled(ops, m, n, k, kind):
     for t in range(4):
         i, j = rows[t], cols[t]
         ex = exact.exact_dot(a_hi[i], a_lo[i], b_hi[:, j], b_lo[:, j])
-        bound = int8_bound(a_hi[i:i + 1], b_hi[:, j:j + 1], 16)[0, 0]
+        bound = int8_bound(a_hi[i:i + 1], b_hi[:, j:j + 1], 15)[0, 0]
         assert exact.err_vs_exact(c_hi[i, j], c_lo[i, j], ex) <= bound
 
 
@@ -135,9 +135,9 @@ def test_int8_backward_matches_int8_forward_products(ops):
                          db[1].data_ptr(), n, ws.data_ptr(), ws.numel(),
                          torch.cuda.current_stream().cuda_stream, opts)
     da_hi, da_lo, db_hi, db_lo = host(*da, *db)
-    want = c8.cascade_int8_ddgemm(w_hi, w_lo, b_hi.T, b_lo.T, s=16)
+    want = c8.cascade_int8_ddgemm(w_hi, w_lo, b_hi.T, b_lo.T, s=15)
     assert np.array_equal(da_hi, want[0]) and np.array_equal(da_lo, want[1])
-    want = c8.cascade_int8_ddgemm(a_hi.T, a_lo.T, w_hi, w_lo, s=16)
+    want = c8.cascade_int8_ddgemm(a_hi.T, a_lo.T, w_hi, w_lo, s=15)
     assert np.array_equal(db_hi, want[0]) and np.array_equal(db_lo, want[1])
 
 
@@ -151,5 +151,5 @@ def test_int8_noalloc_matches_int8_ddgemm(ops):
                         t[3].data_ptr(), n, c[0].data_ptr(), c[1].data_ptr(), n,
                         torch.cuda.current_stream().cuda_stream, _lib.make_opts(variant=INT8))
     got = host(*c)
-    want = c8.cascade_int8_ddgemm(*a, s=16)
+    want = c8.cascade_int8_ddgemm(*a, s=15)
     assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])

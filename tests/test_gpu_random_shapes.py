@@ -50,12 +50,13 @@ def test_random_shape_all_forms(ops, c, m, n, k, kind, ta, tb):
     check_against_oracles(ops, a_hi, a_lo, b_hi, b_lo, trans_a=ta, trans_b=tb,
                           contract=kind == "uniform")
     # INT8 forms, bit for bit
-    for variant, assembly in ((1, "fp64x2"), (4, "exact")):
+    for variant, s, assembly, bits in ((1, 15, "fp64x2", 8), (4, 16, "exact", 7)):
         status = torch.zeros(1, dtype=torch.int32, device="cuda")
         c_hi, c_lo = ops.ddgemm(*dev(*sa), *dev(*sb), trans_a=ta, trans_b=tb, variant=variant,
                                 status=status)
         torch.cuda.synchronize()
         assert int(status.item()) == 0
-        w_hi, w_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16, assembly=assembly)
+        w_hi, w_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=s, assembly=assembly,
+                                            bits=bits)
         assert np.array_equal(c_hi.cpu().numpy(), w_hi), (variant, m, n, k)
         assert np.array_equal(c_lo.cpu().numpy(), w_lo), (variant, m, n, k)
