@@ -20,9 +20,10 @@
  * Conventions for every entry point:
  *   - Matrices are row-major.  Element (r, c) of a matrix with leading
  *     dimension ld is at ptr[r * ld + c].
- *   - Every matrix pointer is DEVICE memory owned by the caller, and the
- *     library never allocates, frees or keeps a pointer after the call:
- *     scratch space is the caller's `workspace`.
+ *   - Every matrix pointer is DEVICE memory owned by the caller (except
+ *     ddgemm_host(), whose matrices are in host memory), and the library
+ *     never allocates device memory, frees or keeps a pointer after the
+ *     call: scratch space is the caller's `workspace`.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Work is enqueued on it and the call returns without waiting.
  *   - The return value reports host-side checks and launch errors only.
@@ -252,6 +253,55 @@ int ddgemm_batched(int count, const ddgemm_problem *probs_host,
                    const ddgemm_problem *probs_dev, void *workspace, size_t ws_bytes,
                    void *stream, const ddgemm_opts *opts,
                    const ddgemm_batch_config *config);
+
+/* Bytes of device buffer ddgemm_host() needs for this problem: dense device
+ * copies of A, B and C (hi and lo of each) and the workspace for the row
+ * chunks it runs.  0 when m or n is 0 or the arguments are invalid. */
+size_t ddgemm_host_buffer_size(int m, int n, int k, const ddgemm_opts *opts);
+
+/* ddgemm() on HOST operands: C := op(A) op(B) with A_hi, A_lo, B_hi, B_lo,
+ * C_hi and C_lo in host memory (same shapes, leading dimensions and trans
+ * flags as ddgemm()).  The paper has no counterpart (its operands are in
+ * the CPU's memory already); this packages the host-to-device copies with
+ * the cascade so that they overlap it.
+ *
+ *   - buffer: device memory of >= ddgemm_host_buffer_size() bytes, 256-byte
+ *     aligned, owned by the caller; it holds the copies and the workspace.
+ *   - The call makes two streams and eleven events of its own (released
+ *     when it returns; the driver keeps them until their work is done).
+ *     B is copied first, then op(A) in up to four chunks of rows: every
+ *     chunk's split and products run on `stream` as soon as its rows have
+ *     arrived, and its rows of C are copied back while the next chunk
+ *     computes.  Chunks hold at least 2048 tiles of the form's kernel, so
+ *     small problems run as one chunk.
+ *   - Each chunk computes exactly what ddgemm() computes for those rows:
+ *     C is bit-identical to ddgemm() on device copies of the operands,
+ *     except that the FP64 form may choose a different split-k grouping
+ *     for a chunk (split_k = 1 makes it bit-identical there too).
+ *   - `stream` waits for the last copy, so synchronising it (or an event
+ *     recorded on it after the call) means C is on the host.  Nothing of the
+ *     call starts before the work already enqueued on `stream`, so calls on
+ *     one stream may reuse one buffer.  The host arrays must stay valid and
+ *     unchanged until then.
+ *   - Page-locked host memory (cudaHostAlloc, cudaHostRegister) lets the
+ *     copies run asynchronously and the call return at once.  With pageable
+ *     memory the driver stages the copies and the call returns only when the
+ *     copies to the host have completed.  Device or managed pointers work
+ *     too (the copies are then device to device).
+ *   - opts as for ddgemm(); phase_events is ignored.  flags_dev, if given,
+ *     is a device array as for ddgemm().
+ *   - Errors: DDGEMM_EINVAL, DDGEMM_EUNSUPPORTED as for ddgemm();
+ *     DDGEMM_EWORKSPACE for a missing, misaligned or small buffer;
+ *     DDGEMM_ECUDA if a stream, event, copy or launch call fails (work
+ *     enqueued before the failure may still be running: synchronise the
+ *     device before reusing the buffer or the host arrays).
+ *   - Not for stream capture (it creates and destroys streams). */
+int ddgemm_host(int m, int n, int k,
+                const double *A_hi, const double *A_lo, int lda,
+                const double *B_hi, const double *B_lo, int ldb,
+                double *C_hi, double *C_lo, int ldc,
+                void *buffer, size_t buffer_bytes, void *stream,
+                const ddgemm_opts *opts);
 
 /* Size of the static device scratch array that ddgemm_noalloc() uses. */
 #define DDGEMM_NOALLOC_SCRATCH_BYTES (64u << 20) /* 64 MiB */

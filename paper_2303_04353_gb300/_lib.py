@@ -70,6 +70,8 @@ _SIGS = {
     "ddgemm_probe_fp64": (ctypes.c_double, [_I, _P, _P]),
     "ddgemm_probe_int8": (ctypes.c_double, [_I, _P, _P]),
     "ddgemm_noalloc": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P]),
+    "ddgemm_host_buffer_size": (_Z, [_I, _I, _I, _P]),
+    "ddgemm_host": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _Z, _P, _P]),
     "ddgemm_backward_workspace_size": (_Z, [_I, _I, _I, _P]),
     "ddgemm_split_int8_a": (_I, [_I, _I, _P, _P, _I, _I, _I, _P, _I, _P, _P, _P]),
     "ddgemm_batched_workspace_size": (_Z, [_I, _P, _P]),
@@ -166,6 +168,19 @@ def ddgemm_noalloc(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo, ldc, s
     (for callers that cannot allocate; see include/ddgemm.h).  Raises on error."""
     _check(load().ddgemm_noalloc(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo, ldc,
                                  stream, ctypes.byref(opts) if opts else None), "ddgemm_noalloc")
+
+
+def ddgemm_host_buffer_size(m: int, n: int, k: int, opts: ddgemm_opts | None = None) -> int:
+    return load().ddgemm_host_buffer_size(m, n, k, ctypes.byref(opts) if opts else None)
+
+
+def ddgemm_host(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo, ldc, buffer, buf_bytes,
+                stream, opts: ddgemm_opts | None = None) -> None:
+    """ddgemm on host operands (raw host pointers, a device buffer; see
+    include/ddgemm.h).  Raises on error."""
+    _check(load().ddgemm_host(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo, ldc, buffer,
+                              buf_bytes, stream, ctypes.byref(opts) if opts else None),
+           "ddgemm_host")
 
 
 def ddgemm_backward_workspace_size(m: int, n: int, k: int, opts: ddgemm_opts | None = None) -> int:

@@ -145,100 +145,259 @@ int check_operands(int m, int n, int k, const void *ah, const void *al, int lda,
     return DDGEMM_OK;
 }
 
-// split-k groups of an FP64-form launch: as many as the workspace holds,
-// within the choice for this grid
-int split_groups(int m, int n, int k, int sms, size_t ws_bytes, const Parsed &p) {
-    if (is_int8(p.variant) || p.flags || p.split_k == 1) return 1;
-    if (m <= 0 || n <= 0 || k <= 0) return 1;
-    const Layout L = layout_for(m, n, k);
-    if (ws_bytes < L.base) return 1;
+// A workspace carved for row chunks of at most mc rows of op(A) against all
+// of op(B): the B regions and their offsets depend on mc, n and k only, so
+// one split of B serves every chunk, and a chunk of mr <= mc rows puts its
+// pieces of A, its exponents and its split-k partials in regions sized for
+// mc.  ddgemm() is the single chunk mc = mr = m.
+struct Carve {
+    int mc = 0;
+    bool int8 = false;
+    Layout L{};
+    Layout8 L8{};
+    size_t base = 0;  // bytes without split-k partials
+};
+
+Carve carve_for(int mc, int n, int k, const Parsed &p) {
+    Carve c;
+    c.mc = mc;
+    c.int8 = is_int8(p.variant);
+    if (c.int8) {
+        c.L8 = layout8_for(mc, n, k, p.slices, p.variant);
+        c.base = c.L8.total;
+    } else {
+        c.L = layout_for(mc, n, k);
+        c.base = c.L.base;
+    }
+    return c;
+}
+
+// split-k groups of an FP64-form launch of mr rows in a workspace carved for
+// mc >= mr rows: as many as the workspace holds, within the choice for the
+// grid of mr x n
+int split_groups_in(int mr, int n, int k, int sms, size_t ws_bytes, const Carve &c,
+                    const Parsed &p) {
+    if (c.int8 || p.flags || p.split_k == 1) return 1;
+    if (mr <= 0 || n <= 0 || k <= 0) return 1;
+    if (ws_bytes < c.base) return 1;
     const int kb = (k + ddg::KC - 1) / ddg::KC;
-    const int room = 1 + (int)std::min<size_t>((ws_bytes - L.base) / (2 * L.part_bytes),
+    const int room = 1 + (int)std::min<size_t>((ws_bytes - c.base) / (2 * c.L.part_bytes),
                                                 SPLIT_MAX - 1);
     int split = 1;
     if (p.split_k > 1)
         split = std::min(std::min(p.split_k, SPLIT_MAX), kb);
     else
-        split = ddg::choose_split(fp64_tiles(m, n), kb, sms, auto_split_cap(m, n, k));
+        split = ddg::choose_split(fp64_tiles(mr, n), kb, sms, auto_split_cap(mr, n, k));
     return std::min(split, room);
 }
 
-int run(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
-        const double *B_hi, const double *B_lo, int ldb, double *C_hi, double *C_lo, int ldc,
-        double *bins, void *workspace, size_t ws_bytes, cudaStream_t stream, const Parsed &p) {
-    const Layout L = layout_for(m, n, k);
-    if (!workspace || ws_bytes < L.base || (uintptr_t)workspace % ALIGN) return DDGEMM_EWORKSPACE;
-    int split = 1;
-    if (!bins && !p.flags && p.split_k != 1) {
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return DDGEMM_ECUDA;
-        split = split_groups(m, n, k, sms, ws_bytes, p);
+int split_groups(int m, int n, int k, int sms, size_t ws_bytes, const Parsed &p) {
+    if (m <= 0 || n <= 0 || k <= 0) return 1;
+    return split_groups_in(m, n, k, sms, ws_bytes, carve_for(m, n, k, p), p);
+}
+
+int sm_count(int &sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return DDGEMM_ECUDA;
+    return DDGEMM_OK;
+}
+
+// Phase one for B (Appendix A; Sec. "FP64x2 in terms of INT8" for the INT8
+// forms): the exponents of tau and the seven panels, or the digit planes.
+// A column of op(B) is a vector; it runs along memory only if trans_b.
+cudaError_t split_b_into(const Carve &c, int n, int k, const double *B_hi, const double *B_lo,
+                         int ldb, char *ws, cudaStream_t s, const Parsed &p) {
+    if (c.int8) {
+        const bool tc = p.variant == DDGEMM_VARIANT_INT8_TC;
+        return ddg::launch_split_int8(p.slices, n, k, B_hi, B_lo, ldb, p.trans_b != 0,
+                                      ws + c.L8.off_b, tc ? ddg::INT8_TC_BN : 0, c.L8.ld,
+                                      reinterpret_cast<int *>(ws + c.L8.off_eb), p.status, s);
     }
-    char *ws = static_cast<char *>(workspace);
-    double *a_s = reinterpret_cast<double *>(ws + L.off_a);
-    double *b_s = reinterpret_cast<double *>(ws + L.off_b);
-    int *e_a = reinterpret_cast<int *>(ws + L.off_ea);
-    int *e_b = reinterpret_cast<int *>(ws + L.off_eb);
-    auto mark = [&](int i) {
-        return !p.events || cudaEventRecord(static_cast<cudaEvent_t>(p.events[i]), stream) ==
-                                cudaSuccess;
-    };
-    if (!mark(0)) return DDGEMM_ECUDA;
-    // A: a row of op(A) is a vector; it runs along memory unless trans_a.
-    cudaError_t e = ddg::launch_split(4, m, k, A_hi, A_lo, lda, !p.trans_a, a_s, L.lda_s,
-                                      ddg::PanelLayout::VEC_MAJOR, e_a, p.status, stream);
-    if (e != cudaSuccess) return DDGEMM_ECUDA;
-    // B: a column of op(B) is a vector; it runs along memory only if trans_b.
-    e = ddg::launch_split(7, n, k, B_hi, B_lo, ldb, p.trans_b != 0, b_s, L.ldb_s,
-                          ddg::PanelLayout::K_MAJOR, e_b, p.status, stream);
-    if (e != cudaSuccess || !mark(1)) return DDGEMM_ECUDA;
+    return ddg::launch_split(7, n, k, B_hi, B_lo, ldb, p.trans_b != 0,
+                             reinterpret_cast<double *>(ws + c.L.off_b), c.L.ldb_s,
+                             ddg::PanelLayout::K_MAJOR, reinterpret_cast<int *>(ws + c.L.off_eb),
+                             p.status, s);
+}
+
+// Phase one for mr rows of op(A) (a row is a vector; it runs along memory
+// unless trans_a).
+cudaError_t split_a_into(const Carve &c, int mr, int k, const double *A_hi, const double *A_lo,
+                         int lda, char *ws, cudaStream_t s, const Parsed &p) {
+    if (c.int8) {
+        const bool tc = p.variant == DDGEMM_VARIANT_INT8_TC;
+        return ddg::launch_split_int8(p.slices, mr, k, A_hi, A_lo, lda, !p.trans_a,
+                                      ws + c.L8.off_a, tc ? ddg::INT8_TC_BM : 0, c.L8.ld,
+                                      reinterpret_cast<int *>(ws + c.L8.off_ea), p.status, s);
+    }
+    return ddg::launch_split(4, mr, k, A_hi, A_lo, lda, !p.trans_a,
+                             reinterpret_cast<double *>(ws + c.L.off_a), c.L.lda_s,
+                             ddg::PanelLayout::VEC_MAJOR, reinterpret_cast<int *>(ws + c.L.off_ea),
+                             p.status, s);
+}
+
+// Phases two and three for the mr rows whose pieces split_a_into wrote: the
+// products, the bins' assembly and the FP64x2 accumulation into C (or, with
+// bins, the bins of the single k-block).
+cudaError_t products_into(const Carve &c, int mr, int n, int k, double *C_hi, double *C_lo,
+                          int ldc, int *flags, double *bins, int split, char *ws, cudaStream_t s,
+                          const Parsed &p) {
+    if (c.int8) {
+        const Layout8 &L = c.L8;
+        const int *e_a = reinterpret_cast<const int *>(ws + L.off_ea);
+        const int *e_b = reinterpret_cast<const int *>(ws + L.off_eb);
+        if (p.variant == DDGEMM_VARIANT_INT8_TC) {
+            ddg::Int8TcArgs a{mr, n, k, p.slices, reinterpret_cast<const uint16_t *>(ws + L.off_a),
+                              reinterpret_cast<const uint16_t *>(ws + L.off_b), e_a, e_b, C_hi,
+                              C_lo, (long long)ldc, p.status};
+            return ddg::launch_cascade_int8_tc(a, s);
+        }
+        ddg::Int8Args a{mr, n, k, p.slices, reinterpret_cast<const int8_t *>(ws + L.off_a),
+                        reinterpret_cast<const int8_t *>(ws + L.off_b), L.ld, e_a, e_b, C_hi,
+                        C_lo, (long long)ldc, p.status};
+        return ddg::launch_cascade_int8(a, s);
+    }
+    const Layout &L = c.L;
     const int products = p.variant == DDGEMM_VARIANT_FP64_GEMM16    ? 1
                          : p.variant == DDGEMM_VARIANT_FP64_DROP456 ? 2
                                                                       : 0;
     double *part = reinterpret_cast<double *>(ws + L.off_part);
-    double *part_lo = reinterpret_cast<double *>(ws + L.off_part + (size_t)(split - 1) * L.part_bytes);
-    ddg::CascadeArgs ca{m, n, k, a_s, L.lda_s, b_s, L.ldb_s, e_a, e_b, C_hi, C_lo,
-                        (long long)ldc, p.flags, p.status, bins, products, split, part, part_lo};
-    e = ddg::launch_cascade_fp64(ca, stream);
-    return e == cudaSuccess && mark(2) ? DDGEMM_OK : DDGEMM_ECUDA;
+    double *part_lo =
+        reinterpret_cast<double *>(ws + L.off_part + (size_t)(split - 1) * L.part_bytes);
+    ddg::CascadeArgs ca{mr, n, k, reinterpret_cast<const double *>(ws + L.off_a), L.lda_s,
+                        reinterpret_cast<const double *>(ws + L.off_b), L.ldb_s,
+                        reinterpret_cast<const int *>(ws + L.off_ea),
+                        reinterpret_cast<const int *>(ws + L.off_eb), C_hi, C_lo,
+                        (long long)ldc, flags, p.status, bins, products, split, part, part_lo};
+    return ddg::launch_cascade_fp64(ca, s);
 }
 
-int run_int8(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
-             const double *B_hi, const double *B_lo, int ldb, double *C_hi, double *C_lo, int ldc,
-             void *workspace, size_t ws_bytes, cudaStream_t stream, const Parsed &p) {
-    const bool tc = p.variant == DDGEMM_VARIANT_INT8_TC;
-    const Layout8 L = layout8_for(m, n, k, p.slices, p.variant);
-    if (!workspace || ws_bytes < L.total || (uintptr_t)workspace % ALIGN) return DDGEMM_EWORKSPACE;
+// One whole problem on device operands: the split of A, the split of B, and
+// the products, with the optional phase events around them.
+int run(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
+        const double *B_hi, const double *B_lo, int ldb, double *C_hi, double *C_lo, int ldc,
+        double *bins, void *workspace, size_t ws_bytes, cudaStream_t stream, const Parsed &p) {
+    const Carve c = carve_for(m, n, k, p);
+    if (!workspace || ws_bytes < c.base || (uintptr_t)workspace % ALIGN) return DDGEMM_EWORKSPACE;
+    int split = 1;
+    if (!c.int8 && !bins && !p.flags && p.split_k != 1) {
+        int sms = 0;
+        if (sm_count(sms) != DDGEMM_OK) return DDGEMM_ECUDA;
+        split = split_groups_in(m, n, k, sms, ws_bytes, c, p);
+    }
     char *ws = static_cast<char *>(workspace);
-    void *da = ws + L.off_a;
-    void *db = ws + L.off_b;
-    int *e_a = reinterpret_cast<int *>(ws + L.off_ea);
-    int *e_b = reinterpret_cast<int *>(ws + L.off_eb);
     auto mark = [&](int i) {
         return !p.events || cudaEventRecord(static_cast<cudaEvent_t>(p.events[i]), stream) ==
                                 cudaSuccess;
     };
     if (!mark(0)) return DDGEMM_ECUDA;
-    cudaError_t e = ddg::launch_split_int8(p.slices, m, k, A_hi, A_lo, lda, !p.trans_a, da,
-                                           tc ? ddg::INT8_TC_BM : 0, L.ld, e_a, p.status, stream);
-    if (e != cudaSuccess) return DDGEMM_ECUDA;
-    e = ddg::launch_split_int8(p.slices, n, k, B_hi, B_lo, ldb, p.trans_b != 0, db,
-                               tc ? ddg::INT8_TC_BN : 0, L.ld, e_b, p.status, stream);
-    if (e != cudaSuccess || !mark(1)) return DDGEMM_ECUDA;
-    if (tc) {
-        ddg::Int8TcArgs a{m, n, k, p.slices, static_cast<const uint16_t *>(da),
-                          static_cast<const uint16_t *>(db), e_a, e_b, C_hi, C_lo,
-                          (long long)ldc, p.status};
-        e = ddg::launch_cascade_int8_tc(a, stream);
-    } else {
-        ddg::Int8Args a{m, n, k, p.slices, static_cast<const int8_t *>(da),
-                        static_cast<const int8_t *>(db), L.ld, e_a, e_b, C_hi, C_lo,
-                        (long long)ldc, p.status};
-        e = ddg::launch_cascade_int8(a, stream);
-    }
+    if (split_a_into(c, m, k, A_hi, A_lo, lda, ws, stream, p) != cudaSuccess ||
+        split_b_into(c, n, k, B_hi, B_lo, ldb, ws, stream, p) != cudaSuccess || !mark(1))
+        return DDGEMM_ECUDA;
+    const cudaError_t e =
+        products_into(c, m, n, k, C_hi, C_lo, ldc, p.flags, bins, split, ws, stream, p);
     return e == cudaSuccess && mark(2) ? DDGEMM_OK : DDGEMM_ECUDA;
+}
+
+// Workspace bytes of ddgemm() for a valid problem (m, n, k all positive),
+// split-k partials included.
+size_t workspace_total(int m, int n, int k, const Parsed &p) {
+    if (is_int8(p.variant)) return layout8_for(m, n, k, p.slices, p.variant).total;
+    return layout_for(m, n, k, split_reserve(m, n, k, p.split_k)).total;
+}
+
+// ---- host buffers: ddgemm_host ---------------------------------------------
+//
+// The operands are copied in and C is copied out by two streams of the call's
+// own, so that the copies overlap the kernels on the caller's stream: B goes
+// first (every C entry needs all of it), then A in row chunks; each chunk's
+// split and products start as soon as its rows have arrived, and its rows of
+// C go back while the next chunk computes.  Exposed: the copy of B and of
+// the first chunk of A, the split of B, and the copy of the last chunk of C.
+
+constexpr int HOST_MAX_CHUNKS = 4;
+constexpr long long HOST_MIN_TILES = 2048;
+
+// Rows of op(A) per chunk: at least HOST_MIN_TILES tiles of the form's own
+// tile shape per chunk, so that a chunk still fills the GPU, and at most
+// HOST_MAX_CHUNKS chunks; a multiple of 128 (every form's tile height divides it).
+int host_chunk_rows(int m, int n, const Parsed &p) {
+    int tm = 64, tn = 64;
+    if (p.variant == DDGEMM_VARIANT_INT8_TC) {
+        tm = ddg::INT8_TC_BM;
+        tn = ddg::INT8_TC_BN;
+    } else if (p.variant == DDGEMM_VARIANT_INT8) {
+        tm = 32;
+        tn = 32;
+    }
+    const long long col_tiles = (n + tn - 1) / tn;
+    const long long rows_min = (HOST_MIN_TILES + col_tiles - 1) / col_tiles * tm;
+    long long mc = std::max<long long>(rows_min, (m + HOST_MAX_CHUNKS - 1) / HOST_MAX_CHUNKS);
+    mc = (mc + 127) / 128 * 128;
+    return (int)std::min<long long>(mc, m);
+}
+
+// Device buffer of ddgemm_host: dense copies of A (chunk after chunk), B and
+// C, each as a hi plane then a lo plane, then the workspace for chunks of
+// mc rows.
+struct HostLayout {
+    int mc = 0;
+    size_t a_plane = 0, b_plane = 0, c_plane = 0;
+    size_t off_a = 0, off_b = 0, off_c = 0, off_ws = 0, ws_bytes = 0, total = 0;
+};
+
+HostLayout host_layout(int m, int n, int k, const Parsed &p) {
+    HostLayout H;
+    H.mc = k == 0 ? m : host_chunk_rows(m, n, p);
+    H.a_plane = round_up((size_t)m * k * sizeof(double), ALIGN);
+    H.b_plane = round_up((size_t)k * n * sizeof(double), ALIGN);
+    H.c_plane = round_up((size_t)m * n * sizeof(double), ALIGN);
+    H.off_a = 0;
+    H.off_b = H.off_a + 2 * H.a_plane;
+    H.off_c = H.off_b + 2 * H.b_plane;
+    H.off_ws = H.off_c + 2 * H.c_plane;
+    H.ws_bytes = k == 0 ? 0 : workspace_total(H.mc, n, k, p);
+    H.total = H.off_ws + H.ws_bytes;
+    return H;
+}
+
+// The copy streams and events of one ddgemm_host call.  They are released
+// when the call returns; the driver keeps each alive until the work enqueued
+// on it has completed.
+struct HostStreams {
+    static constexpr int MAX_EVENTS = 3 + 2 * HOST_MAX_CHUNKS;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev[MAX_EVENTS] = {};
+    bool init() {
+        if (cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking) != cudaSuccess)
+            return false;
+        for (auto &e : ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+        return true;
+    }
+    ~HostStreams() {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+        if (h2d) cudaStreamDestroy(h2d);
+        if (d2h) cudaStreamDestroy(d2h);
+    }
+};
+
+// `to` waits for the work enqueued so far on `from`.
+bool after(cudaStream_t to, cudaStream_t from, cudaEvent_t e) {
+    return cudaEventRecord(e, from) == cudaSuccess && cudaStreamWaitEvent(to, e, 0) == cudaSuccess;
+}
+
+// A rows x cols block of doubles (row pitches in elements), either way
+// between host and device.
+bool copy2d(double *dst, long long dpitch, const double *src, long long spitch, long long cols,
+            long long rows, cudaStream_t s) {
+    if (rows == 0 || cols == 0) return true;
+    return cudaMemcpy2DAsync(dst, (size_t)dpitch * sizeof(double), src,
+                             (size_t)spitch * sizeof(double), (size_t)cols * sizeof(double),
+                             (size_t)rows, cudaMemcpyDefault, s) == cudaSuccess;
 }
 
 }  // namespace
@@ -261,8 +420,7 @@ size_t ddgemm_workspace_size(int m, int n, int k, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
     if (m == 0 || n == 0 || k == 0) return 0;
-    if (is_int8(p.variant)) return layout8_for(m, n, k, p.slices, p.variant).total;
-    return layout_for(m, n, k, split_reserve(m, n, k, p.split_k)).total;
+    return workspace_total(m, n, k, p);
 }
 
 int ddgemm_split_groups(int m, int n, int k, int sms, size_t ws_bytes, const ddgemm_opts *opts) {
@@ -291,11 +449,105 @@ int ddgemm(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
             return DDGEMM_ECUDA;
         return DDGEMM_OK;
     }
-    if (is_int8(p.variant))
-        return run_int8(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, C_hi, C_lo, ldc, workspace,
-                        ws_bytes, s, p);
     return run(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, C_hi, C_lo, ldc, nullptr, workspace,
                ws_bytes, s, p);
+}
+
+size_t ddgemm_host_buffer_size(int m, int n, int k, const ddgemm_opts *opts) {
+    Parsed p;
+    if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
+    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_INT8_TC) return 0;
+    if (m == 0 || n == 0) return 0;
+    return host_layout(m, n, k, p).total;
+}
+
+int ddgemm_host(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
+                const double *B_hi, const double *B_lo, int ldb, double *C_hi, double *C_lo,
+                int ldc, void *buffer, size_t buffer_bytes, void *stream,
+                const ddgemm_opts *opts) {
+    Parsed p;
+    if (!parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
+    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_INT8_TC)
+        return DDGEMM_EUNSUPPORTED;
+    if (is_int8(p.variant) && p.flags) return DDGEMM_EUNSUPPORTED;
+    if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;
+    if (m == 0 || n == 0) return DDGEMM_OK;
+    if (!C_hi || !C_lo || ldc < n) return DDGEMM_EINVAL;
+    p.events = nullptr;
+    const HostLayout H = host_layout(m, n, k, p);
+    if (!buffer || buffer_bytes < H.total || (uintptr_t)buffer % ALIGN) return DDGEMM_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *buf = static_cast<char *>(buffer);
+    double *a_hi = reinterpret_cast<double *>(buf + H.off_a);
+    double *a_lo = reinterpret_cast<double *>(buf + H.off_a + H.a_plane);
+    double *b_hi = reinterpret_cast<double *>(buf + H.off_b);
+    double *b_lo = reinterpret_cast<double *>(buf + H.off_b + H.b_plane);
+    double *c_hi = reinterpret_cast<double *>(buf + H.off_c);
+    double *c_lo = reinterpret_cast<double *>(buf + H.off_c + H.c_plane);
+    char *ws = buf + H.off_ws;
+
+    HostStreams hs;
+    if (!hs.init()) return DDGEMM_ECUDA;
+    // event slots: the entry, B copied, chunk r of A copied, chunk r of C done
+    constexpr int E_ENTRY = 0, E_B = 1, E_A = 2, E_C = 2 + HOST_MAX_CHUNKS;
+    // nothing of this call starts before the work already on the caller's
+    // stream (which may still be using the buffer)
+    if (!after(hs.h2d, s, hs.ev[E_ENTRY]) ||
+        cudaStreamWaitEvent(hs.d2h, hs.ev[E_ENTRY], 0) != cudaSuccess)
+        return DDGEMM_ECUDA;
+    const int nchunks = (m + H.mc - 1) / H.mc;  // 1 when k = 0
+    if (k == 0) {
+        // C := 0 on the device (and the flags), then back
+        ddgemm_opts z{p.trans_a, p.trans_b, p.variant, p.status, p.flags, nullptr, p.slices,
+                      p.split_k};
+        if (int r = ddgemm(m, n, 0, nullptr, nullptr, 0, nullptr, nullptr, 0, c_hi, c_lo, n,
+                           nullptr, 0, stream, &z))
+            return r;
+        if (cudaEventRecord(hs.ev[E_C], s) != cudaSuccess) return DDGEMM_ECUDA;
+    } else {
+        // B whole, then the chunks of A
+        const long long bk = p.trans_b ? n : k, bn = p.trans_b ? k : n;  // stored shape
+        if (!copy2d(b_hi, bn, B_hi, ldb, bn, bk, hs.h2d) ||
+            !copy2d(b_lo, bn, B_lo, ldb, bn, bk, hs.h2d) || !after(s, hs.h2d, hs.ev[E_B]))
+            return DDGEMM_ECUDA;
+        const Carve c = carve_for(H.mc, n, k, p);
+        if (split_b_into(c, n, k, b_hi, b_lo, (int)bn, ws, s, p) != cudaSuccess)
+            return DDGEMM_ECUDA;
+        int sms = 0;
+        if (!c.int8 && sm_count(sms) != DDGEMM_OK) return DDGEMM_ECUDA;
+        for (int r = 0; r < nchunks; ++r) {
+            const int r0 = r * H.mc, mr = std::min(H.mc, m - r0);
+            double *ah = a_hi + (size_t)r0 * k, *al = a_lo + (size_t)r0 * k;
+            // the chunk keeps A's stored orientation: rows r0.. of A, or
+            // columns r0.. of the stored k x m matrix
+            const int lda_c = p.trans_a ? mr : k;
+            const bool ok =
+                p.trans_a ? copy2d(ah, mr, A_hi + r0, lda, mr, k, hs.h2d) &&
+                                copy2d(al, mr, A_lo + r0, lda, mr, k, hs.h2d)
+                          : copy2d(ah, k, A_hi + (size_t)r0 * lda, lda, k, mr, hs.h2d) &&
+                                copy2d(al, k, A_lo + (size_t)r0 * lda, lda, k, mr, hs.h2d);
+            if (!ok || !after(s, hs.h2d, hs.ev[E_A + r])) return DDGEMM_ECUDA;
+            const int split = c.int8 ? 1 : split_groups_in(mr, n, k, sms, H.ws_bytes, c, p);
+            if (split_a_into(c, mr, k, ah, al, lda_c, ws, s, p) != cudaSuccess ||
+                products_into(c, mr, n, k, c_hi + (size_t)r0 * n, c_lo + (size_t)r0 * n, n,
+                              p.flags ? p.flags + (size_t)r0 * n : nullptr, nullptr, split, ws, s,
+                              p) != cudaSuccess ||
+                cudaEventRecord(hs.ev[E_C + r], s) != cudaSuccess)
+                return DDGEMM_ECUDA;
+        }
+    }
+    // C back, chunk by chunk as each is done (all enqueued after the kernels,
+    // so that a pageable destination, which makes a copy wait on the host,
+    // cannot hold back a launch)
+    for (int r = 0; r < nchunks; ++r) {
+        const int r0 = r * H.mc, mr = std::min(H.mc, m - r0);
+        if (cudaStreamWaitEvent(hs.d2h, hs.ev[E_C + r], 0) != cudaSuccess ||
+            !copy2d(C_hi + (size_t)r0 * ldc, ldc, c_hi + (size_t)r0 * n, n, n, mr, hs.d2h) ||
+            !copy2d(C_lo + (size_t)r0 * ldc, ldc, c_lo + (size_t)r0 * n, n, n, mr, hs.d2h))
+            return DDGEMM_ECUDA;
+    }
+    // the caller's stream ends after the last copy
+    return after(s, hs.d2h, hs.ev[HostStreams::MAX_EVENTS - 1]) ? DDGEMM_OK : DDGEMM_ECUDA;
 }
 
 int ddgemm_split_int8_a(int m, int k, const double *A_hi, const double *A_lo, int lda,

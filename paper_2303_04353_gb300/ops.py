@@ -101,6 +101,68 @@ def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, wo
     return c_hi, c_lo
 
 
+def _check_host_pair(hi: torch.Tensor, lo: torch.Tensor, name: str) -> int:
+    if hi.dtype != torch.float64 or lo.dtype != torch.float64:
+        raise TypeError(f"{name}: hi and lo must be float64")
+    if hi.is_cuda or lo.is_cuda:
+        raise ValueError(f"{name}: ddgemm_host takes host (CPU) tensors")
+    if hi.dim() != 2 or hi.shape != lo.shape or hi.stride() != lo.stride():
+        raise ValueError(f"{name}: hi and lo must be 2-D with equal shape and strides")
+    if hi.numel() > 0 and hi.shape[1] > 1 and hi.stride(1) != 1:
+        raise ValueError(f"{name}: the last dimension must be contiguous")
+    return max(hi.stride(0), hi.shape[1], 1)
+
+
+def host_buffer_bytes(m: int, n: int, k: int, variant: int = _lib.DDGEMM_VARIANT_FP64,
+                      int8_slices: int = 0, split_k: int = 0, trans_a=False,
+                      trans_b=False) -> int:
+    return _lib.ddgemm_host_buffer_size(m, n, k, _lib.make_opts(
+        trans_a, trans_b, variant, int8_slices=int8_slices, split_k=split_k))
+
+
+def ddgemm_host(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, buffer=None,
+                device=None, status=None, stream=None, variant=_lib.DDGEMM_VARIANT_FP64,
+                int8_slices=0, split_k=0):
+    """C := op(A) op(B) on HOST (CPU) float64 tensors through ddgemm_host:
+    the library copies the operands in and C out on streams of its own,
+    overlapping the cascade on `stream`.  Use pinned tensors
+    (``pin_memory()``) for asynchronous copies.  Returns (c_hi, c_lo), host
+    tensors that hold C once `stream` has been synchronised.  Keep the input
+    tensors referenced and unchanged until then: PyTorch's pinned-memory
+    cache can hand a freed pinned block out again while the library's copy
+    still reads it.
+
+    buffer: optional device uint8 tensor of >= host_buffer_bytes() bytes
+    (allocated on `device`, default the current CUDA device, when None)."""
+    lda = _check_host_pair(a_hi, a_lo, "A")
+    ldb = _check_host_pair(b_hi, b_lo, "B")
+    m, k = (a_hi.shape[1], a_hi.shape[0]) if trans_a else tuple(a_hi.shape)
+    kb, n = (b_hi.shape[1], b_hi.shape[0]) if trans_b else tuple(b_hi.shape)
+    if k != kb:
+        raise ValueError(f"inner dimensions differ: {k} vs {kb}")
+    if out is None:
+        pin = a_hi.is_pinned()
+        c_hi = torch.empty((m, n), dtype=torch.float64, pin_memory=pin)
+        c_lo = torch.empty((m, n), dtype=torch.float64, pin_memory=pin)
+    else:
+        c_hi, c_lo = out
+        if tuple(c_hi.shape) != (m, n):
+            raise ValueError("out has the wrong shape")
+    ldc = _check_host_pair(c_hi, c_lo, "C")
+    if buffer is None:
+        nbytes = host_buffer_bytes(m, n, k, variant, int8_slices, split_k, trans_a, trans_b)
+        buffer = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device or "cuda")
+    if status is not None and (status.dtype != torch.int32 or not status.is_cuda):
+        raise TypeError("status must be an int32 CUDA tensor")
+    opts = _lib.make_opts(trans_a, trans_b, variant,
+                          status.data_ptr() if status is not None else 0,
+                          int8_slices=int8_slices, split_k=split_k)
+    _lib.ddgemm_host(m, n, k, a_hi.data_ptr(), a_lo.data_ptr(), lda, b_hi.data_ptr(),
+                     b_lo.data_ptr(), ldb, c_hi.data_ptr(), c_lo.data_ptr(), ldc,
+                     buffer.data_ptr(), buffer.numel(), current_stream_ptr(stream), opts)
+    return c_hi, c_lo
+
+
 def assemble_int8(diag: torch.Tensor, scale: torch.Tensor, *, stream=None):
     """The exact assembly of the tensor-core INT8 form on the device: for
     diag [s, count] int32 and scale [count] int32, returns (hi, lo), the
@@ -191,7 +253,7 @@ def ddgemm_backward(a_hi, a_lo, b_hi, b_lo, dc_hi, dc_lo, *, trans_a=False, tran
 def split_int8(x_hi, x_lo, *, as_b=False, trans=False, slices=15, stream=None, status=None):
     """The INT8 split of A (as_b=False; vectors = rows of op(A)) or of B
     (as_b=True; vectors = columns of op(B)).  Returns (digits [s, nvec, k]
-    int8, exps [ceil(k/16384), nvec] int32)."""
+    int8, exps [ceil(k/8192), nvec] int32)."""
     ld = _check_pair(x_hi, x_lo, "X")
     if not as_b:
         nvec, k = (x_hi.shape[1], x_hi.shape[0]) if trans else tuple(x_hi.shape)
@@ -199,7 +261,7 @@ def split_int8(x_hi, x_lo, *, as_b=False, trans=False, slices=15, stream=None, s
         k, nvec = (x_hi.shape[1], x_hi.shape[0]) if trans else tuple(x_hi.shape)
     ldd = max(16, (k + 15) // 16 * 16)
     digits = torch.zeros((slices, nvec, ldd), dtype=torch.int8, device=x_hi.device)
-    exps = torch.zeros(((k + 16383) // 16384, nvec), dtype=torch.int32, device=x_hi.device)
+    exps = torch.zeros(((k + 8191) // 8192, nvec), dtype=torch.int32, device=x_hi.device)
     fn = _lib.ddgemm_split_int8_b if as_b else _lib.ddgemm_split_int8_a
     if as_b:
         fn(k, nvec, x_hi.data_ptr(), x_lo.data_ptr(), ld, trans, slices, digits.data_ptr(), ldd,

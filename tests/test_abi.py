@@ -173,8 +173,8 @@ def test_batched_tc_host_checks():
     arr[1] = _lib.ddgemm_problem(0, 5, 6, 6, 5, 5, 0, 0, 0, 0, 0, 0)
     o = _lib.make_opts(variant=_lib.DDGEMM_VARIANT_INT8_TC)
     need = _lib.ddgemm_batched_workspace_size(2, arr, o)
-    # 15 planes (the default) of a 128 x 16 A tile and a 16 x 16 B tile, bf16
-    assert need >= 15 * (128 + 16) * 16 * 2
+    # 16 planes (the default) of a 128 x 16 A tile and a 16 x 16 B tile, bf16
+    assert need >= 16 * (128 + 16) * 16 * 2
     assert need != _lib.ddgemm_batched_workspace_size(2, arr)
     bad_s = _lib.make_opts(variant=_lib.DDGEMM_VARIANT_INT8_TC, int8_slices=18)
     assert _lib.ddgemm_batched_workspace_size(2, arr, bad_s) == 0
@@ -189,3 +189,68 @@ def test_batched_tc_host_checks():
     int8 = _lib.make_opts(variant=_lib.DDGEMM_VARIANT_INT8)
     assert lib.ddgemm_batched(2, arr, FAKE, FAKE, need, None, ctypes.byref(int8), None) == \
         _lib.DDGEMM_EUNSUPPORTED
+
+
+def host_chunk_rows(m, n, variant):
+    """The row-chunk rule of ddgemm_host, restated: at least 2048 tiles of
+    the form's kernel (64 x 64 FP64, 32 x 32 mma.sync INT8, 128 x 16 tcgen05)
+    per chunk, at most four chunks, a multiple of 128 rows."""
+    tm, tn = {_lib.DDGEMM_VARIANT_FP64: (64, 64), _lib.DDGEMM_VARIANT_INT8: (32, 32),
+              _lib.DDGEMM_VARIANT_INT8_TC: (128, 16)}[variant]
+    rows_min = -(-2048 // -(-n // tn)) * tm
+    mc = -(-max(rows_min, -(-m // 4)) // 128) * 128
+    return min(mc, m)
+
+
+@pytest.mark.parametrize("m,n,k,variant,chunks", [
+    (4096, 4096, 4096, _lib.DDGEMM_VARIANT_FP64, 2),
+    (2100, 8192, 300, _lib.DDGEMM_VARIANT_FP64, 3),
+    (4096, 4096, 4096, _lib.DDGEMM_VARIANT_INT8_TC, 4),
+    (4200, 2048, 300, _lib.DDGEMM_VARIANT_INT8_TC, 3),
+    (2500, 2048, 300, _lib.DDGEMM_VARIANT_INT8, 3),
+    (2100, 8192, 1100, _lib.DDGEMM_VARIANT_FP64, 3),
+    (100, 70, 300, _lib.DDGEMM_VARIANT_FP64, 1),
+    (100, 50, 0, _lib.DDGEMM_VARIANT_FP64, 1)])
+def test_host_buffer_size(m, n, k, variant, chunks):
+    """ddgemm_host's device buffer: dense hi/lo copies of A, B and C (each
+    plane 256-byte aligned) and ddgemm's workspace for one row chunk; the
+    shapes the GPU tests use run in the chunk counts given."""
+    def r(x):
+        return -(-x // 256) * 256
+    o = _lib.make_opts(variant=variant)
+    mc = host_chunk_rows(m, n, variant) if k else m
+    assert -(-m // mc) == chunks
+    ws = _lib.ddgemm_workspace_size(mc, n, k, o) if k else 0
+    want = 2 * r(m * k * 8) + 2 * r(k * n * 8) + 2 * r(m * n * 8) + ws
+    assert _lib.ddgemm_host_buffer_size(m, n, k, o) == want
+
+
+def test_host_entry_checks():
+    lib = _lib.load()
+
+    def host(m, n, k, lda, ldb, ldc, buf=FAKE, nbytes=1 << 40, opts=None):
+        return lib.ddgemm_host(m, n, k, FAKE, FAKE, lda, FAKE, FAKE, ldb, FAKE, FAKE, ldc, buf,
+                               nbytes, None, ctypes.byref(opts) if opts else None)
+    assert _lib.ddgemm_host_buffer_size(0, 5, 5) == 0
+    assert _lib.ddgemm_host_buffer_size(5, 5, 5, _lib.make_opts(variant=9)) == 0
+    assert _lib.ddgemm_host_buffer_size(-1, 5, 5) == 0
+    assert host(-1, 4, 4, 4, 4, 4) == _lib.DDGEMM_EINVAL
+    assert host(4, 4, 4, 3, 4, 4) == _lib.DDGEMM_EINVAL            # lda < k
+    assert host(4, 4, 4, 4, 3, 4) == _lib.DDGEMM_EINVAL            # ldb < n
+    assert host(4, 4, 4, 4, 4, 3) == _lib.DDGEMM_EINVAL            # ldc < n
+    assert host(4, 4, 4, 4, 4, 4, buf=0) == _lib.DDGEMM_EWORKSPACE
+    assert host(4, 4, 4, 4, 4, 4, buf=FAKE + 8) == _lib.DDGEMM_EWORKSPACE
+    assert host(4, 4, 4, 4, 4, 4, nbytes=16) == _lib.DDGEMM_EWORKSPACE
+    assert host(0, 4, 4, 4, 4, 4) == _lib.DDGEMM_OK                # empty: nothing to do
+    assert host(4, 4, 4, 4, 4, 4, opts=_lib.make_opts(variant=7)) == _lib.DDGEMM_EUNSUPPORTED
+    flagged = _lib.make_opts(variant=_lib.DDGEMM_VARIANT_INT8, flags_dev=FAKE)
+    assert host(4, 4, 4, 4, 4, 4, opts=flagged) == _lib.DDGEMM_EUNSUPPORTED
+    assert host(8, 4, 2, 2, 4, 4, opts=_lib.make_opts(trans_a=True)) == _lib.DDGEMM_EINVAL
+
+
+def test_host_ops_refuse_cuda_tensors():
+    torch = pytest.importorskip("torch")
+    from paper_2303_04353_gb300 import ops
+    a = torch.zeros(2, 2, dtype=torch.float32)
+    with pytest.raises(TypeError, match="float64"):
+        ops.ddgemm_host(a, a, a, a)

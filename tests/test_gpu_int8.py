@@ -37,7 +37,7 @@ def host(*tensors):
     return [t.cpu().numpy() for t in tensors]
 
 
-@pytest.mark.parametrize("nvec,k", [(37, 300), (64, 64), (5, 1), (33, 130)])
+@pytest.mark.parametrize("nvec,k", [(37, 300), (64, 64), (5, 1), (33, 130), (3, 8200)])
 @pytest.mark.parametrize("kind", ["uniform", "wide"])
 @pytest.mark.parametrize("as_b,trans", [(False, False), (False, True), (True, False), (True, True)])
 @pytest.mark.parametrize("s", [12, 14, 15])

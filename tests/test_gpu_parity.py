@@ -404,6 +404,24 @@ def test_illconditioned_product(ops):
     assert rel_errors(c_hi, c_lo, a, rows, cols).max() * 3 < rel_errors(o_hi, o_lo, a, rows, cols).max()
 
 
+def test_illconditioned_product_int8(ops):
+    """The same product through the INT8 form on mma.sync (15 eight-bit
+    pieces): bit-identical to its restatement, and like it more accurate
+    than the FP64x2 triple loop."""
+    from oracle import cascade_int8 as c8
+    from workloads.illcond import illcond_inputs
+    from tests.test_illcond import rel_errors
+    n = 128
+    a = illcond_inputs(n, 1e-19, seed=n)[:4]
+    c_hi, c_lo = host(*ops.ddgemm(*dev(*a), variant=1))
+    w_hi, w_lo = c8.cascade_int8_ddgemm(*a, s=15)
+    assert np.array_equal(c_hi, w_hi) and np.array_equal(c_lo, w_lo)
+    rng = np.random.default_rng(2)
+    rows, cols = rng.integers(0, n, 40), rng.integers(0, n, 40)
+    o_hi, o_lo = dd.ddgemm(*a)
+    assert rel_errors(c_hi, c_lo, a, rows, cols).max() * 3 < rel_errors(o_hi, o_lo, a, rows, cols).max()
+
+
 def test_bounded_wait_reports_timeout_and_context_survives(ops):
     """A wait that nothing ends gives up after its limit and reports
     DDGEMM_DEV_TIMEOUT in the status word (the kernels' failure path), and

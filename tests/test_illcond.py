@@ -57,3 +57,17 @@ def test_cascade_more_accurate_than_fp64x2_loop(n, t):
     e_casc = rel_errors(c_hi, c_lo, a, rows, cols)
     e_dd = rel_errors(o_hi, o_lo, a, rows, cols)
     assert e_casc.max() * 10 < e_dd.max()
+
+
+@pytest.mark.parametrize("n,t", [(64, 1e-14), (96, 1e-19)])
+def test_int8_eight_bit_pieces_more_accurate_than_fp64x2_loop(n, t):
+    """The INT8 form with 15 eight-bit pieces (F = 118 fraction bits below
+    the block scale) also beats the FP64x2 triple loop on these products;
+    the seven-bit form with 16 pieces (F = 111) does not have that margin."""
+    from oracle import cascade_int8 as c8
+    a = illcond_inputs(n, t, seed=n)[:4]
+    rng = np.random.default_rng(1)
+    rows, cols = rng.integers(0, n, 50), rng.integers(0, n, 50)
+    c_hi, c_lo = c8.cascade_int8_ddgemm(*a, s=15)
+    o_hi, o_lo = dd.ddgemm(*a)
+    assert rel_errors(c_hi, c_lo, a, rows, cols).max() * 3 < rel_errors(o_hi, o_lo, a, rows, cols).max()
