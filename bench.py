@@ -343,13 +343,16 @@ def run_ours(args, wl):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    e2e_sampler = ClockSampler(physical_index(local))
     barrier()
     torch.cuda.synchronize()
+    e2e_sampler.start()
     e0.record(stream)
     for _ in range(e2e_steps):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
+    e2e_clocks = e2e_sampler.stop()
     e2e_ms = reduce_max(e0.elapsed_time(e1) / e2e_steps, world, dev)
     h2d = sum(h.numel() * 8 for h in host_in)
     d2h = 2 * m * n * 8
@@ -512,7 +515,7 @@ def run_ours(args, wl):
                 "ms_per_step": round(e2e_ms, 3),
                 "path": "ddgemm_host: pinned host operands, library copy streams overlapping "
                         "the cascade in row chunks",
-                "max_err_vs_dd_oracle": e2e_err},
+                "max_err_vs_dd_oracle": e2e_err, "clocks": e2e_clocks},
         # FP64 form: split A, split B, the cascade kernel, the split-k fix-up;
         # INT8 forms: exponents and digits of A and of B, the cascade kernel
         "gpu_launches": ((3 + (groups > 1)) if variant == _lib.DDGEMM_VARIANT_FP64 else 5)
