@@ -341,6 +341,17 @@ def run_ours(args, wl):
                         variant=variant, int8_slices=args.int8_slices)
     e2e_step()                               # warm-up (first-use costs of the copy path)
     torch.cuda.synchronize()
+    # the host link's rate right now (it varies on a shared host): one plain
+    # copy of A_hi in and of C_hi out, outside the timed region
+    c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    c0.record(stream)
+    d_in[0].copy_(host_in[0], non_blocking=True)
+    c1.record(stream)
+    host_out[0].copy_(c_hi, non_blocking=True)
+    c2.record(stream)
+    torch.cuda.synchronize()
+    link = {"h2d_GBs": round(m * k * 8 / (c0.elapsed_time(c1) * 1e-3) / 1e9, 1),
+            "d2h_GBs": round(m * n * 8 / (c1.elapsed_time(c2) * 1e-3) / 1e9, 1)}
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e2e_sampler = ClockSampler(physical_index(local))
@@ -515,7 +526,8 @@ def run_ours(args, wl):
                 "ms_per_step": round(e2e_ms, 3),
                 "path": "ddgemm_host: pinned host operands, library copy streams overlapping "
                         "the cascade in row chunks",
-                "max_err_vs_dd_oracle": e2e_err, "clocks": e2e_clocks},
+                "max_err_vs_dd_oracle": e2e_err, "clocks": e2e_clocks,
+                "link_before": link},
         # FP64 form: split A, split B, the cascade kernel, the split-k fix-up;
         # INT8 forms: exponents and digits of A and of B, the cascade kernel
         "gpu_launches": ((3 + (groups > 1)) if variant == _lib.DDGEMM_VARIANT_FP64 else 5)

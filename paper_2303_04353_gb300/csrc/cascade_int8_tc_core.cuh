@@ -384,13 +384,13 @@ cascade_int8_tc_kernel(const Src src) {
                         const uint32_t a0 = smem_addr(smem + stage * G::STAGE);
                         const uint64_t bdesc = umma::desc_k_sw32(a0 + G::A_STAGE);
                         // planes in the order 0, S-1, 1, S-2, ...: a narrow MMA
-                        // (plane i near S, N = 16 (S - i) below 128) follows a
-                        // wide one.  An M = 128, K = 16 MMA takes at least the
-                        // time of N = 128, so the narrow ones are the triangle's
-                        // waste; interleaved they overlap the wide ones better
-                        // (measured 3 % on the MMA pipe alone).  Plane 0 comes
-                        // first: its MMA covers every column of the set and
-                        // starts the chunk's sums (accumulate = 0).
+                        // (plane i near S, N = 16 (S - i)) follows a wide one.
+                        // A narrow M = 128, K = 16 MMA takes about as long as a
+                        // much wider one, so the narrow ones are the triangle's
+                        // waste; interleaved with the wide ones they cost less
+                        // (measured: 5 % less kernel time at 4096^3).  Plane 0
+                        // comes first: its MMA covers every column of the set
+                        // and starts the chunk's sums (accumulate = 0).
 #pragma unroll
                         for (int q = 0; q < S; ++q) {
                             const int i = (q & 1) ? S - 1 - (q >> 1) : (q >> 1);
