@@ -54,6 +54,8 @@ TRAFFIC_4096 = {"cascade_fp64_kernel": 9.879882e9 + 0.281523e9,
                 "cascade_int8_kernel<15>": 2.923206e9 + 0.268134e9,
                 "cascade_int8_tc_kernel<16>": 9.123969e9 + 0.347044e9}
 
+VARIANT_NAMES = {1: "int8", 4: "int8 on tcgen05", 5: "int8 on tcgen05, eight-bit pieces"}
+
 WORKLOADS = {
     "4096": dict(m=4096, n=4096, k=4096, kind="wide",
                  name="ddgemm 4096x4096x4096 FP64x2, hi log-uniform 2^-20..2^20, seed 0"),
@@ -263,7 +265,8 @@ def run_ours(args, wl):
     d_in = [h.to(dev) for h in host_in]
     c_hi = torch.empty((m, n), dtype=torch.float64, device=dev)
     c_lo = torch.empty((m, n), dtype=torch.float64, device=dev)
-    variant = {"int8": _lib.DDGEMM_VARIANT_INT8, "int8tc": _lib.DDGEMM_VARIANT_INT8_TC}.get(
+    variant = {"int8": _lib.DDGEMM_VARIANT_INT8, "int8tc": _lib.DDGEMM_VARIANT_INT8_TC,
+               "int8tc8": _lib.DDGEMM_VARIANT_INT8_TC8}.get(
         args.variant, _lib.DDGEMM_VARIANT_FP64)
     if not args.int8_slices:   # each form's default: 15 eight-bit / 16 seven-bit pieces
         args.int8_slices = 16 if variant == _lib.DDGEMM_VARIANT_INT8_TC else 15
@@ -420,11 +423,15 @@ def run_ours(args, wl):
                 "max_err_vs_dd_oracle": float(np.max(err8 / absab)),
                 "speedup_vs_fp64_form": round(ms_per_step / ms8, 3)}
 
-    int8_form = int8_tc_form = None
+    int8_form = int8_tc_form = int8_tc8_form = None
     if variant == _lib.DDGEMM_VARIANT_FP64 and not args.no_int8_form:
         int8_form = time_form(_lib.DDGEMM_VARIANT_INT8)
         int8_form["products_on"] = "mma.sync m16n8k32 s8 (int32 accumulation)"
         int8_tc_form = time_form(_lib.DDGEMM_VARIANT_INT8_TC)
+        int8_tc8_form = time_form(_lib.DDGEMM_VARIANT_INT8_TC8)
+        int8_tc8_form["products_on"] = ("tcgen05.mma kind::f16, the mma.sync form's eight-bit "
+                                        "digits in bf16, FP32 in TMEM (exact per 64 entries); "
+                                        "exact assembly")
         int8_tc_form["products_on"] = ("tcgen05.mma kind::f16, bf16 digits, FP32 in TMEM "
                                        "(exact per 256 entries); exact assembly")
 
@@ -453,21 +460,24 @@ def run_ours(args, wl):
             dgemm["int8_form_over_dgemm"] = round(int8_form["ms_per_step"] / dg_ms, 3)
         if int8_tc_form is not None:
             dgemm["int8_tc_form_over_dgemm"] = round(int8_tc_form["ms_per_step"] / dg_ms, 3)
+        if int8_tc8_form is not None:
+            dgemm["int8_tc8_form_over_dgemm"] = round(int8_tc8_form["ms_per_step"] / dg_ms, 3)
         del z
 
     if rank != 0:
         return
     peak, peak_src = fp64_peak_rule()
-    if variant == _lib.DDGEMM_VARIANT_INT8_TC:
+    if variant in (_lib.DDGEMM_VARIANT_INT8_TC, _lib.DDGEMM_VARIANT_INT8_TC8):
         s8 = args.int8_slices
         prods = s8 * (s8 + 1) // 2
         achieved = prods * flops_dd / (casc_ms * 1e-3) / 1e12
         bpeak, bsrc, spk = bf16_peaks()
-        roofline = {"bound": "tensor", "kernel": f"cascade_int8_tc_kernel<{s8}>",
+        kname = (f"cascade_int8_tc_kernel<{s8}>" if variant == _lib.DDGEMM_VARIANT_INT8_TC
+                 else f"cascade_int8_tc_kernel<{s8}> (eight-bit pieces)")
+        roofline = {"bound": "tensor", "kernel": kname,
                     "achieved": round(achieved, 3), "peak": round(bpeak, 3), "unit": "TFLOP/s",
                     "frac": round(achieved / bpeak, 4),
-                    "traffic": TRAFFIC_4096.get(f"cascade_int8_tc_kernel<{s8}>")
-                    if args.workload == "4096" else None,
+                    "traffic": TRAFFIC_4096.get(kname) if args.workload == "4096" else None,
                     "peak_source": bsrc,
                     "frac_vs_sustained": round(achieved / spk, 4) if spk else None,
                     "algorithmic": f"{prods} x 2mnk = {prods * flops_dd:.4g} bf16 flops "
@@ -502,7 +512,7 @@ def run_ours(args, wl):
         "data": "synthetic",
         "config": {"workload": wl["name"], "m": m, "n": n, "k": k,
                    "variant": "fp64 (ten FP64 products)" if variant == _lib.DDGEMM_VARIANT_FP64
-                   else f"{'int8 on tcgen05' if variant == _lib.DDGEMM_VARIANT_INT8_TC else 'int8'}"
+                   else f"{VARIANT_NAMES[variant]}"
                         f" ({args.int8_slices} pieces, "
                         f"{args.int8_slices * (args.int8_slices + 1) // 2} digit products)",
                    "split_k_groups": groups,
@@ -538,6 +548,8 @@ def run_ours(args, wl):
         line["int8_form"] = int8_form
     if int8_tc_form is not None:
         line["int8_tc_form"] = int8_tc_form
+    if int8_tc8_form is not None:
+        line["int8_tc8_form"] = int8_tc8_form
     if dgemm is not None:
         line["dgemm_yardstick"] = dgemm
     if world == 1 and not args.no_cpu_baseline:
@@ -743,7 +755,9 @@ def run_illcond(args):
             res = {}
             for name, variant in (("cascade fp64", _lib.DDGEMM_VARIANT_FP64),
                                   ("cascade int8 s=15", _lib.DDGEMM_VARIANT_INT8),
-                                  ("cascade int8 tcgen05 s=16", _lib.DDGEMM_VARIANT_INT8_TC)):
+                                  ("cascade int8 tcgen05 s=16", _lib.DDGEMM_VARIANT_INT8_TC),
+                                  ("cascade int8 tcgen05 eight-bit s=15",
+                                   _lib.DDGEMM_VARIANT_INT8_TC8)):
                 c = ops.ddgemm(*d_in, variant=variant)
                 torch.cuda.synchronize()
                 res[name] = worst(c[0].cpu().numpy(), c[1].cpu().numpy())
@@ -813,7 +827,8 @@ def run_sweep(args):
     rows, cols = rng.integers(0, m, 128), rng.integers(0, n, 128)
     forms = [("fp64", _lib.DDGEMM_VARIANT_FP64, 0)] + [
         (f"int8 s={s8}", _lib.DDGEMM_VARIANT_INT8, s8) for s8 in (13, 14, 15)] + [
-        (f"int8 tcgen05 s={s8}", _lib.DDGEMM_VARIANT_INT8_TC, s8) for s8 in (14, 15, 16)]
+        (f"int8 tcgen05 s={s8}", _lib.DDGEMM_VARIANT_INT8_TC, s8) for s8 in (14, 15, 16)] + [
+        (f"int8 tcgen05 eight-bit s={s8}", _lib.DDGEMM_VARIANT_INT8_TC8, s8) for s8 in (14, 15)]
     for spread in range(0, 61, 10):
         a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind="wide", seed=0, spread=float(spread))
         d_in = [torch.from_numpy(x).to(dev) for x in (a_hi, a_lo, b_hi, b_lo)]
@@ -853,9 +868,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-int8-form", action="store_true",
                     help="skip the INT8 form's entry in the FP64 line")
-    ap.add_argument("--variant", choices=("fp64", "int8", "int8tc"), default="fp64",
+    ap.add_argument("--variant", choices=("fp64", "int8", "int8tc", "int8tc8"), default="fp64",
                     help="fp64: the ten FP64 products (default); int8: the INT8 form on "
-                         "mma.sync s8; int8tc: the INT8 form on the tcgen05 tensor cores")
+                         "mma.sync s8; int8tc: the INT8 form on the tcgen05 tensor cores; "
+                         "int8tc8: the same with the mma.sync form's eight-bit pieces")
     ap.add_argument("--int8-slices", type=int, default=0,
                     help="pieces of the INT8 forms; 0: 15 eight-bit (mma.sync) or 16 "
                          "seven-bit (tcgen05)")

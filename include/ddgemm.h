@@ -66,8 +66,10 @@ extern "C" {
                                          dropped (ten products, not folded) */
 /* The INT8 form with its digit products on the fifth-generation tensor
  * cores (tcgen05.mma, bf16 digits, FP32 accumulation, exact) and the exact
- * assembly (below): */
+ * assembly (below): seven-bit pieces (INT8_TC), or the mma.sync form's
+ * eight-bit pieces and accuracy (INT8_TC8): */
 #define DDGEMM_VARIANT_INT8_TC 4
+#define DDGEMM_VARIANT_INT8_TC8 5
 
 typedef struct ddgemm_opts {
     /* 0: A is m x k (lda >= k).  1: A is stored k x m (lda >= m) and the
@@ -100,7 +102,15 @@ typedef struct ddgemm_opts {
      * sum_t S_t 2^(-12-7t) sigma tau is formed exactly and rounded once to
      * the nearest FP64x2 (hi = RN(x), lo = RN(x - hi)) before the FP64x2
      * add into C: a more accurate reading of "add the results across bins
-     * in FP64x2" than the smallest-first sum.  flags_dev is not supported. */
+     * in FP64x2" than the smallest-first sum.  flags_dev is not supported.
+     *
+     * INT8_TC8: INT8_TC with the eight-bit pieces of INT8 (balanced
+     * base-256 digits, F = 6 + 8 (s - 1), k-blocks of 8192, s in 12..15):
+     * the fixed point and accuracy of INT8 at the speed of the tensor
+     * cores.  An eight-bit product is at most 2^14, so the FP32
+     * accumulators are read out every 64 entries instead of 256, which
+     * makes it slower than INT8_TC.  Assembly as for INT8_TC, with weights
+     * 2^(-12-8t).  Not available to ddgemm_batched(). */
     int variant;
     /* Optional device word (or NULL): DDGEMM_DEV_* bits are OR-ed into it.
      * The library never clears it. */
@@ -120,7 +130,7 @@ typedef struct ddgemm_opts {
     /* INT8 forms only: pieces per entry, s (s + 1) / 2 digit products per k.
      * INT8: s in {12, 13, 14, 15}, 0 = 15 (the paper estimates 14-15; 120
      * products).  INT8_TC: s in {12, ..., 16}, 0 = 16 (seven-bit pieces;
-     * 136 products). */
+     * 136 products).  INT8_TC8: s in {12, ..., 15}, 0 = 15. */
     int int8_slices;
     /* FP64 forms: split-k over whole 256-entry k-blocks when a grid of 64 x 64
      * tiles would leave SMs idle.  Group g of a tile sums its run of k-blocks

@@ -204,3 +204,9 @@ def cascade_int8_tc_ddgemm(a_hi, a_lo, b_hi, b_lo, s=16):
     """The tcgen05 form's product: seven-bit pieces (k-blocks of 16384) and
     the exact assembly."""
     return cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=s, assembly="exact", bits=BITS_TC)
+
+
+def cascade_int8_tc8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=15):
+    """The tcgen05 form with the mma.sync form's eight-bit pieces (k-blocks
+    of 8192) and the exact assembly."""
+    return cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=s, assembly="exact", bits=BITS)

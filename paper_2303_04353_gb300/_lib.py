@@ -24,6 +24,7 @@ DDGEMM_VARIANT_INT8 = 1
 DDGEMM_VARIANT_FP64_GEMM16 = 2
 DDGEMM_VARIANT_FP64_DROP456 = 3
 DDGEMM_VARIANT_INT8_TC = 4
+DDGEMM_VARIANT_INT8_TC8 = 5
 
 
 class DdgemmError(RuntimeError):

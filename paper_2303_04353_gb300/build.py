@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "split.cu", "cascade_fp64.cu", "probe.cu", "noalloc.cu", "split_int8.cu",
-           "cascade_int8.cu", "cascade_int8_tc.cu", "batched.cu", "batched_int8_tc.cu"]
+           "cascade_int8.cu", "cascade_int8_tc.cu", "cascade_int8_tc8.cu", "batched.cu",
+           "batched_int8_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                      "-I" + INCLUDE, "-I" + CSRC]

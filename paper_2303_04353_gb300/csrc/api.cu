@@ -73,7 +73,16 @@ struct Parsed {
 };
 
 bool is_int8(int variant) {
-    return variant == DDGEMM_VARIANT_INT8 || variant == DDGEMM_VARIANT_INT8_TC;
+    return variant == DDGEMM_VARIANT_INT8 || variant == DDGEMM_VARIANT_INT8_TC ||
+           variant == DDGEMM_VARIANT_INT8_TC8;
+}
+
+// The INT8 forms on the tcgen05 tensor cores, and their digit widths.
+bool is_tc(int variant) {
+    return variant == DDGEMM_VARIANT_INT8_TC || variant == DDGEMM_VARIANT_INT8_TC8;
+}
+int int8_bits(int variant) {
+    return variant == DDGEMM_VARIANT_INT8_TC ? ddg::INT8_TC_BITS : ddg::INT8_BITS;
 }
 
 // Workspace carve of the INT8 forms: digit planes of A and B (int8, or bf16
@@ -85,11 +94,11 @@ struct Layout8 {
 
 Layout8 layout8_for(int m, int n, int k, int slices, int variant) {
     Layout8 L;
-    const int blk = variant == DDGEMM_VARIANT_INT8_TC ? ddg::KB8_TC : ddg::KB8;
+    const int blk = ddg::kblock_of_bits(int8_bits(variant));
     const long long kb = (k + blk - 1) / blk;
     L.ld = (long long)round_up((size_t)k, 64);
     L.off_a = 0;
-    if (variant == DDGEMM_VARIANT_INT8_TC) {
+    if (is_tc(variant)) {
         // bf16 digits in whole tiles of 128 rows (A) and 16 columns (B) by
         // k-steps of 16
         const size_t kpad = round_up((size_t)k, 16);
@@ -118,10 +127,13 @@ bool parse(const ddgemm_opts *o, Parsed &p) {
     }
     if (p.split_k < 0) return false;
     if (p.slices == 0)
-        p.slices = p.variant == DDGEMM_VARIANT_INT8_TC ? ddg::INT8_TC_SLICES_DEFAULT
-                                                       : ddg::INT8_SLICES_DEFAULT;
+        p.slices = p.variant == DDGEMM_VARIANT_INT8_TC    ? ddg::INT8_TC_SLICES_DEFAULT
+                   : p.variant == DDGEMM_VARIANT_INT8_TC8 ? ddg::INT8_TC8_SLICES_DEFAULT
+                                                          : ddg::INT8_SLICES_DEFAULT;
     if (p.variant == DDGEMM_VARIANT_INT8 && !ddg::int8_slices_supported(p.slices)) return false;
     if (p.variant == DDGEMM_VARIANT_INT8_TC && !ddg::int8_tc_slices_supported(p.slices))
+        return false;
+    if (p.variant == DDGEMM_VARIANT_INT8_TC8 && !ddg::int8_tc8_slices_supported(p.slices))
         return false;
     return (p.trans_a == 0 || p.trans_a == 1) && (p.trans_b == 0 || p.trans_b == 1);
 }
@@ -210,9 +222,9 @@ int sm_count(int &sms) {
 cudaError_t split_b_into(const Carve &c, int n, int k, const double *B_hi, const double *B_lo,
                          int ldb, char *ws, cudaStream_t s, const Parsed &p) {
     if (c.int8) {
-        const bool tc = p.variant == DDGEMM_VARIANT_INT8_TC;
         return ddg::launch_split_int8(p.slices, n, k, B_hi, B_lo, ldb, p.trans_b != 0,
-                                      ws + c.L8.off_b, tc ? ddg::INT8_TC_BN : 0, c.L8.ld,
+                                      ws + c.L8.off_b, is_tc(p.variant) ? ddg::INT8_TC_BN : 0,
+                                      int8_bits(p.variant), c.L8.ld,
                                       reinterpret_cast<int *>(ws + c.L8.off_eb), p.status, s);
     }
     return ddg::launch_split(7, n, k, B_hi, B_lo, ldb, p.trans_b != 0,
@@ -226,9 +238,9 @@ cudaError_t split_b_into(const Carve &c, int n, int k, const double *B_hi, const
 cudaError_t split_a_into(const Carve &c, int mr, int k, const double *A_hi, const double *A_lo,
                          int lda, char *ws, cudaStream_t s, const Parsed &p) {
     if (c.int8) {
-        const bool tc = p.variant == DDGEMM_VARIANT_INT8_TC;
         return ddg::launch_split_int8(p.slices, mr, k, A_hi, A_lo, lda, !p.trans_a,
-                                      ws + c.L8.off_a, tc ? ddg::INT8_TC_BM : 0, c.L8.ld,
+                                      ws + c.L8.off_a, is_tc(p.variant) ? ddg::INT8_TC_BM : 0,
+                                      int8_bits(p.variant), c.L8.ld,
                                       reinterpret_cast<int *>(ws + c.L8.off_ea), p.status, s);
     }
     return ddg::launch_split(4, mr, k, A_hi, A_lo, lda, !p.trans_a,
@@ -247,8 +259,9 @@ cudaError_t products_into(const Carve &c, int mr, int n, int k, double *C_hi, do
         const Layout8 &L = c.L8;
         const int *e_a = reinterpret_cast<const int *>(ws + L.off_ea);
         const int *e_b = reinterpret_cast<const int *>(ws + L.off_eb);
-        if (p.variant == DDGEMM_VARIANT_INT8_TC) {
-            ddg::Int8TcArgs a{mr, n, k, p.slices, reinterpret_cast<const uint16_t *>(ws + L.off_a),
+        if (is_tc(p.variant)) {
+            ddg::Int8TcArgs a{mr, n, k, p.slices, int8_bits(p.variant),
+                              reinterpret_cast<const uint16_t *>(ws + L.off_a),
                               reinterpret_cast<const uint16_t *>(ws + L.off_b), e_a, e_b, C_hi,
                               C_lo, (long long)ldc, p.status};
             return ddg::launch_cascade_int8_tc(a, s);
@@ -324,7 +337,7 @@ constexpr long long HOST_MIN_TILES = 2048;
 // HOST_MAX_CHUNKS chunks; a multiple of 128 (every form's tile height divides it).
 int host_chunk_rows(int m, int n, const Parsed &p) {
     int tm = 64, tn = 64;
-    if (p.variant == DDGEMM_VARIANT_INT8_TC) {
+    if (is_tc(p.variant)) {
         tm = ddg::INT8_TC_BM;
         tn = ddg::INT8_TC_BN;
     } else if (p.variant == DDGEMM_VARIANT_INT8) {
@@ -434,7 +447,7 @@ int ddgemm(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
            void *workspace, size_t ws_bytes, void *stream, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
-    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_INT8_TC)
+    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_INT8_TC8)
         return DDGEMM_EUNSUPPORTED;
     if (is_int8(p.variant) && p.flags) return DDGEMM_EUNSUPPORTED;
     if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;
@@ -456,7 +469,7 @@ int ddgemm(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
 size_t ddgemm_host_buffer_size(int m, int n, int k, const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return 0;
-    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_INT8_TC) return 0;
+    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_INT8_TC8) return 0;
     if (m == 0 || n == 0) return 0;
     return host_layout(m, n, k, p).total;
 }
@@ -467,7 +480,7 @@ int ddgemm_host(int m, int n, int k, const double *A_hi, const double *A_lo, int
                 const ddgemm_opts *opts) {
     Parsed p;
     if (!parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
-    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_INT8_TC)
+    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_INT8_TC8)
         return DDGEMM_EUNSUPPORTED;
     if (is_int8(p.variant) && p.flags) return DDGEMM_EUNSUPPORTED;
     if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;
@@ -560,7 +573,7 @@ int ddgemm_split_int8_a(int m, int k, const double *A_hi, const double *A_lo, in
         ld_digits % 16)
         return DDGEMM_EINVAL;
     const cudaError_t e = ddg::launch_split_int8(slices, m, k, A_hi, A_lo, lda, !trans_a, digits,
-                                                 0, ld_digits, exps, status_dev,
+                                                 0, ddg::INT8_BITS, ld_digits, exps, status_dev,
                                                  static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }
@@ -575,7 +588,8 @@ int ddgemm_split_int8_b(int k, int n, const double *B_hi, const double *B_lo, in
         ld_digits % 16)
         return DDGEMM_EINVAL;
     const cudaError_t e = ddg::launch_split_int8(slices, n, k, B_hi, B_lo, ldb, trans_b != 0,
-                                                 digits, 0, ld_digits, exps, status_dev,
+                                                 digits, 0, ddg::INT8_BITS, ld_digits, exps,
+                                                 status_dev,
                                                  static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }

@@ -305,7 +305,7 @@ cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, lon
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || tiles == 0) return e;
     using G = TcGeom<S>;
-    auto kernel = cascade_int8_tc_kernel<S, 1, BatchSource>;
+    auto kernel = cascade_int8_tc_kernel<S, INT8_TC_BITS, 1, BatchSource>;
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)G::SMEM)) != cudaSuccess)
         return e;

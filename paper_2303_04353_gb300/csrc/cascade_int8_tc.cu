@@ -59,43 +59,6 @@
 namespace ddg {
 namespace {
 
-template <int S, int CL>
-cudaError_t launch_tc_cl(const Int8TcArgs &a, cudaStream_t stream) {
-    using G = TcGeom<S>;
-    auto kernel = cascade_int8_tc_kernel<S, CL, SingleSource>;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::SMEM);
-    if (e != cudaSuccess) return e;
-    const long long tiles_n = (a.n + BN - 1) / BN;
-    const long long groups = (long long)((a.m + BM - 1) / BM) * ((tiles_n + CL - 1) / CL);
-    if (groups > 0x7fffffffLL) return cudaErrorInvalidValue;
-    SingleSource src;
-    src.a = a;
-    src.tiles_m = (a.m + BM - 1) / BM;
-    src.tiles_n = (int)tiles_n;
-    src.groups_n = (int)((tiles_n + CL - 1) / CL);
-    src.cl = CL;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    cfg.blockDim = dim3(NTHREADS);
-    cfg.dynamicSmemBytes = G::SMEM;
-    cfg.stream = stream;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    // persistent: as many clusters as can be resident at once
-    int clusters = 0;
-    cfg.gridDim = dim3(CL);
-    if ((e = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg)) != cudaSuccess) return e;
-    if (clusters <= 0) return cudaErrorInvalidConfiguration;
-    const long long use = groups < clusters ? groups : clusters;
-    cfg.gridDim = dim3((unsigned)(use * CL));
-    return cudaLaunchKernelEx(&cfg, kernel, src);
-}
-
 // Cluster size: CTAs along n that share A by multicast copies.  Measured on
 // GB300 at 2048^3 and 4096^3: 2 is as fast as 1 (the L2 reads A causes do
 // not limit the kernel) and 4 is 5-7 % slower (fewer SMs hold whole
@@ -109,9 +72,9 @@ cudaError_t launch_tc(const Int8TcArgs &a, cudaStream_t stream) {
         const int v = atoi(env);
         if (v == 1 || v == 2 || v == 4) cl = v;
     }
-    if (cl == 4) return launch_tc_cl<S, 4>(a, stream);
-    if (cl == 2) return launch_tc_cl<S, 2>(a, stream);
-    return launch_tc_cl<S, 1>(a, stream);
+    if (cl == 4) return launch_tc_cl<S, INT8_TC_BITS, 4>(a, stream);
+    if (cl == 2) return launch_tc_cl<S, INT8_TC_BITS, 2>(a, stream);
+    return launch_tc_cl<S, INT8_TC_BITS, 1>(a, stream);
 }
 
 template <int S>
@@ -122,14 +85,18 @@ assemble_kernel(int count, const int *__restrict__ diag, const int *__restrict__
     if (i >= count) return;
     __int128 H = 0, L = 0;
 #pragma unroll
-    for (int t = 0; t < S; ++t) add_diagonal<S>(t, diag[(long long)t * count + i], H, L);
-    round_dd(H, L, scale[i] - 12 - TB * (S - 1), hi[i], lo[i]);
+    for (int t = 0; t < S; ++t)
+        add_diagonal<S, INT8_TC_BITS>(t, diag[(long long)t * count + i], H, L);
+    round_dd<TcWidth<INT8_TC_BITS>::SPLIT>(H, L, scale[i] - 12 - INT8_TC_BITS * (S - 1), hi[i],
+                                           lo[i]);
 }
 
 }  // namespace
 
 cudaError_t launch_cascade_int8_tc(const Int8TcArgs &a, cudaStream_t stream) {
     if (a.m <= 0 || a.n <= 0 || a.k <= 0) return cudaSuccess;
+    if (a.bits == INT8_BITS) return launch_cascade_int8_tc8(a, stream);
+    if (a.bits != INT8_TC_BITS) return cudaErrorInvalidValue;
     switch (a.slices) {
         case 12: return launch_tc<12>(a, stream);
         case 13: return launch_tc<13>(a, stream);

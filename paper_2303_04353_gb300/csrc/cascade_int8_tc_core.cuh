@@ -16,14 +16,19 @@ namespace ddg {
 namespace {
 
 constexpr int BM = INT8_TC_BM, BN = INT8_TC_BN, BK = 16;
-// Digit width of this form's pieces, and the chunk over which an FP32
-// accumulator stays exact: up to 16 products of |digit| <= 2^(TB-1) per
-// entry, so 2^24 / (16 2^(2 TB - 2)) entries (256 for seven bits).
-constexpr int TB = INT8_TC_BITS;
-constexpr int CHUNK_STEPS = (1 << 24) / (16 << (2 * TB - 2)) / 16;  // k-steps of 16 per chunk
-constexpr int BLOCK_CHUNKS = KB8_TC / (BK * CHUNK_STEPS);           // chunks per k-block
-constexpr int SPLIT = 8 * TB;   // T = H 2^SPLIT + L: L holds the eight smallest diagonals
-static_assert(CHUNK_STEPS >= 1 && SPLIT <= 64, "digit width");
+// What follows from the digit width TB of the pieces: the chunk over which
+// an FP32 accumulator stays exact (up to 16 products of |digit| <= 2^(TB-1)
+// per entry, so 2^24 / (16 2^(2 TB - 2)) entries: 256 for seven bits, 64
+// for eight), the chunks per k-block, and the split of a block value
+// T = H 2^SPLIT + L (L holds the eight smallest diagonals).
+template <int TB>
+struct TcWidth {
+    static constexpr int CHUNK_STEPS = (1 << 24) / (16 << (2 * TB - 2)) / 16;  // k-steps of 16
+    static constexpr int BLOCK_CHUNKS = kblock_of_bits(TB) / (BK * CHUNK_STEPS);
+    static constexpr int SPLIT = 8 * TB;
+    static_assert(TB == 7 || TB == 8, "seven- or eight-bit pieces");
+    static_assert(CHUNK_STEPS >= 1 && SPLIT <= 64, "digit width");
+};
 constexpr int EPI_WARPS = 8;
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
 constexpr uint32_t TMEM_COLS = 512;
@@ -101,6 +106,7 @@ __device__ __forceinline__ double round_int(__int128 r, int e) {
 
 // The FP64x2 nearest to T 2^e with T = H 2^SPLIT + L (|H| < 2^80,
 // |L| < 2^90, SPLIT <= 64): hi = RN(T 2^e), lo = RN(T 2^e - hi).
+template <int SPLIT>
 __device__ __forceinline__ void round_dd(__int128 H, __int128 L, int e, double &hi, double &lo) {
     // carry L's bits above 2^SPLIT into H: T = H1 2^SPLIT + L0,
     // 0 <= L0 < 2^SPLIT (floor division)
@@ -163,7 +169,7 @@ __device__ __forceinline__ void round_dd(__int128 H, __int128 L, int e, double &
 // Diagonal t's term of T = sum_t S_t 2^(TB (s-1-t)) = H 2^SPLIT + L: the
 // eight smallest diagonals go to L, the others to H (multiplications by
 // powers of two: shifts of negative values are not defined in C++17).
-template <int S>
+template <int S, int TB>
 __device__ __forceinline__ void add_diagonal(int t, int v, __int128 &H, __int128 &L) {
     if (t < S - 8)
         H += (__int128)v * ((__int128)1 << (TB * (S - 9 - t)));
@@ -177,7 +183,7 @@ __device__ __forceinline__ void add_diagonal(int t, int v, __int128 &H, __int128
 // earlier one 2^TB more.  Four diagonals at a time are combined exactly in
 // an int64 (|sum| <= 2^24 per diagonal and chunk, so below 2^(25 + 3 TB)),
 // then added in.
-template <int S, int T0, int T1>
+template <int S, int TB, int T0, int T1>
 __device__ __forceinline__ void fold_group(uint32_t base, __int128 (&acc)[8]) {
     static_assert(T1 - T0 <= 8 && T1 > T0, "a half holds 1 to 8 diagonals");
 #pragma unroll
@@ -261,10 +267,12 @@ struct SingleSource {
     }
 };
 
-template <int S, int CL, class Src>
+template <int S, int TB, int CL, class Src>
 __global__ void __launch_bounds__(NTHREADS, 1)
 cascade_int8_tc_kernel(const Src src) {
     using G = TcGeom<S>;
+    using W = TcWidth<TB>;
+    constexpr int CHUNK_STEPS = W::CHUNK_STEPS, BLOCK_CHUNKS = W::BLOCK_CHUNKS;
     constexpr int NST = G::NST;
     constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);
     extern __shared__ unsigned char smem_raw[];
@@ -451,8 +459,8 @@ cascade_int8_tc_kernel(const Src src) {
                 umma::fence_after();
                 const uint32_t base = lane_base + b * ACC_STRIDE;
                 // diagonals 0 .. S-9 belong to H, S-8 .. S-1 to L
-                fold_group<S, 0, S - 8>(base, H);
-                fold_group<S, S - 8, S>(base, L);
+                fold_group<S, TB, 0, S - 8>(base, H);
+                fold_group<S, TB, S - 8, S>(base, L);
                 umma::fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_addr(&sh->acc_empty[b]));
@@ -469,7 +477,7 @@ cascade_int8_tc_kernel(const Src src) {
                                 const int e = ea + j.exp_b[(long long)p * j.n + col] - 12 -
                                               TB * (S - 1);
                                 double h, l;
-                                round_dd(H[x], L[x], e, h, l);
+                                round_dd<W::SPLIT>(H[x], L[x], e, h, l);
                                 const long long o = (long long)row * j.ldc + col;
                                 double ch = 0.0, cl = 0.0;
                                 if (p > 0) {
@@ -495,6 +503,44 @@ cascade_int8_tc_kernel(const Src src) {
         umma::fence_after();
         umma::dealloc(tmem, TMEM_COLS);
     }
+}
+
+// One problem's tiles on a persistent grid of clusters of CL CTAs.
+template <int S, int TB, int CL>
+cudaError_t launch_tc_cl(const Int8TcArgs &a, cudaStream_t stream) {
+    using G = TcGeom<S>;
+    auto kernel = cascade_int8_tc_kernel<S, TB, CL, SingleSource>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    const long long tiles_n = (a.n + BN - 1) / BN;
+    const long long groups = (long long)((a.m + BM - 1) / BM) * ((tiles_n + CL - 1) / CL);
+    if (groups > 0x7fffffffLL) return cudaErrorInvalidValue;
+    SingleSource src;
+    src.a = a;
+    src.tiles_m = (a.m + BM - 1) / BM;
+    src.tiles_n = (int)tiles_n;
+    src.groups_n = (int)((tiles_n + CL - 1) / CL);
+    src.cl = CL;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cfg.stream = stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // persistent: as many clusters as can be resident at once
+    int clusters = 0;
+    cfg.gridDim = dim3(CL);
+    if ((e = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg)) != cudaSuccess) return e;
+    if (clusters <= 0) return cudaErrorInvalidConfiguration;
+    const long long use = groups < clusters ? groups : clusters;
+    cfg.gridDim = dim3((unsigned)(use * CL));
+    return cudaLaunchKernelEx(&cfg, kernel, src);
 }
 
 }  // namespace

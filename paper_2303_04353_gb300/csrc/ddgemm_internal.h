@@ -78,23 +78,27 @@ constexpr int INT8_SLICES_DEFAULT = 15;
 inline bool int8_slices_supported(int s) { return s >= 12 && s <= 15; }
 
 // The tcgen05 form puts the products of plane i with planes 0..s-1-i in one
-// MMA of N = 16 (s - i) <= 256 columns: s <= 16.
+// MMA of N = 16 (s - i) <= 256 columns: s <= 16.  With eight-bit pieces
+// (DDGEMM_VARIANT_INT8_TC8) the fixed-point bound above keeps s <= 15.
 constexpr int INT8_TC_MAX_SLICES = 16;
 constexpr int INT8_TC_SLICES_DEFAULT = 16;
 inline bool int8_tc_slices_supported(int s) { return s >= 12 && s <= INT8_TC_MAX_SLICES; }
+constexpr int INT8_TC8_SLICES_DEFAULT = 15;
+inline bool int8_tc8_slices_supported(int s) { return s >= 12 && s <= 15; }
 
 // tile_rows = 0: int8 digit planes out[(s * nvec + v) * ld_out + l] of
-// INT8_BITS-bit digits, ld_out a multiple of 16 and >= kdim.  tile_rows = TH
-// (a multiple of 8): bf16 INT8_TC_BITS-bit digits in the tcgen05 form's
-// tiled, pre-swizzled order (split_int8.cu), ceil(nvec / TH) * ceil(kdim /
-// 16) * s blocks of TH x 16; entries past kdim up to a multiple of 16 are
-// zero, rows past nvec are not written.  exps[p * nvec + v] per k-block of
-// that width's k-block.  Element (v, l) of the input is at x[v * ldx + l]
-// when vec_contig, else x[l * ldx + v].
+// eight-bit digits (bits = 8), ld_out a multiple of 16 and >= kdim.
+// tile_rows = TH (a multiple of 8): bf16 digits of `bits` bits (7 or 8) in
+// the tcgen05 form's tiled, pre-swizzled order (split_int8.cu),
+// ceil(nvec / TH) * ceil(kdim / 16) * s blocks of TH x 16; entries past kdim
+// up to a multiple of 16 are zero, rows past nvec are not written.
+// exps[p * nvec + v] per k-block of kblock_of_bits(bits) entries.  Element
+// (v, l) of the input is at x[v * ldx + l] when vec_contig, else
+// x[l * ldx + v].
 cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi,
                               const double *x_lo, long long ldx, bool vec_contig, void *out,
-                              int tile_rows, long long ld_out, int *exps, unsigned int *status,
-                              cudaStream_t stream);
+                              int tile_rows, int bits, long long ld_out, int *exps,
+                              unsigned int *status, cudaStream_t stream);
 
 struct Int8Args {
     int m, n, k, slices;
@@ -112,23 +116,28 @@ cudaError_t launch_cascade_int8(const Int8Args &a, cudaStream_t stream);
 
 // The INT8 form on the fifth-generation tensor cores: bf16 digit planes,
 // tcgen05.mma with FP32 accumulation in tensor memory (exact over 256
-// entries), int32 diagonal sums, exact assembly rounded once to FP64x2.
-// Tile heights of the tcgen05 form's tiled digit order: rows of C per tile
-// (A) and columns (B).  Its k-blocks are KB8_TC long.
+// entries of seven-bit digits, 64 of eight-bit ones), int32 diagonal sums,
+// exact assembly rounded once to FP64x2.  Tile heights of the tcgen05
+// form's tiled digit order: rows of C per tile (A) and columns (B).  Its
+// k-blocks are kblock_of_bits(bits) long.
 constexpr int INT8_TC_BM = 128, INT8_TC_BN = 16;
 
 struct Int8TcArgs {
     int m, n, k, slices;
+    int bits;                  // digit width: 7 (INT8_TC) or 8 (INT8_TC8)
     const uint16_t *a_tiles;   // bf16, tiled order with TH = INT8_TC_BM
     const uint16_t *b_tiles;   // bf16, tiled order with TH = INT8_TC_BN
-    const int *exp_a;          // ceil(k/KB8_TC) x m
-    const int *exp_b;          // ceil(k/KB8_TC) x n
+    const int *exp_a;          // ceil(k/kblock_of_bits(bits)) x m
+    const int *exp_b;          // ceil(k/kblock_of_bits(bits)) x n
     double *c_hi, *c_lo;
     long long ldc;
     unsigned int *status;
 };
 
 cudaError_t launch_cascade_int8_tc(const Int8TcArgs &a, cudaStream_t stream);
+// The eight-bit instantiations (cascade_int8_tc8.cu), reached through
+// launch_cascade_int8_tc.
+cudaError_t launch_cascade_int8_tc8(const Int8TcArgs &a, cudaStream_t stream);
 
 // The batched tcgen05 INT8 form (batched_int8_tc.cu): workspace bytes, and
 // the whole pass (returns a DDGEMM_* code).

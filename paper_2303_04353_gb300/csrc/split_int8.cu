@@ -49,63 +49,69 @@ int8_exps_kernel(int nvec, int kdim, int blk, const double *__restrict__ x, long
     }
 }
 
-// int8 planes carry INT8_BITS-bit digits, the tiled bf16 order
-// INT8_TC_BITS-bit ones.
-template <int S, bool CONTIG, bool BF16>
+// BITS-bit digits: int8 planes (eight bits) or the tiled bf16 order (seven
+// or eight).
+template <int S, bool CONTIG, bool BF16, int BITS>
 __global__ void __launch_bounds__(256)
 int8_digits_kernel(int nvec, int kdim, const double *__restrict__ xh,
                    const double *__restrict__ xl, long long ldx, void *__restrict__ out_v,
                    long long ld_out, int th, const int *__restrict__ exps, unsigned int *status) {
     __shared__ double sh[TV][TK + 1];
     __shared__ double sl[TV][TK + 1];
-    digits_unit<S, CONTIG, BF16, BF16 ? INT8_TC_BITS : INT8_BITS>(
-        blockIdx.y * TV, blockIdx.x * TK, nvec, kdim, xh, xl, ldx, out_v, ld_out, th, exps,
-        status, sh, sl);
+    digits_unit<S, CONTIG, BF16, BITS>(blockIdx.y * TV, blockIdx.x * TK, nvec, kdim, xh, xl, ldx,
+                                       out_v, ld_out, th, exps, status, sh, sl);
 }
 
-template <int S, bool BF16>
+template <int S, bool BF16, int BITS>
 cudaError_t launch_digits_t(int nvec, int kdim, const double *xh, const double *xl, long long ldx,
                             bool contig, void *out, long long ld_out, int th, const int *exps,
                             unsigned int *status, cudaStream_t stream) {
     const dim3 grid((kdim + TK - 1) / TK, (nvec + TV - 1) / TV);
     if (grid.y > 65535) return cudaErrorInvalidValue;
     if (contig)
-        int8_digits_kernel<S, true, BF16><<<grid, 256, 0, stream>>>(nvec, kdim, xh, xl, ldx, out,
-                                                                    ld_out, th, exps, status);
+        int8_digits_kernel<S, true, BF16, BITS><<<grid, 256, 0, stream>>>(
+            nvec, kdim, xh, xl, ldx, out, ld_out, th, exps, status);
     else
-        int8_digits_kernel<S, false, BF16><<<grid, 256, 0, stream>>>(nvec, kdim, xh, xl, ldx,
-                                                                     out, ld_out, th, exps,
-                                                                     status);
+        int8_digits_kernel<S, false, BF16, BITS><<<grid, 256, 0, stream>>>(
+            nvec, kdim, xh, xl, ldx, out, ld_out, th, exps, status);
     return cudaGetLastError();
 }
 
-// int8 planes: s in 12..15 (eight-bit digits); tiled bf16: s in 12..16
-// (seven-bit digits).
+// int8 planes: eight-bit digits, s in 12..15.  Tiled bf16: seven-bit digits
+// with s in 12..16, eight-bit ones with s in 12..15 (the fixed-point value
+// needs 6 + bits (s - 1) + 2 <= 127 bits).
 template <int S>
 cudaError_t launch_digits(int nvec, int kdim, const double *xh, const double *xl, long long ldx,
-                          bool contig, void *out, int tile_rows, long long ld_out,
+                          bool contig, void *out, int tile_rows, int bits, long long ld_out,
                           const int *exps, unsigned int *status, cudaStream_t stream) {
-    if (tile_rows)
-        return launch_digits_t<S, true>(nvec, kdim, xh, xl, ldx, contig, out, 0, tile_rows, exps,
-                                        status, stream);
-    if constexpr (S <= 15)
-        return launch_digits_t<S, false>(nvec, kdim, xh, xl, ldx, contig, out, ld_out, 0, exps,
-                                         status, stream);
-    else
+    if (tile_rows && bits == INT8_TC_BITS)
+        return launch_digits_t<S, true, INT8_TC_BITS>(nvec, kdim, xh, xl, ldx, contig, out, 0,
+                                                      tile_rows, exps, status, stream);
+    if constexpr (S <= 15) {
+        if (bits != INT8_BITS) return cudaErrorInvalidValue;
+        if (tile_rows)
+            return launch_digits_t<S, true, INT8_BITS>(nvec, kdim, xh, xl, ldx, contig, out, 0,
+                                                       tile_rows, exps, status, stream);
+        return launch_digits_t<S, false, INT8_BITS>(nvec, kdim, xh, xl, ldx, contig, out, ld_out,
+                                                    0, exps, status, stream);
+    } else {
         return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi,
                               const double *x_lo, long long ldx, bool vec_contig, void *out,
-                              int tile_rows, long long ld_out, int *exps, unsigned int *status,
-                              cudaStream_t stream) {
+                              int tile_rows, int bits, long long ld_out, int *exps,
+                              unsigned int *status, cudaStream_t stream) {
     if (nvec <= 0 || kdim <= 0) return cudaSuccess;
-    if (tile_rows == 0 && (ld_out % 16 != 0 || ld_out < kdim)) return cudaErrorInvalidValue;
+    if (bits != INT8_BITS && bits != INT8_TC_BITS) return cudaErrorInvalidValue;
+    if (tile_rows == 0 && (bits != INT8_BITS || ld_out % 16 != 0 || ld_out < kdim))
+        return cudaErrorInvalidValue;
     if (tile_rows != 0 && tile_rows % 8 != 0) return cudaErrorInvalidValue;
     // block exponents per k-block of the digit width in use
-    const int blk = kblock_of_bits(tile_rows ? INT8_TC_BITS : INT8_BITS);
+    const int blk = kblock_of_bits(bits);
     const int kb = (kdim + blk - 1) / blk;
     if (vec_contig) {
         const long long blocks = ((long long)nvec * kb + 7) / 8;
@@ -121,15 +127,15 @@ cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi
     if (e != cudaSuccess) return e;
     switch (slices) {
         case 12: return launch_digits<12>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,
-                                          ld_out, exps, status, stream);
+                                          bits, ld_out, exps, status, stream);
         case 13: return launch_digits<13>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,
-                                          ld_out, exps, status, stream);
+                                          bits, ld_out, exps, status, stream);
         case 14: return launch_digits<14>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,
-                                          ld_out, exps, status, stream);
+                                          bits, ld_out, exps, status, stream);
         case 15: return launch_digits<15>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,
-                                          ld_out, exps, status, stream);
+                                          bits, ld_out, exps, status, stream);
         case 16: return launch_digits<16>(nvec, kdim, x_hi, x_lo, ldx, vec_contig, out, tile_rows,
-                                          ld_out, exps, status, stream);
+                                          bits, ld_out, exps, status, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -254,3 +254,28 @@ def test_host_ops_refuse_cuda_tensors():
     a = torch.zeros(2, 2, dtype=torch.float32)
     with pytest.raises(TypeError, match="float64"):
         ops.ddgemm_host(a, a, a, a)
+
+
+def test_tc8_workspace_and_pieces():
+    """The eight-bit tcgen05 form: the tiled bf16 digit layout of the
+    seven-bit one with k-blocks of 8192, and s in 12..15."""
+    tc8 = _lib.DDGEMM_VARIANT_INT8_TC8
+    s15 = _lib.ddgemm_workspace_size(300, 40, 20000, _lib.make_opts(variant=tc8))
+    assert s15 == _lib.ddgemm_workspace_size(300, 40, 20000,
+                                             _lib.make_opts(variant=tc8, int8_slices=15))
+    # 15 planes of bf16 digits: 384 rows of A and 48 columns of B, k padded to 16
+    assert s15 >= 15 * (384 + 48) * 20000 * 2
+    assert _lib.ddgemm_workspace_size(300, 40, 20000, _lib.make_opts(variant=tc8,
+                                                                     int8_slices=16)) == 0
+    # three exponent blocks of 8192 against two of 16384 for the seven-bit form
+    s7 = _lib.ddgemm_workspace_size(300, 40, 20000, _lib.make_opts(
+        variant=_lib.DDGEMM_VARIANT_INT8_TC, int8_slices=15))
+    assert s15 > s7
+    lib = _lib.load()
+    flagged = _lib.make_opts(variant=tc8, flags_dev=FAKE)
+    assert call(4, 4, 4, 4, 4, 4, opts=flagged) == _lib.DDGEMM_EUNSUPPORTED
+    arr = (_lib.ddgemm_problem * 1)()
+    arr[0] = _lib.ddgemm_problem(4, 5, 6, 6, 5, 5, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+    o = _lib.make_opts(variant=tc8)
+    assert lib.ddgemm_batched(1, arr, FAKE, FAKE, 1 << 30, None, ctypes.byref(o), None) == \
+        _lib.DDGEMM_EUNSUPPORTED

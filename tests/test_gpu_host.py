@@ -30,7 +30,7 @@ from workloads import gemm_inputs  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 CONTRACT = 1e-28
-FP64, INT8, INT8_TC = 0, 1, 4
+FP64, INT8, INT8_TC, INT8_TC8 = 0, 1, 4, 5
 
 
 @pytest.fixture(scope="module")
@@ -139,7 +139,8 @@ def sample_rows_cols(m, n, mc, seed):
 @pytest.mark.parametrize("variant,m,n,mc,s,ta", [(INT8, 2500, 2048, 1024, 15, False),
                                                 (INT8, 2500, 2048, 1024, 13, True),
                                                 (INT8_TC, 4200, 2048, 2048, 16, False),
-                                                (INT8_TC, 4200, 2048, 2048, 14, True)])
+                                                (INT8_TC, 4200, 2048, 2048, 14, True),
+                                                (INT8_TC8, 4200, 2048, 2048, 15, False)])
 def test_host_int8_forms(ops, variant, m, n, mc, s, ta):
     """Three chunks of op(A)'s rows (1024/1024/452 for mma.sync,
     2048/2048/104 for tcgen05): C is bit-identical to ddgemm() of the same
@@ -159,11 +160,13 @@ def test_host_int8_forms(ops, variant, m, n, mc, s, ta):
     sub = (a_hi[rows], a_lo[rows], b_hi[:, cols], b_lo[:, cols])
     if variant == INT8:
         w_hi, w_lo = c8.cascade_int8_ddgemm(*sub, s=s)
+    elif variant == INT8_TC8:
+        w_hi, w_lo = c8.cascade_int8_tc8_ddgemm(*sub, s=s)
     else:
         w_hi, w_lo = c8.cascade_int8_tc_ddgemm(*sub, s=s)
     assert np.array_equal(c_hi[np.ix_(rows, cols)], w_hi)
     assert np.array_equal(c_lo[np.ix_(rows, cols)], w_lo)
-    if s == (15 if variant == INT8 else 16):
+    if s == (16 if variant == INT8_TC else 15):
         # the default piece counts meet the contract on this workload; fewer
         # pieces trade accuracy for speed (their error is 2^(bits (15 - s))
         # or so larger)

@@ -236,3 +236,92 @@ def test_tc_cluster_multicast_path(ops, cl, monkeypatch):
         c_hi, c_lo = tc(ops, *a)
         w_hi, w_lo = c8.cascade_int8_tc_ddgemm(*a, s=16)
         assert same(c_hi, w_hi) and same(c_lo, w_lo)
+
+
+# ---- the eight-bit tcgen05 form (DDGEMM_VARIANT_INT8_TC8) -----------------
+
+TC8 = 5
+
+
+def tc8(ops, a_hi, a_lo, b_hi, b_lo, s=15, **kw):
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    c_hi, c_lo = ops.ddgemm(*dev(a_hi, a_lo, b_hi, b_lo), variant=TC8, int8_slices=s,
+                            status=status, **kw)
+    c_hi, c_lo, st = host(c_hi, c_lo, status)
+    assert st[0] == 0
+    return c_hi, c_lo
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 16, 256), (1, 1, 1), (130, 20, 300), (200, 50, 1000),
+                                   (129, 17, 16), (70, 100, 65)])
+@pytest.mark.parametrize("kind", ["uniform", "wide"])
+def test_tc8_bitwise_vs_restatement(ops, m, n, k, kind):
+    """Eight-bit pieces on tcgen05, read out every 64 entries (k = 65: a
+    chunk and one entry): bit-identical to the restatement with the
+    mma.sync form's pieces and the exact assembly."""
+    a = gemm_inputs(m, n, k, kind=kind, seed=m + 5 * n + k)
+    c_hi, c_lo = tc8(ops, *a)
+    w_hi, w_lo = c8.cascade_int8_tc8_ddgemm(*a, s=15)
+    assert same(c_hi, w_hi) and same(c_lo, w_lo)
+
+
+@pytest.mark.parametrize("s", [12, 13, 14])
+def test_tc8_other_piece_counts(ops, s):
+    a = gemm_inputs(150, 40, 700, kind="wide", seed=s + 40)
+    c_hi, c_lo = tc8(ops, *a, s=s)
+    w_hi, w_lo = c8.cascade_int8_tc8_ddgemm(*a, s=s)
+    assert same(c_hi, w_hi) and same(c_lo, w_lo)
+
+
+def test_tc8_two_k_blocks_and_transposes(ops):
+    """k > 8192: two k-blocks with their own exponents; transposed storage."""
+    a = gemm_inputs(5, 3, 8300, kind="wide", seed=22)
+    c_hi, c_lo = tc8(ops, *a)
+    w_hi, w_lo = c8.cascade_int8_tc8_ddgemm(*a, s=15)
+    assert same(c_hi, w_hi) and same(c_lo, w_lo)
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(90, 40, 400, kind="wide", seed=8)
+    c_hi, c_lo = tc8(ops, a_hi.T, a_lo.T, b_hi.T, b_lo.T, trans_a=True, trans_b=True)
+    w_hi, w_lo = c8.cascade_int8_tc8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=15)
+    assert same(c_hi, w_hi) and same(c_lo, w_lo)
+
+
+def test_tc8_matches_int8_form_assembly_bound(ops):
+    """Same pieces and products as the mma.sync form, only the assembly
+    differs (one rounding against s): within 4 s 2^-106 |A||B| of it."""
+    a = gemm_inputs(256, 80, 1200, kind="wide", seed=6)
+    c_hi, c_lo = tc8(ops, *a)
+    i_hi, i_lo = host(*ops.ddgemm(*dev(*a), variant=1))
+    absab = np.abs(a[0]) @ np.abs(a[2])
+    diff = np.abs((c_hi - i_hi) + (c_lo - i_lo))
+    assert np.all(diff <= 4 * 15 * 2.0 ** -106 * absab)
+
+
+def test_tc8_full_size_sampled(ops):
+    """4096^3, wide entries: sampled entries within 1e-28 (|A||B|) of the
+    double-double oracle."""
+    m = n = k = 4096
+    a = gemm_inputs(m, n, k, kind="wide", seed=0)
+    c_hi, c_lo = tc8(ops, *a)
+    rng = np.random.default_rng(1)
+    rows, cols = rng.integers(0, m, 48), rng.integers(0, n, 48)
+    o_hi, o_lo = dd.ddgemm_entries(*a, rows, cols)
+    absab = np.array([np.abs(a[0][i]) @ np.abs(a[2][:, j]) for i, j in zip(rows, cols)])
+    err = np.abs((c_hi[rows, cols] - o_hi) + (c_lo[rows, cols] - o_lo))
+    assert np.all(err <= CONTRACT * absab)
+
+
+def test_tc8_illconditioned_beats_fp64x2_loop(ops):
+    """On the ill-conditioned products of the accuracy study the eight-bit
+    pieces (118 fraction bits) beat the FP64x2 triple loop, as the mma.sync
+    form does; bit-identical to the restatement."""
+    from workloads.illcond import illcond_inputs
+    from tests.test_illcond import rel_errors
+    n = 128
+    a = illcond_inputs(n, 1e-19, seed=n)[:4]
+    c_hi, c_lo = tc8(ops, *a)
+    w_hi, w_lo = c8.cascade_int8_tc8_ddgemm(*a, s=15)
+    assert same(c_hi, w_hi) and same(c_lo, w_lo)
+    rng = np.random.default_rng(2)
+    rows, cols = rng.integers(0, n, 40), rng.integers(0, n, 40)
+    o_hi, o_lo = dd.ddgemm(*a)
+    assert rel_errors(c_hi, c_lo, a, rows, cols).max() * 3 < rel_errors(o_hi, o_lo, a, rows, cols).max()
