@@ -29,7 +29,14 @@ struct TcWidth {
     static_assert(TB == 7 || TB == 8, "seven- or eight-bit pieces");
     static_assert(CHUNK_STEPS >= 1 && SPLIT <= 64, "digit width");
 };
-constexpr int EPI_WARPS = 8;
+// Drain warps: four per tensor-memory lane quadrant (a warp reaches only the
+// quadrant warp % 4), each taking DCOLS of the 16 columns of every diagonal.
+// Sixteen warps hide the read-out latency better than eight and leave each
+// thread half the state (its outputs' exact block values).
+constexpr int EPI_WARPS = 16;
+constexpr int DRAIN_PARTS = EPI_WARPS / 4;
+constexpr int DCOLS = BN / DRAIN_PARTS;
+static_assert(DCOLS == 4, "the drain reads 4 columns per diagonal");
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_STRIDE = 256;                  // columns between the two sets
@@ -177,52 +184,56 @@ __device__ __forceinline__ void add_diagonal(int t, int v, __int128 &H, __int128
         L += (__int128)v * ((__int128)1 << (TB * (S - 1 - t)));
 }
 
-// Add diagonals T0 .. T1-1 of one chunk, read from tensor memory (8
+// Add diagonals T0 .. T1-1 of one chunk, read from tensor memory (DCOLS
 // columns each, at base + 16 t), into acc[j] with the weights of
 // T = H 2^SPLIT + L: the diagonal T1-1 has weight 1 in its half, each
-// earlier one 2^TB more.  Four diagonals at a time are combined exactly in
-// an int64 (|sum| <= 2^24 per diagonal and chunk, so below 2^(25 + 3 TB)),
-// then added in.
+// earlier one 2^TB more.  Four diagonals at a time are read with one wait
+// and combined exactly in an int64 (|sum| <= 2^24 per diagonal and chunk,
+// so below 2^(25 + 3 TB)), then added in.
 template <int S, int TB, int T0, int T1>
-__device__ __forceinline__ void fold_group(uint32_t base, __int128 (&acc)[8]) {
+__device__ __forceinline__ void fold_group(uint32_t base, __int128 (&acc)[DCOLS]) {
     static_assert(T1 - T0 <= 8 && T1 > T0, "a half holds 1 to 8 diagonals");
 #pragma unroll
     for (int g0 = T0; g0 < T1; g0 += 4) {
         const int len = (T1 - g0) < 4 ? (T1 - g0) : 4;
-        long long g[8];
+        uint32_t r[4 * DCOLS];
+        if (len == 4) {
+            const uint32_t t[4] = {base + g0 * BN, base + (g0 + 1) * BN, base + (g0 + 2) * BN,
+                                   base + (g0 + 3) * BN};
+            umma::ld_x4_n(t, r);
+        } else if (len == 3) {
+            const uint32_t t[3] = {base + g0 * BN, base + (g0 + 1) * BN, base + (g0 + 2) * BN};
+            uint32_t r3[3 * DCOLS];
+            umma::ld_x4_n(t, r3);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) g[j] = 0;
-        uint32_t r[16];
-        if (len >= 2) {
-            umma::ld_x8_x2(base + g0 * BN, base + (g0 + 1) * BN, r);
+            for (int j = 0; j < 3 * DCOLS; ++j) r[j] = r3[j];
+        } else if (len == 2) {
+            const uint32_t t[2] = {base + g0 * BN, base + (g0 + 1) * BN};
+            uint32_t r2[2 * DCOLS];
+            umma::ld_x4_n(t, r2);
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                g[j] = (long long)__float2int_rn(__uint_as_float(r[j])) * (1 << TB) +
-                       __float2int_rn(__uint_as_float(r[8 + j]));
+            for (int j = 0; j < 2 * DCOLS; ++j) r[j] = r2[j];
         } else {
-            uint32_t r1[8];
-            umma::ld_x8(base + g0 * BN, r1);
+            const uint32_t t[1] = {base + g0 * BN};
+            uint32_t r1[DCOLS];
+            umma::ld_x4_n(t, r1);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) g[j] = __float2int_rn(__uint_as_float(r1[j]));
+            for (int j = 0; j < DCOLS; ++j) r[j] = r1[j];
         }
-        if (len == 3) {
-            uint32_t r1[8];
-            umma::ld_x8(base + (g0 + 2) * BN, r1);
+        long long g[DCOLS];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                g[j] = g[j] * (1 << TB) + __float2int_rn(__uint_as_float(r1[j]));
-        } else if (len == 4) {
-            umma::ld_x8_x2(base + (g0 + 2) * BN, base + (g0 + 3) * BN, r);
+        for (int j = 0; j < DCOLS; ++j) {
+            g[j] = __float2int_rn(__uint_as_float(r[j]));
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                g[j] = (g[j] * (1 << TB) + __float2int_rn(__uint_as_float(r[j]))) * (1 << TB) +
-                       __float2int_rn(__uint_as_float(r[8 + j]));
+            for (int d = 1; d < 4; ++d)
+                if (d < len)
+                    g[j] = g[j] * (1 << TB) + __float2int_rn(__uint_as_float(r[DCOLS * d + j]));
         }
         // weight of the group's last diagonal within its half
         const int last = g0 + len - 1;
         const int shift = TB * (T1 - 1 - last);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] += (__int128)g[j] * ((__int128)1 << shift);
+        for (int j = 0; j < DCOLS; ++j) acc[j] += (__int128)g[j] * ((__int128)1 << shift);
     }
 }
 
@@ -424,9 +435,9 @@ cascade_int8_tc_kernel(const Src src) {
     } else {
         // ---- drain and assembly ---------------------------------------------
         const int quad = warp & 3;               // tensor-memory lanes 32 quad ..
-        const int half = (warp - 2) >> 2;        // columns 8 half .. + 7 of each diagonal
+        const int part = (warp - 2) >> 2;        // columns DCOLS part .. of each diagonal
         const int row_in_tile = quad * 32 + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + half * 8;
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + part * DCOLS;
         uint32_t chunk = 0;
         bool ok = true;
         for (long long tile = first; ok && tile < tiles; tile += stride) {
@@ -435,17 +446,17 @@ cascade_int8_tc_kernel(const Src src) {
             const int nchunks = (ksteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
             const int row = j.tm * BM + row_in_tile;
             // past the last column tile: every col >= n, nothing is stored
-            const int col0 = j.col0 + half * 8;
+            const int col0 = j.col0 + part * DCOLS;
             if (nchunks == 0 && row < j.m) {  // k = 0: C = 0 on this tile
-                for (int x = 0; x < 8; ++x)
+                for (int x = 0; x < DCOLS; ++x)
                     if (col0 + x < j.n) {
                         j.c_hi[(long long)row * j.ldc + col0 + x] = 0.0;
                         j.c_lo[(long long)row * j.ldc + col0 + x] = 0.0;
                     }
             }
-            __int128 H[8], L[8];
+            __int128 H[DCOLS], L[DCOLS];
 #pragma unroll
-            for (int x = 0; x < 8; ++x) H[x] = L[x] = 0;
+            for (int x = 0; x < DCOLS; ++x) H[x] = L[x] = 0;
             for (int c = 0; c < nchunks; ++c, ++chunk) {
                 const int b = chunk & 1;
                 // every lane waits; the warp goes on only together (the
@@ -471,7 +482,7 @@ cascade_int8_tc_kernel(const Src src) {
                     if (row < j.m) {
                         const int ea = j.exp_a[(long long)p * j.m + row];
 #pragma unroll
-                        for (int x = 0; x < 8; ++x) {
+                        for (int x = 0; x < DCOLS; ++x) {
                             const int col = col0 + x;
                             if (col < j.n) {
                                 const int e = ea + j.exp_b[(long long)p * j.n + col] - 12 -
@@ -491,7 +502,7 @@ cascade_int8_tc_kernel(const Src src) {
                         }
                     }
 #pragma unroll
-                    for (int x = 0; x < 8; ++x) H[x] = L[x] = 0;
+                    for (int x = 0; x < DCOLS; ++x) H[x] = L[x] = 0;
                 }
             }
         }
