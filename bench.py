@@ -565,7 +565,7 @@ def run_batched(args):
     import torch
 
     from oracle import dd
-    from paper_2303_04353_gb300 import autotune, ops
+    from paper_2303_04353_gb300 import _lib, autotune, ops
     from workloads import batched_shapes
 
     dev = torch.device("cuda", 0)
@@ -626,26 +626,31 @@ def run_batched(args):
         absab = np.array([np.abs(a[0][r]) @ np.abs(a[2][:, c]) for r, c in zip(rows, cols)])
         worst = max(worst, float(np.max(np.abs((ch[rows, cols] - oh) + (cl[rows, cols] - ol))
                                         / absab)))
-    # the same 512 problems through the batched tcgen05 INT8 form (graph)
-    tc_probs = [(*p[:4], torch.empty_like(p[4]), torch.empty_like(p[5])) for p in probs]
-    tc_batch = ops.Batch(tc_probs, variant=4)
-    tc_graph = torch.cuda.CUDAGraph()
-    tc_batch.run(stream=stream)
-    torch.cuda.synchronize()
-    with torch.cuda.graph(tc_graph, stream=side):
-        tc_batch.run(stream=torch.cuda.current_stream())
-    tc_ms = timed(tc_graph.replay, args.steps)
-    tc_worst = 0.0
-    for i in range(0, 512, 64):
-        a = host[i]
-        m, n, _ = shapes[i]
-        rng = np.random.default_rng(i)
-        rows, cols = rng.integers(0, m, 16), rng.integers(0, n, 16)
-        oh, ol = dd.ddgemm_entries(*a, rows, cols)
-        ch, cl = tc_probs[i][4].cpu().numpy(), tc_probs[i][5].cpu().numpy()
-        absab = np.array([np.abs(a[0][r]) @ np.abs(a[2][:, c]) for r, c in zip(rows, cols)])
-        tc_worst = max(tc_worst, float(np.max(np.abs((ch[rows, cols] - oh) +
-                                                      (cl[rows, cols] - ol)) / absab)))
+    # the same 512 problems through the batched tcgen05 INT8 forms (graph):
+    # seven-bit pieces, and the mma.sync form's eight-bit ones
+    def tc_pass(variant):
+        tc_probs = [(*p[:4], torch.empty_like(p[4]), torch.empty_like(p[5])) for p in probs]
+        tc_batch = ops.Batch(tc_probs, variant=variant)
+        tc_graph = torch.cuda.CUDAGraph()
+        tc_batch.run(stream=stream)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(tc_graph, stream=side):
+            tc_batch.run(stream=torch.cuda.current_stream())
+        ms = timed(tc_graph.replay, args.steps)
+        worst_tc = 0.0
+        for i in range(0, 512, 64):
+            a = host[i]
+            m, n, _ = shapes[i]
+            rng = np.random.default_rng(i)
+            rows, cols = rng.integers(0, m, 16), rng.integers(0, n, 16)
+            oh, ol = dd.ddgemm_entries(*a, rows, cols)
+            ch, cl = tc_probs[i][4].cpu().numpy(), tc_probs[i][5].cpu().numpy()
+            absab = np.array([np.abs(a[0][r]) @ np.abs(a[2][:, c]) for r, c in zip(rows, cols)])
+            worst_tc = max(worst_tc, float(np.max(np.abs((ch[rows, cols] - oh) +
+                                                          (cl[rows, cols] - ol)) / absab)))
+        return ms, worst_tc
+    tc_ms, tc_worst = tc_pass(_lib.DDGEMM_VARIANT_INT8_TC)
+    tc8_ms, tc8_worst = tc_pass(_lib.DDGEMM_VARIANT_INT8_TC8)
     value = flops / (graph_ms * 1e-3) / 1e9
     peak, peak_src = fp64_peak_rule()
     achieved = 10.0 * flops / (graph_ms * 1e-3) / 1e12
@@ -668,6 +673,11 @@ def run_batched(args):
                                 "launches": 5, "max_err_vs_dd_oracle": tc_worst,
                                 "what": "the same problems, batched tcgen05 INT8 form "
                                         "(16 seven-bit pieces), one CUDA-graph replay"},
+            "int8_tc8_batched": {"ms": round(tc8_ms, 3),
+                                 "gflops": round(flops / (tc8_ms * 1e-3) / 1e9, 3),
+                                 "launches": 5, "max_err_vs_dd_oracle": tc8_worst,
+                                 "what": "the same problems, batched tcgen05 INT8 form with "
+                                         "the mma.sync form's 15 eight-bit pieces"},
             "roofline": {"bound": "tensor", "kernel": "whole batched pass (4 launches)",
                          "achieved": round(achieved, 4), "peak": round(peak, 4),
                          "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,

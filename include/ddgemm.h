@@ -110,7 +110,7 @@ typedef struct ddgemm_opts {
      * cores.  An eight-bit product is at most 2^14, so the FP32
      * accumulators are read out every 64 entries instead of 256, which
      * makes it slower than INT8_TC.  Assembly as for INT8_TC, with weights
-     * 2^(-12-8t).  Not available to ddgemm_batched(). */
+     * 2^(-12-8t). */
     int variant;
     /* Optional device word (or NULL): DDGEMM_DEV_* bits are OR-ed into it.
      * The library never clears it. */
@@ -246,12 +246,13 @@ size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem *probs_host
  *               device-side information comes from it, so the call can be
  *               captured into a CUDA graph once it has been uploaded.
  *   workspace   >= ddgemm_batched_workspace_size() bytes, 256-byte aligned.
- *   opts        NULL or: trans flags 0, variant FP64 or INT8_TC, no
- *               flags_dev (else DDGEMM_EUNSUPPORTED); status_dev is
- *               honoured; int8_slices for INT8_TC (12-16; 0 = 16).
+ *   opts        NULL or: trans flags 0, variant FP64, INT8_TC or INT8_TC8,
+ *               no flags_dev (else DDGEMM_EUNSUPPORTED); status_dev is
+ *               honoured; int8_slices for INT8_TC (12-16; 0 = 16) and
+ *               INT8_TC8 (12-15; 0 = 15).
  *   config      NULL = {DDGEMM_TILE_64x64, DDGEMM_ORDER_LONGEST_K_FIRST}.
  *               Not used by INT8_TC.
- * INT8_TC (the INT8 form on the tcgen05 tensor cores, see
+ * INT8_TC and INT8_TC8 (the INT8 form on the tcgen05 tensor cores, see
  * DDGEMM_VARIANT_INT8_TC): five launches, a plan, the exponents of every A
  * and of every B, the digits of all of them, and one persistent tcgen05
  * kernel over the (problem, 128 x 16 tile) items, longest k first; each

@@ -375,7 +375,12 @@ extern "C" size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem 
     if (opts && opts->variant == DDGEMM_VARIANT_INT8_TC) {
         const int s = opts->int8_slices ? opts->int8_slices : ddg::INT8_TC_SLICES_DEFAULT;
         if (!ddg::int8_tc_slices_supported(s)) return 0;
-        return ddg::batched_int8_tc_workspace_size(count, probs_host, s);
+        return ddg::batched_int8_tc_workspace_size(count, probs_host, s, ddg::INT8_TC_BITS);
+    }
+    if (opts && opts->variant == DDGEMM_VARIANT_INT8_TC8) {
+        const int s = opts->int8_slices ? opts->int8_slices : ddg::INT8_TC8_SLICES_DEFAULT;
+        if (!ddg::int8_tc8_slices_supported(s)) return 0;
+        return ddg::batched_int8_tc_workspace_size(count, probs_host, s, ddg::INT8_BITS);
     }
     size_t total = ddg::plan_layout(count).panels;
     for (int i = 0; i < count; ++i) {
@@ -395,14 +400,22 @@ extern "C" int ddgemm_batched(int count, const ddgemm_problem *probs_host,
     unsigned int *status = nullptr;
     if (opts) {
         if (opts->trans_a || opts->trans_b || opts->flags_dev ||
-            (opts->variant != DDGEMM_VARIANT_FP64 && opts->variant != DDGEMM_VARIANT_INT8_TC))
+            (opts->variant != DDGEMM_VARIANT_FP64 && opts->variant != DDGEMM_VARIANT_INT8_TC &&
+             opts->variant != DDGEMM_VARIANT_INT8_TC8))
             return DDGEMM_EUNSUPPORTED;
         status = opts->status_dev;
         if (opts->variant == DDGEMM_VARIANT_INT8_TC) {
             const int s = opts->int8_slices ? opts->int8_slices : INT8_TC_SLICES_DEFAULT;
             if (!int8_tc_slices_supported(s)) return DDGEMM_EINVAL;
             return run_batched_int8_tc(count, probs_host, probs_dev, workspace, ws_bytes,
-                                       static_cast<cudaStream_t>(stream), s, status);
+                                       static_cast<cudaStream_t>(stream), s, INT8_TC_BITS,
+                                       status);
+        }
+        if (opts->variant == DDGEMM_VARIANT_INT8_TC8) {
+            const int s = opts->int8_slices ? opts->int8_slices : INT8_TC8_SLICES_DEFAULT;
+            if (!int8_tc8_slices_supported(s)) return DDGEMM_EINVAL;
+            return run_batched_int8_tc(count, probs_host, probs_dev, workspace, ws_bytes,
+                                       static_cast<cudaStream_t>(stream), s, INT8_BITS, status);
         }
     }
     const int tile = config ? config->tile : DDGEMM_TILE_64x64;

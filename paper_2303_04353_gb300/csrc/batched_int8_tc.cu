@@ -5,9 +5,10 @@
 // input tile), and one persistent tcgen05 kernel that walks the planned list
 // of (problem, 128 x 16 tile) items, longest k first.  The paper has no
 // batched form; this is the tcgen05 INT8 form (cascade_int8_tc.cu) scheduled
-// for many small problems at once.  Every unit runs the single-problem
-// form's device code on that problem's data, so each C is bit-identical to
-// what ddgemm() computes for it with DDGEMM_VARIANT_INT8_TC.
+// for many small problems at once, with seven- or eight-bit pieces.  Every
+// unit runs the single-problem form's device code on that problem's data,
+// so each C is bit-identical to what ddgemm() computes for it with
+// DDGEMM_VARIANT_INT8_TC (or DDGEMM_VARIANT_INT8_TC8).
 //
 // Everything the kernels need is computed on the device from the caller's
 // device copy of the problem list (the host copy only sizes the launches),
@@ -44,6 +45,7 @@ struct TcEntry {
 struct TcHeader {
     long long total_tiles, total_ea, total_eb, total_d;
     int count;
+    int kblk;                  // k-block of the digit width (8192 or 16384)
     unsigned int *status;
 };
 
@@ -67,9 +69,9 @@ __host__ __device__ inline TcPlanLayout tc_plan_layout(int count) {
 }
 
 // Digit and exponent bytes of one problem (the single-problem layout).
-__host__ __device__ inline size_t tc_problem_bytes(int m, int n, int k, int slices) {
+__host__ __device__ inline size_t tc_problem_bytes(int m, int n, int k, int slices, int kblk) {
     if (m <= 0 || n <= 0 || k <= 0) return 0;
-    const size_t kpad = ru_tc((size_t)k, 16), kb8 = (size_t)(k + KB8_TC - 1) / KB8_TC;
+    const size_t kpad = ru_tc((size_t)k, 16), kb8 = (size_t)(k + kblk - 1) / kblk;
     return ru_tc((size_t)slices * ru_tc((size_t)m, INT8_TC_BM) * kpad * 2, TC_ALIGN) +
            ru_tc((size_t)slices * ru_tc((size_t)n, INT8_TC_BN) * kpad * 2, TC_ALIGN) +
            ru_tc(kb8 * m * 4, TC_ALIGN) + ru_tc(kb8 * n * 4, TC_ALIGN);
@@ -94,7 +96,7 @@ __device__ inline bool before_tc(const ddgemm_problem &a, int ia, const ddgemm_p
 
 __global__ void __launch_bounds__(256)
 tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, int slices,
-               unsigned int *status) {
+               int kblk, unsigned int *status) {
     const TcPlanLayout L = tc_plan_layout(count);
     TcHeader *hdr = reinterpret_cast<TcHeader *>(ws);
     TcEntry *ent = reinterpret_cast<TcEntry *>(ws + L.entries);
@@ -108,7 +110,7 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
         const ddgemm_problem q = probs[i];
         TcEntry e;
         e.m = q.m; e.n = q.n; e.k = q.k;
-        e.kb8 = q.k > 0 ? (q.k + KB8_TC - 1) / KB8_TC : 0;
+        e.kb8 = q.k > 0 ? (q.k + kblk - 1) / kblk : 0;
         e.lda = q.lda; e.ldb = q.ldb; e.ldc = q.ldc;
         e.a_hi = q.A_hi; e.a_lo = q.A_lo; e.b_hi = q.B_hi; e.b_lo = q.B_lo;
         e.c_hi = q.C_hi; e.c_lo = q.C_lo;
@@ -169,6 +171,7 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
         hdr->total_eb = tb;
         hdr->total_d = tda + tdb;
         hdr->count = count;
+        hdr->kblk = kblk;
         hdr->status = status;
     }
 }
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(256) tc_exps_a_kernel(const char *ws) {
         const TcEntry &e = V.ent[i];
         const long long local = u - V.ea_pre[i];
         split8::exps_contig_unit(lane, (int)(local / e.kb8), (int)(local % e.kb8), e.m, e.k,
-                                 KB8_TC, e.a_hi, e.lda, e.e_a);
+                                 V.hdr->kblk, e.a_hi, e.lda, e.e_a);
     }
 }
 
@@ -216,13 +219,13 @@ __global__ void __launch_bounds__(256) tc_exps_b_kernel(const char *ws) {
         const TcEntry &e = V.ent[i];
         const long long local = u - V.eb_pre[i];
         const int vtiles = (e.n + 63) / 64;
-        split8::exps_strided_unit((int)(local % vtiles), (int)(local / vtiles), e.n, e.k, KB8_TC,
-                                  e.b_hi, e.ldb, e.e_b, part);
+        split8::exps_strided_unit((int)(local % vtiles), (int)(local / vtiles), e.n, e.k,
+                                  V.hdr->kblk, e.b_hi, e.ldb, e.e_b, part);
     }
 }
 
 // Digits of every A, then of every B: one CTA per 32 x 64 input tile.
-template <int S>
+template <int S, int BITS>
 __global__ void __launch_bounds__(256) tc_digits_kernel(const char *ws) {
     __shared__ double sh[split8::TV][split8::TK + 1];
     __shared__ double sl[split8::TV][split8::TK + 1];
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(256) tc_digits_kernel(const char *ws) {
             const TcEntry &e = V.ent[i];
             const long long local = u - V.da_pre[i];
             const int ktiles = (e.k + split8::TK - 1) / split8::TK;
-            split8::digits_unit<S, true, true, INT8_TC_BITS>((int)(local / ktiles) * split8::TV,
+            split8::digits_unit<S, true, true, BITS>((int)(local / ktiles) * split8::TV,
                                                (int)(local % ktiles) * split8::TK, e.m, e.k,
                                                e.a_hi, e.a_lo, e.lda, e.a_tiles, 0, INT8_TC_BM,
                                                e.e_a, status, sh, sl);
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(256) tc_digits_kernel(const char *ws) {
             const TcEntry &e = V.ent[i];
             const long long local = ub - V.db_pre[i];
             const int ktiles = (e.k + split8::TK - 1) / split8::TK;
-            split8::digits_unit<S, false, true, INT8_TC_BITS>((int)(local / ktiles) * split8::TV,
+            split8::digits_unit<S, false, true, BITS>((int)(local / ktiles) * split8::TV,
                                                 (int)(local % ktiles) * split8::TK, e.n, e.k,
                                                 e.b_hi, e.b_lo, e.ldb, e.b_tiles, 0, INT8_TC_BN,
                                                 e.e_b, status, sh, sl);
@@ -290,7 +293,7 @@ struct BatchSource {
     }
 };
 
-template <int S>
+template <int S, int BITS>
 cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, long long units_eb,
                               long long units_d, int sms, cudaStream_t s) {
     const long long cap = 8LL * sms;
@@ -301,11 +304,11 @@ cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, lon
     if (units_eb > 0)
         tc_exps_b_kernel<<<(unsigned)(units_eb < cap ? units_eb : cap), 256, 0, s>>>(ws);
     if (units_d > 0)
-        tc_digits_kernel<S><<<(unsigned)(units_d < cap ? units_d : cap), 256, 0, s>>>(ws);
+        tc_digits_kernel<S, BITS><<<(unsigned)(units_d < cap ? units_d : cap), 256, 0, s>>>(ws);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || tiles == 0) return e;
     using G = TcGeom<S>;
-    auto kernel = cascade_int8_tc_kernel<S, INT8_TC_BITS, 1, BatchSource>;
+    auto kernel = cascade_int8_tc_kernel<S, BITS, 1, BatchSource>;
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)G::SMEM)) != cudaSuccess)
         return e;
@@ -327,17 +330,22 @@ bool tc_problem_ok(const ddgemm_problem &q) {
 
 }  // namespace
 
-size_t batched_int8_tc_workspace_size(int count, const ddgemm_problem *probs_host, int slices) {
+size_t batched_int8_tc_workspace_size(int count, const ddgemm_problem *probs_host, int slices,
+                                      int bits) {
     if (count <= 0 || !probs_host) return 0;
+    const int kblk = kblock_of_bits(bits);
     size_t total = tc_plan_layout(count).data;
     for (int i = 0; i < count; ++i)
-        total += tc_problem_bytes(probs_host[i].m, probs_host[i].n, probs_host[i].k, slices);
+        total += tc_problem_bytes(probs_host[i].m, probs_host[i].n, probs_host[i].k, slices, kblk);
     return total;
 }
 
 int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
                         const ddgemm_problem *probs_dev, void *workspace, size_t ws_bytes,
-                        cudaStream_t s, int slices, unsigned int *status) {
+                        cudaStream_t s, int slices, int bits, unsigned int *status) {
+    if (bits != INT8_TC_BITS && bits != INT8_BITS) return DDGEMM_EINVAL;
+    if (bits == INT8_BITS && slices > 15) return DDGEMM_EINVAL;
+    const int kblk = kblock_of_bits(bits);
     long long tiles = 0, ea = 0, eb = 0, d = 0;
     for (int i = 0; i < count; ++i) {
         const ddgemm_problem &q = probs_host[i];
@@ -346,7 +354,7 @@ int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
             tiles += (long long)((q.m + INT8_TC_BM - 1) / INT8_TC_BM) *
                      ((q.n + INT8_TC_BN - 1) / INT8_TC_BN);
             if (q.k > 0) {
-                const long long kb8 = (q.k + KB8_TC - 1) / KB8_TC,
+                const long long kb8 = (q.k + kblk - 1) / kblk,
                                 kt = (q.k + split8::TK - 1) / split8::TK;
                 ea += (long long)q.m * kb8;
                 eb += (long long)((q.n + 63) / 64) * kb8;
@@ -355,7 +363,7 @@ int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
             }
         }
     }
-    const size_t need = batched_int8_tc_workspace_size(count, probs_host, slices);
+    const size_t need = batched_int8_tc_workspace_size(count, probs_host, slices, bits);
     if (!workspace || ws_bytes < need || (uintptr_t)workspace % TC_ALIGN) return DDGEMM_EWORKSPACE;
     if (tiles > 0x7fffffffLL) return DDGEMM_EINVAL;
     int dev = 0, sms = 0;
@@ -363,16 +371,26 @@ int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return DDGEMM_ECUDA;
     char *ws = static_cast<char *>(workspace);
-    tc_plan_kernel<<<1, 256, 0, s>>>(count, probs_dev, ws, slices, status);
+    tc_plan_kernel<<<1, 256, 0, s>>>(count, probs_dev, ws, slices, kblk, status);
     if (cudaGetLastError() != cudaSuccess) return DDGEMM_ECUDA;
     cudaError_t e;
-    switch (slices) {
-        case 12: e = launch_batched_tc<12>(ws, tiles, ea, eb, d, sms, s); break;
-        case 13: e = launch_batched_tc<13>(ws, tiles, ea, eb, d, sms, s); break;
-        case 14: e = launch_batched_tc<14>(ws, tiles, ea, eb, d, sms, s); break;
-        case 15: e = launch_batched_tc<15>(ws, tiles, ea, eb, d, sms, s); break;
-        case 16: e = launch_batched_tc<16>(ws, tiles, ea, eb, d, sms, s); break;
-        default: return DDGEMM_EINVAL;
+    if (bits == INT8_BITS) {
+        switch (slices) {
+            case 12: e = launch_batched_tc<12, INT8_BITS>(ws, tiles, ea, eb, d, sms, s); break;
+            case 13: e = launch_batched_tc<13, INT8_BITS>(ws, tiles, ea, eb, d, sms, s); break;
+            case 14: e = launch_batched_tc<14, INT8_BITS>(ws, tiles, ea, eb, d, sms, s); break;
+            case 15: e = launch_batched_tc<15, INT8_BITS>(ws, tiles, ea, eb, d, sms, s); break;
+            default: return DDGEMM_EINVAL;
+        }
+    } else {
+        switch (slices) {
+            case 12: e = launch_batched_tc<12, INT8_TC_BITS>(ws, tiles, ea, eb, d, sms, s); break;
+            case 13: e = launch_batched_tc<13, INT8_TC_BITS>(ws, tiles, ea, eb, d, sms, s); break;
+            case 14: e = launch_batched_tc<14, INT8_TC_BITS>(ws, tiles, ea, eb, d, sms, s); break;
+            case 15: e = launch_batched_tc<15, INT8_TC_BITS>(ws, tiles, ea, eb, d, sms, s); break;
+            case 16: e = launch_batched_tc<16, INT8_TC_BITS>(ws, tiles, ea, eb, d, sms, s); break;
+            default: return DDGEMM_EINVAL;
+        }
     }
     return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }

@@ -141,10 +141,12 @@ cudaError_t launch_cascade_int8_tc8(const Int8TcArgs &a, cudaStream_t stream);
 
 // The batched tcgen05 INT8 form (batched_int8_tc.cu): workspace bytes, and
 // the whole pass (returns a DDGEMM_* code).
-size_t batched_int8_tc_workspace_size(int count, const ddgemm_problem *probs_host, int slices);
+// bits: 7 (DDGEMM_VARIANT_INT8_TC) or 8 (DDGEMM_VARIANT_INT8_TC8).
+size_t batched_int8_tc_workspace_size(int count, const ddgemm_problem *probs_host, int slices,
+                                      int bits);
 int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
                         const ddgemm_problem *probs_dev, void *workspace, size_t ws_bytes,
-                        cudaStream_t s, int slices, unsigned int *status);
+                        cudaStream_t s, int slices, int bits, unsigned int *status);
 
 // The exact assembly alone: (hi[i], lo[i]) = the FP64x2 nearest to
 // sum_t diag[t * count + i] 2^(-12-7t) 2^scale[i].

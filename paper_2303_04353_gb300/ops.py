@@ -285,8 +285,9 @@ class Batch:
     used."""
 
     def __init__(self, problems, device=None, variant=_lib.DDGEMM_VARIANT_FP64, int8_slices=0):
-        """variant: DDGEMM_VARIANT_FP64 (the persistent FP64 kernel) or
-        DDGEMM_VARIANT_INT8_TC (the INT8 form on the tcgen05 tensor cores)."""
+        """variant: DDGEMM_VARIANT_FP64 (the persistent FP64 kernel),
+        DDGEMM_VARIANT_INT8_TC (the INT8 form on the tcgen05 tensor cores) or
+        DDGEMM_VARIANT_INT8_TC8 (the same with eight-bit pieces)."""
         self.count = len(problems)
         self.variant = variant
         self.int8_slices = int8_slices

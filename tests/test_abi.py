@@ -274,8 +274,17 @@ def test_tc8_workspace_and_pieces():
     lib = _lib.load()
     flagged = _lib.make_opts(variant=tc8, flags_dev=FAKE)
     assert call(4, 4, 4, 4, 4, 4, opts=flagged) == _lib.DDGEMM_EUNSUPPORTED
+    # batched: the seven-bit form's layout with the eight-bit k-blocks, s <= 15
     arr = (_lib.ddgemm_problem * 1)()
-    arr[0] = _lib.ddgemm_problem(4, 5, 6, 6, 5, 5, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+    arr[0] = _lib.ddgemm_problem(4, 5, 20000, 20000, 5, 5, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
     o = _lib.make_opts(variant=tc8)
-    assert lib.ddgemm_batched(1, arr, FAKE, FAKE, 1 << 30, None, ctypes.byref(o), None) == \
-        _lib.DDGEMM_EUNSUPPORTED
+    need8 = _lib.ddgemm_batched_workspace_size(1, arr, o)
+    need7 = _lib.ddgemm_batched_workspace_size(1, arr, _lib.make_opts(
+        variant=_lib.DDGEMM_VARIANT_INT8_TC, int8_slices=15))
+    assert need8 >= need7 > 0
+    bad = _lib.make_opts(variant=tc8, int8_slices=16)
+    assert _lib.ddgemm_batched_workspace_size(1, arr, bad) == 0
+    assert lib.ddgemm_batched(1, arr, FAKE, FAKE, 1 << 30, None, ctypes.byref(bad), None) == \
+        _lib.DDGEMM_EINVAL
+    assert lib.ddgemm_batched(1, arr, FAKE, FAKE, 16, None, ctypes.byref(o), None) == \
+        _lib.DDGEMM_EWORKSPACE

@@ -158,10 +158,10 @@ def test_autotuner_picks_and_caches(mods, tmp_path, monkeypatch):
 TC = 4
 
 
-def reference_tc(ops, probs):
+def reference_tc(ops, probs, variant=TC):
     out = []
     for a_hi, a_lo, b_hi, b_lo, _, _ in probs:
-        out.append(ops.ddgemm(a_hi, a_lo, b_hi, b_lo, variant=TC))
+        out.append(ops.ddgemm(a_hi, a_lo, b_hi, b_lo, variant=variant))
     torch.cuda.synchronize()
     return [(h.cpu().numpy(), l.cpu().numpy()) for h, l in out]
 
@@ -218,3 +218,23 @@ def test_batched_tc_512_uneven_graph_replay(mods):
         gh, gl = got[i]
         assert np.all(np.abs((gh[rr.ravel(), cc.ravel()] - oh) + (gl[rr.ravel(), cc.ravel()] - ol))
                       <= 1e-28 * absab)
+
+
+TC8 = 5
+
+
+def test_batched_tc8_bit_identical_to_ddgemm(mods):
+    """The eight-bit tcgen05 form batched: every problem equals ddgemm() with
+    DDGEMM_VARIANT_INT8_TC8 on that problem alone, bit for bit, including a
+    problem with two k-blocks of 8192."""
+    _lib, ops, _ = mods
+    shapes = MIXED + [(20, 30, 8300)]
+    batch, probs, _ = make_batch(ops, shapes, seed=61, kind="wide", variant=TC8)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    batch.run(status=status)
+    got = results(probs)
+    want = reference_tc(ops, probs, variant=TC8)
+    assert int(status.item()) == 0
+    for (gh, gl), (wh, wl), (m, n, k) in zip(got, want, shapes):
+        if m and n:
+            assert np.array_equal(gh, wh) and np.array_equal(gl, wl), (m, n, k)
