@@ -184,56 +184,89 @@ __device__ __forceinline__ void add_diagonal(int t, int v, __int128 &H, __int128
         L += (__int128)v * ((__int128)1 << (TB * (S - 1 - t)));
 }
 
-// Add diagonals T0 .. T1-1 of one chunk, read from tensor memory (DCOLS
-// columns each, at base + 16 t), into acc[j] with the weights of
-// T = H 2^SPLIT + L: the diagonal T1-1 has weight 1 in its half, each
-// earlier one 2^TB more.  Four diagonals at a time are read with one wait
-// and combined exactly in an int64 (|sum| <= 2^24 per diagonal and chunk,
-// so below 2^(25 + 3 TB)), then added in.
-template <int S, int TB, int T0, int T1>
-__device__ __forceinline__ void fold_group(uint32_t base, __int128 (&acc)[DCOLS]) {
-    static_assert(T1 - T0 <= 8 && T1 > T0, "a half holds 1 to 8 diagonals");
+// The diagonals in groups of up to four: the H half [0, S-8) and the L half
+// [S-8, S) of T = H 2^SPLIT + L, each cut from its start.  Within its half
+// the last diagonal has weight 1 and each earlier one 2^TB more, so group q
+// enters its half with weight 2^shift(q) times its own combination.
+template <int S, int TB>
+struct Groups {
+    static constexpr int H_GROUPS = (S - 8 + 3) / 4;
+    static constexpr int COUNT = H_GROUPS + 2;
+    __device__ static constexpr int first(int q) {
+        return q < H_GROUPS ? 4 * q : S - 8 + 4 * (q - H_GROUPS);
+    }
+    __device__ static constexpr int end(int q) { return q < H_GROUPS ? S - 8 : S; }
+    __device__ static constexpr int len(int q) {
+        return end(q) - first(q) < 4 ? end(q) - first(q) : 4;
+    }
+    __device__ static constexpr int shift(int q) { return TB * (end(q) - first(q) - len(q)); }
+};
+
+// Group q of one chunk: its diagonals read from tensor memory (DCOLS
+// columns each, at base + 16 t) with one wait, combined exactly in an int64
+// (each FP32 value is an integer of magnitude <= 2^24, so the combination
+// stays below 2^(25 + 3 TB)) and added to the group's k-block sums acc[j].
+// Over a k-block a diagonal sums to below 2^31 (the k-block is chosen for
+// it), so a group's sum stays below 2^(32 + 3 TB) <= 2^56: exact in int64.
+template <int S, int TB, int Q>
+__device__ __forceinline__ void read_group(uint32_t base, long long (&acc)[DCOLS]) {
+    using Gr = Groups<S, TB>;
+    constexpr int g0 = Gr::first(Q), len = Gr::len(Q);
+    uint32_t r[4 * DCOLS];
+    if constexpr (len == 4) {
+        const uint32_t t[4] = {base + g0 * BN, base + (g0 + 1) * BN, base + (g0 + 2) * BN,
+                               base + (g0 + 3) * BN};
+        umma::ld_x4_n(t, r);
+    } else if constexpr (len == 3) {
+        const uint32_t t[3] = {base + g0 * BN, base + (g0 + 1) * BN, base + (g0 + 2) * BN};
+        uint32_t r3[3 * DCOLS];
+        umma::ld_x4_n(t, r3);
 #pragma unroll
-    for (int g0 = T0; g0 < T1; g0 += 4) {
-        const int len = (T1 - g0) < 4 ? (T1 - g0) : 4;
-        uint32_t r[4 * DCOLS];
-        if (len == 4) {
-            const uint32_t t[4] = {base + g0 * BN, base + (g0 + 1) * BN, base + (g0 + 2) * BN,
-                                   base + (g0 + 3) * BN};
-            umma::ld_x4_n(t, r);
-        } else if (len == 3) {
-            const uint32_t t[3] = {base + g0 * BN, base + (g0 + 1) * BN, base + (g0 + 2) * BN};
-            uint32_t r3[3 * DCOLS];
-            umma::ld_x4_n(t, r3);
+        for (int j = 0; j < 3 * DCOLS; ++j) r[j] = r3[j];
+    } else if constexpr (len == 2) {
+        const uint32_t t[2] = {base + g0 * BN, base + (g0 + 1) * BN};
+        uint32_t r2[2 * DCOLS];
+        umma::ld_x4_n(t, r2);
 #pragma unroll
-            for (int j = 0; j < 3 * DCOLS; ++j) r[j] = r3[j];
-        } else if (len == 2) {
-            const uint32_t t[2] = {base + g0 * BN, base + (g0 + 1) * BN};
-            uint32_t r2[2 * DCOLS];
-            umma::ld_x4_n(t, r2);
+        for (int j = 0; j < 2 * DCOLS; ++j) r[j] = r2[j];
+    } else {
+        const uint32_t t[1] = {base + g0 * BN};
+        uint32_t r1[DCOLS];
+        umma::ld_x4_n(t, r1);
 #pragma unroll
-            for (int j = 0; j < 2 * DCOLS; ++j) r[j] = r2[j];
-        } else {
-            const uint32_t t[1] = {base + g0 * BN};
-            uint32_t r1[DCOLS];
-            umma::ld_x4_n(t, r1);
+        for (int j = 0; j < DCOLS; ++j) r[j] = r1[j];
+    }
 #pragma unroll
-            for (int j = 0; j < DCOLS; ++j) r[j] = r1[j];
-        }
-        long long g[DCOLS];
+    for (int j = 0; j < DCOLS; ++j) {
+        long long g = __float2int_rn(__uint_as_float(r[j]));
 #pragma unroll
-        for (int j = 0; j < DCOLS; ++j) {
-            g[j] = __float2int_rn(__uint_as_float(r[j]));
-#pragma unroll
-            for (int d = 1; d < 4; ++d)
-                if (d < len)
-                    g[j] = g[j] * (1 << TB) + __float2int_rn(__uint_as_float(r[DCOLS * d + j]));
-        }
-        // weight of the group's last diagonal within its half
-        const int last = g0 + len - 1;
-        const int shift = TB * (T1 - 1 - last);
-#pragma unroll
-        for (int j = 0; j < DCOLS; ++j) acc[j] += (__int128)g[j] * ((__int128)1 << shift);
+        for (int d = 1; d < len; ++d)
+            g = g * (1 << TB) + __float2int_rn(__uint_as_float(r[DCOLS * d + j]));
+        acc[j] += g;
+    }
+}
+
+template <int S, int TB, int Q = 0>
+__device__ __forceinline__ void read_groups(uint32_t base,
+                                            long long (&acc)[Groups<S, TB>::COUNT][DCOLS]) {
+    if constexpr (Q < Groups<S, TB>::COUNT) {
+        read_group<S, TB, Q>(base, acc[Q]);
+        read_groups<S, TB, Q + 1>(base, acc);
+    }
+}
+
+// The k-block value of column x, T = H 2^SPLIT + L, from the group sums.
+template <int S, int TB, int Q = 0>
+__device__ __forceinline__ void block_value(const long long (&acc)[Groups<S, TB>::COUNT][DCOLS],
+                                            int x, __int128 &H, __int128 &L) {
+    if constexpr (Q < Groups<S, TB>::COUNT) {
+        using Gr = Groups<S, TB>;
+        const __int128 v = (__int128)acc[Q][x] * ((__int128)1 << Gr::shift(Q));
+        if (Q < Gr::H_GROUPS)
+            H += v;
+        else
+            L += v;
+        block_value<S, TB, Q + 1>(acc, x, H, L);
     }
 }
 
@@ -454,9 +487,12 @@ cascade_int8_tc_kernel(const Src src) {
                         j.c_lo[(long long)row * j.ldc + col0 + x] = 0.0;
                     }
             }
-            __int128 H[DCOLS], L[DCOLS];
+            // per group of diagonals and column, the k-block's exact sums
+            long long acc[Groups<S, TB>::COUNT][DCOLS];
 #pragma unroll
-            for (int x = 0; x < DCOLS; ++x) H[x] = L[x] = 0;
+            for (int q = 0; q < Groups<S, TB>::COUNT; ++q)
+#pragma unroll
+                for (int x = 0; x < DCOLS; ++x) acc[q][x] = 0;
             for (int c = 0; c < nchunks; ++c, ++chunk) {
                 const int b = chunk & 1;
                 // every lane waits; the warp goes on only together (the
@@ -470,8 +506,7 @@ cascade_int8_tc_kernel(const Src src) {
                 umma::fence_after();
                 const uint32_t base = lane_base + b * ACC_STRIDE;
                 // diagonals 0 .. S-9 belong to H, S-8 .. S-1 to L
-                fold_group<S, TB, 0, S - 8>(base, H);
-                fold_group<S, TB, S - 8, S>(base, L);
+                read_groups<S, TB>(base, acc);
                 umma::fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_addr(&sh->acc_empty[b]));
@@ -487,8 +522,10 @@ cascade_int8_tc_kernel(const Src src) {
                             if (col < j.n) {
                                 const int e = ea + j.exp_b[(long long)p * j.n + col] - 12 -
                                               TB * (S - 1);
+                                __int128 H = 0, L = 0;
+                                block_value<S, TB>(acc, x, H, L);
                                 double h, l;
-                                round_dd<W::SPLIT>(H[x], L[x], e, h, l);
+                                round_dd<W::SPLIT>(H, L, e, h, l);
                                 const long long o = (long long)row * j.ldc + col;
                                 double ch = 0.0, cl = 0.0;
                                 if (p > 0) {
@@ -502,7 +539,9 @@ cascade_int8_tc_kernel(const Src src) {
                         }
                     }
 #pragma unroll
-                    for (int x = 0; x < DCOLS; ++x) H[x] = L[x] = 0;
+                    for (int q = 0; q < Groups<S, TB>::COUNT; ++q)
+#pragma unroll
+                        for (int x = 0; x < DCOLS; ++x) acc[q][x] = 0;
                 }
             }
         }
