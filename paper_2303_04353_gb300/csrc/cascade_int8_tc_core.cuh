@@ -91,6 +91,29 @@ __device__ __forceinline__ int bitlen128(unsigned __int128 x) {
     return l ? 64 - __clzll((long long)l) : 0;
 }
 
+// m 2^e as a double, for 0 < m <= 2^53 (every such m is exact in a double):
+// the IEEE bits are put together on the integer pipes when the result is a
+// normal number (the FP64 pipe is narrow on this GPU and the epilogues run
+// this per output), otherwise scalbn does it.
+__device__ __forceinline__ double scaled(unsigned long long m, int e) {
+    const int b = 64 - __clzll((long long)m);  // 1 .. 54
+    if (b > 53) {                              // m = 2^53
+        m >>= 1;
+        e += 1;
+    } else {
+        m <<= 53 - b;
+        e -= 53 - b;
+    }
+    const int be = e + 52 + 1023;              // biased exponent of m 2^e
+    if (be >= 1 && be <= 2046)
+        return __longlong_as_double(((long long)be << 52) | (long long)(m & ((1ull << 52) - 1)));
+    return scalbn((double)m, e);
+}
+
+__device__ __forceinline__ double with_sign(double v, bool neg) {
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
+}
+
 // Nearest double (ties to even) to the signed integer r times 2^e, |r| < 2^127.
 __device__ __forceinline__ double round_int(__int128 r, int e) {
     if (r == 0) return 0.0;
@@ -99,16 +122,16 @@ __device__ __forceinline__ double round_int(__int128 r, int e) {
     const int q = bitlen128(u);
     double v;
     if (q <= 53) {
-        v = scalbn((double)(unsigned long long)u, e);
+        v = scaled((unsigned long long)u, e);
     } else {
         const int sh = q - 53;
         unsigned long long m = (unsigned long long)(u >> sh);
         const unsigned __int128 rem = u & (((unsigned __int128)1 << sh) - 1);
         const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
         if (rem > half || (rem == half && (m & 1ull))) ++m;
-        v = scalbn((double)m, sh + e);
+        v = scaled(m, sh + e);
     }
-    return neg ? -v : v;
+    return with_sign(v, neg);
 }
 
 // The FP64x2 nearest to T 2^e with T = H 2^SPLIT + L (|H| < 2^80,
@@ -142,8 +165,7 @@ __device__ __forceinline__ void round_dd(__int128 H, __int128 L, int e, double &
     }
     const int p = Hm ? SPLIT + bitlen128(Hm) : 64 - __clzll((long long)Lm);
     if (p <= 53) {  // then Hm = 0 and |T| = Lm < 2^53
-        const double v = scalbn((double)Lm, e);
-        hi = neg ? -v : v;
+        hi = with_sign(scaled(Lm, e), neg);
         lo = 0.0;
         return;
     }
@@ -168,8 +190,7 @@ __device__ __forceinline__ void round_dd(__int128 H, __int128 L, int e, double &
     } else {
         r = (__int128)rem;
     }
-    const double vh = scalbn((double)m, sh + e);
-    hi = neg ? -vh : vh;
+    hi = with_sign(scaled(m, sh + e), neg);
     lo = round_int(neg ? -r : r, e);
 }
 
@@ -527,14 +548,22 @@ cascade_int8_tc_kernel(const Src src) {
                                 double h, l;
                                 round_dd<W::SPLIT>(H, L, e, h, l);
                                 const long long o = (long long)row * j.ldc + col;
-                                double ch = 0.0, cl = 0.0;
                                 if (p > 0) {
-                                    ch = j.c_hi[o];
-                                    cl = j.c_lo[o];
+                                    double ch = j.c_hi[o], cl = j.c_lo[o];
+                                    dd_add(ch, cl, h, l, ch, cl);
+                                    j.c_hi[o] = ch;
+                                    j.c_lo[o] = cl;
+                                } else {
+                                    // C = (0, 0) + (h, l): with h, l not -0 and
+                                    // |l| <= |h| (round_dd), the FP64x2 add reduces to
+                                    // the same FastTwoSum of h and l and the add of
+                                    // the zero low word (which turns a -0 into +0)
+                                    const double s1 = __dadd_rn(h, l);
+                                    const double e1 = __dadd_rn(
+                                        __dsub_rn(l, __dsub_rn(s1, h)), 0.0);
+                                    j.c_hi[o] = s1;
+                                    j.c_lo[o] = e1;
                                 }
-                                dd_add(ch, cl, h, l, ch, cl);
-                                j.c_hi[o] = ch;
-                                j.c_lo[o] = cl;
                             }
                         }
                     }
