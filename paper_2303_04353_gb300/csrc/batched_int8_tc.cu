@@ -87,12 +87,14 @@ __device__ inline int find_tc(const long long *prefix, int count, long long u) {
 }
 
 // Longest k first, then larger m n, then index.
-__device__ inline bool before_tc(const ddgemm_problem &a, int ia, const ddgemm_problem &b, int ib) {
-    if (a.k != b.k) return a.k > b.k;
-    const long long sa = (long long)a.m * a.n, sb = (long long)b.m * b.n;
+__device__ inline bool before_tc(int ka, long long sa, int ia, int kb, long long sb, int ib) {
+    if (ka != kb) return ka > kb;
     if (sa != sb) return sa > sb;
     return ia < ib;
 }
+
+// Problems whose ordering keys the plan kernel keeps in shared memory.
+constexpr int PLAN_SMEM_KEYS = 2048;
 
 __global__ void __launch_bounds__(256)
 tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, int slices,
@@ -106,6 +108,18 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
     long long *eb_pre = reinterpret_cast<long long *>(ws + L.eb_pre);
     long long *da_pre = reinterpret_cast<long long *>(ws + L.da_pre);
     long long *db_pre = reinterpret_cast<long long *>(ws + L.db_pre);
+    // the ordering keys (k, m n) in shared memory when they fit: the rank of
+    // a problem compares it with every other one
+    __shared__ int key_k[PLAN_SMEM_KEYS];
+    __shared__ long long key_mn[PLAN_SMEM_KEYS];
+    const bool keys_in_smem = count <= PLAN_SMEM_KEYS;
+    if (keys_in_smem) {
+        for (int i = threadIdx.x; i < count; i += blockDim.x) {
+            key_k[i] = probs[i].k;
+            key_mn[i] = (long long)probs[i].m * probs[i].n;
+        }
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
         const ddgemm_problem q = probs[i];
         TcEntry e;
@@ -123,16 +137,79 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
         e.da_units = work ? (long long)((q.m + split8::TV - 1) / split8::TV) * ktiles : 0;
         e.db_units = work ? (long long)((q.n + split8::TV - 1) / split8::TV) * ktiles : 0;
         ent[i] = e;
+        const long long qmn = (long long)q.m * q.n;
         int r = 0;
-        for (int j = 0; j < count; ++j)
-            if (j != i && before_tc(probs[j], j, q, i)) ++r;
+        if (keys_in_smem) {
+            for (int j = 0; j < count; ++j)
+                if (j != i && before_tc(key_k[j], key_mn[j], j, q.k, qmn, i)) ++r;
+        } else {
+            for (int j = 0; j < count; ++j)
+                if (j != i && before_tc(probs[j].k, (long long)probs[j].m * probs[j].n, j, q.k,
+                                        qmn, i))
+                    ++r;
+        }
         order[r] = i;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        size_t off = L.data;
-        long long ta = 0, tb = 0, tda = 0, tdb = 0;
-        for (int i = 0; i < count; ++i) {
+    // Prefix sums over the problems (units, workspace bytes) and over the
+    // ranks (tiles): thread t takes a contiguous segment, the 256 segment
+    // totals are scanned by one warp per quantity, then every thread walks
+    // its segment again from its offsets.
+    constexpr int NQ = 6;  // ea, eb, da, db units; bytes; tiles (rank order)
+    __shared__ long long part[NQ][256];  // blockDim.x <= 256
+    const int nt = blockDim.x, t = threadIdx.x;
+    const int seg = (count + nt - 1) / nt;
+    const int i0 = min(count, t * seg), i1 = min(count, i0 + seg);
+    auto bytes_of = [&](const TcEntry &e) -> size_t {
+        if (e.ea_units <= 0) return 0;
+        const size_t kpad = ru_tc((size_t)e.k, 16);
+        return ru_tc((size_t)slices * ru_tc((size_t)e.m, INT8_TC_BM) * kpad * 2, TC_ALIGN) +
+               ru_tc((size_t)slices * ru_tc((size_t)e.n, INT8_TC_BN) * kpad * 2, TC_ALIGN) +
+               ru_tc((size_t)e.kb8 * e.m * 4, TC_ALIGN) + ru_tc((size_t)e.kb8 * e.n * 4, TC_ALIGN);
+    };
+    {
+        long long acc[NQ] = {0, 0, 0, 0, 0, 0};
+        for (int i = i0; i < i1; ++i) {
+            const TcEntry &e = ent[i];
+            acc[0] += e.ea_units;
+            acc[1] += e.eb_units;
+            acc[2] += e.da_units;
+            acc[3] += e.db_units;
+            acc[4] += (long long)bytes_of(e);
+            acc[5] += ent[order[i]].tiles;
+        }
+        for (int q = 0; q < NQ; ++q) part[q][t] = acc[q];
+    }
+    __syncthreads();
+    {
+        // exclusive scan of part[q][0 .. nt-1] by warp q (nt <= 256)
+        const int w = t >> 5, lane = t & 31;
+        if (w < NQ) {
+            long long v[8], run = 0;
+            for (int j = 0; j < 8; ++j) {
+                const int x = lane * 8 + j;
+                v[j] = x < nt ? part[w][x] : 0;
+                run += v[j];
+            }
+            long long incl = run;
+            for (int off = 1; off < 32; off <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            long long pre = incl - run;
+            for (int j = 0; j < 8; ++j) {
+                const int x = lane * 8 + j;
+                if (x < nt) part[w][x] = pre;
+                pre += v[j];
+            }
+        }
+    }
+    __syncthreads();
+    {
+        long long ta = part[0][t], tb = part[1][t], tda = part[2][t],
+                  tdb = part[3][t], tt = part[5][t];
+        size_t off = L.data + (size_t)part[4][t];
+        for (int i = i0; i < i1; ++i) {
             TcEntry &e = ent[i];
             ea_pre[i] = ta;
             eb_pre[i] = tb;
@@ -155,24 +232,23 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
                 e.e_b = reinterpret_cast<int *>(ws + off);
                 off += ru_tc((size_t)e.kb8 * e.n * 4, TC_ALIGN);
             }
+            tile_pre[i] = tt;
+            tt += ent[order[i]].tiles;
         }
-        ea_pre[count] = ta;
-        eb_pre[count] = tb;
-        da_pre[count] = tda;
-        db_pre[count] = tdb;
-        long long tt = 0;
-        for (int r = 0; r < count; ++r) {
-            tile_pre[r] = tt;
-            tt += ent[order[r]].tiles;
+        if (i1 == count && i0 < i1) {  // the last non-empty segment: the totals
+            ea_pre[count] = ta;
+            eb_pre[count] = tb;
+            da_pre[count] = tda;
+            db_pre[count] = tdb;
+            tile_pre[count] = tt;
+            hdr->total_tiles = tt;
+            hdr->total_ea = ta;
+            hdr->total_eb = tb;
+            hdr->total_d = tda + tdb;
+            hdr->count = count;
+            hdr->kblk = kblk;
+            hdr->status = status;
         }
-        tile_pre[count] = tt;
-        hdr->total_tiles = tt;
-        hdr->total_ea = ta;
-        hdr->total_eb = tb;
-        hdr->total_d = tda + tdb;
-        hdr->count = count;
-        hdr->kblk = kblk;
-        hdr->status = status;
     }
 }
 
@@ -226,7 +302,7 @@ __global__ void __launch_bounds__(256) tc_exps_b_kernel(const char *ws) {
 
 // Digits of every A, then of every B: one CTA per 32 x 64 input tile.
 template <int S, int BITS>
-__global__ void __launch_bounds__(256) tc_digits_kernel(const char *ws) {
+__global__ void __launch_bounds__(256, 4) tc_digits_kernel(const char *ws) {
     __shared__ double sh[split8::TV][split8::TK + 1];
     __shared__ double sl[split8::TV][split8::TK + 1];
     const TcView V(ws);
