@@ -86,6 +86,29 @@ __device__ inline int find_tc(const long long *prefix, int count, long long u) {
     return lo;
 }
 
+// The same search for a caller that visits units in increasing order:
+// from its previous answer `i` it gallops forward (a few steps when the next
+// unit is near), falling back to the full search if u lies before it.
+__device__ inline int advance_tc(const long long *prefix, int count, long long u, int i) {
+    if (prefix[i] > u) return find_tc(prefix, count, u);
+    int lo = i, step = 1, hi;
+    for (;;) {
+        hi = lo + step;
+        if (hi >= count) {
+            hi = count;  // prefix[count] = total > u
+            break;
+        }
+        if (prefix[hi] > u) break;
+        lo = hi;
+        step <<= 1;
+    }
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // Longest k first, then larger m n, then index.
 __device__ inline bool before_tc(int ka, long long sa, int ia, int kb, long long sb, int ib) {
     if (ka != kb) return ka > kb;
@@ -270,7 +293,8 @@ struct TcView {
     }
 };
 
-// Exponents of every A: one warp per (problem, row, k-block).
+// Exponents of every A: one warp per (problem, row, k-block).  Neighbouring
+// warps take neighbouring units (a contiguous run per warp measured slower).
 __global__ void __launch_bounds__(256) tc_exps_a_kernel(const char *ws) {
     const TcView V(ws);
     const int count = V.hdr->count, lane = threadIdx.x & 31;
@@ -309,10 +333,14 @@ __global__ void __launch_bounds__(256, 4) tc_digits_kernel(const char *ws) {
     const int count = V.hdr->count;
     const long long total_a = V.da_pre[count];
     unsigned int *status = V.hdr->status;
-    for (long long u = blockIdx.x; u < V.hdr->total_d; u += gridDim.x) {
+    // each CTA walks a contiguous run of units
+    const long long total = V.hdr->total_d, run = (total + gridDim.x - 1) / gridDim.x;
+    const long long u0 = (long long)blockIdx.x * run, u1 = u0 + run < total ? u0 + run : total;
+    int ia = 0, ib = 0;
+    for (long long u = u0; u < u1; ++u) {
         __syncthreads();  // the previous unit is done with sh, sl
         if (u < total_a) {
-            const int i = find_tc(V.da_pre, count, u);
+            const int i = ia = advance_tc(V.da_pre, count, u, ia);
             const TcEntry &e = V.ent[i];
             const long long local = u - V.da_pre[i];
             const int ktiles = (e.k + split8::TK - 1) / split8::TK;
@@ -322,7 +350,7 @@ __global__ void __launch_bounds__(256, 4) tc_digits_kernel(const char *ws) {
                                                e.e_a, status, sh, sl);
         } else {
             const long long ub = u - total_a;
-            const int i = find_tc(V.db_pre, count, ub);
+            const int i = ib = advance_tc(V.db_pre, count, ub, ib);
             const TcEntry &e = V.ent[i];
             const long long local = ub - V.db_pre[i];
             const int ktiles = (e.k + split8::TK - 1) / split8::TK;
@@ -344,9 +372,11 @@ struct BatchSource {
     __device__ unsigned int *status() const {
         return reinterpret_cast<const TcHeader *>(ws)->status;
     }
-    __device__ TcJob job(long long item, int) const {
+    // hint: the rank of the caller's previous item (items come in
+    // increasing order)
+    __device__ TcJob job(long long item, int, int &hint) const {
         const TcView V(ws);
-        const int r = find_tc(V.tile_pre, V.hdr->count, item);
+        const int r = hint = advance_tc(V.tile_pre, V.hdr->count, item, hint);
         const TcEntry &e = V.ent[V.order[r]];
         const long long local = item - V.tile_pre[r];
         int tm, tn;

@@ -310,7 +310,7 @@ struct SingleSource {
     int tiles_m, tiles_n, groups_n, cl;
     __device__ long long items() const { return (long long)tiles_m * groups_n; }
     __device__ unsigned int *status() const { return a.status; }
-    __device__ TcJob job(long long item, int rank) const {
+    __device__ TcJob job(long long item, int rank, int &) const {
         int tm, tg;
         grouped_tile((unsigned)item, tiles_m, groups_n, TILE_GROUP, tm, tg);
         const int tn = tg * cl + rank;
@@ -385,8 +385,9 @@ cascade_int8_tc_kernel(const Src src) {
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
+            int hint = 0;  // the job source's position (items come in order)
             for (long long tile = first; ok && tile < tiles; tile += stride) {
-                const TcJob j = src.job(tile, rank);
+                const TcJob j = src.job(tile, rank, hint);
                 const int ksteps = (j.k + BK - 1) / BK;
                 for (int ks = 0; ks < ksteps; ++ks, ++it) {
                     const int stage = it % NST;
@@ -430,8 +431,9 @@ cascade_int8_tc_kernel(const Src src) {
         if (lane == 0) {
             uint32_t it = 0, chunk = 0;
             bool ok = true;
+            int hint = 0;
             for (long long tile = first; ok && tile < tiles; tile += stride) {
-                const TcJob j = src.job(tile, rank);
+                const TcJob j = src.job(tile, rank, hint);
                 const int ksteps = (j.k + BK - 1) / BK;
                 const int nchunks = (ksteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
                 for (int c = 0; ok && c < nchunks; ++c, ++chunk) {
@@ -494,8 +496,9 @@ cascade_int8_tc_kernel(const Src src) {
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + part * DCOLS;
         uint32_t chunk = 0;
         bool ok = true;
+        int hint = 0;
         for (long long tile = first; ok && tile < tiles; tile += stride) {
-            const TcJob j = src.job(tile, rank);
+            const TcJob j = src.job(tile, rank, hint);
             const int ksteps = (j.k + BK - 1) / BK;
             const int nchunks = (ksteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
             const int row = j.tm * BM + row_in_tile;
