@@ -557,6 +557,38 @@ def run_ours(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_batched_tc_only(args, shapes, probs, flops, stream):
+    """The batched tcgen05 INT8 pass alone on the 512-problem workload (for
+    profiling it): --steps timed calls after --warmup, no graph, no other
+    form.  Study line."""
+    import torch
+
+    from paper_2303_04353_gb300 import _lib, ops
+
+    variant = (_lib.DDGEMM_VARIANT_INT8_TC if args.variant == "int8tc"
+               else _lib.DDGEMM_VARIANT_INT8_TC8)
+    batch = ops.Batch(probs, variant=variant)
+    status = torch.zeros(1, dtype=torch.int32, device=stream.device)
+    for _ in range(args.warmup):
+        batch.run(stream=stream, status=status)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.run(stream=stream, status=status)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if int(status.item()):
+        raise SystemExit(f"bench.py: device status {int(status.item()):#x}")
+    ms = e0.elapsed_time(e1) / args.steps
+    tiles = sum(((m + 127) // 128) * ((n + 15) // 16) for m, n, _ in shapes if m and n)
+    print(json.dumps({"study": "batched tcgen05 INT8 pass alone", "variant": args.variant,
+                      "problems": len(shapes), "tiles": tiles, "ms": round(ms, 3),
+                      "effective_gflops": round(flops / (ms * 1e-3) / 1e9, 1),
+                      "launches": 5}), flush=True)
+
+
 def run_batched(args):
     """Config 3: 512 independent problems, m, n, k each log-uniform in
     [64, 1024], uniform entries; one graph-captured pass of the batched form
@@ -579,6 +611,9 @@ def run_batched(args):
         probs.append((*t, torch.empty((m, n), dtype=torch.float64, device=dev),
                       torch.empty((m, n), dtype=torch.float64, device=dev)))
     flops = sum(2.0 * m * n * k for m, n, k in shapes)
+    if args.variant in ("int8tc", "int8tc8"):
+        run_batched_tc_only(args, shapes, probs, flops, stream)
+        return
     batch = ops.Batch(probs)
     cfg, tune_ms = autotune.tune(batch, reps=2)
 
