@@ -202,7 +202,7 @@ def test_cascade_meets_paper_bound(m, n, k, kind):
 
 
 def test_cascade_vs_dd_oracle_contract():
-    """The spec contract |C - C_dd| <= 1e-28 (|A||B|) holds for the
+    """The accuracy contract |C - C_dd| <= 1e-28 (|A||B|) holds for the
     cascade restated on the CPU (uniform and wide inputs)."""
     for kind in ("uniform", "wide"):
         a_hi, a_lo, b_hi, b_lo = gemm_inputs(40, 48, 600, kind=kind, seed=9)
