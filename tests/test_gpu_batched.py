@@ -238,3 +238,23 @@ def test_batched_tc8_bit_identical_to_ddgemm(mods):
     for (gh, gl), (wh, wl), (m, n, k) in zip(got, want, shapes):
         if m and n:
             assert np.array_equal(gh, wh) and np.array_equal(gl, wl), (m, n, k)
+
+
+@pytest.mark.parametrize("count", [1001, 2100])
+def test_batched_tc_many_small_problems(mods, count):
+    """Many small problems (and empty ones): the plan's ranking (its keys in
+    shared memory up to 2048 problems, from global memory above) and its
+    segmented prefix sums; every C equals ddgemm() with the tcgen05 form."""
+    _lib, ops, _ = mods
+    rng = np.random.default_rng(count)
+    shapes = [(int(rng.integers(0, 40)), int(rng.integers(0, 40)), int(rng.integers(0, 300)))
+              for _ in range(count)]
+    batch, probs, _ = make_batch(ops, shapes, seed=7, kind="wide", variant=TC)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    batch.run(status=status)
+    got = results(probs)
+    want = reference_tc(ops, probs)
+    assert int(status.item()) == 0
+    for (gh, gl), (wh, wl), (m, n, k) in zip(got, want, shapes):
+        if m and n:
+            assert np.array_equal(gh, wh) and np.array_equal(gl, wl), (m, n, k)
