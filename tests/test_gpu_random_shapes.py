@@ -2,8 +2,8 @@
 k drawn in [1, 300] with ragged tiles, both value kinds, random
 transposition of either operand.
 
-* the INT8 form on mma.sync and on tcgen05: bit-identical to their CPU
-  restatements (oracle/cascade_int8.py);
+* the INT8 form on mma.sync and on tcgen05 (seven- and eight-bit pieces):
+  bit-identical to their CPU restatements (oracle/cascade_int8.py);
 * the FP64 form: within the paper's bound of the double-double oracle and
   within the summation-order tolerance of the cascade restatement
   (tests/test_gpu_parity.py's check)."""
@@ -50,7 +50,8 @@ def test_random_shape_all_forms(ops, c, m, n, k, kind, ta, tb):
     check_against_oracles(ops, a_hi, a_lo, b_hi, b_lo, trans_a=ta, trans_b=tb,
                           contract=kind == "uniform")
     # INT8 forms, bit for bit
-    for variant, s, assembly, bits in ((1, 15, "fp64x2", 8), (4, 16, "exact", 7)):
+    for variant, s, assembly, bits in ((1, 15, "fp64x2", 8), (4, 16, "exact", 7),
+                                       (5, 15, "exact", 8)):
         status = torch.zeros(1, dtype=torch.int32, device="cuda")
         c_hi, c_lo = ops.ddgemm(*dev(*sa), *dev(*sb), trans_a=ta, trans_b=tb, variant=variant,
                                 status=status)
