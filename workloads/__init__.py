@@ -73,3 +73,18 @@ def batched_shapes(count=512, lo=64, hi=1024, seed=0):
     rng = np.random.default_rng(seed)
     u = rng.uniform(np.log(lo), np.log(hi + 1), size=(count, 3))
     return np.floor(np.exp(u)).astype(np.int64).clip(lo, hi)
+
+
+def device_uniform_dd(shape, seed, device="cuda"):
+    """A uniform FP64x2 matrix drawn on a CUDA device, for operands too large
+    to draw on the host: hi ~ U[-1, 1], lo = hi * 2**-53 * U[-1, 1], from
+    torch's seeded generator on that device (its own stream of values, not
+    numpy's: tests gather the entries they check back to the host)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    hi = torch.empty(shape, dtype=torch.float64, device=device).uniform_(-1.0, 1.0, generator=g)
+    lo = torch.empty_like(hi).uniform_(-1.0, 1.0, generator=g)
+    lo.mul_(hi).mul_(TWO_M53)
+    return hi, lo
