@@ -12,10 +12,10 @@
  * Appendix A): k is staged in blocks of K_C = 256.  For every k-block each
  * row of A and each column of B is scaled by a power of two (sigma, tau)
  * and split into four FP64 pieces holding 22, 21 and 21 fixed-point digits
- * (more for a block shorter than 256) plus an FP64 remainder; B also gets the combined panels B4, B5, B6.  Ten
- * FP64 products land in four bins (0, 1, 2 exact; 3-6 rounded), which are
- * added from bin 3-6 up to bin 0 in FP64x2, scaled back by sigma tau and
- * accumulated into C in FP64x2.
+ * (more for a block shorter than 256) plus an FP64 remainder; B also gets
+ * the combined panels B4, B5, B6.  Ten FP64 products land in four bins
+ * (0, 1, 2 exact; 3-6 rounded), which are added from bin 3-6 up to bin 0
+ * in FP64x2, scaled back by sigma tau and accumulated into C in FP64x2.
  *
  * Conventions for every entry point:
  *   - Matrices are row-major.  Element (r, c) of a matrix with leading
