@@ -97,11 +97,34 @@ __host__ __device__ constexpr __int128 digit_offset() {
     return c;
 }
 
-// bf16 encoding of a small integer: the upper half of its FP32 encoding,
-// exact because the FP32 significand of |d| <= 128 has at most 8 bits (bf16
-// keeps 8).
-__device__ __forceinline__ unsigned long long bf16_bits(int d) {
-    return (unsigned long long)(__float_as_uint((float)d) >> 16);
+// Field i (least significant first) of the offset value Y, 0 <= field <
+// 2^BITS + 1: digit i plus 2^(BITS-1).  The top field (i = S-1) is Y's
+// signed top part plus 2^(BITS-1).
+template <int S, int BITS>
+__device__ __forceinline__ uint32_t digit_field(__int128 Y, int i) {
+    if (i == S - 1) return (uint32_t)((int)(Y >> (BITS * (S - 1))) + (1 << (BITS - 1)));
+    const int b0 = BITS * i;
+    const unsigned long long y_lo = (unsigned long long)Y;
+    const unsigned long long y_hi = (unsigned long long)(Y >> 64);
+    unsigned long long field;
+    if (b0 + BITS <= 64)
+        field = y_lo >> b0;
+    else if (b0 >= 64)
+        field = y_hi >> (b0 - 64);
+    else
+        field = (y_lo >> b0) | (y_hi << (64 - b0));
+    return (uint32_t)field & ((1u << BITS) - 1u);
+}
+
+// The FP32 encoding of the digit d = f - 2^(BITS-1) for a field
+// 0 <= f < 2^23: the bit pattern 0x4B000000 | f is the float 2^23 + f, and
+// subtracting 2^23 + 2^(BITS-1) is exact (every operand and the result are
+// integers below 2^24).  Its upper half is the bf16 encoding of d, exact
+// because |d| <= 2^BITS has at most 8 significant bits (bf16 keeps 8).
+template <int BITS>
+__device__ __forceinline__ uint32_t digit_fp32(uint32_t f) {
+    constexpr float bias = 8388608.0f + (float)(1 << (BITS - 1));
+    return __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | f), bias));
 }
 
 // Element offset of the 8-entry group (v, l .. l+7) of plane s in the tiled
@@ -154,69 +177,62 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
     if (gv >= nvec) return;
     const int e = exps[(long long)(l0 / kblock_of_bits(BITS)) * nvec + gv];
     constexpr int F = 6 + BITS * (S - 1);
-    // 8 entries per plane: one 8-byte word of int8, or two of bf16
-    constexpr int WORDS = BF16 ? 2 : 1;
-    unsigned long long word[S][WORDS];
-#pragma unroll
-    for (int s = 0; s < S; ++s)
-#pragma unroll
-        for (int w = 0; w < WORDS; ++w) word[s][w] = 0;
     bool bad = false;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const double hi = sh[v][lg * 8 + j], lo = sl[v][lg * 8 + j];
-        bad |= !isfinite(hi) || !isfinite(lo);
+    const int gl = l0 + lg * 8;
+    if constexpr (BF16) {
         // Balanced base-2^BITS digits as bit fields: with Y = X +
         // sum_{i<s-1} 2^(BITS-1) 2^(BITS i), digit i (least significant
         // first) is field i of Y minus 2^(BITS-1), and the top digit is
-        // Y >> BITS (s-1).  The same digits as peeling d = ((X + h) mod 2 h)
-        // - h, X = (X - d) / 2h (h = 2^(BITS-1)), one 128-bit subtract and
-        // shift at a time, in a few operations each.
-        const __int128 Y =
-            rne_scaled(hi, F - e) + rne_scaled(lo, F - e) + digit_offset<S, BITS>();
-        const unsigned long long y_lo = (unsigned long long)Y;
-        const unsigned long long y_hi = (unsigned long long)(Y >> 64);
+        // Y >> BITS (s-1) (the same digits as peeling d = ((X + h) mod 2 h)
+        // - h, X = (X - d) / 2h with h = 2^(BITS-1)).
+        __int128 Y[8];
 #pragma unroll
-        for (int s = S - 1; s >= 0; --s) {
-            const int i = S - 1 - s;  // digit position, least significant first
-            int d;
-            if (s > 0) {
-                const int b0 = BITS * i;   // first bit of the field
-                unsigned long long field;
-                if (b0 + BITS <= 64)
-                    field = y_lo >> b0;
-                else if (b0 >= 64)
-                    field = y_hi >> (b0 - 64);
-                else
-                    field = (y_lo >> b0) | (y_hi << (64 - b0));
-                d = (int)(field & ((1ull << BITS) - 1)) - (1 << (BITS - 1));
-            } else {
-                d = (int)(Y >> (BITS * (S - 1)));
-            }
-            if constexpr (BF16)
-                word[s][j >> 2] |= bf16_bits(d) << (16 * (j & 3));
-            else
-                word[s][0] |= (unsigned long long)(uint8_t)(int8_t)d << (8 * j);
+        for (int j = 0; j < 8; ++j) {
+            const double hi = sh[v][lg * 8 + j], lo = sl[v][lg * 8 + j];
+            bad |= !isfinite(hi) || !isfinite(lo);
+            Y[j] = rne_scaled(hi, F - e) + rne_scaled(lo, F - e) + digit_offset<S, BITS>();
         }
-    }
-    if (bad && status) atomicOr(status, DEV_NONFINITE);
-    const int gl = l0 + lg * 8;
-    if constexpr (BF16) {
+        if (bad && status) atomicOr(status, DEV_NONFINITE);
         // the tiled order is read a whole k-step of 16 at a time: groups past
         // kdim up to the next multiple of 16 are written with zero digits
         if (gl >= (kdim + 15) / 16 * 16) return;
         const int ksteps = (kdim + 15) / 16;
+        // plane s holds digit S-1-s; two entries' bf16 digits share a
+        // 32-bit word, each plane's 8 entries one 16-byte store
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            uint4 q;
-            q.x = (unsigned)word[s][0];
-            q.y = (unsigned)(word[s][0] >> 32);
-            q.z = (unsigned)word[s][1];
-            q.w = (unsigned)(word[s][1] >> 32);
+            uint32_t w[4];
+#pragma unroll
+            for (int jp = 0; jp < 4; ++jp)
+                w[jp] = __byte_perm(digit_fp32<BITS>(digit_field<S, BITS>(Y[2 * jp], S - 1 - s)),
+                                    digit_fp32<BITS>(digit_field<S, BITS>(Y[2 * jp + 1], S - 1 - s)),
+                                    0x7632);
             *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(out_v) +
-                                       tiled_offset<S>(gv, gl, s, th, ksteps)) = q;
+                                       tiled_offset<S>(gv, gl, s, th, ksteps)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
         }
     } else {
+        // int8 planes (eight-bit pieces): 8 entries per plane in one 8-byte
+        // word
+        static_assert(BITS == 8, "int8 planes hold eight-bit pieces");
+        unsigned long long word[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) word[s] = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const double hi = sh[v][lg * 8 + j], lo = sl[v][lg * 8 + j];
+            bad |= !isfinite(hi) || !isfinite(lo);
+            // the digits as in the bf16 branch; the int8 digit d = f - 128 is
+            // the byte f ^ 0x80
+            const __int128 Y =
+                rne_scaled(hi, F - e) + rne_scaled(lo, F - e) + digit_offset<S, BITS>();
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                word[s] |= (unsigned long long)((digit_field<S, BITS>(Y, S - 1 - s) ^ 0x80u) &
+                                                0xffu)
+                           << (8 * j);
+        }
+        if (bad && status) atomicOr(status, DEV_NONFINITE);
         if (gl >= kdim) return;
         // entries past kdim in the last group of 8 carry zero digits; they
         // sit in the row padding (ld_out >= kdim rounded up to 16) and are
@@ -224,7 +240,7 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const long long o = ((long long)s * nvec + gv) * ld_out + gl;
-            *reinterpret_cast<unsigned long long *>(static_cast<int8_t *>(out_v) + o) = word[s][0];
+            *reinterpret_cast<unsigned long long *>(static_cast<int8_t *>(out_v) + o) = word[s];
         }
     }
 }
