@@ -4,7 +4,9 @@ libddgemm's kernels.  Inputs must be float64 CUDA tensors with unit stride
 in their last dimension; a (hi, lo) pair must share shape and strides."""
 from __future__ import annotations
 
+import contextlib
 import ctypes
+import functools
 
 import torch
 
@@ -25,6 +27,21 @@ def _check_pair(hi: torch.Tensor, lo: torch.Tensor, name: str) -> int:
 
 def current_stream_ptr(stream: torch.cuda.Stream | None = None) -> int:
     return (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+
+
+def _on_call_stream(fn):
+    """Runs a wrapper with its `stream` argument as torch's current stream,
+    so that its outputs and temporaries are allocated (and zero-filled) on
+    the stream its kernels use.  The caching allocator ties every block to
+    the stream it was allocated on: a workspace freed when the call returns
+    is then not handed out to another stream while those kernels may still
+    run."""
+    @functools.wraps(fn)
+    def call(*args, stream=None, **kwargs):
+        ctx = torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext()
+        with ctx:
+            return fn(*args, stream=stream, **kwargs)
+    return call
 
 
 def workspace_bytes(m: int, n: int, k: int, variant: int = _lib.DDGEMM_VARIANT_FP64,
@@ -51,6 +68,7 @@ def alloc_workspace(m: int, n: int, k: int, device=None, variant: int = _lib.DDG
     return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device or "cuda")
 
 
+@_on_call_stream
 def ddgemm(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, workspace=None,
            status=None, flags=None, stream=None, phase_events=None,
            variant=_lib.DDGEMM_VARIANT_FP64, int8_slices=0, split_k=0):
@@ -120,6 +138,7 @@ def host_buffer_bytes(m: int, n: int, k: int, variant: int = _lib.DDGEMM_VARIANT
         trans_a, trans_b, variant, int8_slices=int8_slices, split_k=split_k))
 
 
+@_on_call_stream
 def ddgemm_host(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=None, buffer=None,
                 device=None, status=None, stream=None, variant=_lib.DDGEMM_VARIANT_FP64,
                 int8_slices=0, split_k=0):
@@ -163,6 +182,7 @@ def ddgemm_host(a_hi, a_lo, b_hi, b_lo, *, trans_a=False, trans_b=False, out=Non
     return c_hi, c_lo
 
 
+@_on_call_stream
 def assemble_int8(diag: torch.Tensor, scale: torch.Tensor, *, stream=None):
     """The exact assembly of the tensor-core INT8 form on the device: for
     diag [s, count] int32 and scale [count] int32, returns (hi, lo), the
@@ -179,6 +199,7 @@ def assemble_int8(diag: torch.Tensor, scale: torch.Tensor, *, stream=None):
     return hi, lo
 
 
+@_on_call_stream
 def split_a(a_hi, a_lo, *, trans_a=False, stream=None, status=None):
     """The split step for A: returns (slices [4, m, k], exps [ceil(k/256), m])."""
     lda = _check_pair(a_hi, a_lo, "A")
@@ -192,6 +213,7 @@ def split_a(a_hi, a_lo, *, trans_a=False, stream=None, status=None):
     return slices, exps
 
 
+@_on_call_stream
 def split_b(b_hi, b_lo, *, trans_b=False, stream=None, status=None):
     """The split step for B: returns (panels [7, k, n], exps [ceil(k/256), n])."""
     ldb = _check_pair(b_hi, b_lo, "B")
@@ -205,6 +227,7 @@ def split_b(b_hi, b_lo, *, trans_b=False, stream=None, status=None):
     return slices, exps
 
 
+@_on_call_stream
 def bins(a_hi, a_lo, b_hi, b_lo, *, stream=None):
     """The four bins of the single k-block (k <= 256), shape [4, m, n]."""
     lda = _check_pair(a_hi, a_lo, "A")
@@ -219,6 +242,7 @@ def bins(a_hi, a_lo, b_hi, b_lo, *, stream=None):
     return out
 
 
+@_on_call_stream
 def ddgemm_backward(a_hi, a_lo, b_hi, b_lo, dc_hi, dc_lo, *, trans_a=False, trans_b=False,
                     workspace=None, status=None, stream=None,
                     variant=_lib.DDGEMM_VARIANT_FP64, int8_slices=0):
@@ -250,6 +274,7 @@ def ddgemm_backward(a_hi, a_lo, b_hi, b_lo, dc_hi, dc_lo, *, trans_a=False, tran
     return da[0], da[1], db[0], db[1]
 
 
+@_on_call_stream
 def split_int8(x_hi, x_lo, *, as_b=False, trans=False, slices=15, stream=None, status=None):
     """The INT8 split of A (as_b=False; vectors = rows of op(A)) or of B
     (as_b=True; vectors = columns of op(B)).  Returns (digits [s, nvec, k]
@@ -282,7 +307,8 @@ class Batch:
     problem descriptors and allocates the workspace (PyTorch memory), so
     ``run()`` only enqueues the four launches and can be captured into a
     CUDA graph.  The tensors must stay alive and in place while the batch is
-    used."""
+    used, and the Batch itself (its workspace) until the work of its last
+    ``run()`` has completed on the stream it was enqueued on."""
 
     def __init__(self, problems, device=None, variant=_lib.DDGEMM_VARIANT_FP64, int8_slices=0):
         """variant: DDGEMM_VARIANT_FP64 (the persistent FP64 kernel),
