@@ -29,17 +29,37 @@ def current_stream_ptr(stream: torch.cuda.Stream | None = None) -> int:
     return (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
 
 
+def _cuda_devices(args, kwargs, stream):
+    """The CUDA devices of the tensors among a call's arguments (one level
+    of tuples and lists included) and of its stream."""
+    devs = set()
+    for a in list(args) + list(kwargs.values()):
+        for t in (a if isinstance(a, (tuple, list)) else (a,)):
+            if isinstance(t, torch.Tensor) and t.is_cuda:
+                devs.add(t.device)
+    if stream is not None:
+        devs.add(stream.device)
+    return devs
+
+
 def _on_call_stream(fn):
-    """Runs a wrapper with its `stream` argument as torch's current stream,
-    so that its outputs and temporaries are allocated (and zero-filled) on
-    the stream its kernels use.  The caching allocator ties every block to
-    the stream it was allocated on: a workspace freed when the call returns
-    is then not handed out to another stream while those kernels may still
-    run."""
+    """Runs a wrapper on the device of its CUDA tensors (all on one device,
+    else ValueError: the library launches on the current device), with its
+    `stream` argument as torch's current stream, so that its outputs and
+    temporaries are allocated (and zero-filled) on the stream its kernels
+    use.  The caching allocator ties every block to the stream it was
+    allocated on: a workspace freed when the call returns is then not
+    handed out to another stream while those kernels may still run."""
     @functools.wraps(fn)
     def call(*args, stream=None, **kwargs):
-        ctx = torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext()
-        with ctx:
+        devs = _cuda_devices(args, kwargs, stream)
+        if len(devs) > 1:
+            raise ValueError(f"tensors and stream on different devices: {sorted(map(str, devs))}")
+        with contextlib.ExitStack() as scope:
+            if devs:
+                scope.enter_context(torch.cuda.device(devs.pop()))
+            if stream is not None:
+                scope.enter_context(torch.cuda.stream(stream))
             return fn(*args, stream=stream, **kwargs)
     return call
 
@@ -334,6 +354,9 @@ class Batch:
             self.shapes.append((m, n, k))
             self._keep.append((a_hi, a_lo, b_hi, b_lo, c_hi, c_lo))
         self.host = arr
+        devs = {t.device for p in problems for t in p}
+        if len(devs) > 1 or (device is not None and devs and torch.device(device) not in devs):
+            raise ValueError(f"problems on different devices: {sorted(map(str, devs))}")
         dev = device or (problems[0][0].device if problems else "cuda")
         raw = bytearray(ctypes.string_at(ctypes.addressof(arr), ctypes.sizeof(arr)))
         self.dev = torch.frombuffer(raw, dtype=torch.uint8).to(dev)
@@ -348,5 +371,9 @@ class Batch:
             config = _lib.ddgemm_batch_config(*config)
         opts = _lib.make_opts(variant=self.variant, int8_slices=self.int8_slices,
                               status_dev=status.data_ptr() if status is not None else 0)
-        _lib.ddgemm_batched(self.count, self.host, self.dev.data_ptr(), self.workspace.data_ptr(),
-                            self.workspace.numel(), current_stream_ptr(stream), opts, config)
+        if stream is not None and stream.device != self.workspace.device:
+            raise ValueError("the stream is on another device than the batch")
+        with torch.cuda.device(self.workspace.device):
+            _lib.ddgemm_batched(self.count, self.host, self.dev.data_ptr(),
+                                self.workspace.data_ptr(), self.workspace.numel(),
+                                current_stream_ptr(stream), opts, config)
