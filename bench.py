@@ -52,7 +52,7 @@ NOMINAL_BF16_TFLOPS = 2250.0
 # other workloads report null.
 TRAFFIC_4096 = {"cascade_fp64_kernel": 9.879882e9 + 0.281523e9,
                 "cascade_int8_kernel<15>": 2.923206e9 + 0.268134e9,
-                "cascade_int8_tc_kernel<16>": 9.057265e9 + 0.275351e9}
+                "cascade_int8_tc_kernel<16>": 9.122322e9 + 0.272443e9}
 
 VARIANT_NAMES = {1: "int8", 4: "int8 on tcgen05", 5: "int8 on tcgen05, eight-bit pieces"}
 
