@@ -128,3 +128,23 @@ def test_entries_match_full():
     cols = np.array([8, 0, 4, 5])
     eh, el = dd.ddgemm_entries(a_hi, a_lo, b_hi, b_lo, rows, cols)
     assert np.array_equal(eh, c_hi[rows, cols]) and np.array_equal(el, c_lo[rows, cols])
+
+
+def test_dd_add_relative_error_under_cancellation():
+    """The accurate FP64x2 addition (two TwoSums, Sec. "FP64 and FP64x2
+    numbers") errs by at most a few 2^-106 of |a + b| even when a + b
+    cancels most of a and b; the one-TwoSum ("sloppy") addition does not
+    (its error is relative to |a| + |b|), so this pins which one the
+    oracle uses."""
+    rng = np.random.default_rng(7)
+    for _ in range(400):
+        ah = float(rng.standard_normal())
+        al = ah * 2.0 ** -53 * float(rng.uniform(-1, 1))
+        # b = -a plus a small relative change, in both words
+        d = 2.0 ** -float(rng.integers(1, 50))
+        bh = -ah * (1.0 + d * float(rng.uniform(-1, 1)))
+        bl = -al * float(rng.uniform(0.0, 2.0))
+        rh, rl = dd.dd_add(ah, al, bh, bl)
+        true = exact.dd_fixed(ah, al) + exact.dd_fixed(bh, bl)
+        err = abs(exact.dd_fixed(rh, rl) - true)
+        assert (err << 104) <= abs(true) + 1, (ah, al, bh, bl)
