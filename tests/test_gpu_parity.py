@@ -9,8 +9,9 @@
   the order of bin 3-6's sum allows.
 * Edge cases: k = 0, empty m or n, ragged tiles, one element, transposed
   operands, integer matrices (exact), identity, the paper's worked example,
-  non-finite inputs, cancellation flags, and the full 4096^3 and
-  8192 x 1024 x 4096 sizes on sampled entries."""
+  non-finite inputs, cancellation flags, k-blocks whose values cancel (the
+  INT8 forms, bit for bit), and the full 4096^3 and 8192 x 1024 x 4096
+  sizes on sampled entries."""
 import math
 import os
 
@@ -420,6 +421,38 @@ def test_illconditioned_product_int8(ops):
     rows, cols = rng.integers(0, n, 40), rng.integers(0, n, 40)
     o_hi, o_lo = dd.ddgemm(*a)
     assert rel_errors(c_hi, c_lo, a, rows, cols).max() * 3 < rel_errors(o_hi, o_lo, a, rows, cols).max()
+
+
+@pytest.mark.parametrize("variant,s,assembly,bits", [(1, 15, "fp64x2", 8), (4, 16, "exact", 7),
+                                                     (5, 15, "exact", 8)])
+def test_cancellation_across_k_blocks_int8(ops, variant, s, assembly, bits):
+    """Two k-blocks whose values nearly cancel (B's second block is minus
+    the first times 1 + 2^-30 u): C = block 0 + block 1 is about 2^-30 of
+    either, and the device's FP64x2 accumulation of the block values into C
+    (the accurate addition, two TwoSums) matches the restatement bit for
+    bit; against exact rationals the result stays within the 1e-28 |A||B|
+    contract."""
+    from oracle import cascade_int8 as c8
+    kb = c8.kblock(bits)
+    m = n = 8
+    rng = np.random.default_rng(90 + variant)
+    a0 = rng.uniform(-1, 1, (m, kb))
+    a0_lo = a0 * 2.0 ** -53 * rng.uniform(-1, 1, (m, kb))
+    b0 = rng.uniform(-1, 1, (kb, n))
+    b0_lo = b0 * 2.0 ** -53 * rng.uniform(-1, 1, (kb, n))
+    b1 = -b0 * (1.0 + 2.0 ** -30 * rng.uniform(-1, 1, (kb, n)))
+    a_hi, a_lo = np.hstack([a0, a0]), np.hstack([a0_lo, a0_lo])
+    b_hi, b_lo = np.vstack([b0, b1]), np.vstack([b0_lo, -b0_lo])
+    c_hi, c_lo = host(*ops.ddgemm(*dev(a_hi, a_lo, b_hi, b_lo), variant=variant, int8_slices=s))
+    w_hi, w_lo = c8.cascade_int8_ddgemm(a_hi, a_lo, b_hi, b_lo, s=s, assembly=assembly,
+                                        bits=bits)
+    assert np.array_equal(c_hi, w_hi) and np.array_equal(c_lo, w_lo)
+    absab = exact.abs_product(a_hi, b_hi)
+    block0 = np.abs(a0 @ b0)
+    assert np.all(np.abs(c_hi) < 2.0 ** -20 * np.maximum(block0, 1.0))  # it does cancel
+    for i, j in ((0, 0), (3, 5), (7, 7)):
+        ex = exact.exact_dot(a_hi[i], a_lo[i], b_hi[:, j], b_lo[:, j])
+        assert exact.err_vs_exact(c_hi[i, j], c_lo[i, j], ex) <= CONTRACT * absab[i, j]
 
 
 def test_bounded_wait_reports_timeout_and_context_survives(ops):
