@@ -145,20 +145,21 @@ typedef struct ddgemm_opts {
 } ddgemm_opts;
 
 /* Bytes of device workspace ddgemm() can use for this problem (0 when m, n
- * or k is 0).  Holds the four cascaded pieces of A (4 m k doubles), the seven
- * cascaded panels of B (7 k n doubles), the per-block exponents of sigma and
- * tau, and, for grids of fewer than 4096 tiles of 64 x 64, room for split-k
- * partial C (2 m n doubles each, at most 15 and at most about 0.5 GB in
- * all; see split_k).  ddgemm()
- * accepts a smaller workspace down to the size without the partials and
- * then splits less or not at all.  opts may be NULL (all defaults).
- * Returns 0 on invalid sizes. */
+ * or k is 0).  Holds the four cascaded pieces of A (4 m k doubles, Appendix
+ * A), the seven cascaded panels of B (7 k n doubles), the per-block
+ * exponents of sigma and tau, and, for grids of fewer than 4096 tiles of
+ * 64 x 64, room for split-k partial C (2 m n doubles each, at most 15 and
+ * at most about 0.5 GB in all; see split_k).  ddgemm() accepts a smaller
+ * workspace down to the size without the partials and then splits less or
+ * not at all.  opts may be NULL (all defaults).  Returns 0 on invalid
+ * sizes. */
 size_t ddgemm_workspace_size(int m, int n, int k, const ddgemm_opts *opts);
 
-/* How many split-k groups ddgemm() launches for this problem (see split_k)
- * on a GPU with `sms` multiprocessors and a workspace of ws_bytes: 1 for the
- * INT8 form, with flags_dev, or when there is no room for partials.  Host
- * only, no GPU needed.  Returns 0 on invalid arguments. */
+/* How many split-k groups ddgemm() launches for this problem (see split_k;
+ * the paper's k-blocking, Sec. "Blocking for the k dimension", summed in
+ * groups) on a GPU with `sms` multiprocessors and a workspace of ws_bytes:
+ * 1 for the INT8 form, with flags_dev, or when there is no room for
+ * partials.  Host only, no GPU needed.  Returns 0 on invalid arguments. */
 int ddgemm_split_groups(int m, int n, int k, int sms, size_t ws_bytes, const ddgemm_opts *opts);
 
 /* C := A B in FP64x2 by the ten-GEMM cascade (eq. Gemm10).
@@ -380,7 +381,8 @@ int ddgemm_split_b(int k, int n, const double *B_hi, const double *B_lo, int ldb
                    int trans_b, double *slices, int ld_slices, int *exps,
                    unsigned int *status_dev, void *stream);
 
-/* The split step of the INT8 form alone (see ddgemm_opts.variant).
+/* The split step of the INT8 form alone (Sec. "FP64x2 in terms of INT8";
+ * see ddgemm_opts.variant).
  *   slices      s, as for ddgemm_opts.int8_slices (no 0 default here).
  *   digits      device int8, s x m x ld_digits for A (row i of A is row i of
  *               each plane) and s x n x ld_digits for B (column j of B is row
@@ -397,7 +399,9 @@ int ddgemm_split_int8_b(int k, int n, const double *B_hi, const double *B_lo, in
                         int trans_b, int slices, signed char *digits, int ld_digits,
                         int *exps, unsigned int *status_dev, void *stream);
 
-/* The assembly step of DDGEMM_VARIANT_INT8_TC alone, on the device: for
+/* The assembly step of DDGEMM_VARIANT_INT8_TC alone (the diagonal sums
+ * added "in FP64x2", Sec. "FP64x2 in terms of INT8", read as one exact sum
+ * rounded once), on the device: for
  * i < count, (hi[i], lo[i]) = the FP64x2 nearest to
  *     x_i = sum_{t < slices} diag[t*count + i] 2^(-12-7t) 2^scale[i]
  * (hi = RN(x_i), lo = RN(x_i - hi), round to nearest, ties to even), x_i
