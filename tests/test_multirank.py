@@ -69,3 +69,30 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(args, bench.WORKLOADS["256"])
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_line_has_the_contract_keys(monkeypatch):
+    """Rank 0 (or a single process) prints one JSON line with the keys of
+    the bench contract, for the oracle timed on the host cores."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for var in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(var, raising=False)
+    args = type("A", (), {"steps": 1, "warmup": 3})()
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(args, bench.WORKLOADS["256"])
+    lines = buf.getvalue().strip().splitlines()
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "impl", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["n_gpus"] == 1 and line["steps"] == 1 and line["warmup"] == 3
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
