@@ -83,13 +83,21 @@ __device__ inline long long find(const long long *prefix, int count, long long u
 }
 
 // Ordering key for "longest k first": larger k, then larger m n, then index.
-__device__ inline bool before(const ddgemm_problem &a, int ia, const ddgemm_problem &b, int ib) {
-    if (a.k != b.k) return a.k > b.k;
-    const long long sa = (long long)a.m * a.n, sb = (long long)b.m * b.n;
+__device__ inline bool before(int ka, long long sa, int ia, int kb, long long sb, int ib) {
+    if (ka != kb) return ka > kb;
     if (sa != sb) return sa > sb;
     return ia < ib;
 }
 
+// Problems whose ordering keys the plan kernel keeps in shared memory.
+constexpr int PLAN_SMEM_KEYS = 2048;
+
+// One CTA of 256 threads.  Every thread fills the entries of its problems
+// and their ranks in the schedule (a rank compares the problem with every
+// other one); then the prefix sums over the problems (split units,
+// workspace bytes) and over the ranks (tiles): thread t takes a contiguous
+// segment, the 256 segment totals are scanned by one warp per quantity, and
+// every thread walks its segment again from its offsets.
 __global__ void __launch_bounds__(256)
 plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, int order_mode, int bm,
             int bn) {
@@ -100,6 +108,17 @@ plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, int o
     long long *tile_pre = reinterpret_cast<long long *>(ws + L.tile_pre);
     long long *a_pre = reinterpret_cast<long long *>(ws + L.a_pre);
     long long *b_pre = reinterpret_cast<long long *>(ws + L.b_pre);
+    const bool by_k = order_mode == DDGEMM_ORDER_LONGEST_K_FIRST;
+    __shared__ int key_k[PLAN_SMEM_KEYS];
+    __shared__ long long key_mn[PLAN_SMEM_KEYS];
+    const bool keys_in_smem = by_k && count <= PLAN_SMEM_KEYS;
+    if (keys_in_smem) {
+        for (int i = threadIdx.x; i < count; i += blockDim.x) {
+            key_k[i] = probs[i].k;
+            key_mn[i] = (long long)probs[i].m * probs[i].n;
+        }
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
         const ddgemm_problem q = probs[i];
         Entry e;
@@ -118,21 +137,72 @@ plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, int o
         const bool work = mn && q.k > 0;
         e.a_units = work ? (long long)q.m * e.kb : 0;
         e.b_units = work ? (long long)e.kb * ((q.n + 63) / 64) : 0;
+        e.a_s = e.b_s = nullptr;
+        e.e_a = e.e_b = nullptr;
         ent[i] = e;
         // rank for the schedule
         int r = i;
-        if (order_mode == DDGEMM_ORDER_LONGEST_K_FIRST) {
+        if (by_k) {
+            const long long qmn = (long long)q.m * q.n;
             r = 0;
-            for (int j = 0; j < count; ++j)
-                if (j != i && before(probs[j], j, q, i)) ++r;
+            if (keys_in_smem) {
+                for (int j = 0; j < count; ++j)
+                    if (j != i && before(key_k[j], key_mn[j], j, q.k, qmn, i)) ++r;
+            } else {
+                for (int j = 0; j < count; ++j)
+                    if (j != i && before(probs[j].k, (long long)probs[j].m * probs[j].n, j, q.k,
+                                         qmn, i))
+                        ++r;
+            }
         }
         order[r] = i;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        size_t off = L.panels;
-        long long ta = 0, tb = 0;
-        for (int i = 0; i < count; ++i) {
+    constexpr int NQ = 4;  // a units, b units, workspace bytes, tiles (rank order)
+    __shared__ long long part[NQ][256];  // blockDim.x <= 256
+    const int nt = blockDim.x, t = threadIdx.x;
+    const int seg = (count + nt - 1) / nt;
+    const int i0 = min(count, t * seg), i1 = min(count, i0 + seg);
+    {
+        long long acc[NQ] = {0, 0, 0, 0};
+        for (int i = i0; i < i1; ++i) {
+            const Entry &e = ent[i];
+            acc[0] += e.a_units;
+            acc[1] += e.b_units;
+            acc[2] += (long long)panel_bytes(e.m, e.n, e.k);
+            acc[3] += ent[order[i]].tiles;
+        }
+        for (int q = 0; q < NQ; ++q) part[q][t] = acc[q];
+    }
+    __syncthreads();
+    {
+        // exclusive scan of part[q][0 .. nt-1] by warp q (nt <= 256)
+        const int w = t >> 5, lane = t & 31;
+        if (w < NQ) {
+            long long v[8], run = 0;
+            for (int j = 0; j < 8; ++j) {
+                const int x = lane * 8 + j;
+                v[j] = x < nt ? part[w][x] : 0;
+                run += v[j];
+            }
+            long long incl = run;
+            for (int off = 1; off < 32; off <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            long long pre = incl - run;
+            for (int j = 0; j < 8; ++j) {
+                const int x = lane * 8 + j;
+                if (x < nt) part[w][x] = pre;
+                pre += v[j];
+            }
+        }
+    }
+    __syncthreads();
+    {
+        long long ta = part[0][t], tb = part[1][t], tt = part[3][t];
+        size_t off = L.panels + (size_t)part[2][t];
+        for (int i = i0; i < i1; ++i) {
             Entry &e = ent[i];
             a_pre[i] = ta;
             b_pre[i] = tb;
@@ -147,24 +217,20 @@ plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, int o
                 off += ru((size_t)e.kb * e.m * 4, ALIGN);
                 e.e_b = reinterpret_cast<int *>(ws + off);
                 off += ru((size_t)e.kb * e.n * 4, ALIGN);
-            } else {
-                e.a_s = e.b_s = nullptr;
-                e.e_a = e.e_b = nullptr;
             }
+            tile_pre[i] = tt;
+            tt += ent[order[i]].tiles;
         }
-        a_pre[count] = ta;
-        b_pre[count] = tb;
-        long long tt = 0;
-        for (int r = 0; r < count; ++r) {
-            tile_pre[r] = tt;
-            tt += ent[order[r]].tiles;
+        if (i1 == count && i0 < i1) {  // the last non-empty segment: the totals
+            a_pre[count] = ta;
+            b_pre[count] = tb;
+            tile_pre[count] = tt;
+            hdr->total_tiles = tt;
+            hdr->total_a = ta;
+            hdr->total_b = tb;
+            hdr->counter = 0ull;
+            hdr->count = count;
         }
-        tile_pre[count] = tt;
-        hdr->total_tiles = tt;
-        hdr->total_a = ta;
-        hdr->total_b = tb;
-        hdr->counter = 0ull;
-        hdr->count = count;
     }
 }
 

@@ -258,3 +258,24 @@ def test_batched_tc_many_small_problems(mods, count):
     for (gh, gl), (wh, wl), (m, n, k) in zip(got, want, shapes):
         if m and n:
             assert np.array_equal(gh, wh) and np.array_equal(gl, wl), (m, n, k)
+
+
+@pytest.mark.parametrize("count,order", [(1001, 1), (2100, 1), (2100, 0)])
+def test_batched_fp64_many_small_problems(mods, count, order):
+    """The FP64 form's plan on many small (and empty) problems: its ranking
+    (keys in shared memory up to 2048 problems, from global memory above,
+    or the given order) and its segmented prefix sums; every C equals
+    ddgemm() on that problem alone."""
+    _lib, ops, _ = mods
+    rng = np.random.default_rng(count + order)
+    shapes = [(int(rng.integers(0, 40)), int(rng.integers(0, 40)), int(rng.integers(0, 600)))
+              for _ in range(count)]
+    batch, probs, _ = make_batch(ops, shapes, seed=11, kind="wide")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    batch.run(status=status, config=(3, order))
+    got = results(probs)
+    want = reference(ops, probs)
+    assert int(status.item()) == 0
+    for (gh, gl), (wh, wl), (m, n, k) in zip(got, want, shapes):
+        if m and n:
+            assert np.array_equal(gh, wh) and np.array_equal(gl, wl), (m, n, k)
