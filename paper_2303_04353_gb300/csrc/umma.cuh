@@ -93,59 +93,11 @@ __device__ __forceinline__ void commit_multicast(uint32_t bar, uint16_t mask) {
         : "memory");
 }
 
-// Two loads of 8 consecutive 32-bit columns (at t0 and t1) for the 32
-// tensor-memory lanes of this warp's quadrant, then the wait for them: lane
-// i of the warp receives lane (quadrant base + i).  One asm statement, so
-// the registers are not read before the data has arrived.
-__device__ __forceinline__ void ld_x8_x2(uint32_t t0, uint32_t t1, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(t0), "r"(t1)
-        : "memory");
-}
-
-// Three and four such loads (at t0 .. t3) with one wait: the drain of a
-// group of diagonals pays the tensor-memory latency once.
-__device__ __forceinline__ void ld_x8_x3(uint32_t t0, uint32_t t1, uint32_t t2,
-                                         uint32_t (&r)[24]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%24];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%25];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%26];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
-        : "r"(t0), "r"(t1), "r"(t2)
-        : "memory");
-}
-
-__device__ __forceinline__ void ld_x8_x4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3,
-                                         uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%32];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%33];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%34];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%35];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(t0), "r"(t1), "r"(t2), "r"(t3)
-        : "memory");
-}
-
 // One to four loads of 4 consecutive 32-bit columns each (at t[0..N-1])
-// for the 32 lanes of this warp's quadrant, then one wait.
+// for the 32 tensor-memory lanes of this warp's quadrant (lane i of the
+// warp receives lane quadrant base + i), then one wait, all in one asm
+// statement so that the registers are not read before the data has
+// arrived: a group of diagonals pays the tensor-memory latency once.
 __device__ __forceinline__ void ld_x4_n(const uint32_t (&t)[1], uint32_t (&r)[4]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
@@ -186,16 +138,6 @@ __device__ __forceinline__ void ld_x4_n(const uint32_t (&t)[4], uint32_t (&r)[16
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(t[0]), "r"(t[1]), "r"(t[2]), "r"(t[3])
-        : "memory");
-}
-
-__device__ __forceinline__ void ld_x8(uint32_t t0, uint32_t (&r)[8]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7])
-        : "r"(t0)
         : "memory");
 }
 
