@@ -30,11 +30,6 @@ def exact_dot(a_hi, a_lo, b_hi, b_lo) -> int:
     return s
 
 
-def exact_gemm_entries(a_hi, a_lo, b_hi, b_lo, rows, cols):
-    """Exact C[i, j] (scaled by 2^2148) for the listed entries."""
-    return [exact_dot(a_hi[i], a_lo[i], b_hi[:, j], b_lo[:, j]) for i, j in zip(rows, cols)]
-
-
 def err_vs_exact(c_hi: float, c_lo: float, exact_scaled: int) -> float:
     """|c_hi + c_lo - exact| as a float, exact given scaled by 2^2148."""
     got = dd_fixed(c_hi, c_lo) << SHIFT
