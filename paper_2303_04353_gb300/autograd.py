@@ -42,5 +42,6 @@ class DDMatmul(torch.autograd.Function):
 def ddmatmul(a_hi, a_lo, b_hi, b_lo, variant=0):
     """C = A B in FP64x2 (differentiable); returns (c_hi, c_lo).  variant:
     0 the FP64 form (default), 1 the INT8 form on mma.sync, 4 the INT8 form
-    on the tcgen05 tensor cores; forward and backward use the same form."""
+    on the tcgen05 tensor cores (seven-bit pieces), 5 the same with
+    eight-bit pieces; forward and backward use the same form."""
     return DDMatmul.apply(a_hi, a_lo, b_hi, b_lo, variant)
