@@ -42,7 +42,6 @@ namespace {
 using Tile = Fp64Tile<4, 2>;  // 64 x 64, 8 warps
 constexpr int BM = Tile::BM, BN = Tile::BN, BK = CBK, NST = 3, NTHREADS = Tile::NTHREADS;
 constexpr int A_STAGE = Tile::A_STAGE;
-constexpr int B_STAGE = Tile::B_STAGE;
 constexpr int STAGE = Tile::STAGE;
 constexpr uint32_t STAGE_BYTES = STAGE * sizeof(double);
 constexpr int STEPS_PER_BLOCK = KC / BK;
