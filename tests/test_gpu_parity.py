@@ -12,7 +12,6 @@
   non-finite inputs, cancellation flags, k-blocks whose values cancel (the
   INT8 forms, bit for bit), and the full 4096^3 and 8192 x 1024 x 4096
   sizes on sampled entries."""
-import math
 import os
 
 import numpy as np

@@ -11,7 +11,6 @@ problems, and checks each result against the ordinary ddgemm entry point
 parity tests.  This file is collected last so that a run stopping at the
 first failure has already run every other test; nothing here depends on
 what ran before."""
-import ctypes
 
 import numpy as np
 import pytest
