@@ -903,7 +903,7 @@ def run_sweep(args):
                               "median_err_rel_absAabsB": float(np.median(err))}), flush=True)
 
 
-def main():
+def make_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -929,7 +929,11 @@ def main():
                     help="Gemm10 / Gemm16 / dropped-bins accuracy study instead of the line")
     ap.add_argument("--splitk", action="store_true",
                     help="split-k study on grids of few waves instead of the line")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = make_parser().parse_args()
     if args.splitk:
         run_splitk(args)
         return
