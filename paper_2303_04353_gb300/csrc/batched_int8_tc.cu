@@ -374,7 +374,7 @@ struct BatchSource {
     }
     // hint: the rank of the caller's previous item (items come in
     // increasing order)
-    __device__ TcJob job(long long item, int, int &hint) const {
+    __device__ TcJob job(long long item, int &hint) const {
         const TcView V(ws);
         const int r = hint = advance_tc(V.tile_pre, V.hdr->count, item, hint);
         const TcEntry &e = V.ent[V.order[r]];
@@ -414,7 +414,7 @@ cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, lon
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || tiles == 0) return e;
     using G = TcGeom<S>;
-    auto kernel = cascade_int8_tc_kernel<S, BITS, 1, BatchSource>;
+    auto kernel = cascade_int8_tc_kernel<S, BITS, BatchSource>;
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)G::SMEM)) != cudaSuccess)
         return e;

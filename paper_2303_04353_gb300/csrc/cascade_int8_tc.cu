@@ -22,11 +22,6 @@
 // the FP64x2 add.  This is one rounding where the paper's smallest-first
 // FP64x2 sum of the diagonals has s.
 //
-// Clusters (optional, default off).  CL CTAs take neighbouring column
-// tiles of one row tile; each loads S / CL of the A planes and multicasts
-// them to all, and a stage is free once every CTA's MMAs have read it
-// (multicast commits, CL arrivals per use).
-//
 // Tiling.  A C tile is 128 rows x 16 columns; k advances by 16.  The split
 // wrote the digits tiled and pre-swizzled (split_int8.cu), so one bulk copy
 // per operand and stage brings all s digit planes of A ([s][128][16] bf16,
@@ -59,22 +54,10 @@
 namespace ddg {
 namespace {
 
-// Cluster size: CTAs along n that share A by multicast copies.  Measured on
-// GB300 at 2048^3 and 4096^3: 2 is as fast as 1 (the L2 reads A causes do
-// not limit the kernel) and 4 is 5-7 % slower (fewer SMs hold whole
-// clusters), so the default is 1.  DDGEMM_INT8TC_CLUSTER = 1, 2 or 4
-// overrides it, for measurement and for the tests of the shared path.
 template <int S>
 cudaError_t launch_tc(const Int8TcArgs &a, cudaStream_t stream) {
     if ((uintptr_t)a.a_tiles % 16 || (uintptr_t)a.b_tiles % 16) return cudaErrorInvalidValue;
-    int cl = 1;
-    if (const char *env = getenv("DDGEMM_INT8TC_CLUSTER")) {
-        const int v = atoi(env);
-        if (v == 1 || v == 2 || v == 4) cl = v;
-    }
-    if (cl == 4) return launch_tc_cl<S, INT8_TC_BITS, 4>(a, stream);
-    if (cl == 2) return launch_tc_cl<S, INT8_TC_BITS, 2>(a, stream);
-    return launch_tc_cl<S, INT8_TC_BITS, 1>(a, stream);
+    return launch_tc_single<S, INT8_TC_BITS>(a, stream);
 }
 
 template <int S>

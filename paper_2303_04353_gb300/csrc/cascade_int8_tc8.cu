@@ -6,8 +6,6 @@
 // as a template argument.  An eight-bit product is at most 2^14, so an FP32
 // accumulator stays exact over 64 entries (64 * 16 * 2^14 = 2^24): the
 // tensor memory is read out four times as often as with seven-bit pieces.
-// No cluster variant: the shared-A path did not pay off for the seven-bit
-// form either.
 #include "cascade_int8_tc_core.cuh"
 
 namespace ddg {
@@ -17,10 +15,10 @@ cudaError_t launch_cascade_int8_tc8(const Int8TcArgs &a, cudaStream_t stream) {
     if (a.bits != INT8_BITS) return cudaErrorInvalidValue;
     if ((uintptr_t)a.a_tiles % 16 || (uintptr_t)a.b_tiles % 16) return cudaErrorInvalidValue;
     switch (a.slices) {
-        case 12: return launch_tc_cl<12, INT8_BITS, 1>(a, stream);
-        case 13: return launch_tc_cl<13, INT8_BITS, 1>(a, stream);
-        case 14: return launch_tc_cl<14, INT8_BITS, 1>(a, stream);
-        case 15: return launch_tc_cl<15, INT8_BITS, 1>(a, stream);
+        case 12: return launch_tc_single<12, INT8_BITS>(a, stream);
+        case 13: return launch_tc_single<13, INT8_BITS>(a, stream);
+        case 14: return launch_tc_single<14, INT8_BITS>(a, stream);
+        case 15: return launch_tc_single<15, INT8_BITS>(a, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -307,23 +307,21 @@ struct TcJob {
     long long ldc;
 };
 
-// The tiles of one problem (Int8TcArgs), in groups of TILE_GROUP row tiles;
-// with clusters, an item is CL neighbouring column tiles of one row tile.
+// The tiles of one problem (Int8TcArgs), in groups of TILE_GROUP row tiles.
 struct SingleSource {
     Int8TcArgs a;
-    int tiles_m, tiles_n, groups_n, cl;
-    __device__ long long items() const { return (long long)tiles_m * groups_n; }
+    int tiles_m, tiles_n;
+    __device__ long long items() const { return (long long)tiles_m * tiles_n; }
     __device__ unsigned int *status() const { return a.status; }
-    __device__ TcJob job(long long item, int rank, int &) const {
-        int tm, tg;
-        grouped_tile((unsigned)item, tiles_m, groups_n, TILE_GROUP, tm, tg);
-        const int tn = tg * cl + rank;
+    __device__ TcJob job(long long item, int &) const {
+        int tm, tn;
+        grouped_tile((unsigned)item, tiles_m, tiles_n, TILE_GROUP, tm, tn);
         TcJob j;
         j.m = a.m;
         j.n = a.n;
         j.k = a.k;
         j.tm = tm;
-        j.tn_load = min(tn, tiles_n - 1);  // a rank past the last tile loads a copy
+        j.tn_load = tn;
         j.col0 = tn * BN;
         j.a_tiles = a.a_tiles;
         j.b_tiles = a.b_tiles;
@@ -336,14 +334,13 @@ struct SingleSource {
     }
 };
 
-template <int S, int TB, int CL, class Src>
+template <int S, int TB, class Src>
 __global__ void __launch_bounds__(NTHREADS, 1)
 cascade_int8_tc_kernel(const Src src) {
     using G = TcGeom<S>;
     using W = TcWidth<TB>;
     constexpr int CHUNK_STEPS = W::CHUNK_STEPS, BLOCK_CHUNKS = W::BLOCK_CHUNKS;
     constexpr int NST = G::NST;
-    constexpr uint16_t CL_MASK = (uint16_t)((1u << CL) - 1u);
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -351,19 +348,14 @@ cascade_int8_tc_kernel(const Src src) {
     static_assert(sizeof(Shared<NST>) <= BAR_BYTES, "barriers fit their region");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // a cluster of CL CTAs takes CL neighbouring column tiles of one row
-    // tile; rank r loads A planes [r S / CL, (r+1) S / CL) for all of them
-    const int rank = CL > 1 ? (int)cluster_rank() : 0;
     const long long tiles = src.items();
-    const long long first = blockIdx.x / CL, stride = gridDim.x / CL;
-    const int p0 = rank * S / CL, p1 = (rank + 1) * S / CL;
+    const long long first = blockIdx.x, stride = gridDim.x;
     unsigned int *status = src.status();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(smem_addr(&sh->full[s]), 1);
-            // one arrival per CTA of the cluster: each one's MMAs read the stage
-            mbar_init(smem_addr(&sh->empty[s]), CL);
+            mbar_init(smem_addr(&sh->empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_addr(&sh->acc_full[b]), 1);
@@ -379,8 +371,6 @@ cascade_int8_tc_kernel(const Src src) {
     }
     umma::fence_before();
     __syncthreads();
-    // no peer may copy into or arrive on this CTA's barriers before they exist
-    if constexpr (CL > 1) cluster_sync();
     umma::fence_after();
     const uint32_t tmem = sh->tmem_base;
 
@@ -391,7 +381,7 @@ cascade_int8_tc_kernel(const Src src) {
             bool ok = true;
             int hint = 0;  // the job source's position (items come in order)
             for (long long tile = first; ok && tile < tiles; tile += stride) {
-                const TcJob j = src.job(tile, rank, hint);
+                const TcJob j = src.job(tile, hint);
                 const int ksteps = (j.k + BK - 1) / BK;
                 for (int ks = 0; ks < ksteps; ++ks, ++it) {
                     const int stage = it % NST;
@@ -406,14 +396,10 @@ cascade_int8_tc_kernel(const Src src) {
                     mbar_arrive_expect_tx(bar, (uint32_t)G::TX);
                     // k-step ks of all S planes: S consecutive blocks
                     const uint16_t *src_a =
-                        j.a_tiles + (((long long)j.tm * ksteps + ks) * S + p0) * (BM * BK);
+                        j.a_tiles + ((long long)j.tm * ksteps + ks) * S * (BM * BK);
                     const uint16_t *src_b =
                         j.b_tiles + ((long long)j.tn_load * ksteps + ks) * S * (BN * BK);
-                    if constexpr (CL > 1)
-                        bulk_load_multicast(smem_addr(dst + p0 * G::A_PLANE), src_a,
-                                            (uint32_t)((p1 - p0) * G::A_PLANE), bar, CL_MASK);
-                    else
-                        bulk_load(smem_addr(dst), src_a, (uint32_t)G::A_STAGE, bar);
+                    bulk_load(smem_addr(dst), src_a, (uint32_t)G::A_STAGE, bar);
                     bulk_load(smem_addr(dst + G::A_STAGE), src_b, (uint32_t)(S * G::B_PLANE),
                               bar);
                 }
@@ -422,11 +408,6 @@ cascade_int8_tc_kernel(const Src src) {
                 // copies issued but perhaps not consumed: let them land (bounded)
                 for (uint32_t u = it > (uint32_t)NST ? it - NST : 0; u < it; ++u)
                     mbar_wait(smem_addr(&sh->full[u % NST]), (u / NST) & 1);
-            } else if (CL > 1) {
-                // the last use of every stage: all CTAs' MMAs have arrived on
-                // this CTA's empty barriers before it may exit (bounded)
-                for (uint32_t u = it > (uint32_t)NST ? it - NST : 0; u < it; ++u)
-                    mbar_wait(smem_addr(&sh->empty[u % NST]), (u / NST) & 1);
             }
         }
         __syncwarp();
@@ -437,7 +418,7 @@ cascade_int8_tc_kernel(const Src src) {
             bool ok = true;
             int hint = 0;
             for (long long tile = first; ok && tile < tiles; tile += stride) {
-                const TcJob j = src.job(tile, rank, hint);
+                const TcJob j = src.job(tile, hint);
                 const int ksteps = (j.k + BK - 1) / BK;
                 const int nchunks = (ksteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
                 for (int c = 0; ok && c < nchunks; ++c, ++chunk) {
@@ -478,11 +459,8 @@ cascade_int8_tc_kernel(const Src src) {
                                            umma::idesc_bf16_f32(BM, (S - i) * BN),
                                            (ks > ks0 || q > 0) ? 1u : 0u);
                         }
-                        // the stage is free once every CTA that shares it is done
-                        if constexpr (CL > 1)
-                            umma::commit_multicast(smem_addr(&sh->empty[stage]), CL_MASK);
-                        else
-                            umma::commit(smem_addr(&sh->empty[stage]));
+                        // the stage is free once these MMAs have read it
+                        umma::commit(smem_addr(&sh->empty[stage]));
                     }
                     if (ok) umma::commit(smem_addr(&sh->acc_full[b]));
                 }
@@ -502,11 +480,10 @@ cascade_int8_tc_kernel(const Src src) {
         bool ok = true;
         int hint = 0;
         for (long long tile = first; ok && tile < tiles; tile += stride) {
-            const TcJob j = src.job(tile, rank, hint);
+            const TcJob j = src.job(tile, hint);
             const int ksteps = (j.k + BK - 1) / BK;
             const int nchunks = (ksteps + CHUNK_STEPS - 1) / CHUNK_STEPS;
             const int row = j.tm * BM + row_in_tile;
-            // past the last column tile: every col >= n, nothing is stored
             const int col0 = j.col0 + part * DCOLS;
             if (nchunks == 0 && row < j.m) {  // k = 0: C = 0 on this tile
                 for (int x = 0; x < DCOLS; ++x)
@@ -584,49 +561,35 @@ cascade_int8_tc_kernel(const Src src) {
     }
     umma::fence_before();
     __syncthreads();
-    if constexpr (CL > 1) cluster_sync();   // peers are done with this CTA's memory
     if (warp == 1) {
         umma::fence_after();
         umma::dealloc(tmem, TMEM_COLS);
     }
 }
 
-// One problem's tiles on a persistent grid of clusters of CL CTAs.
-template <int S, int TB, int CL>
-cudaError_t launch_tc_cl(const Int8TcArgs &a, cudaStream_t stream) {
+// One problem's tiles on a persistent grid: one CTA per SM (at most one per
+// tile).
+template <int S, int TB>
+cudaError_t launch_tc_single(const Int8TcArgs &a, cudaStream_t stream) {
     using G = TcGeom<S>;
-    auto kernel = cascade_int8_tc_kernel<S, TB, CL, SingleSource>;
+    auto kernel = cascade_int8_tc_kernel<S, TB, SingleSource>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)G::SMEM);
     if (e != cudaSuccess) return e;
-    const long long tiles_n = (a.n + BN - 1) / BN;
-    const long long groups = (long long)((a.m + BM - 1) / BM) * ((tiles_n + CL - 1) / CL);
-    if (groups > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const long long tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
+    if (tiles_m * tiles_n > 0x7fffffffLL) return cudaErrorInvalidValue;
     SingleSource src;
     src.a = a;
-    src.tiles_m = (a.m + BM - 1) / BM;
+    src.tiles_m = (int)tiles_m;
     src.tiles_n = (int)tiles_n;
-    src.groups_n = (int)((tiles_n + CL - 1) / CL);
-    src.cl = CL;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    cfg.blockDim = dim3(NTHREADS);
-    cfg.dynamicSmemBytes = G::SMEM;
-    cfg.stream = stream;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    // persistent: as many clusters as can be resident at once
-    int clusters = 0;
-    cfg.gridDim = dim3(CL);
-    if ((e = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg)) != cudaSuccess) return e;
-    if (clusters <= 0) return cudaErrorInvalidConfiguration;
-    const long long use = groups < clusters ? groups : clusters;
-    cfg.gridDim = dim3((unsigned)(use * CL));
-    return cudaLaunchKernelEx(&cfg, kernel, src);
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const long long tiles = tiles_m * tiles_n;
+    const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
+    kernel<<<grid, NTHREADS, G::SMEM, stream>>>(src);
+    return cudaGetLastError();
 }
 
 }  // namespace

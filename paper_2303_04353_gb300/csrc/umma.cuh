@@ -83,16 +83,6 @@ __device__ __forceinline__ void commit(uint32_t bar) {
         : "memory");
 }
 
-// The same, arriving on the mbarrier at the same offset in every CTA of the
-// cluster named in `mask`.
-__device__ __forceinline__ void commit_multicast(uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(bar),
-        "h"(mask)
-        : "memory");
-}
-
 // One to four loads of 4 consecutive 32-bit columns each (at t[0..N-1])
 // for the 32 tensor-memory lanes of this warp's quadrant (lane i of the
 // warp receives lane quadrant base + i), then one wait, all in one asm

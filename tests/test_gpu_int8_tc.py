@@ -225,19 +225,6 @@ def test_tc_noalloc_matches_tc_ddgemm(ops):
     assert same(got[0], want[0]) and same(got[1], want[1])
 
 
-@pytest.mark.parametrize("cl", ["2", "4"])
-def test_tc_cluster_multicast_path(ops, cl, monkeypatch):
-    """The cluster form (A shared by multicast copies across CL CTAs, the
-    last ranks past n computing a copy and storing nothing): the same bits
-    as the restatement."""
-    monkeypatch.setenv("DDGEMM_INT8TC_CLUSTER", cl)
-    for m, n, k in [(200, 50, 1000), (70, 100, 513), (130, 20, 300)]:
-        a = gemm_inputs(m, n, k, kind="wide", seed=m + n)
-        c_hi, c_lo = tc(ops, *a)
-        w_hi, w_lo = c8.cascade_int8_tc_ddgemm(*a, s=16)
-        assert same(c_hi, w_hi) and same(c_lo, w_lo)
-
-
 # ---- the eight-bit tcgen05 form (DDGEMM_VARIANT_INT8_TC8) -----------------
 
 TC8 = 5
