@@ -47,9 +47,8 @@ NOMINAL_FP64_TFLOPS = 1.25
 NOMINAL_BF16_TFLOPS = 2250.0
 
 # DRAM bytes per launch (read + write) of the dominant kernel, from one ncu
-# capture of the current kernels at 4096^3 (profiles/dram_traffic_4096.md, and
-# profiles/cascade_int8_tc_kernel_2048.md for the tcgen05 kernel);
-# other workloads report null.
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
+# kernels at 4096^3; other workloads report null.
 TRAFFIC_4096 = {"cascade_fp64_kernel": 9.879882e9 + 0.281523e9,
                 "cascade_int8_kernel<15>": 2.923206e9 + 0.268134e9,
                 "cascade_int8_tc_kernel<16>": 9.122322e9 + 0.272443e9}
@@ -210,6 +209,347 @@ def cpu_baseline(a_hi, a_lo, b_hi, b_lo, target_s=12.0):
     return {"value": round(value, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
             "sample": f"{rows} of {m} rows of C ({rows * n} entries, k = {k}), "
                       f"scalar double-double TwoProd/TwoSum loop, {t:.1f} s"}
+
+
+# ---- the other workloads of the benchmark line ----------------------------
+# Each is one compact record in the default line, timed with CUDA events on
+# the launching stream after warm-up, with its own clock record and its
+# largest error against the double-double oracle on sampled entries.
+
+TC_FORMS = {1: ("int8 mma.sync, 15 x 8-bit pieces", 15),
+            4: ("int8 tcgen05, 16 x 7-bit pieces", 16),
+            5: ("int8 tcgen05, 15 x 8-bit pieces", 15)}
+
+
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def _timed(fn, reps, warmup, stream):
+    """Milliseconds per call of fn() on `stream` (CUDA events), and the
+    clock record taken while the timed calls ran."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = _events(2)
+    sampler = ClockSampler(physical_index(stream.device.index or 0))
+    sampler.start()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    return e0.elapsed_time(e1) / reps, clocks
+
+
+def _sampled_error(a, c, rows, cols):
+    """max |C - C_dd| / (|A||B|) over the sampled entries (A, B as (hi, lo)
+    host arrays, C as a (hi, lo) pair of device tensors)."""
+    from oracle import dd
+    oh, ol = dd.ddgemm_entries(*a, rows, cols)
+    ch, cl = c[0].cpu().numpy(), c[1].cpu().numpy()
+    absab = np.array([np.abs(a[0][i]) @ np.abs(a[2][:, j]) for i, j in zip(rows, cols)])
+    return float(np.max(np.abs((ch[rows, cols] - oh) + (cl[rows, cols] - ol)) / absab))
+
+
+def _form_step(d_in, m, n, k, variant, slices, reps, warmup, stream, dev):
+    """One form's whole step (split + products) timed, and its products
+    kernel timed by the phase events on the same calls."""
+    import torch
+
+    from paper_2303_04353_gb300 import ops
+    ws = ops.alloc_workspace(m, n, k, dev, variant, slices)
+    c = (torch.empty((m, n), dtype=torch.float64, device=dev),
+         torch.empty((m, n), dtype=torch.float64, device=dev))
+    phase = [_events(3) for _ in range(reps)]
+    for evs in phase:
+        for e in evs:
+            e.record(stream)            # an event must exist before the library records it
+    calls = {"timed": 0}
+
+    def step(timed=True):
+        evs = None
+        if timed:
+            evs = phase[calls["timed"] % reps]
+            calls["timed"] += 1
+        ops.ddgemm(*d_in, out=c, workspace=ws, stream=stream, variant=variant,
+                   int8_slices=slices, phase_events=evs)
+    for _ in range(warmup):
+        step(timed=False)
+    ms, clocks = _timed(step, reps, 0, stream)
+    kernel_ms = sum(ev[1].elapsed_time(ev[2]) for ev in phase) / reps
+    del ws
+    return ms, kernel_ms, clocks, c
+
+
+def _roofline_of(variant, slices, flops_dd, kernel_ms, int8_peak):
+    """Roofline fraction of a form's products kernel: FP64 flops against the
+    FP64 peak rule, integer ops against the live mma.sync s8 probe, bf16
+    digit flops against the measured bf16 burst peak."""
+    if variant == 0:
+        peak, src = fp64_peak_rule()
+        achieved = 10 * flops_dd / (kernel_ms * 1e-3) / 1e12
+        return {"bound": "fp64 pipe", "achieved": round(achieved, 4), "peak": round(peak, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "peak_source": src}
+    prods = slices * (slices + 1) // 2
+    achieved = prods * flops_dd / (kernel_ms * 1e-3) / 1e12
+    if variant == 1:
+        return {"bound": "tensor (mma.sync s8)", "achieved": round(achieved, 3),
+                "peak": round(int8_peak, 3), "unit": "TOPS", "frac": round(achieved / int8_peak, 4),
+                "peak_source": "of measured: live mma.sync s8 probe in this run"}
+    bpeak, bsrc, _ = bf16_peaks()
+    return {"bound": "tensor (tcgen05 bf16)", "achieved": round(achieved, 3),
+            "peak": round(bpeak, 3), "unit": "TFLOP/s", "frac": round(achieved / bpeak, 4),
+            "peak_source": bsrc}
+
+
+def _probe_tops(stream):
+    import torch
+
+    from paper_2303_04353_gb300 import _lib
+    sink = torch.zeros(1, dtype=torch.float64, device=stream.device)
+    best = 0.0
+    for iters in (200, 4000, 4000):
+        p0, p1 = _events(2)
+        p0.record(stream)
+        work = _lib.ddgemm_probe_int8(iters, sink.data_ptr(), stream.cuda_stream)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, work / (p0.elapsed_time(p1) * 1e-3) / 1e12)
+    return best
+
+
+def config_small(dev, stream):
+    """256^3, uniform entries, seed 0: the latency case.  Every entry is
+    checked against the full oracle."""
+    from oracle import dd
+    import torch
+    m = n = k = 256
+    a = gemm_inputs(m, n, k, kind="uniform", seed=0)
+    d_in = [torch.from_numpy(x).to(dev) for x in a]
+    oh, ol = dd.ddgemm(*a)
+    absab = np.abs(a[0]) @ np.abs(a[2])
+    out = {"workload": "ddgemm 256x256x256 FP64x2, hi U[-1,1], seed 0 (all entries checked)"}
+    for name, variant, s8 in (("fp64", 0, 0), ("int8_tc", 4, 16), ("int8_tc8", 5, 15)):
+        ms, kms, clocks, c = _form_step(d_in, m, n, k, variant, s8, 50, 5, stream, dev)
+        ch, cl = c[0].cpu().numpy(), c[1].cpu().numpy()
+        err = float(np.max(np.abs((ch - oh) + (cl - ol)) / absab))
+        out[name] = {"us_per_call": round(ms * 1e3, 2), "kernel_us": round(kms * 1e3, 2),
+                     "value": round(2.0 * m * n * k / (ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+                     "max_err_vs_dd_oracle": err, "launches": 3 if variant == 0 else 5,
+                     "clocks": clocks}
+    return out
+
+
+def config_rect(dev, stream):
+    """8192 x 1024 x 4096, wide entries (the rectangular case): the FP64
+    form with its automatic split-k grouping."""
+    import torch
+
+    from paper_2303_04353_gb300 import ops
+    m, n, k = 8192, 1024, 4096
+    a = gemm_inputs(m, n, k, kind="wide", seed=0)
+    d_in = [torch.from_numpy(x).to(dev) for x in a]
+    rng = np.random.default_rng(11)
+    rows, cols = rng.integers(0, m, 64), rng.integers(0, n, 64)
+    ms, kms, clocks, c = _form_step(d_in, m, n, k, 0, 0, 3, 3, stream, dev)
+    ws_bytes = ops.workspace_bytes(m, n, k)
+    return {"workload": "ddgemm 8192x1024x4096 FP64x2, hi log-uniform 2^-20..2^20, seed 0",
+            "ms_per_step": round(ms, 3), "value": round(2.0 * m * n * k / (ms * 1e-3) / 1e9, 4),
+            "unit": "GFLOP/s", "split_k_groups": ops.split_groups(m, n, k, dev, ws_bytes),
+            "roofline": _roofline_of(0, 0, 2.0 * m * n * k, kms, None),
+            "max_err_vs_dd_oracle": _sampled_error(a, c, rows, cols), "steps": 3, "warmup": 3,
+            "clocks": clocks}
+
+
+def config_int8_large(dev, stream, int8_peak):
+    """8192^3, wide entries: the three INT8 forms against one FP64-form step
+    on the same inputs (equal accuracy is read off the sampled errors)."""
+    import torch
+    m = n = k = 8192
+    a = gemm_inputs(m, n, k, kind="wide", seed=0)
+    d_in = [torch.from_numpy(x).to(dev) for x in a]
+    rng = np.random.default_rng(12)
+    rows, cols = rng.integers(0, m, 64), rng.integers(0, n, 64)
+    flops = 2.0 * m * n * k
+    out = {"workload": "ddgemm 8192x8192x8192 FP64x2, hi log-uniform 2^-20..2^20, seed 0"}
+    fp64_ms = None
+    for name, variant, s8, reps, warm in (("fp64", 0, 0, 1, 1), ("int8", 1, 15, 3, 3),
+                                          ("int8_tc", 4, 16, 5, 3), ("int8_tc8", 5, 15, 5, 3)):
+        ms, kms, clocks, c = _form_step(d_in, m, n, k, variant, s8, reps, warm, stream, dev)
+        rec = {"ms_per_step": round(ms, 3), "value": round(flops / (ms * 1e-3) / 1e9, 3),
+               "unit": "GFLOP/s", "roofline": _roofline_of(variant, s8, flops, kms, int8_peak),
+               "max_err_vs_dd_oracle": _sampled_error(a, c, rows, cols),
+               "steps": reps, "warmup": warm, "clocks": clocks}
+        if variant:
+            rec["pieces"] = s8
+            rec["products"] = s8 * (s8 + 1) // 2
+            rec["speedup_vs_fp64_form"] = round(fp64_ms / ms, 3)
+        else:
+            fp64_ms = ms
+        out[name] = rec
+        del c
+        torch.cuda.empty_cache()
+    return out
+
+
+def config_spread_sweep(dev, stream):
+    """Exponent-spread sweep at 2048^3: hi = +-2^u, u ~ U[-S/2, S/2], for
+    S = 0, 20, 40, 60 octaves; max error per form on 64 sampled entries."""
+    import torch
+
+    from paper_2303_04353_gb300 import ops
+    m = n = k = 2048
+    rng = np.random.default_rng(3)
+    rows, cols = rng.integers(0, m, 64), rng.integers(0, n, 64)
+    forms = (("fp64", 0, 0), ("int8", 1, 15), ("int8_tc", 4, 16), ("int8_tc8", 5, 15))
+    out = {"workload": "ddgemm 2048^3, hi = +-2^u, u ~ U[-S/2, S/2], seed 0; 64 sampled entries",
+           "spreads": [0, 20, 40, 60], "max_err_vs_dd_oracle": {f[0]: [] for f in forms}}
+    for spread in out["spreads"]:
+        a = gemm_inputs(m, n, k, kind="wide", seed=0, spread=float(spread))
+        d_in = [torch.from_numpy(x).to(dev) for x in a]
+        for name, variant, s8 in forms:
+            c = ops.ddgemm(*d_in, stream=stream, variant=variant, int8_slices=s8)
+            out["max_err_vs_dd_oracle"][name].append(_sampled_error(a, c, rows, cols))
+    return out
+
+
+def config_batched(dev, stream):
+    """512 problems, m, n, k each log-uniform in [64, 1024], uniform entries:
+    one ddgemm per problem against ddgemm_batched (autotuned tiles, eager and
+    graph-replayed) for the FP64 form, and the batched tcgen05 forms
+    graph-replayed.  Three problems are checked against the oracle."""
+    import torch
+
+    from paper_2303_04353_gb300 import autotune, ops
+    from workloads import batched_shapes
+    shapes = [tuple(int(v) for v in sh) for sh in batched_shapes(512, seed=0)]
+    host, probs = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        a = gemm_inputs(m, n, k, kind="uniform", seed=1000 + i)
+        host.append(a)
+        t = [torch.from_numpy(x).to(dev) for x in a]
+        probs.append((*t, torch.empty((m, n), dtype=torch.float64, device=dev),
+                      torch.empty((m, n), dtype=torch.float64, device=dev)))
+    flops = sum(2.0 * m * n * k for m, n, k in shapes)
+    checked = (0, 170, 341)
+
+    def worst(plist):
+        e = 0.0
+        for i in checked:
+            m, n, _ = shapes[i]
+            rng = np.random.default_rng(i)
+            rows, cols = rng.integers(0, m, 32), rng.integers(0, n, 32)
+            e = max(e, _sampled_error(host[i], (plist[i][4], plist[i][5]), rows, cols))
+        return e
+
+    def graph_of(batch, cfg=None):
+        side = torch.cuda.Stream(dev)
+        g = torch.cuda.CUDAGraph()
+        batch.run(stream=stream, config=cfg)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=side):
+            batch.run(stream=torch.cuda.current_stream(), config=cfg)
+        return g
+
+    out = {"workload": "batched: 512 problems, m, n, k log-uniform in [64, 1024], hi U[-1,1]",
+           "sum_2mnk": flops}
+    ws = ops.alloc_workspace(max(sh[0] for sh in shapes), max(sh[1] for sh in shapes),
+                             max(sh[2] for sh in shapes), dev)
+
+    def per_problem():
+        for a_hi, a_lo, b_hi, b_lo, c_hi, c_lo in probs:
+            ops.ddgemm(a_hi, a_lo, b_hi, b_lo, out=(c_hi, c_lo), workspace=ws, stream=stream)
+    per_ms, per_clocks = _timed(per_problem, 2, 1, stream)
+    del ws
+    batch = ops.Batch(probs)
+    cfg, tune_ms = autotune.tune(batch, reps=2, use_cache=False)
+    eager_ms, _ = _timed(lambda: batch.run(stream=stream, config=cfg), 3, 3, stream)
+    g = graph_of(batch, cfg)
+    graph_ms, graph_clocks = _timed(g.replay, 3, 3, stream)
+    out["fp64"] = {"per_problem_ms": round(per_ms, 3), "per_problem_launches": 3 * len(shapes),
+                   "per_problem_value": round(flops / (per_ms * 1e-3) / 1e9, 3),
+                   "batched_eager_ms": round(eager_ms, 3),
+                   "batched_graph_ms": round(graph_ms, 3),
+                   "value": round(flops / (graph_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+                   "autotuned": {"tile_order": list(cfg), "candidates_ms": tune_ms},
+                   "max_err_vs_dd_oracle": worst(probs), "launches": 4,
+                   "clocks": graph_clocks, "per_problem_clocks": per_clocks}
+    bpeak, bsrc, _ = bf16_peaks()
+    for name, variant, s8 in (("int8_tc", 4, 16), ("int8_tc8", 5, 15)):
+        tp = [(*p[:4], torch.empty_like(p[4]), torch.empty_like(p[5])) for p in probs]
+        tb = ops.Batch(tp, variant=variant)
+        tg = graph_of(tb)
+        ms, clocks = _timed(tg.replay, 5, 3, stream)
+        prods = s8 * (s8 + 1) // 2
+        achieved = prods * flops / (ms * 1e-3) / 1e12
+        out[name] = {"batched_graph_ms": round(ms, 3),
+                     "value": round(flops / (ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+                     "pieces": s8, "launches": 5,
+                     "speedup_vs_fp64_batched": round(graph_ms / ms, 3),
+                     "pass_roofline": {"bound": "tensor (tcgen05 bf16)",
+                                       "achieved": round(achieved, 3), "peak": round(bpeak, 3),
+                                       "unit": "TFLOP/s", "frac": round(achieved / bpeak, 4),
+                                       "peak_source": bsrc,
+                                       "what": f"{prods} x sum 2mnk digit flops over the "
+                                               "whole pass (5 launches)"},
+                     "max_err_vs_dd_oracle": worst(tp), "clocks": clocks}
+        del tg, tb, tp
+    return out
+
+
+def config_backward(dev, stream):
+    """2048^3 forward and backward (L = sum(W * C), dC = W, uniform A, B,
+    W): one step = C, then dA = W B^T and dB = A^T W, each by the cascade;
+    dA and dB checked on 64 sampled entries against the oracle's gradient."""
+    import torch
+
+    from paper_2303_04353_gb300 import ops
+    from workloads import dd_matrix
+    m = n = k = 2048
+    a = gemm_inputs(m, n, k, kind="uniform", seed=0)
+    w = dd_matrix(np.random.default_rng(99), (m, n))
+    d_in = [torch.from_numpy(x).to(dev) for x in a]
+    d_w = [torch.from_numpy(x).to(dev) for x in w]
+    rng = np.random.default_rng(13)
+    rows, cols = rng.integers(0, m, 64), rng.integers(0, k, 64)
+    bt = (np.ascontiguousarray(a[2].T), np.ascontiguousarray(a[3].T))
+    at = (np.ascontiguousarray(a[0].T), np.ascontiguousarray(a[1].T))
+    out = {"workload": "ddgemm 2048^3 forward + backward, L = sum(W * C), A, B, W hi U[-1,1]"}
+    for name, variant, s8 in (("fp64", 0, 0), ("int8_tc", 4, 16), ("int8_tc8", 5, 15)):
+        res = {}
+
+        def step():
+            ops.ddgemm(*d_in, stream=stream, variant=variant, int8_slices=s8)
+            res["g"] = ops.ddgemm_backward(*d_in, *d_w, stream=stream, variant=variant,
+                                           int8_slices=s8)
+        ms, clocks = _timed(step, 3, 3, stream)
+        da_hi, da_lo, db_hi, db_lo = res["g"]
+        err_da = _sampled_error((w[0], w[1], bt[0], bt[1]), (da_hi, da_lo), rows, cols)
+        err_db = _sampled_error((at[0], at[1], w[0], w[1]), (db_hi, db_lo), rows, cols)
+        out[name] = {"ms_per_step": round(ms, 3), "cascades": 3,
+                     "value": round(3 * 2.0 * m * n * k / (ms * 1e-3) / 1e9, 3),
+                     "unit": "GFLOP/s (3 x 2mnk per step)",
+                     "max_err_dA_vs_dd_oracle": err_da, "max_err_dB_vs_dd_oracle": err_db,
+                     "clocks": clocks}
+    return out
+
+
+def run_configs(dev, stream):
+    """All the other workloads, in the order of their cost."""
+    t0 = time.perf_counter()
+    int8_peak = _probe_tops(stream)
+    out = {"config0_256": config_small(dev, stream),
+           "config1_rect": config_rect(dev, stream),
+           "config2_8192": config_int8_large(dev, stream, int8_peak),
+           "config2_sweep": config_spread_sweep(dev, stream),
+           "config3_batched": config_batched(dev, stream),
+           "config4_backward": config_backward(dev, stream)}
+    out["configs_wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 def run_reference(args, wl):
@@ -464,6 +804,12 @@ def run_ours(args, wl):
             dgemm["int8_tc8_form_over_dgemm"] = round(int8_tc8_form["ms_per_step"] / dg_ms, 3)
         del z
 
+    # ---- the other workloads (configs 0, 2, 3, 4 and the rectangular case) --
+    configs = None
+    if world == 1 and variant == _lib.DDGEMM_VARIANT_FP64 and not args.no_configs:
+        torch.cuda.empty_cache()
+        configs = run_configs(dev, stream)
+
     if rank != 0:
         return
     peak, peak_src = fp64_peak_rule()
@@ -496,7 +842,9 @@ def run_ours(args, wl):
                     "algorithmic": f"{prods} x 2mnk = {prods * flops_dd:.4g} INT8 ops per launch"}
     else:
         achieved = 10.0 * flops_dd / (casc_ms * 1e-3) / 1e12
-        roofline = {"bound": "tensor", "kernel": "cascade_fp64_kernel",
+        # the FP64 MMA (mma.sync f64) runs on the FP64 pipe of sm_103a: ncu
+        # shows sm__pipe_fp64_cycles_active near 97 % and the tensor pipe idle
+        roofline = {"bound": "fp64 pipe", "kernel": "cascade_fp64_kernel",
                     "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                     "frac": round(achieved / peak, 4),
                     "traffic": TRAFFIC_4096["cascade_fp64_kernel"]
@@ -519,8 +867,10 @@ def run_ours(args, wl):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs (512 MiB) and panels larger than L2; no flush"
                          if m * k >= 1 << 22 else "small case; L2-resident"},
-        **({"pct_fp64_tc_peak": round(100.0 * 10.0 * flops_dd / (ms_per_step * 1e-3) / 1e12
-                                      / probe_tflops, 2)}
+        **({"pct_fp64_peak": round(100.0 * 10.0 * flops_dd / (ms_per_step * 1e-3) / 1e12
+                                   / probe_tflops, 2),
+            "pct_fp64_peak_of": "the live FP64 MMA probe; the metric's FP64-TC path is the FP64 "
+                                "pipe on sm_103a (tcgen05 has no f64 kind)"}
            if variant == _lib.DDGEMM_VARIANT_FP64 else
            {"pct_int8_tc_peak": round(100.0 * (args.int8_slices * (args.int8_slices + 1) // 2)
                                       * flops_dd / (ms_per_step * 1e-3) / 1e12 / probe_tops, 2)}
@@ -552,6 +902,13 @@ def run_ours(args, wl):
         line["int8_tc8_form"] = int8_tc8_form
     if dgemm is not None:
         line["dgemm_yardstick"] = dgemm
+    if int8_tc_form is not None and int8_tc8_form is not None:
+        line["int8_tc_headline"] = (
+            "int8_tc8_form (15 eight-bit pieces) is the tcgen05 form at the FP64 form's accuracy "
+            "everywhere measured, ill-conditioned products included; int8_tc_form (16 seven-bit "
+            "pieces) is faster and matches it on these inputs but not on ill-conditioned ones")
+    if configs is not None:
+        line.update(configs)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a_hi, a_lo, b_hi, b_lo)
     print(json.dumps(line), flush=True)
@@ -602,7 +959,7 @@ def run_batched(args):
 
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    shapes = [tuple(int(v) for v in sh) for sh in batched_shapes(512, seed=0)]
+    shapes = [tuple(int(v) for v in sh) for sh in batched_shapes(args.batch_count, seed=0)]
     host, probs = [], []
     for i, (m, n, k) in enumerate(shapes):
         a = gemm_inputs(m, n, k, kind="uniform", seed=1000 + i)
@@ -651,7 +1008,7 @@ def run_batched(args):
     clocks = sampler.stop()
     # accuracy on sampled entries of a few problems
     worst = 0.0
-    for i in range(0, 512, 64):
+    for i in range(0, len(shapes), 64):
         a = host[i]
         m, n, _ = shapes[i]
         rng = np.random.default_rng(i)
@@ -673,7 +1030,7 @@ def run_batched(args):
             tc_batch.run(stream=torch.cuda.current_stream())
         ms = timed(tc_graph.replay, args.steps)
         worst_tc = 0.0
-        for i in range(0, 512, 64):
+        for i in range(0, len(shapes), 64):
             a = host[i]
             m, n, _ = shapes[i]
             rng = np.random.default_rng(i)
@@ -911,6 +1268,8 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default="4096")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the records of the other workloads in the default line")
     ap.add_argument("--no-int8-form", action="store_true",
                     help="skip the INT8 form's entry in the FP64 line")
     ap.add_argument("--variant", choices=("fp64", "int8", "int8tc", "int8tc8"), default="fp64",
@@ -923,6 +1282,8 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--sweep", action="store_true",
                     help="exponent-spread study of both forms instead of the benchmark line")
     ap.add_argument("--sweep-size", type=int, default=2048)
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="problems of the batched workload (512; fewer for a small profile)")
     ap.add_argument("--illcond", action="store_true",
                     help="ill-conditioned accuracy study instead of the benchmark line")
     ap.add_argument("--ablation", action="store_true",

@@ -24,6 +24,9 @@
  *     ddgemm_host(), whose matrices are in host memory), and the library
  *     never allocates device memory, frees or keeps a pointer after the
  *     call: scratch space is the caller's `workspace`.
+ *   - When a call sets DDGEMM_DEV_TIMEOUT in the status word, its outputs
+ *     are undefined (the FP64 form writes NaN into the tiles whose wait gave
+ *     up; the other forms leave the tiles they did not finish as they were).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Work is enqueued on it and the call returns without waiting.
  *   - The return value reports host-side checks and launch errors only.
@@ -55,7 +58,7 @@ extern "C" {
 /* Device status bits, OR-ed into *opts->status_dev. */
 #define DDGEMM_DEV_NONFINITE 0x1u /* an input entry was Inf or NaN */
 #define DDGEMM_DEV_TIMEOUT   0x2u /* a bounded wait inside a kernel gave up;
-                                     outputs of that call are incomplete */
+                                     outputs of that call are undefined */
 
 /* opts->variant */
 #define DDGEMM_VARIANT_FP64  0    /* ten FP64 products on the FP64 tensor path */
@@ -279,8 +282,11 @@ size_t ddgemm_host_buffer_size(int m, int n, int k, const ddgemm_opts *opts);
  *
  *   - buffer: device memory of >= ddgemm_host_buffer_size() bytes, 256-byte
  *     aligned, owned by the caller; it holds the copies and the workspace.
- *   - The call makes two streams and eleven events of its own (released
- *     when it returns; the driver keeps them until their work is done).
+ *   - The copies run on two streams of the library's own, ordered by eleven
+ *     events: a call takes such a set from a per-device pool and returns
+ *     it when it returns, so only the first call on a device (and a call
+ *     that overlaps another one on the host) creates them; they live until
+ *     the process exits (do not reset the device between calls).
  *     B is copied first, then op(A) in up to four chunks of rows: every
  *     chunk's split and products run on `stream` as soon as its rows have
  *     arrived, and its rows of C are copied back while the next chunk
@@ -307,7 +313,8 @@ size_t ddgemm_host_buffer_size(int m, int n, int k, const ddgemm_opts *opts);
  *     DDGEMM_ECUDA if a stream, event, copy or launch call fails (work
  *     enqueued before the failure may still be running: synchronise the
  *     device before reusing the buffer or the host arrays).
- *   - Not for stream capture (it creates and destroys streams). */
+ *   - Not for stream capture (it records and waits on events of its own
+ *     streams and may create a set of them). */
 int ddgemm_host(int m, int n, int k,
                 const double *A_hi, const double *A_lo, int lda,
                 const double *B_hi, const double *B_lo, int ldb,
@@ -343,7 +350,10 @@ int ddgemm_host(int m, int n, int k,
  *   - Every call on a device shares the one array, which keeps the last
  *     call's contents (nothing in it needs clearing between calls): calls
  *     whose work overlaps on the GPU (different streams, no ordering) race
- *     and give wrong results.  Serialise them, e.g. on one stream. */
+ *     and give wrong results.  Serialise them, e.g. on one stream.
+ *   - C is undefined when the status word reports DDGEMM_DEV_TIMEOUT; a
+ *     split-k group whose wait gave up writes NaN into its partial tile, so
+ *     an earlier call's partial sums left in the array never reach C. */
 int ddgemm_noalloc(int m, int n, int k,
                    const double *A_hi, const double *A_lo, int lda,
                    const double *B_hi, const double *B_lo, int ldb,
@@ -423,29 +433,6 @@ int ddgemm_bins(int m, int n, int k,
                 const double *B_hi, const double *B_lo, int ldb,
                 double *bins, void *workspace, size_t ws_bytes, void *stream,
                 const ddgemm_opts *opts);
-
-/* Measurement aid, not part of the method: enqueue a throughput kernel of
- * the FP64 tensor path (mma.sync m8n8k4 f64, 4 CTAs of 256 threads per SM,
- * eight independent accumulator chains per warp, `iters` rounds) on
- * `stream` and return the number of FP64 flops it performs (-1 on error).
- * The caller times it; flops / time is the measured ceiling of the ten
- * products.  sink: device pointer to one double (never written in
- * practice). */
-double ddgemm_probe_fp64(int iters, double *sink, void *stream);
-
-/* The same for the integer tensor path of the INT8 form (mma.sync m16n8k32
- * s8 with s32 accumulation, four independent chains per warp); returns the
- * number of integer operations (2 per multiply-add), or -1 on error. */
-double ddgemm_probe_int8(int iters, double *sink, void *stream);
-
-/* Check of the kernels' failure handling, not part of the method: one
- * thread waits, with the same bounded mbarrier wait the cascade kernels
- * use, on a barrier that nothing arrives on.  After limit_ns nanoseconds
- * (1 .. 10^10) it gives up and ORs DDGEMM_DEV_TIMEOUT into *status_dev, as
- * a cascade kernel does when a wait runs out; the context stays usable.
- * Returns DDGEMM_EINVAL for a null status or a limit out of range. */
-int ddgemm_probe_wait_timeout(unsigned long long limit_ns, unsigned int *status_dev,
-                              void *stream);
 
 /* Static text for a return code. */
 const char *ddgemm_status_string(int code);

@@ -20,7 +20,7 @@ the paper builds, step by step and in the paper's order:
      scaling, and FP64x2 accumulation over k-blocks
      (Sec. "Simple: FP64x2 GEMM via ten FP64 GEMMs").
 
-Readings where the paper is silent or garbled (all listed in the design doc):
+Readings where the paper is silent or garbled:
   * sigma = 2**e with e the frexp exponent of max |hi| over the block, i.e.
     the smallest power of two strictly above the largest magnitude; an
     all-zero block gets sigma = 1.

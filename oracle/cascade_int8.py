@@ -8,7 +8,7 @@ operand to fixed point, store it as about 15 INT8 pieces, compute the
 pair-products that matter (the triangle i + j <= s - 1, Sec. "Safely dropping
 lower order bins") with 32-bit integer accumulation, and add the results
 across bins in FP64x2.  The paper gives no further detail; the readings
-below (listed in the design doc) fill it in.
+below fill it in.
 
   * Scale: sigma = 2^e per (row of A, k-block) and per (k-block, column of
     B), e the frexp exponent of max |hi| in the block, as in the FP64 form.

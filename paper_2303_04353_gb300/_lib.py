@@ -1,4 +1,5 @@
-"""Thin ctypes binding of libddgemm: the C ABI of include/ddgemm.h under the
+"""Thin ctypes binding of libddgemm: the C ABI of include/ddgemm.h (and the
+measurement and failure-handling aids of include/ddgemm_diag.h) under the
 same names, with argument marshalling only (every step of the computation
 runs in the library's CUDA kernels).  Device memory and streams come from
 PyTorch; pointers and sizes go through unchanged.
@@ -80,6 +81,10 @@ _SIGS = {
     "ddgemm_split_int8_b": (_I, [_I, _I, _P, _P, _I, _I, _I, _P, _I, _P, _P, _P]),
     "ddgemm_backward": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P,
                              _I, _P, _Z, _P, _P]),
+    "ddgemm_diag_withheld_copy": (_I, [_I, _I, _I, _P, _P, _I, _P, _P, _I, _P, _P, _I, _P, _Z, _P,
+                                       _P, _I, ctypes.c_longlong, ctypes.c_ulonglong]),
+    "ddgemm_diag_batched_withheld_copy": (_I, [_I, _P, _P, _P, _Z, _P, _P, _I, ctypes.c_longlong,
+                                               ctypes.c_ulonglong]),
 }
 DDGEMM_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -238,3 +243,24 @@ def ddgemm_batched(count, probs_host, probs_dev, workspace, ws_bytes, stream,
     _check(load().ddgemm_batched(count, probs_host, probs_dev, workspace, ws_bytes, stream,
                                  ctypes.byref(opts) if opts else None,
                                  ctypes.byref(config) if config else None), "ddgemm_batched")
+
+
+def ddgemm_diag_withheld_copy(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo, ldc,
+                              workspace, ws_bytes, stream, opts: ddgemm_opts, cta: int, step: int,
+                              limit_ns: int) -> None:
+    """ddgemm with one copy of CTA `cta` withheld, so that its bounded waits
+    run out after limit_ns (see include/ddgemm_diag.h).  Raises on error."""
+    _check(load().ddgemm_diag_withheld_copy(m, n, k, a_hi, a_lo, lda, b_hi, b_lo, ldb, c_hi, c_lo,
+                                            ldc, workspace, ws_bytes, stream, ctypes.byref(opts),
+                                            cta, step, limit_ns), "ddgemm_diag_withheld_copy")
+
+
+def ddgemm_diag_batched_withheld_copy(count, probs_host, probs_dev, workspace, ws_bytes, stream,
+                                      opts: ddgemm_opts, cta: int, step: int,
+                                      limit_ns: int) -> None:
+    """ddgemm_batched (tcgen05 forms) with one copy withheld; see
+    include/ddgemm_diag.h.  Raises on error."""
+    _check(load().ddgemm_diag_batched_withheld_copy(count, probs_host, probs_dev, workspace,
+                                                    ws_bytes, stream, ctypes.byref(opts), cta,
+                                                    step, limit_ns),
+           "ddgemm_diag_batched_withheld_copy")

@@ -5,8 +5,12 @@
 #include <algorithm>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
 
 #include "../../include/ddgemm.h"
+#include "../../include/ddgemm_diag.h"
 #include "ddgemm_internal.h"
 
 namespace {
@@ -70,6 +74,7 @@ struct Parsed {
     void **events = nullptr;
     int slices = 0;  // 0: the form's default
     int split_k = 0;
+    ddg::WaitPlan wait{};  // only the diagnostic entry point changes it
 };
 
 bool is_int8(int variant) {
@@ -263,12 +268,12 @@ cudaError_t products_into(const Carve &c, int mr, int n, int k, double *C_hi, do
             ddg::Int8TcArgs a{mr, n, k, p.slices, int8_bits(p.variant),
                               reinterpret_cast<const uint16_t *>(ws + L.off_a),
                               reinterpret_cast<const uint16_t *>(ws + L.off_b), e_a, e_b, C_hi,
-                              C_lo, (long long)ldc, p.status};
+                              C_lo, (long long)ldc, p.status, p.wait};
             return ddg::launch_cascade_int8_tc(a, s);
         }
         ddg::Int8Args a{mr, n, k, p.slices, reinterpret_cast<const int8_t *>(ws + L.off_a),
                         reinterpret_cast<const int8_t *>(ws + L.off_b), L.ld, e_a, e_b, C_hi,
-                        C_lo, (long long)ldc, p.status};
+                        C_lo, (long long)ldc, p.status, p.wait};
         return ddg::launch_cascade_int8(a, s);
     }
     const Layout &L = c.L;
@@ -282,7 +287,8 @@ cudaError_t products_into(const Carve &c, int mr, int n, int k, double *C_hi, do
                         reinterpret_cast<const double *>(ws + L.off_b), L.ldb_s,
                         reinterpret_cast<const int *>(ws + L.off_ea),
                         reinterpret_cast<const int *>(ws + L.off_eb), C_hi, C_lo,
-                        (long long)ldc, flags, p.status, bins, products, split, part, part_lo};
+                        (long long)ldc, flags, p.status, bins, products, split, part, part_lo,
+                        p.wait};
     return ddg::launch_cascade_fp64(ca, s);
 }
 
@@ -375,9 +381,14 @@ HostLayout host_layout(int m, int n, int k, const Parsed &p) {
     return H;
 }
 
-// The copy streams and events of one ddgemm_host call.  They are released
-// when the call returns; the driver keeps each alive until the work enqueued
-// on it has completed.
+// The copy streams and events of one ddgemm_host call.  A call takes a set
+// from its device's pool and puts it back when it returns: the first call on
+// a device (and each call that overlaps another on the host) creates one,
+// later calls reuse them, so a call creates nothing.  A set is used by one
+// call at a time, so its event records and waits cannot interleave with
+// another call's; work a call left on the set's streams only orders the next
+// call's copies after it (both wait for their own caller's stream anyway).
+// The sets live until the process exits.
 struct HostStreams {
     static constexpr int MAX_EVENTS = 3 + 2 * HOST_MAX_CHUNKS;
     cudaStream_t h2d = nullptr, d2h = nullptr;
@@ -390,11 +401,54 @@ struct HostStreams {
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
         return true;
     }
-    ~HostStreams() {
-        for (auto e : ev)
-            if (e) cudaEventDestroy(e);
-        if (h2d) cudaStreamDestroy(h2d);
-        if (d2h) cudaStreamDestroy(d2h);
+    void release() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e), e = nullptr;
+        if (h2d) cudaStreamDestroy(h2d), h2d = nullptr;
+        if (d2h) cudaStreamDestroy(d2h), d2h = nullptr;
+    }
+};
+
+std::mutex g_host_pool_mutex;
+std::unordered_map<int, std::vector<HostStreams *>> g_host_pool;  // by device
+
+// A set of copy streams and events on the current device, from the pool or
+// new (nullptr if creating one fails); returned with put_host_streams.
+HostStreams *take_host_streams(int dev) {
+    {
+        std::lock_guard<std::mutex> lock(g_host_pool_mutex);
+        auto &free = g_host_pool[dev];
+        if (!free.empty()) {
+            HostStreams *h = free.back();
+            free.pop_back();
+            return h;
+        }
+    }
+    HostStreams *h = new HostStreams;
+    if (!h->init()) {
+        h->release();
+        delete h;
+        return nullptr;
+    }
+    return h;
+}
+
+void put_host_streams(int dev, HostStreams *h) {
+    std::lock_guard<std::mutex> lock(g_host_pool_mutex);
+    g_host_pool[dev].push_back(h);
+}
+
+// Holds a pooled set for the length of one call.
+struct PooledHostStreams {
+    int dev = -1;
+    HostStreams *h = nullptr;
+    bool acquire() {
+        if (cudaGetDevice(&dev) != cudaSuccess) return false;
+        h = take_host_streams(dev);
+        return h != nullptr;
+    }
+    ~PooledHostStreams() {
+        if (h) put_host_streams(dev, h);
     }
 };
 
@@ -474,6 +528,28 @@ size_t ddgemm_host_buffer_size(int m, int n, int k, const ddgemm_opts *opts) {
     return host_layout(m, n, k, p).total;
 }
 
+int ddgemm_diag_withheld_copy(int m, int n, int k, const double *A_hi, const double *A_lo,
+                              int lda, const double *B_hi, const double *B_lo, int ldb,
+                              double *C_hi, double *C_lo, int ldc, void *workspace,
+                              size_t ws_bytes, void *stream, const ddgemm_opts *opts, int cta,
+                              long long step, unsigned long long limit_ns) {
+    Parsed p;
+    if (!opts || !opts->status_dev || !parse(opts, p) || !dims_ok(m, n, k)) return DDGEMM_EINVAL;
+    if (cta < 0 || step < 0 || limit_ns < 1000ull || limit_ns > 10000000000ull)
+        return DDGEMM_EINVAL;
+    if (p.variant < DDGEMM_VARIANT_FP64 || p.variant > DDGEMM_VARIANT_INT8_TC8 || p.flags)
+        return DDGEMM_EUNSUPPORTED;
+    if (int r = check_operands(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, p)) return r;
+    if (m == 0 || n == 0 || k == 0) return DDGEMM_EINVAL;  // no kernel to withhold from
+    if (!C_hi || !C_lo || ldc < n) return DDGEMM_EINVAL;
+    p.events = nullptr;
+    p.wait.limit_ns = limit_ns;
+    p.wait.cta = cta;
+    p.wait.step = step;
+    return run(m, n, k, A_hi, A_lo, lda, B_hi, B_lo, ldb, C_hi, C_lo, ldc, nullptr, workspace,
+               ws_bytes, static_cast<cudaStream_t>(stream), p);
+}
+
 int ddgemm_host(int m, int n, int k, const double *A_hi, const double *A_lo, int lda,
                 const double *B_hi, const double *B_lo, int ldb, double *C_hi, double *C_lo,
                 int ldc, void *buffer, size_t buffer_bytes, void *stream,
@@ -499,8 +575,9 @@ int ddgemm_host(int m, int n, int k, const double *A_hi, const double *A_lo, int
     double *c_lo = reinterpret_cast<double *>(buf + H.off_c + H.c_plane);
     char *ws = buf + H.off_ws;
 
-    HostStreams hs;
-    if (!hs.init()) return DDGEMM_ECUDA;
+    PooledHostStreams pooled;
+    if (!pooled.acquire()) return DDGEMM_ECUDA;
+    HostStreams &hs = *pooled.h;
     // event slots: the entry, B copied, chunk r of A copied, chunk r of C done
     constexpr int E_ENTRY = 0, E_B = 1, E_A = 2, E_C = 2 + HOST_MAX_CHUNKS;
     // nothing of this call starts before the work already on the caller's

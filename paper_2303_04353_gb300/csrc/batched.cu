@@ -17,6 +17,7 @@
 #include <cstdint>
 
 #include "../../include/ddgemm.h"
+#include "../../include/ddgemm_diag.h"
 #include "cascade_core.cuh"
 #include "ddgemm_internal.h"
 #include "split_device.cuh"
@@ -526,4 +527,35 @@ extern "C" int ddgemm_batched(int count, const ddgemm_problem *probs_host,
         default: e = launch_cascade<4, 2>(ws, sms, s); break;
     }
     return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
+}
+
+extern "C" int ddgemm_diag_batched_withheld_copy(int count, const ddgemm_problem *probs_host,
+                                                 const ddgemm_problem *probs_dev, void *workspace,
+                                                 size_t ws_bytes, void *stream,
+                                                 const ddgemm_opts *opts, int cta, long long step,
+                                                 unsigned long long limit_ns) {
+    using namespace ddg;
+    if (!opts || !opts->status_dev || count <= 0 || !probs_host || !probs_dev)
+        return DDGEMM_EINVAL;
+    if (cta < 0 || step < 0 || limit_ns < 1000ull || limit_ns > 10000000000ull)
+        return DDGEMM_EINVAL;
+    if (opts->trans_a || opts->trans_b || opts->flags_dev) return DDGEMM_EUNSUPPORTED;
+    int bits, s;
+    if (opts->variant == DDGEMM_VARIANT_INT8_TC) {
+        bits = INT8_TC_BITS;
+        s = opts->int8_slices ? opts->int8_slices : INT8_TC_SLICES_DEFAULT;
+        if (!int8_tc_slices_supported(s)) return DDGEMM_EINVAL;
+    } else if (opts->variant == DDGEMM_VARIANT_INT8_TC8) {
+        bits = INT8_BITS;
+        s = opts->int8_slices ? opts->int8_slices : INT8_TC8_SLICES_DEFAULT;
+        if (!int8_tc8_slices_supported(s)) return DDGEMM_EINVAL;
+    } else {
+        return DDGEMM_EUNSUPPORTED;
+    }
+    WaitPlan wait;
+    wait.limit_ns = limit_ns;
+    wait.cta = cta;
+    wait.step = step;
+    return run_batched_int8_tc(count, probs_host, probs_dev, workspace, ws_bytes,
+                               static_cast<cudaStream_t>(stream), s, bits, opts->status_dev, wait);
 }

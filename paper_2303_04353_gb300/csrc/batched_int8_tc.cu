@@ -366,12 +366,14 @@ __global__ void __launch_bounds__(256, 4) tc_digits_kernel(const char *ws) {
 // tiles go in groups of TILE_GROUP row tiles.
 struct BatchSource {
     const char *ws;
+    WaitPlan plan;
     __device__ long long items() const {
         return reinterpret_cast<const TcHeader *>(ws)->total_tiles;
     }
     __device__ unsigned int *status() const {
         return reinterpret_cast<const TcHeader *>(ws)->status;
     }
+    __device__ const WaitPlan &wait() const { return plan; }
     // hint: the rank of the caller's previous item (items come in
     // increasing order)
     __device__ TcJob job(long long item, int &hint) const {
@@ -401,7 +403,7 @@ struct BatchSource {
 
 template <int S, int BITS>
 cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, long long units_eb,
-                              long long units_d, int sms, cudaStream_t s) {
+                              long long units_d, int sms, cudaStream_t s, const WaitPlan &wait) {
     const long long cap = 8LL * sms;
     if (units_ea > 0) {
         const long long blocks = (units_ea + 7) / 8;
@@ -419,7 +421,7 @@ cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, lon
                                   (int)G::SMEM)) != cudaSuccess)
         return e;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    BatchSource src{ws};
+    BatchSource src{ws, wait};
     kernel<<<grid, NTHREADS, G::SMEM, s>>>(src);
     return cudaGetLastError();
 }
@@ -448,7 +450,8 @@ size_t batched_int8_tc_workspace_size(int count, const ddgemm_problem *probs_hos
 
 int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
                         const ddgemm_problem *probs_dev, void *workspace, size_t ws_bytes,
-                        cudaStream_t s, int slices, int bits, unsigned int *status) {
+                        cudaStream_t s, int slices, int bits, unsigned int *status,
+                        const WaitPlan &wait) {
     if (bits != INT8_TC_BITS && bits != INT8_BITS) return DDGEMM_EINVAL;
     if (bits == INT8_BITS && slices > 15) return DDGEMM_EINVAL;
     const int kblk = kblock_of_bits(bits);
@@ -480,24 +483,26 @@ int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
     tc_plan_kernel<<<1, 256, 0, s>>>(count, probs_dev, ws, slices, kblk, status);
     if (cudaGetLastError() != cudaSuccess) return DDGEMM_ECUDA;
     cudaError_t e;
+#define DDG_TC(S, B) launch_batched_tc<S, B>(ws, tiles, ea, eb, d, sms, s, wait)
     if (bits == INT8_BITS) {
         switch (slices) {
-            case 12: e = launch_batched_tc<12, INT8_BITS>(ws, tiles, ea, eb, d, sms, s); break;
-            case 13: e = launch_batched_tc<13, INT8_BITS>(ws, tiles, ea, eb, d, sms, s); break;
-            case 14: e = launch_batched_tc<14, INT8_BITS>(ws, tiles, ea, eb, d, sms, s); break;
-            case 15: e = launch_batched_tc<15, INT8_BITS>(ws, tiles, ea, eb, d, sms, s); break;
+            case 12: e = DDG_TC(12, INT8_BITS); break;
+            case 13: e = DDG_TC(13, INT8_BITS); break;
+            case 14: e = DDG_TC(14, INT8_BITS); break;
+            case 15: e = DDG_TC(15, INT8_BITS); break;
             default: return DDGEMM_EINVAL;
         }
     } else {
         switch (slices) {
-            case 12: e = launch_batched_tc<12, INT8_TC_BITS>(ws, tiles, ea, eb, d, sms, s); break;
-            case 13: e = launch_batched_tc<13, INT8_TC_BITS>(ws, tiles, ea, eb, d, sms, s); break;
-            case 14: e = launch_batched_tc<14, INT8_TC_BITS>(ws, tiles, ea, eb, d, sms, s); break;
-            case 15: e = launch_batched_tc<15, INT8_TC_BITS>(ws, tiles, ea, eb, d, sms, s); break;
-            case 16: e = launch_batched_tc<16, INT8_TC_BITS>(ws, tiles, ea, eb, d, sms, s); break;
+            case 12: e = DDG_TC(12, INT8_TC_BITS); break;
+            case 13: e = DDG_TC(13, INT8_TC_BITS); break;
+            case 14: e = DDG_TC(14, INT8_TC_BITS); break;
+            case 15: e = DDG_TC(15, INT8_TC_BITS); break;
+            case 16: e = DDG_TC(16, INT8_TC_BITS); break;
             default: return DDGEMM_EINVAL;
         }
     }
+#undef DDG_TC
     return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
 }
 

@@ -170,4 +170,26 @@ __device__ __forceinline__ void epilogue(Acc &acc, int p, bool first, int row0, 
     }
 }
 
+// NaN into every output of one warp's sub-tile at (row0, col0) (hi and lo):
+// what a CTA whose wait gave up leaves, so that no later pass can mistake
+// its outputs for results.
+__device__ __forceinline__ void poison(int row0, int col0, int lane, const EpilogueOut &o) {
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int row = row0 + i * 8 + (lane >> 2);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int col = col0 + j * 8 + 2 * (lane & 3) + h;
+                if (row < o.m && col < o.n) {
+                    const long long x = (long long)row * o.ldc + col;
+                    o.c_hi[x] = nan;
+                    o.c_lo[x] = nan;
+                }
+            }
+    }
+}
+
 }  // namespace ddg

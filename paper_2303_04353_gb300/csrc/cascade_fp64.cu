@@ -25,9 +25,11 @@
 // FP64x2 additions, scale by 2^(e_a + e_b) (exact), FP64x2-add into C (C
 // itself holds the running sum between k-blocks; each CTA owns its tile).
 //
-// Waits.  Every mbarrier wait gives up after ~2 s of global time: the CTA
-// then sets DDGEMM_DEV_TIMEOUT, waits (again bounded) for its own copies
-// still in flight and returns.
+// Waits.  Every mbarrier wait gives up after args.wait.limit_ns (~2 s) of
+// global time: the CTA then sets DDGEMM_DEV_TIMEOUT, writes NaN into the
+// outputs it owns (its C tile, or its partial tile under split-k, so that
+// the fix-up cannot add stale partial sums into a plausible C), waits
+// (again bounded) for its own copies still in flight and returns.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -75,7 +77,11 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
     }
     __syncthreads();
 
+    // the failure-handling tests withhold one k-step's copy of one CTA
+    const long long withheld = (int)blockIdx.x == args.wait.cta ? args.wait.step : -1;
+    const unsigned long long limit = args.wait.limit_ns;
     auto issue = [&](int t, int stage) {
+        if (t == withheld) return;
         const uint32_t bar = smem_addr(&bars[stage]);
         double *dst = smem + stage * STAGE;
         mbar_arrive_expect_tx(bar, STAGE_BYTES);
@@ -100,14 +106,16 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
     for (int t = 0; t < ksteps; ++t) {
         const int stage = t % NST;
         const uint32_t parity = (t / NST) & 1;
-        const bool ok = mbar_wait(smem_addr(&bars[stage]), parity);
+        const bool ok = mbar_wait_limit(smem_addr(&bars[stage]), parity, limit);
         if (__syncthreads_or(!ok)) {
+            if constexpr (!DUMP_BINS) poison(m0 + wm * 16, n0 + wn * 32, lane, out);
             if (tid == 0) {
                 if (args.status) atomicOr(args.status, DEV_TIMEOUT_BIT);
                 // Copies already issued for steps t .. t+NST-1 may still be in
                 // flight into this CTA's shared memory: wait for them, bounded.
                 for (int u = t; u < t + NST && u < ksteps; ++u)
-                    mbar_wait(smem_addr(&bars[u % NST]), (u / NST) & 1);
+                    if (u != withheld)
+                        mbar_wait_limit(smem_addr(&bars[u % NST]), (u / NST) & 1, limit);
             }
             return;
         }

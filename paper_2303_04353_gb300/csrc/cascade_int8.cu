@@ -89,7 +89,11 @@ cascade_int8_kernel(const __grid_constant__ CUtensorMap tm_a,
     }
     __syncthreads();
 
+    // the failure-handling tests withhold one k-step's copy of one CTA
+    const long long withheld = (int)blockIdx.x == args.wait.cta ? args.wait.step : -1;
+    const unsigned long long limit = args.wait.limit_ns;
     auto issue = [&](int t, int stage) {
+        if (t == withheld) return;
         const uint32_t bar = smem_addr(&bars[stage]);
         unsigned char *dst = smem + stage * G::STAGE;
         mbar_arrive_expect_tx(bar, (uint32_t)G::STAGE);
@@ -110,12 +114,13 @@ cascade_int8_kernel(const __grid_constant__ CUtensorMap tm_a,
 
     for (int t = 0; t < ksteps; ++t) {
         const int stage = t % NST;
-        const bool ok = mbar_wait(smem_addr(&bars[stage]), (t / NST) & 1);
+        const bool ok = mbar_wait_limit(smem_addr(&bars[stage]), (t / NST) & 1, limit);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 if (args.status) atomicOr(args.status, DEV_TIMEOUT_BIT);
                 for (int u = t; u < t + NST && u < ksteps; ++u)
-                    mbar_wait(smem_addr(&bars[u % NST]), (u / NST) & 1);
+                    if (u != withheld)
+                        mbar_wait_limit(smem_addr(&bars[u % NST]), (u / NST) & 1, limit);
             }
             return;
         }

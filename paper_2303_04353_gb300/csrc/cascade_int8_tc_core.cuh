@@ -67,19 +67,20 @@ struct Shared {
     int abort_flag;
 };
 
-// A bounded wait that also gives up when another role has aborted.
-// sleep_ns > 0: sleep between polls (the drain warps, which share their SM
-// sub-partitions with the copy and MMA threads and can wait a little
-// longer: measured 0.8 % off the eight-bit form at 4096^3).
+// A wait bounded by limit_ns that also gives up when another role has
+// aborted.  sleep_ns > 0: sleep between polls (the drain warps, which share
+// their SM sub-partitions with the copy and MMA threads and can wait a
+// little longer: measured 0.8 % off the eight-bit form at 4096^3).
 template <class SH>
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, SH *sh,
-                                              unsigned int *status, unsigned sleep_ns = 0) {
+                                              unsigned int *status, uint64_t limit_ns,
+                                              unsigned sleep_ns = 0) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     volatile int *flag = &sh->abort_flag;
     while (!mbar_try_wait(bar, parity)) {
         if (*flag) return false;
-        if (global_ns() - t0 > WAIT_LIMIT_NS) {
+        if (global_ns() - t0 > limit_ns) {
             *flag = 1;
             if (status) atomicOr(status, DEV_TIMEOUT_BIT);
             return false;
@@ -313,6 +314,7 @@ struct SingleSource {
     int tiles_m, tiles_n;
     __device__ long long items() const { return (long long)tiles_m * tiles_n; }
     __device__ unsigned int *status() const { return a.status; }
+    __device__ const WaitPlan &wait() const { return a.wait; }
     __device__ TcJob job(long long item, int &) const {
         int tm, tn;
         grouped_tile((unsigned)item, tiles_m, tiles_n, TILE_GROUP, tm, tn);
@@ -351,6 +353,7 @@ cascade_int8_tc_kernel(const Src src) {
     const long long tiles = src.items();
     const long long first = blockIdx.x, stride = gridDim.x;
     unsigned int *status = src.status();
+    const uint64_t limit = src.wait().limit_ns;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
@@ -377,6 +380,9 @@ cascade_int8_tc_kernel(const Src src) {
     if (warp == 0) {
         // ---- TMA producer -----------------------------------------------
         if (lane == 0) {
+            // the failure-handling tests withhold one ring iteration's copies
+            const long long withheld =
+                (int)blockIdx.x == src.wait().cta ? src.wait().step : -1;
             uint32_t it = 0;
             bool ok = true;
             int hint = 0;  // the job source's position (items come in order)
@@ -386,11 +392,12 @@ cascade_int8_tc_kernel(const Src src) {
                 for (int ks = 0; ks < ksteps; ++ks, ++it) {
                     const int stage = it % NST;
                     const uint32_t use = it / NST;
-                    if (use > 0 &&
-                        !wait_or_abort(smem_addr(&sh->empty[stage]), (use - 1) & 1, sh, status)) {
+                    if (use > 0 && !wait_or_abort(smem_addr(&sh->empty[stage]), (use - 1) & 1, sh,
+                                                  status, limit)) {
                         ok = false;
                         break;
                     }
+                    if ((long long)it == withheld) continue;
                     unsigned char *dst = smem + stage * G::STAGE;
                     const uint32_t bar = smem_addr(&sh->full[stage]);
                     mbar_arrive_expect_tx(bar, (uint32_t)G::TX);
@@ -407,7 +414,8 @@ cascade_int8_tc_kernel(const Src src) {
             if (!ok) {
                 // copies issued but perhaps not consumed: let them land (bounded)
                 for (uint32_t u = it > (uint32_t)NST ? it - NST : 0; u < it; ++u)
-                    mbar_wait(smem_addr(&sh->full[u % NST]), (u / NST) & 1);
+                    if ((long long)u != withheld)
+                        mbar_wait_limit(smem_addr(&sh->full[u % NST]), (u / NST) & 1, limit);
             }
         }
         __syncwarp();
@@ -425,7 +433,7 @@ cascade_int8_tc_kernel(const Src src) {
                     const int b = chunk & 1;
                     const uint32_t use = chunk >> 1;
                     if (use > 0 && !wait_or_abort(smem_addr(&sh->acc_empty[b]), (use - 1) & 1,
-                                                  sh, status)) {
+                                                  sh, status, limit)) {
                         ok = false;
                         break;
                     }
@@ -436,7 +444,7 @@ cascade_int8_tc_kernel(const Src src) {
                     for (int ks = ks0; ks < ks1; ++ks, ++it) {
                         const int stage = it % NST;
                         if (!wait_or_abort(smem_addr(&sh->full[stage]), (it / NST) & 1, sh,
-                                           status)) {
+                                           status, limit)) {
                             ok = false;
                             break;
                         }
@@ -467,7 +475,7 @@ cascade_int8_tc_kernel(const Src src) {
             }
             // every product of this CTA is done before tensor memory is freed
             umma::commit(smem_addr(&sh->mma_done));
-            mbar_wait(smem_addr(&sh->mma_done), 0);
+            mbar_wait_limit(smem_addr(&sh->mma_done), 0, limit);
         }
         __syncwarp();
     } else {
@@ -503,7 +511,7 @@ cascade_int8_tc_kernel(const Src src) {
                 // every lane waits; the warp goes on only together (the
                 // tensor-memory loads below are warp-wide)
                 const bool lane_ok = wait_or_abort(smem_addr(&sh->acc_full[b]), (chunk >> 1) & 1,
-                                                   sh, status, 200);
+                                                   sh, status, limit, 200);
                 if (!__all_sync(0xffffffffu, lane_ok)) {
                     ok = false;
                     break;

@@ -15,6 +15,19 @@ constexpr int KC = 256;
 // dot products"): c0 = 22, c1 = 21, c2 = 21.
 constexpr int C0 = 22, C1 = 21, C2 = 21;
 
+// The kernels' bounded waits.  Every mbarrier wait gives up after limit_ns
+// of global time, sets DDGEMM_DEV_TIMEOUT and ends the CTA's work.  For the
+// failure-handling tests, a plan may also name one copy that is never issued
+// (the producer of CTA `cta` skips its k-step or stage `step`): the barrier
+// it would complete then never does, and the wait runs out without any fault.
+// Only the diagnostic entry points (include/ddgemm_diag.h) set cta >= 0.
+constexpr unsigned long long WAIT_LIMIT_DEFAULT_NS = 2000000000ull;  // ~2 s
+struct WaitPlan {
+    unsigned long long limit_ns = WAIT_LIMIT_DEFAULT_NS;
+    int cta = -1;         // CTA whose copy is withheld (-1: none)
+    long long step = -1;  // the producer's k-step (or ring iteration) withheld
+};
+
 // Output orientation of the cascaded panels.
 //   VEC_MAJOR: out[(s * nvec + v) * ld + l]   (A: slices x m x k)
 //   K_MAJOR:   out[(s * kdim + l) * ld + v]   (B: slices x k x n)
@@ -46,6 +59,7 @@ struct CascadeArgs {
     int products;            // 0: eq. Gemm10 (the method); 1: Gemm16; 2: bins 4-6 dropped
     int split;               // k-block groups per tile (1: no split)
     double *part_hi, *part_lo;  // split > 1: partial C of groups 1..split-1, [split-1][m][n]
+    WaitPlan wait{};
 };
 
 // Split-k over whole k-blocks: the number of groups for a grid of `tiles`
@@ -110,6 +124,7 @@ struct Int8Args {
     double *c_hi, *c_lo;
     long long ldc;
     unsigned int *status;
+    WaitPlan wait{};
 };
 
 cudaError_t launch_cascade_int8(const Int8Args &a, cudaStream_t stream);
@@ -132,6 +147,7 @@ struct Int8TcArgs {
     double *c_hi, *c_lo;
     long long ldc;
     unsigned int *status;
+    WaitPlan wait{};
 };
 
 cudaError_t launch_cascade_int8_tc(const Int8TcArgs &a, cudaStream_t stream);
@@ -146,7 +162,8 @@ size_t batched_int8_tc_workspace_size(int count, const ddgemm_problem *probs_hos
                                       int bits);
 int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
                         const ddgemm_problem *probs_dev, void *workspace, size_t ws_bytes,
-                        cudaStream_t s, int slices, int bits, unsigned int *status);
+                        cudaStream_t s, int slices, int bits, unsigned int *status,
+                        const WaitPlan &wait = WaitPlan{});
 
 // The exact assembly alone: (hi[i], lo[i]) = the FP64x2 nearest to
 // sum_t diag[t * count + i] 2^(-12-7t) 2^scale[i].

@@ -4,7 +4,7 @@
 // independent accumulator chains.
 #include <cuda_runtime.h>
 
-#include "../../include/ddgemm.h"
+#include "../../include/ddgemm_diag.h"
 #include "tma.cuh"
 
 namespace {

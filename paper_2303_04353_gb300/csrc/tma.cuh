@@ -10,10 +10,11 @@
 #include <cstdint>
 #include <mutex>
 
+#include "ddgemm_internal.h"
+
 namespace ddg {
 
 constexpr unsigned DEV_TIMEOUT_BIT = 0x2u;              // DDGEMM_DEV_TIMEOUT
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;       // a wait gives up after ~2 s
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -66,9 +67,9 @@ __device__ __forceinline__ bool mbar_wait_limit(uint32_t bar, uint32_t parity, u
     return true;
 }
 
-// The kernels' wait: gives up after WAIT_LIMIT_NS.
+// The kernels' default wait: gives up after WAIT_LIMIT_DEFAULT_NS.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    return mbar_wait_limit(bar, parity, WAIT_LIMIT_NS);
+    return mbar_wait_limit(bar, parity, WAIT_LIMIT_DEFAULT_NS);
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,

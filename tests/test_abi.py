@@ -1,7 +1,8 @@
 """The C ABI without a GPU: the library builds and loads, exports every
-function include/ddgemm.h declares, and its host-side checks answer before
-any CUDA call."""
+function include/*.h declares, and its host-side checks answer before any
+CUDA call."""
 import ctypes
+import glob
 import os
 import re
 
@@ -9,21 +10,31 @@ import pytest
 
 from paper_2303_04353_gb300 import _lib
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "ddgemm.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
+HEADER = os.path.join(INCLUDE, "ddgemm.h")
+DIAG_HEADER = os.path.join(INCLUDE, "ddgemm_diag.h")
 FAKE = 0x10000  # never dereferenced: every call below returns before a CUDA call
 
 
-def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(ddgemm\w*)\s*\(", text)))
+def declared_functions(path=None):
+    paths = [path] if path else sorted(glob.glob(os.path.join(INCLUDE, "*.h")))
+    names = set()
+    for p in paths:
+        text = re.sub(r"/\*.*?\*/", "", open(p).read(), flags=re.S)
+        names |= set(re.findall(r"\b(ddgemm\w*)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
-    names = declared_functions()
+    names = declared_functions(HEADER)
     for want in ("ddgemm", "ddgemm_workspace_size", "ddgemm_split_a", "ddgemm_split_b",
-                 "ddgemm_bins", "ddgemm_status_string"):
+                 "ddgemm_bins", "ddgemm_status_string", "ddgemm_batched", "ddgemm_backward"):
         assert want in names
+    # the measurement and failure-handling aids live in their own header
+    diag = declared_functions(DIAG_HEADER)
+    assert set(diag) == {"ddgemm_probe_fp64", "ddgemm_probe_int8", "ddgemm_probe_wait_timeout",
+                         "ddgemm_diag_withheld_copy", "ddgemm_diag_batched_withheld_copy"}
+    assert not set(diag) & set(names)
 
 
 def test_library_exports_every_declared_symbol():
@@ -287,4 +298,41 @@ def test_tc8_workspace_and_pieces():
     assert lib.ddgemm_batched(1, arr, FAKE, FAKE, 1 << 30, None, ctypes.byref(bad), None) == \
         _lib.DDGEMM_EINVAL
     assert lib.ddgemm_batched(1, arr, FAKE, FAKE, 16, None, ctypes.byref(o), None) == \
+        _lib.DDGEMM_EWORKSPACE
+
+
+def test_diag_withheld_copy_host_checks():
+    """The failure-handling entry points check their arguments on the host
+    (nothing is enqueued on an error): a status word is required, the wait
+    limit lies in 10^3 .. 10^10 ns, the CTA and step are >= 0, and an empty
+    problem has no kernel to withhold a copy from."""
+    lib = _lib.load()
+    with_status = _lib.make_opts(status_dev=FAKE)
+
+    def call(m=4, n=4, k=4, opts=with_status, cta=0, step=0, limit=20_000_000):
+        return lib.ddgemm_diag_withheld_copy(m, n, k, FAKE, FAKE, k, FAKE, FAKE, n, FAKE, FAKE, n,
+                                             FAKE, 1 << 30, None,
+                                             ctypes.byref(opts) if opts else None, cta, step,
+                                             limit)
+    assert call(opts=None) == _lib.DDGEMM_EINVAL
+    assert call(opts=_lib.make_opts()) == _lib.DDGEMM_EINVAL      # no status word
+    assert call(limit=10) == _lib.DDGEMM_EINVAL
+    assert call(limit=10 ** 11) == _lib.DDGEMM_EINVAL
+    assert call(cta=-1) == _lib.DDGEMM_EINVAL
+    assert call(step=-1) == _lib.DDGEMM_EINVAL
+    assert call(m=0) == _lib.DDGEMM_EINVAL
+    assert call(opts=_lib.make_opts(status_dev=FAKE, flags_dev=FAKE)) == _lib.DDGEMM_EUNSUPPORTED
+    arr = (_lib.ddgemm_problem * 1)()
+    arr[0] = _lib.ddgemm_problem(4, 5, 6, 6, 5, 5, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+    fp64 = _lib.make_opts(status_dev=FAKE)
+    tc = _lib.make_opts(variant=_lib.DDGEMM_VARIANT_INT8_TC, status_dev=FAKE)
+    batched = lib.ddgemm_diag_batched_withheld_copy
+    # the FP64 batched kernel has no barrier wait to run out
+    assert batched(1, arr, FAKE, FAKE, 1 << 30, None, ctypes.byref(fp64), 0, 0,
+                   20_000_000) == _lib.DDGEMM_EUNSUPPORTED
+    assert batched(1, arr, FAKE, FAKE, 1 << 30, None, None, 0, 0, 20_000_000) == \
+        _lib.DDGEMM_EINVAL
+    assert batched(1, arr, FAKE, FAKE, 1 << 30, None, ctypes.byref(tc), 0, 0, 10) == \
+        _lib.DDGEMM_EINVAL
+    assert batched(1, arr, FAKE, FAKE, 16, None, ctypes.byref(tc), 0, 0, 20_000_000) == \
         _lib.DDGEMM_EWORKSPACE

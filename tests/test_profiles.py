@@ -2,7 +2,7 @@
 those commands must still run on the committed files: every `bench.py`
 invocation parses with bench.py's own argument parser, every `ncu` command
 leaves the GPU clocks alone (`--clock-control none`) and writes its output
-under gpurun_out/."""
+under the scratch output folder OUT_DIR."""
 import glob
 import os
 import re
@@ -10,6 +10,7 @@ import shlex
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+OUT_DIR = "gpurun_out/"
 
 
 def commands(text):
@@ -49,7 +50,7 @@ def test_profile_commands_run_committed_files():
                     argv[argv.index("--clock-control") + 1] == "none", cmd
                 for flag in ("-o", "--log-file"):
                     if flag in argv:
-                        assert argv[argv.index(flag) + 1].startswith("gpurun_out/"), cmd
+                        assert argv[argv.index(flag) + 1].startswith(OUT_DIR), cmd
             if "bench.py" in argv:
                 rest = argv[argv.index("bench.py") + 1:]
                 parser.parse_args(rest)  # exits on an unknown flag or value
