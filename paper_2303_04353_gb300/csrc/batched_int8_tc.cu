@@ -29,14 +29,22 @@ constexpr size_t TC_ALIGN = 256;
 
 __host__ __device__ inline size_t ru_tc(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// One problem as the kernels see it.
+// One problem as the kernels see it.  trans: the tile grid covers C^T =
+// B^T A^T (B's columns are the 128-row side, A's rows the 16-column side),
+// chosen when that needs fewer tiles; every diagonal sum, so every bit of C,
+// is the same either way (each is a sum over the same digit products).
 struct TcEntry {
-    int m, n, k, kb8, lda, ldb;
+    int m, n, k, kb8, lda, ldb, trans;
     long long ldc;
     const double *a_hi, *a_lo, *b_hi, *b_lo;
     double *c_hi, *c_lo;
     uint16_t *a_tiles, *b_tiles;
     int *e_a, *e_b;
+    // the same seen from the tile grid (swapped when trans): its rows and
+    // columns, the digits and exponents of its row side and column side
+    int g_m, g_n;
+    const uint16_t *g_a_tiles, *g_b_tiles;
+    const int *g_e_a, *g_e_b;
     int tiles_n;
     long long tiles;
     long long ea_units, eb_units, da_units, db_units;
@@ -68,12 +76,29 @@ __host__ __device__ inline TcPlanLayout tc_plan_layout(int count) {
     return L;
 }
 
-// Digit and exponent bytes of one problem (the single-problem layout).
+// Tiles of 128 x 16 over C (m x n), or over C^T (n x m) when transposed.
+__host__ __device__ inline long long tc_tiles(int m, int n, bool trans) {
+    const int rows = trans ? n : m, cols = trans ? m : n;
+    return (long long)((rows + INT8_TC_BM - 1) / INT8_TC_BM) * ((cols + INT8_TC_BN - 1) / INT8_TC_BN);
+}
+
+// The orientation with fewer tiles (ties: as given).
+__host__ __device__ inline bool tc_trans(int m, int n) {
+    return tc_tiles(m, n, true) < tc_tiles(m, n, false);
+}
+
+// Tile heights of A's rows and B's columns in the digit order.
+__host__ __device__ inline int tc_th_a(bool trans) { return trans ? INT8_TC_BN : INT8_TC_BM; }
+__host__ __device__ inline int tc_th_b(bool trans) { return trans ? INT8_TC_BM : INT8_TC_BN; }
+
+// Digit and exponent bytes of one problem (the single-problem layout, with
+// the tile heights of its orientation).
 __host__ __device__ inline size_t tc_problem_bytes(int m, int n, int k, int slices, int kblk) {
     if (m <= 0 || n <= 0 || k <= 0) return 0;
+    const bool tr = tc_trans(m, n);
     const size_t kpad = ru_tc((size_t)k, 16), kb8 = (size_t)(k + kblk - 1) / kblk;
-    return ru_tc((size_t)slices * ru_tc((size_t)m, INT8_TC_BM) * kpad * 2, TC_ALIGN) +
-           ru_tc((size_t)slices * ru_tc((size_t)n, INT8_TC_BN) * kpad * 2, TC_ALIGN) +
+    return ru_tc((size_t)slices * ru_tc((size_t)m, tc_th_a(tr)) * kpad * 2, TC_ALIGN) +
+           ru_tc((size_t)slices * ru_tc((size_t)n, tc_th_b(tr)) * kpad * 2, TC_ALIGN) +
            ru_tc(kb8 * m * 4, TC_ALIGN) + ru_tc(kb8 * n * 4, TC_ALIGN);
 }
 
@@ -152,8 +177,9 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
         e.a_hi = q.A_hi; e.a_lo = q.A_lo; e.b_hi = q.B_hi; e.b_lo = q.B_lo;
         e.c_hi = q.C_hi; e.c_lo = q.C_lo;
         const bool mn = q.m > 0 && q.n > 0, work = mn && q.k > 0;
-        e.tiles_n = mn ? (q.n + INT8_TC_BN - 1) / INT8_TC_BN : 0;
-        e.tiles = mn ? (long long)((q.m + INT8_TC_BM - 1) / INT8_TC_BM) * e.tiles_n : 0;
+        e.trans = mn && tc_trans(q.m, q.n);
+        e.tiles_n = mn ? ((e.trans ? q.m : q.n) + INT8_TC_BN - 1) / INT8_TC_BN : 0;
+        e.tiles = mn ? tc_tiles(q.m, q.n, e.trans) : 0;
         const long long ktiles = work ? (q.k + split8::TK - 1) / split8::TK : 0;
         e.ea_units = work ? (long long)q.m * e.kb8 : 0;
         e.eb_units = work ? (long long)((q.n + 63) / 64) * e.kb8 : 0;
@@ -185,10 +211,7 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
     const int i0 = min(count, t * seg), i1 = min(count, i0 + seg);
     auto bytes_of = [&](const TcEntry &e) -> size_t {
         if (e.ea_units <= 0) return 0;
-        const size_t kpad = ru_tc((size_t)e.k, 16);
-        return ru_tc((size_t)slices * ru_tc((size_t)e.m, INT8_TC_BM) * kpad * 2, TC_ALIGN) +
-               ru_tc((size_t)slices * ru_tc((size_t)e.n, INT8_TC_BN) * kpad * 2, TC_ALIGN) +
-               ru_tc((size_t)e.kb8 * e.m * 4, TC_ALIGN) + ru_tc((size_t)e.kb8 * e.n * 4, TC_ALIGN);
+        return tc_problem_bytes(e.m, e.n, e.k, slices, kblk);
     };
     {
         long long acc[NQ] = {0, 0, 0, 0, 0, 0};
@@ -247,14 +270,22 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
             if (e.ea_units > 0) {
                 const size_t kpad = ru_tc((size_t)e.k, 16);
                 e.a_tiles = reinterpret_cast<uint16_t *>(ws + off);
-                off += ru_tc((size_t)slices * ru_tc((size_t)e.m, INT8_TC_BM) * kpad * 2, TC_ALIGN);
+                off += ru_tc((size_t)slices * ru_tc((size_t)e.m, tc_th_a(e.trans)) * kpad * 2,
+                             TC_ALIGN);
                 e.b_tiles = reinterpret_cast<uint16_t *>(ws + off);
-                off += ru_tc((size_t)slices * ru_tc((size_t)e.n, INT8_TC_BN) * kpad * 2, TC_ALIGN);
+                off += ru_tc((size_t)slices * ru_tc((size_t)e.n, tc_th_b(e.trans)) * kpad * 2,
+                             TC_ALIGN);
                 e.e_a = reinterpret_cast<int *>(ws + off);
                 off += ru_tc((size_t)e.kb8 * e.m * 4, TC_ALIGN);
                 e.e_b = reinterpret_cast<int *>(ws + off);
                 off += ru_tc((size_t)e.kb8 * e.n * 4, TC_ALIGN);
             }
+            e.g_m = e.trans ? e.n : e.m;
+            e.g_n = e.trans ? e.m : e.n;
+            e.g_a_tiles = e.trans ? e.b_tiles : e.a_tiles;
+            e.g_b_tiles = e.trans ? e.a_tiles : e.b_tiles;
+            e.g_e_a = e.trans ? e.e_b : e.e_a;
+            e.g_e_b = e.trans ? e.e_a : e.e_b;
             tile_pre[i] = tt;
             tt += ent[order[i]].tiles;
         }
@@ -346,8 +377,8 @@ __global__ void __launch_bounds__(256, 4) tc_digits_kernel(const char *ws) {
             const int ktiles = (e.k + split8::TK - 1) / split8::TK;
             split8::digits_unit<S, true, true, BITS>((int)(local / ktiles) * split8::TV,
                                                (int)(local % ktiles) * split8::TK, e.m, e.k,
-                                               e.a_hi, e.a_lo, e.lda, e.a_tiles, 0, INT8_TC_BM,
-                                               e.e_a, status, sh, sl);
+                                               e.a_hi, e.a_lo, e.lda, e.a_tiles, 0,
+                                               tc_th_a(e.trans), e.e_a, status, sh, sl);
         } else {
             const long long ub = u - total_a;
             const int i = ib = advance_tc(V.db_pre, count, ub, ib);
@@ -356,8 +387,8 @@ __global__ void __launch_bounds__(256, 4) tc_digits_kernel(const char *ws) {
             const int ktiles = (e.k + split8::TK - 1) / split8::TK;
             split8::digits_unit<S, false, true, BITS>((int)(local / ktiles) * split8::TV,
                                                 (int)(local % ktiles) * split8::TK, e.n, e.k,
-                                                e.b_hi, e.b_lo, e.ldb, e.b_tiles, 0, INT8_TC_BN,
-                                                e.e_b, status, sh, sl);
+                                                e.b_hi, e.b_lo, e.ldb, e.b_tiles, 0,
+                                                tc_th_b(e.trans), e.e_b, status, sh, sl);
         }
     }
 }
@@ -381,22 +412,24 @@ struct BatchSource {
         const int r = hint = advance_tc(V.tile_pre, V.hdr->count, item, hint);
         const TcEntry &e = V.ent[V.order[r]];
         const long long local = item - V.tile_pre[r];
-        int tm, tn;
-        grouped_tile((unsigned)local, (e.m + BM - 1) / BM, e.tiles_n, TILE_GROUP, tm, tn);
         TcJob j;
-        j.m = e.m;
-        j.n = e.n;
+        // transposed: the grid's rows are B's columns, its columns A's rows
+        j.m = e.g_m;
+        j.n = e.g_n;
         j.k = e.k;
+        int tm, tn;
+        grouped_tile((unsigned)local, (j.m + BM - 1) / BM, e.tiles_n, TILE_GROUP, tm, tn);
         j.tm = tm;
         j.tn_load = tn;
         j.col0 = tn * BN;
-        j.a_tiles = e.a_tiles;
-        j.b_tiles = e.b_tiles;
-        j.exp_a = e.e_a;
-        j.exp_b = e.e_b;
+        j.a_tiles = e.g_a_tiles;
+        j.b_tiles = e.g_b_tiles;
+        j.exp_a = e.g_e_a;
+        j.exp_b = e.g_e_b;
         j.c_hi = e.c_hi;
         j.c_lo = e.c_lo;
         j.ldc = e.ldc;
+        j.trans = e.trans != 0;
         return j;
     }
 };
@@ -460,8 +493,7 @@ int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
         const ddgemm_problem &q = probs_host[i];
         if (!tc_problem_ok(q)) return DDGEMM_EINVAL;
         if (q.m > 0 && q.n > 0) {
-            tiles += (long long)((q.m + INT8_TC_BM - 1) / INT8_TC_BM) *
-                     ((q.n + INT8_TC_BN - 1) / INT8_TC_BN);
+            tiles += tc_tiles(q.m, q.n, tc_trans(q.m, q.n));
             if (q.k > 0) {
                 const long long kb8 = (q.k + kblk - 1) / kblk,
                                 kt = (q.k + split8::TK - 1) / split8::TK;

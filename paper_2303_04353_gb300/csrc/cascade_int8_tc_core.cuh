@@ -296,9 +296,13 @@ __device__ __forceinline__ void block_value(const long long (&acc)[Groups<S, TB>
     }
 }
 
-// One output tile of one problem, as a CTA sees it.
+// One output tile of one problem, as a CTA sees it.  The tile's rows (the
+// MMA's M side) are vectors of a_tiles and its columns (N side) vectors of
+// b_tiles; output (row, col) is stored at row * ldc + col, or, for a product
+// computed transposed (trans: C^T = B^T A^T), at col * ldc + row, straight
+// into C.
 struct TcJob {
-    int m, n, k;
+    int m, n, k;   // rows and columns of the tile grid's product, and k
     int tm;        // row tile
     int tn_load;   // column tile whose B digits are loaded
     int col0;      // first column this CTA stores (>= n: nothing is stored)
@@ -306,6 +310,10 @@ struct TcJob {
     const int *exp_a, *exp_b;
     double *c_hi, *c_lo;
     long long ldc;
+    bool trans;
+    __device__ long long out_index(int row, int col) const {
+        return trans ? (long long)col * ldc + row : (long long)row * ldc + col;
+    }
 };
 
 // The tiles of one problem (Int8TcArgs), in groups of TILE_GROUP row tiles.
@@ -332,6 +340,7 @@ struct SingleSource {
         j.c_hi = a.c_hi;
         j.c_lo = a.c_lo;
         j.ldc = a.ldc;
+        j.trans = false;
         return j;
     }
 };
@@ -496,8 +505,9 @@ cascade_int8_tc_kernel(const Src src) {
             if (nchunks == 0 && row < j.m) {  // k = 0: C = 0 on this tile
                 for (int x = 0; x < DCOLS; ++x)
                     if (col0 + x < j.n) {
-                        j.c_hi[(long long)row * j.ldc + col0 + x] = 0.0;
-                        j.c_lo[(long long)row * j.ldc + col0 + x] = 0.0;
+                        const long long o = j.out_index(row, col0 + x);
+                        j.c_hi[o] = 0.0;
+                        j.c_lo[o] = 0.0;
                     }
             }
             // per group of diagonals and column, the k-block's exact sums
@@ -529,6 +539,9 @@ cascade_int8_tc_kernel(const Src src) {
                     const int p = c / BLOCK_CHUNKS;
                     if (row < j.m) {
                         const int ea = j.exp_a[(long long)p * j.m + row];
+                        // this thread's DCOLS outputs: o_base + x o_step
+                        const long long o_base = j.out_index(row, col0);
+                        const long long o_step = j.trans ? j.ldc : 1;
 #pragma unroll
                         for (int x = 0; x < DCOLS; ++x) {
                             const int col = col0 + x;
@@ -539,7 +552,7 @@ cascade_int8_tc_kernel(const Src src) {
                                 block_value<S, TB>(acc, x, H, L);
                                 double h, l;
                                 round_dd<W::SPLIT>(H, L, e, h, l);
-                                const long long o = (long long)row * j.ldc + col;
+                                const long long o = o_base + x * o_step;
                                 if (p > 0) {
                                     double ch = j.c_hi[o], cl = j.c_lo[o];
                                     dd_add(ch, cl, h, l, ch, cl);
