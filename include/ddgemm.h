@@ -225,10 +225,23 @@ typedef struct ddgemm_problem {
 #define DDGEMM_TILE_32x32 3
 #define DDGEMM_ORDER_GIVEN           0 /* tiles in problem order */
 #define DDGEMM_ORDER_LONGEST_K_FIRST 1 /* problems by k, then m n, descending */
+/* tcgen05 forms: the tile grid of a problem */
+#define DDGEMM_ORIENT_FEWER_TILES 0 /* C or C^T = B^T A^T, whichever needs fewer tiles */
+#define DDGEMM_ORIENT_GIVEN       1 /* always C */
+/* tcgen05 forms: the order of a k-step's MMAs over the A digit planes */
+#define DDGEMM_PLANES_INTERLEAVED 0 /* 0, S-1, 1, S-2, ...: a narrow MMA after a wide one */
+#define DDGEMM_PLANES_ASCENDING   1 /* 0, 1, ..., S-1 */
 
 typedef struct ddgemm_batch_config {
-    int tile;   /* DDGEMM_TILE_*: C tile of the persistent kernel's CTAs */
-    int order;  /* DDGEMM_ORDER_*: order in which CTAs pull the tiles */
+    int tile;      /* FP64 form: DDGEMM_TILE_*, the C tile of the persistent
+                      kernel's CTAs (the tcgen05 forms' tile is 128 x 16) */
+    int order;     /* both forms: DDGEMM_ORDER_*, the order in which the
+                      persistent CTAs take the problems' tiles */
+    int orient;    /* tcgen05 forms: DDGEMM_ORIENT_* */
+    int planes;    /* tcgen05 forms: DDGEMM_PLANES_* */
+    int row_group; /* tcgen05 forms: row tiles per group of a problem's tile
+                      order (the CTAs walk a group's columns, then the next
+                      group), 1 .. 8; 0 = 4 */
 } ddgemm_batch_config;
 
 /* Workspace bytes for ddgemm_batched() over these problems (host array)
@@ -237,7 +250,9 @@ typedef struct ddgemm_batch_config {
 size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem *probs_host,
                                      const ddgemm_opts *opts);
 
-/* C_i := A_i B_i for count problems.  FP64 form: four launches on `stream`:
+/* C_i := A_i B_i for count problems.  The schedule (config) changes the
+ * time, never a bit of any C_i: every configuration computes each problem
+ * bit-identically.  FP64 form: four launches on `stream`:
  *   1. a one-CTA plan kernel that reads probs_dev and writes the problems'
  *      workspace offsets, the tile schedule and a work counter into the
  *      workspace;
@@ -254,14 +269,16 @@ size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem *probs_host
  *               no flags_dev (else DDGEMM_EUNSUPPORTED); status_dev is
  *               honoured; int8_slices for INT8_TC (12-16; 0 = 16) and
  *               INT8_TC8 (12-15; 0 = 15).
- *   config      NULL = {DDGEMM_TILE_64x64, DDGEMM_ORDER_LONGEST_K_FIRST}.
- *               Not used by INT8_TC.
+ *   config      NULL = {DDGEMM_TILE_64x64, DDGEMM_ORDER_LONGEST_K_FIRST,
+ *               DDGEMM_ORIENT_FEWER_TILES, DDGEMM_PLANES_INTERLEAVED, 4}.
+ *               Out-of-range fields: DDGEMM_EINVAL.
  * INT8_TC and INT8_TC8 (the INT8 form on the tcgen05 tensor cores, see
  * DDGEMM_VARIANT_INT8_TC): five launches, a plan, the exponents of every A
  * and of every B, the digits of all of them, and one persistent tcgen05
- * kernel over the (problem, 128 x 16 tile) items, longest k first; each
- * C_i is bit-identical to ddgemm() with that variant.  The workspace size
- * depends on opts (pass the same opts to both calls).
+ * kernel over the (problem, 128 x 16 tile) items (tile grids over C or C^T
+ * and the tile order as config says); each C_i is bit-identical to ddgemm()
+ * with that variant.  The workspace size depends on opts (pass the same opts
+ * to both calls), not on config.
  * Problems with m or n = 0 are skipped; k = 0 writes C = 0.  The ordering
  * by k costs count^2 / 256 comparisons in the plan kernel. */
 int ddgemm_batched(int count, const ddgemm_problem *probs_host,

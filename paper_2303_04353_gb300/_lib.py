@@ -50,11 +50,14 @@ class ddgemm_problem(ctypes.Structure):
 
 
 class ddgemm_batch_config(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int), ("order", ctypes.c_int)]
+    _fields_ = [("tile", ctypes.c_int), ("order", ctypes.c_int), ("orient", ctypes.c_int),
+                ("planes", ctypes.c_int), ("row_group", ctypes.c_int)]
 
 
 DDGEMM_TILE_64x64, DDGEMM_TILE_32x64, DDGEMM_TILE_64x32, DDGEMM_TILE_32x32 = 0, 1, 2, 3
 DDGEMM_ORDER_GIVEN, DDGEMM_ORDER_LONGEST_K_FIRST = 0, 1
+DDGEMM_ORIENT_FEWER_TILES, DDGEMM_ORIENT_GIVEN = 0, 1
+DDGEMM_PLANES_INTERLEAVED, DDGEMM_PLANES_ASCENDING = 0, 1
 
 _LIB = None
 

@@ -463,6 +463,7 @@ extern "C" int ddgemm_batched(int count, const ddgemm_problem *probs_host,
                               const ddgemm_batch_config *config) {
     using namespace ddg;
     if (count < 0 || (count > 0 && (!probs_host || !probs_dev))) return DDGEMM_EINVAL;
+    if (!batch_config_ok(config)) return DDGEMM_EINVAL;
     if (count == 0) return DDGEMM_OK;
     unsigned int *status = nullptr;
     if (opts) {
@@ -476,13 +477,14 @@ extern "C" int ddgemm_batched(int count, const ddgemm_problem *probs_host,
             if (!int8_tc_slices_supported(s)) return DDGEMM_EINVAL;
             return run_batched_int8_tc(count, probs_host, probs_dev, workspace, ws_bytes,
                                        static_cast<cudaStream_t>(stream), s, INT8_TC_BITS,
-                                       status);
+                                       status, config);
         }
         if (opts->variant == DDGEMM_VARIANT_INT8_TC8) {
             const int s = opts->int8_slices ? opts->int8_slices : INT8_TC8_SLICES_DEFAULT;
             if (!int8_tc8_slices_supported(s)) return DDGEMM_EINVAL;
             return run_batched_int8_tc(count, probs_host, probs_dev, workspace, ws_bytes,
-                                       static_cast<cudaStream_t>(stream), s, INT8_BITS, status);
+                                       static_cast<cudaStream_t>(stream), s, INT8_BITS, status,
+                                       config);
         }
     }
     const int tile = config ? config->tile : DDGEMM_TILE_64x64;
@@ -557,5 +559,6 @@ extern "C" int ddgemm_diag_batched_withheld_copy(int count, const ddgemm_problem
     wait.cta = cta;
     wait.step = step;
     return run_batched_int8_tc(count, probs_host, probs_dev, workspace, ws_bytes,
-                               static_cast<cudaStream_t>(stream), s, bits, opts->status_dev, wait);
+                               static_cast<cudaStream_t>(stream), s, bits, opts->status_dev,
+                               nullptr, wait);
 }

@@ -79,7 +79,8 @@ __host__ __device__ inline TcPlanLayout tc_plan_layout(int count) {
 // Tiles of 128 x 16 over C (m x n), or over C^T (n x m) when transposed.
 __host__ __device__ inline long long tc_tiles(int m, int n, bool trans) {
     const int rows = trans ? n : m, cols = trans ? m : n;
-    return (long long)((rows + INT8_TC_BM - 1) / INT8_TC_BM) * ((cols + INT8_TC_BN - 1) / INT8_TC_BN);
+    return (long long)((rows + INT8_TC_BM - 1) / INT8_TC_BM) *
+           ((cols + INT8_TC_BN - 1) / INT8_TC_BN);
 }
 
 // The orientation with fewer tiles (ties: as given).
@@ -92,10 +93,10 @@ __host__ __device__ inline int tc_th_a(bool trans) { return trans ? INT8_TC_BN :
 __host__ __device__ inline int tc_th_b(bool trans) { return trans ? INT8_TC_BM : INT8_TC_BN; }
 
 // Digit and exponent bytes of one problem (the single-problem layout, with
-// the tile heights of its orientation).
-__host__ __device__ inline size_t tc_problem_bytes(int m, int n, int k, int slices, int kblk) {
+// the tile heights of the orientation tr).
+__host__ __device__ inline size_t tc_problem_bytes(int m, int n, int k, int slices, int kblk,
+                                                   bool tr) {
     if (m <= 0 || n <= 0 || k <= 0) return 0;
-    const bool tr = tc_trans(m, n);
     const size_t kpad = ru_tc((size_t)k, 16), kb8 = (size_t)(k + kblk - 1) / kblk;
     return ru_tc((size_t)slices * ru_tc((size_t)m, tc_th_a(tr)) * kpad * 2, TC_ALIGN) +
            ru_tc((size_t)slices * ru_tc((size_t)n, tc_th_b(tr)) * kpad * 2, TC_ALIGN) +
@@ -144,9 +145,11 @@ __device__ inline bool before_tc(int ka, long long sa, int ia, int kb, long long
 // Problems whose ordering keys the plan kernel keeps in shared memory.
 constexpr int PLAN_SMEM_KEYS = 2048;
 
+// order: DDGEMM_ORDER_* (the rank of a problem in the tile list); orient:
+// DDGEMM_ORIENT_* (whether a problem's grid may cover C^T).
 __global__ void __launch_bounds__(256)
 tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, int slices,
-               int kblk, unsigned int *status) {
+               int kblk, unsigned int *status, int order_rule, int orient) {
     const TcPlanLayout L = tc_plan_layout(count);
     TcHeader *hdr = reinterpret_cast<TcHeader *>(ws);
     TcEntry *ent = reinterpret_cast<TcEntry *>(ws + L.entries);
@@ -177,7 +180,7 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
         e.a_hi = q.A_hi; e.a_lo = q.A_lo; e.b_hi = q.B_hi; e.b_lo = q.B_lo;
         e.c_hi = q.C_hi; e.c_lo = q.C_lo;
         const bool mn = q.m > 0 && q.n > 0, work = mn && q.k > 0;
-        e.trans = mn && tc_trans(q.m, q.n);
+        e.trans = mn && orient == DDGEMM_ORIENT_FEWER_TILES && tc_trans(q.m, q.n);
         e.tiles_n = mn ? ((e.trans ? q.m : q.n) + INT8_TC_BN - 1) / INT8_TC_BN : 0;
         e.tiles = mn ? tc_tiles(q.m, q.n, e.trans) : 0;
         const long long ktiles = work ? (q.k + split8::TK - 1) / split8::TK : 0;
@@ -187,15 +190,18 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
         e.db_units = work ? (long long)((q.n + split8::TV - 1) / split8::TV) * ktiles : 0;
         ent[i] = e;
         const long long qmn = (long long)q.m * q.n;
-        int r = 0;
-        if (keys_in_smem) {
-            for (int j = 0; j < count; ++j)
-                if (j != i && before_tc(key_k[j], key_mn[j], j, q.k, qmn, i)) ++r;
-        } else {
-            for (int j = 0; j < count; ++j)
-                if (j != i && before_tc(probs[j].k, (long long)probs[j].m * probs[j].n, j, q.k,
-                                        qmn, i))
-                    ++r;
+        int r = i;  // DDGEMM_ORDER_GIVEN
+        if (order_rule == DDGEMM_ORDER_LONGEST_K_FIRST) {
+            r = 0;
+            if (keys_in_smem) {
+                for (int j = 0; j < count; ++j)
+                    if (j != i && before_tc(key_k[j], key_mn[j], j, q.k, qmn, i)) ++r;
+            } else {
+                for (int j = 0; j < count; ++j)
+                    if (j != i && before_tc(probs[j].k, (long long)probs[j].m * probs[j].n, j,
+                                            q.k, qmn, i))
+                        ++r;
+            }
         }
         order[r] = i;
     }
@@ -211,7 +217,7 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
     const int i0 = min(count, t * seg), i1 = min(count, i0 + seg);
     auto bytes_of = [&](const TcEntry &e) -> size_t {
         if (e.ea_units <= 0) return 0;
-        return tc_problem_bytes(e.m, e.n, e.k, slices, kblk);
+        return tc_problem_bytes(e.m, e.n, e.k, slices, kblk, e.trans != 0);
     };
     {
         long long acc[NQ] = {0, 0, 0, 0, 0, 0};
@@ -393,10 +399,11 @@ __global__ void __launch_bounds__(256, 4) tc_digits_kernel(const char *ws) {
     }
 }
 
-// The planned (problem, tile) items, longest k first; within a problem the
-// tiles go in groups of TILE_GROUP row tiles.
+// The planned (problem, tile) items in the plan's problem order; within a
+// problem the tiles go in groups of row_group row tiles.
 struct BatchSource {
     const char *ws;
+    int row_group;  // row tiles per group of a problem's tile order
     WaitPlan plan;
     __device__ long long items() const {
         return reinterpret_cast<const TcHeader *>(ws)->total_tiles;
@@ -418,7 +425,7 @@ struct BatchSource {
         j.n = e.g_n;
         j.k = e.k;
         int tm, tn;
-        grouped_tile((unsigned)local, (j.m + BM - 1) / BM, e.tiles_n, TILE_GROUP, tm, tn);
+        grouped_tile((unsigned)local, (j.m + BM - 1) / BM, e.tiles_n, row_group, tm, tn);
         j.tm = tm;
         j.tn_load = tn;
         j.col0 = tn * BN;
@@ -434,9 +441,10 @@ struct BatchSource {
     }
 };
 
-template <int S, int BITS>
+template <int S, int BITS, int PLANES>
 cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, long long units_eb,
-                              long long units_d, int sms, cudaStream_t s, const WaitPlan &wait) {
+                              long long units_d, int sms, cudaStream_t s, int row_group,
+                              const WaitPlan &wait) {
     const long long cap = 8LL * sms;
     if (units_ea > 0) {
         const long long blocks = (units_ea + 7) / 8;
@@ -449,12 +457,12 @@ cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, lon
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || tiles == 0) return e;
     using G = TcGeom<S>;
-    auto kernel = cascade_int8_tc_kernel<S, BITS, BatchSource>;
+    auto kernel = cascade_int8_tc_kernel<S, BITS, BatchSource, PLANES>;
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)G::SMEM)) != cudaSuccess)
         return e;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    BatchSource src{ws, wait};
+    BatchSource src{ws, row_group, wait};
     kernel<<<grid, NTHREADS, G::SMEM, s>>>(src);
     return cudaGetLastError();
 }
@@ -476,24 +484,34 @@ size_t batched_int8_tc_workspace_size(int count, const ddgemm_problem *probs_hos
     if (count <= 0 || !probs_host) return 0;
     const int kblk = kblock_of_bits(bits);
     size_t total = tc_plan_layout(count).data;
-    for (int i = 0; i < count; ++i)
-        total += tc_problem_bytes(probs_host[i].m, probs_host[i].n, probs_host[i].k, slices, kblk);
+    // room for either orientation, so that one workspace serves every config
+    for (int i = 0; i < count; ++i) {
+        const ddgemm_problem &q = probs_host[i];
+        const size_t a = tc_problem_bytes(q.m, q.n, q.k, slices, kblk, false);
+        const size_t b = tc_problem_bytes(q.m, q.n, q.k, slices, kblk, true);
+        total += a > b ? a : b;
+    }
     return total;
 }
 
 int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
                         const ddgemm_problem *probs_dev, void *workspace, size_t ws_bytes,
                         cudaStream_t s, int slices, int bits, unsigned int *status,
-                        const WaitPlan &wait) {
+                        const ddgemm_batch_config *config, const WaitPlan &wait) {
     if (bits != INT8_TC_BITS && bits != INT8_BITS) return DDGEMM_EINVAL;
     if (bits == INT8_BITS && slices > 15) return DDGEMM_EINVAL;
     const int kblk = kblock_of_bits(bits);
+    const int order_rule = config ? config->order : DDGEMM_ORDER_LONGEST_K_FIRST;
+    const int orient = config ? config->orient : DDGEMM_ORIENT_FEWER_TILES;
+    const int planes = config ? config->planes : DDGEMM_PLANES_INTERLEAVED;
+    const int row_group = config && config->row_group ? config->row_group : TILE_GROUP;
     long long tiles = 0, ea = 0, eb = 0, d = 0;
     for (int i = 0; i < count; ++i) {
         const ddgemm_problem &q = probs_host[i];
         if (!tc_problem_ok(q)) return DDGEMM_EINVAL;
         if (q.m > 0 && q.n > 0) {
-            tiles += tc_tiles(q.m, q.n, tc_trans(q.m, q.n));
+            tiles += tc_tiles(q.m, q.n,
+                              orient == DDGEMM_ORIENT_FEWER_TILES && tc_trans(q.m, q.n));
             if (q.k > 0) {
                 const long long kb8 = (q.k + kblk - 1) / kblk,
                                 kt = (q.k + split8::TK - 1) / split8::TK;
@@ -512,10 +530,14 @@ int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return DDGEMM_ECUDA;
     char *ws = static_cast<char *>(workspace);
-    tc_plan_kernel<<<1, 256, 0, s>>>(count, probs_dev, ws, slices, kblk, status);
+    tc_plan_kernel<<<1, 256, 0, s>>>(count, probs_dev, ws, slices, kblk, status, order_rule,
+                                     orient);
     if (cudaGetLastError() != cudaSuccess) return DDGEMM_ECUDA;
     cudaError_t e;
-#define DDG_TC(S, B) launch_batched_tc<S, B>(ws, tiles, ea, eb, d, sms, s, wait)
+#define DDG_TC(S, B)                                                                     \
+    (planes == DDGEMM_PLANES_ASCENDING                                                   \
+         ? launch_batched_tc<S, B, 1>(ws, tiles, ea, eb, d, sms, s, row_group, wait)     \
+         : launch_batched_tc<S, B, 0>(ws, tiles, ea, eb, d, sms, s, row_group, wait))
     if (bits == INT8_BITS) {
         switch (slices) {
             case 12: e = DDG_TC(12, INT8_BITS); break;

@@ -345,7 +345,9 @@ struct SingleSource {
     }
 };
 
-template <int S, int TB, class Src>
+// PLANES: the order of a k-step's MMAs over the A planes,
+// DDGEMM_PLANES_INTERLEAVED (0) or DDGEMM_PLANES_ASCENDING (1).
+template <int S, int TB, class Src, int PLANES = DDGEMM_PLANES_INTERLEAVED>
 __global__ void __launch_bounds__(NTHREADS, 1)
 cascade_int8_tc_kernel(const Src src) {
     using G = TcGeom<S>;
@@ -466,11 +468,14 @@ cascade_int8_tc_kernel(const Src src) {
                         // much wider one, so the narrow ones are the triangle's
                         // waste; interleaved with the wide ones they cost less
                         // (measured: 5 % less kernel time at 4096^3).  Plane 0
-                        // comes first: its MMA covers every column of the set
-                        // and starts the chunk's sums (accumulate = 0).
+                        // comes first in either order: its MMA covers every
+                        // column of the set and starts the chunk's sums
+                        // (accumulate = 0).  The sums are exact integers, so
+                        // the order changes no bit.
 #pragma unroll
                         for (int q = 0; q < S; ++q) {
-                            const int i = (q & 1) ? S - 1 - (q >> 1) : (q >> 1);
+                            const int i = PLANES == DDGEMM_PLANES_ASCENDING ? q
+                                          : (q & 1) ? S - 1 - (q >> 1) : (q >> 1);
                             umma::mma_bf16(d_base + i * BN,
                                            umma::desc_k_sw32(a0 + i * G::A_PLANE), bdesc,
                                            umma::idesc_bf16_f32(BM, (S - i) * BN),

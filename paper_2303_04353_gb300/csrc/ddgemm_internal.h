@@ -160,10 +160,20 @@ cudaError_t launch_cascade_int8_tc8(const Int8TcArgs &a, cudaStream_t stream);
 // bits: 7 (DDGEMM_VARIANT_INT8_TC) or 8 (DDGEMM_VARIANT_INT8_TC8).
 size_t batched_int8_tc_workspace_size(int count, const ddgemm_problem *probs_host, int slices,
                                       int bits);
+// config: NULL (defaults) or checked by the caller.
 int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
                         const ddgemm_problem *probs_dev, void *workspace, size_t ws_bytes,
                         cudaStream_t s, int slices, int bits, unsigned int *status,
-                        const WaitPlan &wait = WaitPlan{});
+                        const ddgemm_batch_config *config, const WaitPlan &wait = WaitPlan{});
+
+// Whether a batch configuration's fields are in range (both forms).
+inline bool batch_config_ok(const ddgemm_batch_config *c) {
+    return !c || (c->tile >= DDGEMM_TILE_64x64 && c->tile <= DDGEMM_TILE_32x32 &&
+                  c->order >= DDGEMM_ORDER_GIVEN && c->order <= DDGEMM_ORDER_LONGEST_K_FIRST &&
+                  c->orient >= DDGEMM_ORIENT_FEWER_TILES && c->orient <= DDGEMM_ORIENT_GIVEN &&
+                  c->planes >= DDGEMM_PLANES_INTERLEAVED && c->planes <= DDGEMM_PLANES_ASCENDING &&
+                  c->row_group >= 0 && c->row_group <= 8);
+}
 
 // The exact assembly alone: (hi[i], lo[i]) = the FP64x2 nearest to
 // sum_t diag[t * count + i] 2^(-12-7t) 2^scale[i].

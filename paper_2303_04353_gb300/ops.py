@@ -366,7 +366,8 @@ class Batch:
 
     def run(self, stream=None, config=None, status=None):
         """Enqueue the batch.  config: None (library default), a
-        ddgemm_batch_config, or a (tile, order) pair."""
+        ddgemm_batch_config, or a tuple of its fields (tile, order[, orient,
+        planes, row_group]); missing fields are 0."""
         if config is not None and not isinstance(config, _lib.ddgemm_batch_config):
             config = _lib.ddgemm_batch_config(*config)
         opts = _lib.make_opts(variant=self.variant, int8_slices=self.int8_slices,

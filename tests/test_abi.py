@@ -336,3 +336,24 @@ def test_diag_withheld_copy_host_checks():
         _lib.DDGEMM_EINVAL
     assert batched(1, arr, FAKE, FAKE, 16, None, ctypes.byref(tc), 0, 0, 20_000_000) == \
         _lib.DDGEMM_EWORKSPACE
+
+
+def test_batch_config_range_checks():
+    """Out-of-range schedule fields are refused before any CUDA call, for
+    both forms."""
+    lib = _lib.load()
+    arr = (_lib.ddgemm_problem * 1)()
+    arr[0] = _lib.ddgemm_problem(4, 5, 6, 6, 5, 5, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+    tc = _lib.make_opts(variant=_lib.DDGEMM_VARIANT_INT8_TC)
+    for bad in [(0, 2, 0, 0, 0), (0, 0, 2, 0, 0), (0, 0, 0, 2, 0), (0, 0, 0, 0, 9),
+                (0, 0, 0, 0, -1), (4, 0, 0, 0, 0)]:
+        cfg = _lib.ddgemm_batch_config(*bad)
+        for opts in (None, ctypes.byref(tc)):
+            assert lib.ddgemm_batched(1, arr, FAKE, FAKE, 1 << 30, None, opts,
+                                      ctypes.byref(cfg)) == _lib.DDGEMM_EINVAL, bad
+    # the workspace of the tcgen05 forms covers either tile grid
+    need = _lib.ddgemm_batched_workspace_size(1, arr, tc)
+    ok = _lib.ddgemm_batch_config(0, 1, 1, 1, 8)
+    assert lib.ddgemm_batched(1, arr, FAKE, FAKE, need - 256, None, ctypes.byref(tc),
+                              ctypes.byref(ok)) == _lib.DDGEMM_EWORKSPACE
+

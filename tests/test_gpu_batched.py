@@ -279,3 +279,36 @@ def test_batched_fp64_many_small_problems(mods, count, order):
     for (gh, gl), (wh, wl), (m, n, k) in zip(got, want, shapes):
         if m and n:
             assert np.array_equal(gh, wh) and np.array_equal(gl, wl), (m, n, k)
+
+
+@pytest.mark.parametrize("variant", [TC, 5])
+def test_batched_tc_every_schedule_bit_identical(mods, variant):
+    """Every schedule the autotuner may pick for the tcgen05 forms (problem
+    order, tile grid over C or C^T, plane order, row group) gives each
+    problem bit for bit what ddgemm() gives it alone; wide and tall shapes
+    make the transposed grid win for some problems."""
+    _lib, ops, autotune = mods
+    shapes = MIXED + [(40, 900, 300), (700, 20, 129), (64, 64, 64), (127, 129, 200)]
+    batch, probs, _ = make_batch(ops, shapes, seed=90, variant=variant)
+    want = reference_tc(ops, probs, variant)
+    for cfg in autotune.candidates(variant):
+        for p in probs:
+            p[4].fill_(np.nan)
+            p[5].fill_(np.nan)
+        batch.run(config=cfg)
+        for (gh, gl), (wh, wl), (m, n, k) in zip(results(probs), want, shapes):
+            if m and n:
+                assert np.array_equal(gh, wh) and np.array_equal(gl, wl), (cfg, m, n, k)
+
+
+def test_autotuner_tc_picks_a_schedule(mods, tmp_path, monkeypatch):
+    _lib, ops, autotune = mods
+    monkeypatch.setenv("DDGEMM_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    batch, probs, _ = make_batch(ops, MIXED, seed=41, variant=TC)
+    cfg, timings = autotune.tune(batch, reps=1)
+    assert cfg in autotune.TC_CANDIDATES and len(timings) == len(autotune.TC_CANDIDATES)
+    cfg2, _ = autotune.tune(batch, reps=1)
+    assert cfg2 == cfg
+    # the FP64 batch of the same shapes is tuned (and cached) on its own
+    fp64, _, _ = make_batch(ops, MIXED, seed=41)
+    assert autotune.tune(fp64, reps=1)[0] in autotune.CANDIDATES
