@@ -462,6 +462,10 @@ cascade_int8_tc_kernel(const Src src) {
                         umma::fence_after();
                         const uint32_t a0 = smem_addr(smem + stage * G::STAGE);
                         const uint64_t bdesc = umma::desc_k_sw32(a0 + G::A_STAGE);
+                        // plane i's descriptor: the start-address field
+                        // (address / 16, bits 0-13) advanced by i A_PLANE / 16;
+                        // shared addresses stay below 2^18, so it never carries
+                        const uint64_t adesc0 = umma::desc_k_sw32(a0);
                         // planes in the order 0, S-1, 1, S-2, ...: a narrow MMA
                         // (plane i near S, N = 16 (S - i)) follows a wide one.
                         // A narrow M = 128, K = 16 MMA takes about as long as a
@@ -477,7 +481,7 @@ cascade_int8_tc_kernel(const Src src) {
                             const int i = PLANES == DDGEMM_PLANES_ASCENDING ? q
                                           : (q & 1) ? S - 1 - (q >> 1) : (q >> 1);
                             umma::mma_bf16(d_base + i * BN,
-                                           umma::desc_k_sw32(a0 + i * G::A_PLANE), bdesc,
+                                           adesc0 + (uint64_t)(i * (G::A_PLANE >> 4)), bdesc,
                                            umma::idesc_bf16_f32(BM, (S - i) * BN),
                                            (ks > ks0 || q > 0) ? 1u : 0u);
                         }
