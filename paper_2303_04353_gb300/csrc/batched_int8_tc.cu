@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(256) tc_exps_a_kernel(const char *ws) {
 
 // Exponents of every B: one CTA per (problem, 64 columns, k-block).
 __global__ void __launch_bounds__(256) tc_exps_b_kernel(const char *ws) {
-    __shared__ double part[4][64];
+    __shared__ unsigned long long part[4][64];
     const TcView V(ws);
     const int count = V.hdr->count;
     for (long long u = blockIdx.x; u < V.hdr->total_eb; u += gridDim.x) {

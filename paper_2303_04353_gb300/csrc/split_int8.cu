@@ -44,7 +44,7 @@ int8_exps_kernel(int nvec, int kdim, int blk, const double *__restrict__ x, long
         if (w >= (long long)nvec * kb) return;
         exps_contig_unit(lane, (int)(w / kb), (int)(w % kb), nvec, kdim, blk, x, ldx, exps);
     } else {
-        __shared__ double part[4][64];
+        __shared__ unsigned long long part[4][64];
         exps_strided_unit(blockIdx.x, blockIdx.y, nvec, kdim, blk, x, ldx, exps, part);
     }
 }

@@ -12,10 +12,25 @@ namespace split8 {
 
 constexpr unsigned DEV_NONFINITE = 0x1u;
 
-__device__ __forceinline__ int block_exponent(double mx) {
-    int e = 0;
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
-    return e;
+// The block maxima and exponents are formed on the integer pipes (the FP64
+// pipe is narrow on this GPU): the bit patterns of non-negative doubles
+// order as their values, so max |x| is the largest pattern with the sign
+// cleared (an Inf or NaN in the block wins, and gives e = 0).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// e with |x| = f 2^e, f in [1/2, 1) (frexp's exponent), from the pattern of
+// |x|; 0 for zero, Inf and NaN.
+__device__ __forceinline__ int block_exponent(unsigned long long b) {
+    const int be = (int)(b >> 52);
+    if (b == 0 || be == 0x7ff) return 0;
+    if (be > 0) return be - 1022;                      // normal
+    return (64 - __clzll((long long)b)) - 1074;         // subnormal
+}
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
 }
 
 // One warp: the exponent of block p (of kb entries) of vector v, whose
@@ -25,10 +40,11 @@ __device__ __forceinline__ void exps_contig_unit(int lane, int v, int p, int nve
                                                  long long ldx, int *__restrict__ exps) {
     const double *row = x + (long long)v * ldx;
     const int lend = min((p + 1) * kb, kdim);
-    double mx = 0.0;
-    for (int l = p * kb + lane; l < lend; l += 32) mx = fmax(mx, fabs(row[l]));
+    unsigned long long mx = 0;
+    for (int l = p * kb + lane; l < lend; l += 32) mx = umax64(mx, abs_bits(row[l]));
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    for (int off = 16; off > 0; off >>= 1)
+        mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     if (lane == 0) exps[(long long)p * nvec + v] = block_exponent(mx);
 }
 
@@ -37,17 +53,19 @@ __device__ __forceinline__ void exps_contig_unit(int lane, int v, int p, int nve
 // x[l*ldx + v]).
 __device__ __forceinline__ void exps_strided_unit(int vt, int p, int nvec, int kdim, int kb,
                                                   const double *__restrict__ x, long long ldx,
-                                                  int *__restrict__ exps, double (&part)[4][64]) {
+                                                  int *__restrict__ exps,
+                                                  unsigned long long (&part)[4][64]) {
     const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
     const int v = vt * 64 + tx;
     const int lend = min((p + 1) * kb, kdim);
-    double mx = 0.0;
+    unsigned long long mx = 0;
     if (v < nvec)
-        for (int l = p * kb + ty; l < lend; l += 4) mx = fmax(mx, fabs(x[(long long)l * ldx + v]));
+        for (int l = p * kb + ty; l < lend; l += 4)
+            mx = umax64(mx, abs_bits(x[(long long)l * ldx + v]));
     part[ty][tx] = mx;
     __syncthreads();
     if (ty == 0 && v < nvec) {
-        mx = fmax(fmax(part[0][tx], part[1][tx]), fmax(part[2][tx], part[3][tx]));
+        mx = umax64(umax64(part[0][tx], part[1][tx]), umax64(part[2][tx], part[3][tx]));
         exps[(long long)p * nvec + v] = block_exponent(mx);
     }
     __syncthreads();  // part is reused by the next unit
@@ -189,7 +207,7 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const double hi = sh[v][lg * 8 + j], lo = sl[v][lg * 8 + j];
-            bad |= !isfinite(hi) || !isfinite(lo);
+            bad |= ((abs_bits(hi) >> 52) == 0x7ff) | ((abs_bits(lo) >> 52) == 0x7ff);
             Y[j] = rne_scaled(hi, F - e) + rne_scaled(lo, F - e) + digit_offset<S, BITS>();
         }
         if (bad && status) atomicOr(status, DEV_NONFINITE);
@@ -221,7 +239,7 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const double hi = sh[v][lg * 8 + j], lo = sl[v][lg * 8 + j];
-            bad |= !isfinite(hi) || !isfinite(lo);
+            bad |= ((abs_bits(hi) >> 52) == 0x7ff) | ((abs_bits(lo) >> 52) == 0x7ff);
             // the digits as in the bf16 branch; the int8 digit d = f - 128 is
             // the byte f ^ 0x80
             const __int128 Y =

@@ -16,9 +16,8 @@ the method are tight.
   within a chunk of 256 entries (seven-bit pieces) or 64 (eight-bit) every
   partial sum of a diagonal stays at or below 2^24 and the largest reaches
   85 % (seven-bit) or 75 % (eight-bit) of it; summed in FP32 the chunk is
-  exact.  A chunk twice as
-  long (a planted mistake) passes 2^24 and FP32 then loses bits, so these
-  inputs tell the right chunk from a wrong one."""
+  exact.  A chunk twice as long (a planted mistake) passes 2^24 and FP32
+  then loses bits, so these inputs tell the right chunk from a wrong one."""
 import numpy as np
 import pytest
 

@@ -70,9 +70,10 @@ def int8_max_digits(m, n, k, bits, slices, seed=0, spread=20):
     (its lowest set bit at 2^max(0, F - 105)): digits below that are 0, and
     the digit across it takes the most negative value that keeps only the
     bits above it.  So -1 < x / 2^r < -1/2, and the normalised pair (hi, lo)
-    holds X exactly: hi 2^F and lo 2^F are integers that add up to X.  Returns (a_hi, a_lo, b_hi, b_lo, da, db, ra, rb): da [s][m][k]
-    and db [s][n][k] the digits of A's rows and B's columns, ra and rb the
-    scale exponents."""
+    holds X exactly: hi 2^F and lo 2^F are integers that add up to X.
+    Returns (a_hi, a_lo, b_hi, b_lo, da, db, ra, rb): da [s][m][k] and
+    db [s][n][k] the digits of A's rows and B's columns, ra and rb the scale
+    exponents."""
     rng = np.random.default_rng(seed)
     s = slices
     f = 6 + bits * (s - 1)
