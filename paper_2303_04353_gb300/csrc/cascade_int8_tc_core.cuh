@@ -568,15 +568,17 @@ cascade_int8_tc_kernel(const Src src) {
                                     j.c_hi[o] = ch;
                                     j.c_lo[o] = cl;
                                 } else {
-                                    // C = (0, 0) + (h, l): with h, l not -0 and
-                                    // |l| <= |h| (round_dd), the FP64x2 add reduces to
-                                    // the same FastTwoSum of h and l and the add of
-                                    // the zero low word (which turns a -0 into +0)
-                                    const double s1 = __dadd_rn(h, l);
-                                    const double e1 = __dadd_rn(
-                                        __dsub_rn(l, __dsub_rn(s1, h)), 0.0);
-                                    j.c_hi[o] = s1;
-                                    j.c_lo[o] = e1;
+                                    // C = (0, 0) + (h, l) is (h, l) itself, with no
+                                    // FP64 operation (the FP64 pipe is narrow here):
+                                    // the FP64x2 add reduces to FastTwoSum(h, l) and
+                                    // the add of a zero low word.  round_dd gives
+                                    // |l| <= ulp(h)/2, with |l| = ulp(h)/2 only when
+                                    // h = RN(T) was a tie and so even: h + l rounds
+                                    // to h, the FastTwoSum returns (h, l), and l is
+                                    // never -0 (round_dd returns +0 for a zero), so
+                                    // adding +0 leaves it.
+                                    j.c_hi[o] = h;
+                                    j.c_lo[o] = l;
                                 }
                             }
                         }

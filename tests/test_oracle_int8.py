@@ -294,3 +294,32 @@ def test_planted_rounding_is_caught(monkeypatch):
     monkeypatch.setattr(c8, "rne_scaled", lambda x, sh: math.floor(Fraction(x) * Fraction(2) ** sh))
     with pytest.raises(AssertionError):
         test_rne_scaled_is_round_half_even()
+
+
+def test_first_block_add_into_zero_is_the_pair_itself():
+    """The first k-block's FP64x2 add into C = (0, 0) (Sec. "Simple": the
+    blocks are accumulated into C in FP64x2) returns the exactly rounded
+    pair (RN(x), RN(x - RN(x))) unchanged, bit for bit, ties included: the
+    tcgen05 kernels store that pair without an FP64 operation."""
+    from oracle import cascade as cs
+    rng = random.Random(12)
+    cases = []
+    for _ in range(3000):
+        bits = rng.randrange(1, 140)
+        num = rng.getrandbits(bits) * rng.choice((-1, 1))
+        cases.append((num, rng.randrange(-200, 60)))
+    for _ in range(500):                  # ties at the first rounding (x = hi + ulp/2)
+        m = rng.getrandbits(53) | (1 << 52)
+        sh = rng.randrange(1, 80)
+        cases.append(((m << sh) + (1 << (sh - 1)), rng.randrange(-150, 0)))
+        cases.append((-((m << sh) + (1 << (sh - 1))), rng.randrange(-150, 0)))
+    for _ in range(500):                  # just below a power of two
+        p = rng.randrange(54, 130)
+        cases.append(((1 << p) - rng.randrange(1, 1 << 20), rng.randrange(-150, 0)))
+    his, los = zip(*(c8.round_dd(num, e) for num, e in cases))
+    h = np.array(his)
+    lo = np.array(los)
+    zh, zl = cs.dd_add(np.zeros_like(h), np.zeros_like(lo), h, lo)
+    assert np.array_equal(zh.view(np.int64), h.view(np.int64))
+    assert np.array_equal(zl.view(np.int64), lo.view(np.int64))
+    assert not np.any((lo == 0) & np.signbit(lo))      # no -0 low word
