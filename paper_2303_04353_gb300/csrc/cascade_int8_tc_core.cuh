@@ -296,6 +296,105 @@ __device__ __forceinline__ void block_value(const long long (&acc)[Groups<S, TB>
     }
 }
 
+// T = sum_q acc_q 2^(W_q) as a 192-bit two's complement th 2^128 + tl, with
+// W_q the weight of group q in T = H 2^SPLIT + L (block_value's terms).
+template <int S, int TB, int Q = 0>
+__device__ __forceinline__ void block_value_192(const long long (&acc)[Groups<S, TB>::COUNT][DCOLS],
+                                                int x, long long &th, unsigned __int128 &tl) {
+    if constexpr (Q < Groups<S, TB>::COUNT) {
+        using Gr = Groups<S, TB>;
+        constexpr int W = (Q < Gr::H_GROUPS ? TcWidth<TB>::SPLIT : 0) + Gr::shift(Q);
+        static_assert(W < 64 + 32, "a group's term fits 128 bits before its shift by 64");
+        unsigned __int128 low;
+        long long high;
+        if constexpr (W < 64) {
+            const __int128 v = (__int128)acc[Q][x] * ((__int128)1 << W);  // |v| < 2^120
+            low = (unsigned __int128)v;
+            high = v < 0 ? -1 : 0;
+        } else {
+            const __int128 v = (__int128)acc[Q][x] * ((__int128)1 << (W - 64));  // < 2^88
+            low = (unsigned __int128)v << 64;
+            high = (long long)(v >> 64);
+        }
+        const unsigned __int128 sum = tl + low;
+        th += high + (sum < tl ? 1 : 0);
+        tl = sum;
+        block_value_192<S, TB, Q + 1>(acc, x, th, tl);
+    }
+}
+
+// RN((u + f) 2^e) for 2^53 <= u < 2^75 and a fraction 0 <= f < 1 of which
+// only f != 0 (sticky) is known; or u < 2^53 and f = 0 (exact).
+__device__ __forceinline__ double round_mag75(unsigned __int128 u, bool sticky, int e) {
+    const int q = bitlen128(u);
+    if (q <= 53) return scaled((unsigned long long)u, e);
+    const int sh = q - 53;                       // 1 .. 22
+    unsigned long long m = (unsigned long long)(u >> sh);
+    const unsigned long long rem = (unsigned long long)u & ((1ull << sh) - 1ull);
+    const unsigned long long half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (sticky || (m & 1ull)))) ++m;
+    return scaled(m, sh + e);
+}
+
+// The k-block value of column x, T 2^e with T from the group sums, rounded
+// to the nearest FP64x2: hi = RN(T 2^e), lo = RN(T 2^e - hi), the same
+// values as round_dd on block_value's (H, L).  The magnitude is left-aligned
+// once into 128 bits (bits below the window, when |T| >= 2^128, only make a
+// sticky bit), so that hi's 53 bits, its rounding bit and the remainder are
+// fixed bit fields.  Only a remainder that is both inexact in the window and
+// below 2^53 of its units (about one value in 2^22 above 2^128) takes
+// round_dd.
+template <int S, int TB>
+__device__ __forceinline__ void round_block(const long long (&acc)[Groups<S, TB>::COUNT][DCOLS],
+                                            int x, int e, double &hi, double &lo) {
+    long long th = 0;
+    unsigned __int128 tl = 0;
+    block_value_192<S, TB>(acc, x, th, tl);
+    const bool neg = th < 0;
+    if (neg) {  // the magnitude, two's complement negation over 192 bits
+        tl = ~tl + 1;
+        th = ~th + (tl == 0 ? 1 : 0);
+    }
+    unsigned __int128 w;  // |T| 2^(128 - p), most significant bit at 127
+    int p;                // bit length of |T|
+    bool sticky = false;  // bits of |T| below the window
+    if (th != 0) {
+        const int sb = 64 - __clzll(th);         // 1 .. 63: |T| < 2^191
+        p = 128 + sb;
+        w = ((unsigned __int128)(unsigned long long)th << (128 - sb)) | (tl >> sb);
+        sticky = ((unsigned long long)tl & ((1ull << sb) - 1ull)) != 0;
+    } else {
+        if (tl == 0) {
+            hi = 0.0;
+            lo = 0.0;
+            return;
+        }
+        p = bitlen128(tl);
+        if (p <= 53) {
+            hi = with_sign(scaled((unsigned long long)tl, e), neg);
+            lo = 0.0;
+            return;
+        }
+        w = tl << (128 - p);
+    }
+    const unsigned long long mant = (unsigned long long)(w >> 75);
+    const unsigned __int128 low75 = w & (((unsigned __int128)1 << 75) - 1);
+    const bool rbit = (unsigned long long)(w >> 74) & 1ull;
+    const bool rest = sticky || (w & (((unsigned __int128)1 << 74) - 1)) != 0;
+    const bool up = rbit && (rest || (mant & 1ull));
+    // |T - hi| in units of 2^(p - 128): r + f, 0 <= f < 1 (f != 0 iff sticky)
+    const unsigned __int128 r =
+        up ? ((unsigned __int128)1 << 75) - low75 - (sticky ? 1 : 0) : low75;
+    if (sticky && bitlen128(r) <= 53) {
+        __int128 H = 0, L = 0;
+        block_value<S, TB>(acc, x, H, L);
+        round_dd<TcWidth<TB>::SPLIT>(H, L, e, hi, lo);
+        return;
+    }
+    hi = with_sign(scaled(mant + (up ? 1ull : 0ull), p - 53 + e), neg);
+    lo = (r == 0 && !sticky) ? 0.0 : with_sign(round_mag75(r, sticky, p - 128 + e), neg != up);
+}
+
 // One output tile of one problem, as a CTA sees it.  The tile's rows (the
 // MMA's M side) are vectors of a_tiles and its columns (N side) vectors of
 // b_tiles; output (row, col) is stored at row * ldc + col, or, for a product
@@ -557,10 +656,8 @@ cascade_int8_tc_kernel(const Src src) {
                             if (col < j.n) {
                                 const int e = ea + j.exp_b[(long long)p * j.n + col] - 12 -
                                               TB * (S - 1);
-                                __int128 H = 0, L = 0;
-                                block_value<S, TB>(acc, x, H, L);
                                 double h, l;
-                                round_dd<W::SPLIT>(H, L, e, h, l);
+                                round_block<S, TB>(acc, x, e, h, l);
                                 const long long o = o_base + x * o_step;
                                 if (p > 0) {
                                     double ch = j.c_hi[o], cl = j.c_lo[o];

@@ -312,3 +312,38 @@ def test_tc8_illconditioned_beats_fp64x2_loop(ops):
     rows, cols = rng.integers(0, n, 40), rng.integers(0, n, 40)
     o_hi, o_lo = dd.ddgemm(*a)
     assert rel_errors(c_hi, c_lo, a, rows, cols).max() * 3 < rel_errors(o_hi, o_lo, a, rows, cols).max()
+
+
+def test_tc_block_rounding_ties_and_carries(ops):
+    """The epilogue's exact rounding of a block value to FP64x2 (hi = RN(x),
+    lo = RN(x - hi)) on values that land on ties, on the next power of two
+    and on wide remainders: C = A B with k = 1, A's column the chosen
+    integers (exact FP64x2 pairs) and B's row signed powers of two, so every
+    C entry is a known integer; C must be its correctly rounded pair, both
+    forms (seven- and eight-bit pieces)."""
+    import random
+    rng = random.Random(5)
+    vals = []
+    for _ in range(48):                          # ties at hi's rounding
+        sh = rng.randrange(1, 50)
+        m = rng.getrandbits(53) | (1 << 52)
+        vals.append((m << sh) + (1 << (sh - 1)))
+    for _ in range(40):                          # just below a power of two
+        vals.append((1 << rng.randrange(54, 100)) - rng.randrange(1, 1 << 12))
+    for _ in range(40):                          # wide values (lo carries many bits)
+        vals.append(rng.getrandbits(rng.randrange(54, 100)) | 1)
+    vals = [v if rng.random() < 0.5 else -v for v in vals]
+    m, n = len(vals), 16
+    a_hi = np.array([float(v) for v in vals])[:, None]
+    a_lo = np.array([float(v - int(float(v))) for v in vals])[:, None]
+    pw = [rng.randrange(0, 30) for _ in range(n)]
+    sg = [rng.choice((-1, 1)) for _ in range(n)]
+    b_hi = np.array([[s * 2.0 ** p for s, p in zip(sg, pw)]])
+    b_lo = np.zeros_like(b_hi)
+    want_hi = np.array([[float(v * s << p) for s, p in zip(sg, pw)] for v in vals])
+    want_lo = np.array([[float((v * s << p) - int(float(v * s << p))) for s, p in zip(sg, pw)]
+                        for v in vals])
+    for variant in (TC, 5):
+        c = ops.ddgemm(*dev(a_hi, a_lo, b_hi, b_lo), variant=variant)
+        c_hi, c_lo = host(*c)
+        assert same(c_hi, want_hi) and same(c_lo, want_lo), variant
