@@ -49,9 +49,9 @@ NOMINAL_BF16_TFLOPS = 2250.0
 # DRAM bytes per launch (read + write) of the dominant kernel, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
 # kernels at 4096^3; other workloads report null.
-TRAFFIC_4096 = {"cascade_fp64_kernel": 9.879882e9 + 0.281523e9,
-                "cascade_int8_kernel<15>": 2.923206e9 + 0.268134e9,
-                "cascade_int8_tc_kernel<16>": 9.122322e9 + 0.272443e9}
+TRAFFIC_4096 = {"cascade_fp64_kernel": 9.884234e9 + 0.286038e9,
+                "cascade_int8_kernel<15>": 3.096227e9 + 0.268912e9,
+                "cascade_int8_tc_kernel<16>": 9.188401e9 + 0.287655e9}
 
 VARIANT_NAMES = {1: "int8", 4: "int8 on tcgen05", 5: "int8 on tcgen05, eight-bit pieces"}
 
