@@ -331,18 +331,29 @@ struct TcView {
 };
 
 // Exponents of every A: one warp per (problem, row, k-block).  Neighbouring
-// warps take neighbouring units (a contiguous run per warp measured slower).
+// warps take neighbouring chunks of units (a contiguous run per warp
+// measured slower: the runs differ in length of rows).
+constexpr int EA_CHUNK = 8;
 __global__ void __launch_bounds__(256) tc_exps_a_kernel(const char *ws) {
     const TcView V(ws);
-    const int count = V.hdr->count, lane = threadIdx.x & 31;
+    const int count = V.hdr->count, lane = threadIdx.x & 31, kblk = V.hdr->kblk;
+    const long long total = V.hdr->total_ea;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-         u < V.hdr->total_ea; u += nw) {
-        const int i = find_tc(V.ea_pre, count, u);
-        const TcEntry &e = V.ent[i];
-        const long long local = u - V.ea_pre[i];
-        split8::exps_contig_unit(lane, (int)(local / e.kb8), (int)(local % e.kb8), e.m, e.k,
-                                 V.hdr->kblk, e.a_hi, e.lda, e.e_a);
+    // chunks of EA_CHUNK consecutive units (mostly rows of one problem), so
+    // that a search of the unit prefix serves several units; the chunks are
+    // dealt out round robin for balance
+    int i = 0;
+    for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+         c * EA_CHUNK < total; c += nw) {
+        const long long u1 = c * EA_CHUNK + EA_CHUNK < total ? c * EA_CHUNK + EA_CHUNK : total;
+        for (long long u = c * EA_CHUNK; u < u1; ++u) {
+            i = advance_tc(V.ea_pre, count, u, i);
+            const TcEntry &e = V.ent[i];
+            const int local = (int)(u - V.ea_pre[i]);
+            const int row = e.kb8 == 1 ? local : local / e.kb8;
+            split8::exps_contig_unit(lane, row, local - row * e.kb8, e.m, e.k, kblk, e.a_hi,
+                                     e.lda, e.e_a);
+        }
     }
 }
 
@@ -351,12 +362,13 @@ __global__ void __launch_bounds__(256) tc_exps_b_kernel(const char *ws) {
     __shared__ unsigned long long part[4][64];
     const TcView V(ws);
     const int count = V.hdr->count;
+    int i = 0;
     for (long long u = blockIdx.x; u < V.hdr->total_eb; u += gridDim.x) {
-        const int i = find_tc(V.eb_pre, count, u);
+        i = advance_tc(V.eb_pre, count, u, i);
         const TcEntry &e = V.ent[i];
         const long long local = u - V.eb_pre[i];
         const int vtiles = (e.n + 63) / 64;
-        split8::exps_strided_unit((int)(local % vtiles), (int)(local / vtiles), e.n, e.k,
+        split8::exps_strided_unit<4>((int)(local % vtiles), (int)(local / vtiles), e.n, e.k,
                                   V.hdr->kblk, e.b_hi, e.ldb, e.e_b, part);
     }
 }
@@ -447,7 +459,7 @@ cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, lon
                               const WaitPlan &wait) {
     const long long cap = 8LL * sms;
     if (units_ea > 0) {
-        const long long blocks = (units_ea + 7) / 8;
+        const long long blocks = (units_ea + 8 * EA_CHUNK - 1) / (8 * EA_CHUNK);
         tc_exps_a_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(ws);
     }
     if (units_eb > 0)

@@ -30,23 +30,27 @@ namespace {
 
 using namespace split8;
 
-// Per (vector, k-block) exponents.  CONTIG: element (v, l) at x[v*ldx + l]
-// (one warp per vector and block); else at x[l*ldx + v] (one CTA per 64
-// vectors and block, 4 row groups).
-template <bool CONTIG>
+// Per (vector, k-block) exponents, element (v, l) at x[v*ldx + l]: one warp
+// per vector and block.
 __global__ void __launch_bounds__(256)
-int8_exps_kernel(int nvec, int kdim, int blk, const double *__restrict__ x, long long ldx,
-                 int *__restrict__ exps) {
+int8_exps_contig_kernel(int nvec, int kdim, int blk, const double *__restrict__ x, long long ldx,
+                        int *__restrict__ exps) {
     const int kb = (kdim + blk - 1) / blk;
-    if constexpr (CONTIG) {
-        const int lane = threadIdx.x & 31;
-        const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        if (w >= (long long)nvec * kb) return;
-        exps_contig_unit(lane, (int)(w / kb), (int)(w % kb), nvec, kdim, blk, x, ldx, exps);
-    } else {
-        __shared__ unsigned long long part[4][64];
-        exps_strided_unit(blockIdx.x, blockIdx.y, nvec, kdim, blk, x, ldx, exps, part);
-    }
+    const int lane = threadIdx.x & 31;
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= (long long)nvec * kb) return;
+    exps_contig_unit(lane, (int)(w / kb), (int)(w % kb), nvec, kdim, blk, x, ldx, exps);
+}
+
+// The same with element (v, l) at x[l*ldx + v]: one CTA per 64 vectors and
+// block, with 16 row groups, as one problem has few such units (64 at
+// n = 4096) and each must keep many loads in flight.
+constexpr int EXPS_RG = 16;
+__global__ void __launch_bounds__(64 * EXPS_RG)
+int8_exps_strided_kernel(int nvec, int kdim, int blk, const double *__restrict__ x,
+                         long long ldx, int *__restrict__ exps) {
+    __shared__ unsigned long long part[EXPS_RG][64];
+    exps_strided_unit<EXPS_RG>(blockIdx.x, blockIdx.y, nvec, kdim, blk, x, ldx, exps, part);
 }
 
 // BITS-bit digits: int8 planes (eight bits) or the tiled bf16 order (seven
@@ -116,12 +120,12 @@ cudaError_t launch_split_int8(int slices, int nvec, int kdim, const double *x_hi
     if (vec_contig) {
         const long long blocks = ((long long)nvec * kb + 7) / 8;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-        int8_exps_kernel<true><<<(unsigned)blocks, 256, 0, stream>>>(nvec, kdim, blk, x_hi, ldx,
-                                                                     exps);
+        int8_exps_contig_kernel<<<(unsigned)blocks, 256, 0, stream>>>(nvec, kdim, blk, x_hi, ldx,
+                                                                      exps);
     } else {
         if (kb > 65535) return cudaErrorInvalidValue;
-        int8_exps_kernel<false><<<dim3((nvec + 63) / 64, kb), 256, 0, stream>>>(nvec, kdim, blk,
-                                                                               x_hi, ldx, exps);
+        int8_exps_strided_kernel<<<dim3((nvec + 63) / 64, kb), 64 * EXPS_RG, 0, stream>>>(
+            nvec, kdim, blk, x_hi, ldx, exps);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

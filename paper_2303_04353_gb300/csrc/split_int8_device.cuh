@@ -40,68 +40,138 @@ __device__ __forceinline__ void exps_contig_unit(int lane, int v, int p, int nve
                                                  long long ldx, int *__restrict__ exps) {
     const double *row = x + (long long)v * ldx;
     const int lend = min((p + 1) * kb, kdim);
-    unsigned long long mx = 0;
-    for (int l = p * kb + lane; l < lend; l += 32) mx = umax64(mx, abs_bits(row[l]));
+    // four independent chains keep four loads of each lane in flight
+    unsigned long long m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    int l = p * kb + lane;
+    for (; l + 96 < lend; l += 128) {
+        m0 = umax64(m0, abs_bits(row[l]));
+        m1 = umax64(m1, abs_bits(row[l + 32]));
+        m2 = umax64(m2, abs_bits(row[l + 64]));
+        m3 = umax64(m3, abs_bits(row[l + 96]));
+    }
+    for (; l < lend; l += 32) m0 = umax64(m0, abs_bits(row[l]));
+    unsigned long long mx = umax64(umax64(m0, m1), umax64(m2, m3));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
         mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     if (lane == 0) exps[(long long)p * nvec + v] = block_exponent(mx);
 }
 
-// One CTA of 256 threads: the exponents of block p (of kb entries) of
+// One CTA of 64 RG threads: the exponents of block p (of kb entries) of
 // vectors [64 vt, 64 vt + 64), whose entries are strided (element l at
-// x[l*ldx + v]).
+// x[l*ldx + v]); RG row groups take every RG-th entry, four loads in flight
+// each.
+template <int RG>
 __device__ __forceinline__ void exps_strided_unit(int vt, int p, int nvec, int kdim, int kb,
                                                   const double *__restrict__ x, long long ldx,
                                                   int *__restrict__ exps,
-                                                  unsigned long long (&part)[4][64]) {
+                                                  unsigned long long (&part)[RG][64]) {
     const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
     const int v = vt * 64 + tx;
     const int lend = min((p + 1) * kb, kdim);
     unsigned long long mx = 0;
-    if (v < nvec)
-        for (int l = p * kb + ty; l < lend; l += 4)
-            mx = umax64(mx, abs_bits(x[(long long)l * ldx + v]));
+    if (v < nvec) {
+        unsigned long long m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+        int l = p * kb + ty;
+        for (; l + 3 * RG < lend; l += 4 * RG) {
+            m0 = umax64(m0, abs_bits(x[(long long)l * ldx + v]));
+            m1 = umax64(m1, abs_bits(x[(long long)(l + RG) * ldx + v]));
+            m2 = umax64(m2, abs_bits(x[(long long)(l + 2 * RG) * ldx + v]));
+            m3 = umax64(m3, abs_bits(x[(long long)(l + 3 * RG) * ldx + v]));
+        }
+        for (; l < lend; l += RG) m0 = umax64(m0, abs_bits(x[(long long)l * ldx + v]));
+        mx = umax64(umax64(m0, m1), umax64(m2, m3));
+    }
     part[ty][tx] = mx;
     __syncthreads();
     if (ty == 0 && v < nvec) {
-        mx = umax64(umax64(part[0][tx], part[1][tx]), umax64(part[2][tx], part[3][tx]));
+#pragma unroll
+        for (int g = 1; g < RG; ++g) mx = umax64(mx, part[g][tx]);
         exps[(long long)p * nvec + v] = block_exponent(mx);
     }
     __syncthreads();  // part is reused by the next unit
 }
 
-// round-half-even(x * 2^sh) as a 128-bit integer, from the bits of x.
-__device__ __forceinline__ __int128 rne_scaled(double x, int sh) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    const int ex = (int)((bits >> 52) & 0x7ff);
-    unsigned long long mant = bits & 0xfffffffffffffull;
-    if (ex == 0x7ff || (ex == 0 && mant == 0)) return 0;  // non-finite is flagged elsewhere
+// The upper word of (hi:lo) << (s mod 32).
+__host__ __device__ __forceinline__ uint32_t funnel_l(uint32_t lo, uint32_t hi, int s) {
+#ifdef __CUDA_ARCH__
+    return __funnelshift_l(lo, hi, (unsigned)s);
+#else
+    const int r = s & 31;
+    return r ? (hi << r) | (lo >> (32 - r)) : hi;
+#endif
+}
+
+__host__ __device__ __forceinline__ unsigned long long double_bits(double x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(x);
+#else
+    unsigned long long b;
+    __builtin_memcpy(&b, &x, sizeof b);
+    return b;
+#endif
+}
+
+// round-half-even(|x| 2^sh) as a 128-bit magnitude in 32-bit words v[0..3]
+// (least significant first), from the two words of x's bit pattern (hw:
+// sign, exponent and the fraction's top 20 bits).  The shifts are word
+// funnel shifts and the rounding one carry trick, on the integer pipes.
+// Returns false for Inf and NaN (v = 0; the caller flags them).  An entry
+// with |x| 2^sh >= 2^74 (a lo part far above its block's max |hi|, outside
+// the form's range) gives 0.
+__host__ __device__ __forceinline__ bool scaled_magnitude(uint32_t hw, uint32_t lw, int sh,
+                                                          uint32_t (&v)[4]) {
+    const int ex = (int)((hw >> 20) & 0x7ffu);
+    uint32_t m1 = hw & 0xfffffu;  // |x| = (m1:lw) 2^(p - sh)
     int p;
     if (ex == 0) {
-        p = 1 - 1075 + sh;                 // subnormal: no implicit bit
+        p = 1 - 1075 + sh;        // zero or subnormal: no implicit bit
     } else {
-        mant |= 1ull << 52;
+        m1 |= 0x100000u;
         p = ex - 1075 + sh;
     }
-    __int128 v;
-    if (p > 127 - 54) {
-        // only an entry far above its block's max |hi| gets here (a lo part
-        // much larger than every hi of the block): outside the form's range
-        v = 0;
-    } else if (p >= 0) {
-        v = (__int128)mant << p;
-    } else if (p < -63) {
-        v = 0;                             // below one half
-    } else {
+    v[0] = v[1] = v[2] = v[3] = 0u;
+    if (ex == 0x7ff) return false;
+    if (p > 127 - 54) return true;
+    if (p >= 0) {
+        // (m1:lw) << p: three words from word p / 32 up (the third is zero
+        // when p >= 64, as m1 < 2^21 and p <= 73)
+        const uint32_t t0 = lw << (p & 31), t1 = funnel_l(lw, m1, p), t2 = funnel_l(m1, 0u, p);
+        const int q = p >> 5;
+        v[0] = q == 0 ? t0 : 0u;
+        v[1] = q == 0 ? t1 : (q == 1 ? t0 : 0u);
+        v[2] = q == 0 ? t2 : (q == 1 ? t1 : t0);
+        v[3] = q == 1 ? t2 : (q == 2 ? t1 : 0u);
+    } else if (p >= -63) {
+        // m / 2^r rounded half to even is (m + 2^(r-1) - 1 + bit r of m) >> r
+        // (no overflow: m < 2^53); below 2^-63 the value rounds to 0
         const int r = -p;
-        unsigned long long q = mant >> r;
-        const unsigned long long rem = mant & ((1ull << r) - 1ull);
-        const unsigned long long half = 1ull << (r - 1);
-        if (rem > half || (rem == half && (q & 1ull))) ++q;
-        v = (__int128)q;
+        const unsigned long long m = ((unsigned long long)m1 << 32) | lw;
+        const unsigned long long q = (m + ((1ull << (r - 1)) - 1ull) + ((m >> r) & 1ull)) >> r;
+        v[0] = (uint32_t)q;
+        v[1] = (uint32_t)(q >> 32);
     }
-    return (bits >> 63) ? -v : v;
+    return true;
+}
+
+__host__ __device__ __forceinline__ unsigned __int128 words128(const uint32_t (&v)[4], uint32_t mask) {
+    return ((unsigned __int128)(((unsigned long long)(v[3] ^ mask) << 32) | (v[2] ^ mask)) << 64) |
+           (((unsigned long long)(v[1] ^ mask) << 32) | (v[0] ^ mask));
+}
+
+// C + rne(hi 2^sh) + rne(lo 2^sh) as a 128-bit two's complement integer,
+// each term rounded on its own; clears `finite` when hi or lo is Inf or
+// NaN.  A negative term -v enters as ~v + 1: its words XORed with all ones
+// and the 1 added to the constant C.
+__host__ __device__ __forceinline__ __int128 fixed_sum(double hi, double lo, int sh, __int128 c,
+                                                       bool &finite) {
+    const unsigned long long bh = double_bits(hi), bl = double_bits(lo);
+    uint32_t vh[4], vl[4];
+    finite &= scaled_magnitude((uint32_t)(bh >> 32), (uint32_t)bh, sh, vh);
+    finite &= scaled_magnitude((uint32_t)(bl >> 32), (uint32_t)bl, sh, vl);
+    const uint32_t nh = (uint32_t)(bh >> 63), nl = (uint32_t)(bl >> 63);
+    return (__int128)(words128(vh, 0u - nh) + words128(vl, 0u - nl) +
+                      ((unsigned __int128)c + nh + nl));
 }
 
 constexpr int TV = 32, TK = 64;  // tile: 32 vectors x 64 k
@@ -195,7 +265,6 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
     if (gv >= nvec) return;
     const int e = exps[(long long)(l0 / kblock_of_bits(BITS)) * nvec + gv];
     constexpr int F = 6 + BITS * (S - 1);
-    bool bad = false;
     const int gl = l0 + lg * 8;
     if constexpr (BF16) {
         // Balanced base-2^BITS digits as bit fields: with Y = X +
@@ -204,13 +273,12 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
         // Y >> BITS (s-1) (the same digits as peeling d = ((X + h) mod 2 h)
         // - h, X = (X - d) / 2h with h = 2^(BITS-1)).
         __int128 Y[8];
+        bool finite = true;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const double hi = sh[v][lg * 8 + j], lo = sl[v][lg * 8 + j];
-            bad |= ((abs_bits(hi) >> 52) == 0x7ff) | ((abs_bits(lo) >> 52) == 0x7ff);
-            Y[j] = rne_scaled(hi, F - e) + rne_scaled(lo, F - e) + digit_offset<S, BITS>();
-        }
-        if (bad && status) atomicOr(status, DEV_NONFINITE);
+        for (int j = 0; j < 8; ++j)
+            Y[j] = fixed_sum(sh[v][lg * 8 + j], sl[v][lg * 8 + j], F - e,
+                             digit_offset<S, BITS>(), finite);
+        if (!finite && status) atomicOr(status, DEV_NONFINITE);
         // the tiled order is read a whole k-step of 16 at a time: groups past
         // kdim up to the next multiple of 16 are written with zero digits
         if (gl >= (kdim + 15) / 16 * 16) return;
@@ -236,21 +304,20 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
         unsigned long long word[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) word[s] = 0;
+        bool finite = true;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const double hi = sh[v][lg * 8 + j], lo = sl[v][lg * 8 + j];
-            bad |= ((abs_bits(hi) >> 52) == 0x7ff) | ((abs_bits(lo) >> 52) == 0x7ff);
             // the digits as in the bf16 branch; the int8 digit d = f - 128 is
             // the byte f ^ 0x80
-            const __int128 Y =
-                rne_scaled(hi, F - e) + rne_scaled(lo, F - e) + digit_offset<S, BITS>();
+            const __int128 Y = fixed_sum(sh[v][lg * 8 + j], sl[v][lg * 8 + j], F - e,
+                                         digit_offset<S, BITS>(), finite);
 #pragma unroll
             for (int s = 0; s < S; ++s)
                 word[s] |= (unsigned long long)((digit_field<S, BITS>(Y, S - 1 - s) ^ 0x80u) &
                                                 0xffu)
                            << (8 * j);
         }
-        if (bad && status) atomicOr(status, DEV_NONFINITE);
+        if (!finite && status) atomicOr(status, DEV_NONFINITE);
         if (gl >= kdim) return;
         // entries past kdim in the last group of 8 carry zero digits; they
         // sit in the row padding (ld_out >= kdim rounded up to 16) and are
