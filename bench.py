@@ -488,6 +488,19 @@ def config_batched(dev, stream):
         ms, clocks = _timed(tg.replay, 5, 3, stream)
         prods = s8 * (s8 + 1) // 2
         achieved = prods * flops / (ms * 1e-3) / 1e12
+        # the persistent kernel alone: the library's phase events around it,
+        # eager runs of the tuned schedule
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        for e in ev:
+            e.record(stream)
+        split_ms = kern_ms = 0.0
+        reps = 5
+        for _ in range(reps):
+            tb.run(stream=stream, config=tcfg, phase_events=ev)
+            ev[2].synchronize()
+            split_ms += ev[0].elapsed_time(ev[1]) / reps
+            kern_ms += ev[1].elapsed_time(ev[2]) / reps
+        k_achieved = prods * flops / (kern_ms * 1e-3) / 1e12
         out[name] = {"batched_graph_ms": round(ms, 3),
                      "value": round(flops / (ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
                      "pieces": s8, "launches": 5,
@@ -501,6 +514,16 @@ def config_batched(dev, stream):
                                        "peak_source": bsrc,
                                        "what": f"{prods} x sum 2mnk digit flops over the "
                                                "whole pass (5 launches)"},
+                     "phases_ms": {"plan_and_split": round(split_ms, 3),
+                                   "persistent_kernel": round(kern_ms, 3)},
+                     "kernel_roofline": {"bound": "tensor (tcgen05 bf16)",
+                                         "kernel": "cascade_int8_tc_kernel (BatchSource)",
+                                         "achieved": round(k_achieved, 3),
+                                         "peak": round(bpeak, 3), "unit": "TFLOP/s",
+                                         "frac": round(k_achieved / bpeak, 4),
+                                         "peak_source": bsrc,
+                                         "what": f"{prods} x sum 2mnk digit flops / the "
+                                                 "persistent kernel's time (phase events)"},
                      "max_err_vs_dd_oracle": worst(tp), "clocks": clocks}
         del tg, tb, tp
     return out
@@ -944,9 +967,21 @@ def run_batched_tc_only(args, shapes, probs, flops, stream):
     if int(status.item()):
         raise SystemExit(f"bench.py: device status {int(status.item()):#x}")
     ms = e0.elapsed_time(e1) / args.steps
+    # the split and the persistent kernel apart (the library's phase events)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for e in ev:
+        e.record(stream)
+    split_ms = kern_ms = 0.0
+    for _ in range(args.steps):
+        batch.run(stream=stream, status=status, phase_events=ev)
+        ev[2].synchronize()
+        split_ms += ev[0].elapsed_time(ev[1]) / args.steps
+        kern_ms += ev[1].elapsed_time(ev[2]) / args.steps
     tiles = sum(((m + 127) // 128) * ((n + 15) // 16) for m, n, _ in shapes if m and n)
     print(json.dumps({"study": "batched tcgen05 INT8 pass alone", "variant": args.variant,
                       "problems": len(shapes), "tiles": tiles, "ms": round(ms, 3),
+                      "phases_ms": {"plan_and_split": round(split_ms, 3),
+                                    "persistent_kernel": round(kern_ms, 3)},
                       "effective_gflops": round(flops / (ms * 1e-3) / 1e9, 1),
                       "launches": 5}), flush=True)
 

@@ -128,7 +128,9 @@ typedef struct ddgemm_opts {
     /* Optional (or NULL): three cudaEvent_t handles, passed as void*, that
      * ddgemm() records on `stream` before the split (phase one), between the
      * split and the ten products (phases two and three, one kernel) and
-     * after it, so that a caller can time each phase on the device. */
+     * after it, so that a caller can time each phase on the device
+     * (ddgemm_batched(): before its plan, before its persistent kernel and
+     * after it). */
     void **phase_events;
     /* INT8 forms only: pieces per entry, s (s + 1) / 2 digit products per k.
      * INT8: s in {12, 13, 14, 15}, 0 = 15 (the paper estimates 14-15; 120
@@ -268,7 +270,10 @@ size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem *probs_host
  *   opts        NULL or: trans flags 0, variant FP64, INT8_TC or INT8_TC8,
  *               no flags_dev (else DDGEMM_EUNSUPPORTED); status_dev is
  *               honoured; int8_slices for INT8_TC (12-16; 0 = 16) and
- *               INT8_TC8 (12-15; 0 = 15).
+ *               INT8_TC8 (12-15; 0 = 15); phase_events NULL or three
+ *               cudaEvent_t (as void *) recorded on `stream` before the
+ *               plan, after the splits (before the persistent kernel) and
+ *               after the persistent kernel.
  *   config      NULL = {DDGEMM_TILE_64x64, DDGEMM_ORDER_LONGEST_K_FIRST,
  *               DDGEMM_ORIENT_FEWER_TILES, DDGEMM_PLANES_INTERLEAVED, 4}.
  *               Out-of-range fields: DDGEMM_EINVAL.

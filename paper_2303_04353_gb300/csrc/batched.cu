@@ -477,14 +477,14 @@ extern "C" int ddgemm_batched(int count, const ddgemm_problem *probs_host,
             if (!int8_tc_slices_supported(s)) return DDGEMM_EINVAL;
             return run_batched_int8_tc(count, probs_host, probs_dev, workspace, ws_bytes,
                                        static_cast<cudaStream_t>(stream), s, INT8_TC_BITS,
-                                       status, config);
+                                       status, config, WaitPlan{}, opts->phase_events);
         }
         if (opts->variant == DDGEMM_VARIANT_INT8_TC8) {
             const int s = opts->int8_slices ? opts->int8_slices : INT8_TC8_SLICES_DEFAULT;
             if (!int8_tc8_slices_supported(s)) return DDGEMM_EINVAL;
             return run_batched_int8_tc(count, probs_host, probs_dev, workspace, ws_bytes,
                                        static_cast<cudaStream_t>(stream), s, INT8_BITS, status,
-                                       config);
+                                       config, WaitPlan{}, opts->phase_events);
         }
     }
     const int tile = config ? config->tile : DDGEMM_TILE_64x64;
@@ -509,8 +509,13 @@ extern "C" int ddgemm_batched(int count, const ddgemm_problem *probs_host,
         return DDGEMM_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(workspace);
+    void *const *events = opts ? opts->phase_events : nullptr;
+    auto mark = [&](int i) {
+        return !events || cudaEventRecord(static_cast<cudaEvent_t>(events[i]), s) == cudaSuccess;
+    };
     int bm, bn;
     tile_shape(tile, bm, bn);
+    if (!mark(0)) return DDGEMM_ECUDA;
     plan_kernel<<<1, 256, 0, s>>>(count, probs_dev, ws, order, bm, bn);
     if (cudaGetLastError() != cudaSuccess) return DDGEMM_ECUDA;
     if (total_a > 0) {
@@ -521,6 +526,7 @@ extern "C" int ddgemm_batched(int count, const ddgemm_problem *probs_host,
                                  s>>>(ws, status);
         if (cudaGetLastError() != cudaSuccess) return DDGEMM_ECUDA;
     }
+    if (!mark(1)) return DDGEMM_ECUDA;
     cudaError_t e;
     switch (tile) {
         case DDGEMM_TILE_32x64: e = launch_cascade<2, 2>(ws, sms, s); break;
@@ -528,7 +534,7 @@ extern "C" int ddgemm_batched(int count, const ddgemm_problem *probs_host,
         case DDGEMM_TILE_32x32: e = launch_cascade<2, 1>(ws, sms, s); break;
         default: e = launch_cascade<4, 2>(ws, sms, s); break;
     }
-    return e == cudaSuccess ? DDGEMM_OK : DDGEMM_ECUDA;
+    return e == cudaSuccess && mark(2) ? DDGEMM_OK : DDGEMM_ECUDA;
 }
 
 extern "C" int ddgemm_diag_batched_withheld_copy(int count, const ddgemm_problem *probs_host,

@@ -456,7 +456,7 @@ struct BatchSource {
 template <int S, int BITS, int PLANES>
 cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, long long units_eb,
                               long long units_d, int sms, cudaStream_t s, int row_group,
-                              const WaitPlan &wait) {
+                              const WaitPlan &wait, void *const *events) {
     const long long cap = 8LL * sms;
     if (units_ea > 0) {
         const long long blocks = (units_ea + 8 * EA_CHUNK - 1) / (8 * EA_CHUNK);
@@ -467,7 +467,11 @@ cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, lon
     if (units_d > 0)
         tc_digits_kernel<S, BITS><<<(unsigned)(units_d < cap ? units_d : cap), 256, 0, s>>>(ws);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || tiles == 0) return e;
+    if (e == cudaSuccess && events)
+        e = cudaEventRecord(static_cast<cudaEvent_t>(events[1]), s);
+    if (e != cudaSuccess) return e;
+    if (tiles == 0)
+        return events ? cudaEventRecord(static_cast<cudaEvent_t>(events[2]), s) : cudaSuccess;
     using G = TcGeom<S>;
     auto kernel = cascade_int8_tc_kernel<S, BITS, BatchSource, PLANES>;
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -476,7 +480,9 @@ cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, lon
     const int grid = (int)(tiles < sms ? tiles : sms);
     BatchSource src{ws, row_group, wait};
     kernel<<<grid, NTHREADS, G::SMEM, s>>>(src);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && events) e = cudaEventRecord(static_cast<cudaEvent_t>(events[2]), s);
+    return e;
 }
 
 bool tc_problem_ok(const ddgemm_problem &q) {
@@ -509,7 +515,8 @@ size_t batched_int8_tc_workspace_size(int count, const ddgemm_problem *probs_hos
 int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
                         const ddgemm_problem *probs_dev, void *workspace, size_t ws_bytes,
                         cudaStream_t s, int slices, int bits, unsigned int *status,
-                        const ddgemm_batch_config *config, const WaitPlan &wait) {
+                        const ddgemm_batch_config *config, const WaitPlan &wait,
+                        void *const *events) {
     if (bits != INT8_TC_BITS && bits != INT8_BITS) return DDGEMM_EINVAL;
     if (bits == INT8_BITS && slices > 15) return DDGEMM_EINVAL;
     const int kblk = kblock_of_bits(bits);
@@ -542,14 +549,16 @@ int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return DDGEMM_ECUDA;
     char *ws = static_cast<char *>(workspace);
+    if (events && cudaEventRecord(static_cast<cudaEvent_t>(events[0]), s) != cudaSuccess)
+        return DDGEMM_ECUDA;
     tc_plan_kernel<<<1, 256, 0, s>>>(count, probs_dev, ws, slices, kblk, status, order_rule,
                                      orient);
     if (cudaGetLastError() != cudaSuccess) return DDGEMM_ECUDA;
     cudaError_t e;
 #define DDG_TC(S, B)                                                                     \
     (planes == DDGEMM_PLANES_ASCENDING                                                   \
-         ? launch_batched_tc<S, B, 1>(ws, tiles, ea, eb, d, sms, s, row_group, wait)     \
-         : launch_batched_tc<S, B, 0>(ws, tiles, ea, eb, d, sms, s, row_group, wait))
+         ? launch_batched_tc<S, B, 1>(ws, tiles, ea, eb, d, sms, s, row_group, wait, events) \
+         : launch_batched_tc<S, B, 0>(ws, tiles, ea, eb, d, sms, s, row_group, wait, events))
     if (bits == INT8_BITS) {
         switch (slices) {
             case 12: e = DDG_TC(12, INT8_BITS); break;

@@ -160,11 +160,14 @@ cudaError_t launch_cascade_int8_tc8(const Int8TcArgs &a, cudaStream_t stream);
 // bits: 7 (DDGEMM_VARIANT_INT8_TC) or 8 (DDGEMM_VARIANT_INT8_TC8).
 size_t batched_int8_tc_workspace_size(int count, const ddgemm_problem *probs_host, int slices,
                                       int bits);
-// config: NULL (defaults) or checked by the caller.
+// config: NULL (defaults) or checked by the caller.  events: NULL or three
+// cudaEvent_t recorded before the plan, before the persistent kernel and
+// after it.
 int run_batched_int8_tc(int count, const ddgemm_problem *probs_host,
                         const ddgemm_problem *probs_dev, void *workspace, size_t ws_bytes,
                         cudaStream_t s, int slices, int bits, unsigned int *status,
-                        const ddgemm_batch_config *config, const WaitPlan &wait = WaitPlan{});
+                        const ddgemm_batch_config *config, const WaitPlan &wait = WaitPlan{},
+                        void *const *events = nullptr);
 
 // Whether a batch configuration's fields are in range (both forms).
 inline bool batch_config_ok(const ddgemm_batch_config *c) {

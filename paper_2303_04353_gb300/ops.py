@@ -364,14 +364,22 @@ class Batch:
             self.count, arr, _lib.make_opts(variant=variant, int8_slices=int8_slices))
         self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
 
-    def run(self, stream=None, config=None, status=None):
+    def run(self, stream=None, config=None, status=None, phase_events=None):
         """Enqueue the batch.  config: None (library default), a
         ddgemm_batch_config, or a tuple of its fields (tile, order[, orient,
-        planes, row_group]); missing fields are 0."""
+        planes, row_group]); missing fields are 0.  phase_events: optional
+        three recorded torch.cuda.Event objects, re-recorded before the plan,
+        before the persistent kernel and after it."""
         if config is not None and not isinstance(config, _lib.ddgemm_batch_config):
             config = _lib.ddgemm_batch_config(*config)
+        evs = None
+        if phase_events is not None:
+            if len(phase_events) != 3 or not all(e.cuda_event for e in phase_events):
+                raise ValueError("phase_events: three torch.cuda.Event, each recorded once")
+            evs = (ctypes.c_void_p * 3)(*[e.cuda_event for e in phase_events])
         opts = _lib.make_opts(variant=self.variant, int8_slices=self.int8_slices,
-                              status_dev=status.data_ptr() if status is not None else 0)
+                              status_dev=status.data_ptr() if status is not None else 0,
+                              phase_events=evs)
         if stream is not None and stream.device != self.workspace.device:
             raise ValueError("the stream is on another device than the batch")
         with torch.cuda.device(self.workspace.device):

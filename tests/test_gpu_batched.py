@@ -312,3 +312,33 @@ def test_autotuner_tc_picks_a_schedule(mods, tmp_path, monkeypatch):
     # the FP64 batch of the same shapes is tuned (and cached) on its own
     fp64, _, _ = make_batch(ops, MIXED, seed=41)
     assert autotune.tune(fp64, reps=1)[0] in autotune.CANDIDATES
+
+
+@pytest.mark.parametrize("variant", [0, TC, 5])
+def test_batched_phase_events(mods, variant):
+    """ddgemm_batched records the three phase events (before the plan,
+    before the persistent kernel, after it) in stream order, and a run with
+    them gives the same bits as one without."""
+    _, ops, _ = mods
+    rng = np.random.default_rng(11)
+    shapes = [tuple(int(v) for v in rng.integers(30, 300, 3)) for _ in range(40)]
+    batch, probs, _ = make_batch(ops, shapes, seed=50, variant=variant)
+    batch.run()
+    want = [(h.copy(), lo.copy()) for h, lo in results(probs)]
+    for p in probs:
+        p[4].fill_(np.nan)
+        p[5].fill_(np.nan)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for e in ev:
+        e.record(stream)
+    end = torch.cuda.Event(enable_timing=True)
+    batch.run(phase_events=ev)
+    end.record(stream)
+    end.synchronize()
+    split_ms, kern_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    assert split_ms > 0 and kern_ms > 0
+    assert ev[2].elapsed_time(end) >= 0
+    for (h, lo), (wh, wl) in zip(results(probs), want):
+        assert np.array_equal(h.view(np.int64), wh.view(np.int64))
+        assert np.array_equal(lo.view(np.int64), wl.view(np.int64))
