@@ -259,13 +259,24 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
         sl[v][l] = b;
     }
     __syncthreads();
-    // each thread: one vector, 8 consecutive k; one 8-byte word per digit plane
-    const int v = tid >> 3, lg = tid & 7;
+    // each thread: one vector, 8 consecutive k.  For the tiled bf16 order a
+    // warp takes one k-step of 16 entries (two lanes per vector) of 16
+    // vectors: the k-steps a ragged tile has past its end, and a vector half
+    // past nvec, then leave whole warps idle instead of lanes of every warp,
+    // and a warp's stores of a plane are 512 contiguous bytes.  The int8
+    // planes keep a vector's 64 entries in one warp (64-byte rows).
+    const int warp = tid >> 5, lane = tid & 31;
+    const int v = BF16 ? (warp >> 2) * 16 + (lane >> 1) : tid >> 3;
+    const int lg = BF16 ? (warp & 3) * 2 + (lane & 1) : tid & 7;
     const int gv = v0 + v;
     if (gv >= nvec) return;
+    const int gl = l0 + lg * 8;
+    // the tiled bf16 order is read a whole k-step of 16 at a time: groups
+    // past kdim up to the next multiple of 16 are written with zero digits
+    // (their entries were loaded as zeros); the int8 planes stop at kdim
+    if (gl >= (BF16 ? (kdim + 15) / 16 * 16 : kdim)) return;
     const int e = exps[(long long)(l0 / kblock_of_bits(BITS)) * nvec + gv];
     constexpr int F = 6 + BITS * (S - 1);
-    const int gl = l0 + lg * 8;
     if constexpr (BF16) {
         // Balanced base-2^BITS digits as bit fields: with Y = X +
         // sum_{i<s-1} 2^(BITS-1) 2^(BITS i), digit i (least significant
@@ -279,9 +290,6 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
             Y[j] = fixed_sum(sh[v][lg * 8 + j], sl[v][lg * 8 + j], F - e,
                              digit_offset<S, BITS>(), finite);
         if (!finite && status) atomicOr(status, DEV_NONFINITE);
-        // the tiled order is read a whole k-step of 16 at a time: groups past
-        // kdim up to the next multiple of 16 are written with zero digits
-        if (gl >= (kdim + 15) / 16 * 16) return;
         const int ksteps = (kdim + 15) / 16;
         // plane s holds digit S-1-s; two entries' bf16 digits share a
         // 32-bit word, each plane's 8 entries one 16-byte store
@@ -318,7 +326,6 @@ __device__ __forceinline__ void digits_unit(int v0, int l0, int nvec, int kdim,
                            << (8 * j);
         }
         if (!finite && status) atomicOr(status, DEV_NONFINITE);
-        if (gl >= kdim) return;
         // entries past kdim in the last group of 8 carry zero digits; they
         // sit in the row padding (ld_out >= kdim rounded up to 16) and are
         // never read
