@@ -8,19 +8,20 @@
 // 64; the mma.sync form takes eight-bit ones): a product is at most 2^12 and
 // diagonal t holds t + 1 <= 16 products per k, so over a chunk of 256
 // entries every partial sum of a diagonal is an integer of magnitude
-// <= 256 * 16 * 2^12 = 2^24: exact in FP32.  With eight-bit pieces the chunk
-// would be 64 entries, and four times as many read-outs starve the MMA
-// issue (measured: 13.75 ms for 15 eight-bit pieces against 12.05 ms for 16
-// seven-bit ones at 4096^3).  After each chunk the FP32 sums are read out of
+// <= 256 * 16 * 2^12 = 2^24: exact in FP32.  With eight-bit pieces
+// (cascade_int8_tc8.cu, the same kernel core) the chunk is 64 entries, and
+// four times as many read-outs and accumulator switches make that form
+// slower per product.  After each chunk the FP32 sums are read out of
 // tensor memory, converted (exactly) to integers and added into each
-// output's exact k-block value; over a k-block of 16384 entries a
+// output's exact k-block sums; over a k-block of 16384 entries a
 // diagonal's sum stays within 2^30.
 //
 // Assembly.  Per k-block the exact value sum_t S_t 2^(-12-7t) sigma tau is
-// formed in 128-bit integer arithmetic and rounded once to the nearest
-// FP64x2 (hi = RN(x), lo = RN(x - hi)); the blocks are added into C with
-// the FP64x2 add.  This is one rounding where the paper's smallest-first
-// FP64x2 sum of the diagonals has s.
+// formed in 192-bit integer arithmetic and rounded once to the nearest
+// FP64x2 (hi = RN(x), lo = RN(x - hi)) from one left alignment of its
+// magnitude; the blocks are added into C with the FP64x2 add (the first
+// block is stored as it is).  This is one rounding where the paper's
+// smallest-first FP64x2 sum of the diagonals has s.
 //
 // Tiling.  A C tile is 128 rows x 16 columns; k advances by 16.  The split
 // wrote the digits tiled and pre-swizzled (split_int8.cu), so one bulk copy
@@ -35,14 +36,14 @@
 // of 16 s columns alternate between chunks, so the drain of one overlaps
 // the products of the next.
 //
-// Warps.  Warp 0 issues the TMA copies, warp 1 allocates tensor memory and
-// issues the MMAs (one thread), warps 2-9 drain the accumulators and
+// Warps.  Warp 0 issues the bulk copies, warp 1 allocates tensor memory and
+// issues the MMAs (one thread), warps 2-17 drain the accumulators and
 // assemble: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows of
-// the tile) and columns 8 ((w - 2) / 4) .. + 7 of every diagonal.  Per
-// output it keeps the block value exactly, as T = H 2^56 + L in two 128-bit
-// integers: each chunk's diagonal sums are folded in four at a time (four
-// consecutive diagonals make an exact int64 below 2^46), so a thread holds
-// 8 x 2 128-bit sums instead of 16 x 8 int32 totals.  The kernel is
+// the tile) and columns 4 ((w - 2) / 4) .. + 3 of every diagonal.  Per
+// output it keeps the k-block's sums exactly in int64s, one per group of up
+// to four consecutive diagonals (a group's chunk sum, combined with powers
+// of 2^7, stays below 2^46 and its k-block sum below 2^56), and forms the
+// block value from them once at the k-block's end.  The kernel is
 // persistent: one CTA per SM walks the tiles in groups of 4 row tiles.
 //
 // Waits.  Every wait gives up after ~2 s, sets DDGEMM_DEV_TIMEOUT and a flag
