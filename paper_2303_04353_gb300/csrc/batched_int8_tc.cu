@@ -3,7 +3,8 @@
 // (one warp per row and k-block) and of every B (one CTA per 64 columns and
 // k-block), the tiled bf16 digits of every A and B (one CTA per 32 x 64
 // input tile), and one persistent tcgen05 kernel that walks the planned list
-// of (problem, 128 x 16 tile) items, longest k first.  The paper has no
+// of (problem, 128 x 16 tile) items in the configured order (longest k
+// first unless ddgemm_batch_config says otherwise).  The paper has no
 // batched form; this is the tcgen05 INT8 form (cascade_int8_tc.cu) scheduled
 // for many small problems at once, with seven- or eight-bit pieces.  Every
 // unit runs the single-problem form's device code on that problem's data,
