@@ -312,8 +312,8 @@ size_t ddgemm_host_buffer_size(int m, int n, int k, const ddgemm_opts *opts);
  *     B is copied first, then op(A) in up to four chunks of rows: every
  *     chunk's split and products run on `stream` as soon as its rows have
  *     arrived, and its rows of C are copied back while the next chunk
- *     computes.  Chunks hold at least 2048 tiles of the form's kernel, so
- *     small problems run as one chunk.
+ *     computes.  Chunks hold at least 1024 tiles of the form's kernel
+ *     (about seven waves of the GPU), so small problems run as one chunk.
  *   - Each chunk computes exactly what ddgemm() computes for those rows:
  *     C is bit-identical to ddgemm() on device copies of the operands,
  *     except that the FP64 form may choose a different split-k grouping

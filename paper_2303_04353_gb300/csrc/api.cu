@@ -336,7 +336,7 @@ size_t workspace_total(int m, int n, int k, const Parsed &p) {
 // the first chunk of A, the split of B, and the copy of the last chunk of C.
 
 constexpr int HOST_MAX_CHUNKS = 4;
-constexpr long long HOST_MIN_TILES = 2048;
+constexpr long long HOST_MIN_TILES = 1024;
 
 // Rows of op(A) per chunk: at least HOST_MIN_TILES tiles of the form's own
 // tile shape per chunk, so that a chunk still fills the GPU, and at most

@@ -203,23 +203,24 @@ def test_batched_tc_host_checks():
 
 
 def host_chunk_rows(m, n, variant):
-    """The row-chunk rule of ddgemm_host, restated: at least 2048 tiles of
+    """The row-chunk rule of ddgemm_host, restated: at least 1024 tiles of
     the form's kernel (64 x 64 FP64, 32 x 32 mma.sync INT8, 128 x 16 tcgen05)
     per chunk, at most four chunks, a multiple of 128 rows."""
     tm, tn = {_lib.DDGEMM_VARIANT_FP64: (64, 64), _lib.DDGEMM_VARIANT_INT8: (32, 32),
               _lib.DDGEMM_VARIANT_INT8_TC: (128, 16)}[variant]
-    rows_min = -(-2048 // -(-n // tn)) * tm
+    rows_min = -(-1024 // -(-n // tn)) * tm
     mc = -(-max(rows_min, -(-m // 4)) // 128) * 128
     return min(mc, m)
 
 
 @pytest.mark.parametrize("m,n,k,variant,chunks", [
-    (4096, 4096, 4096, _lib.DDGEMM_VARIANT_FP64, 2),
-    (2100, 8192, 300, _lib.DDGEMM_VARIANT_FP64, 3),
+    (4096, 4096, 4096, _lib.DDGEMM_VARIANT_FP64, 4),
+    (2100, 8192, 300, _lib.DDGEMM_VARIANT_FP64, 4),
     (4096, 4096, 4096, _lib.DDGEMM_VARIANT_INT8_TC, 4),
-    (4200, 2048, 300, _lib.DDGEMM_VARIANT_INT8_TC, 3),
-    (2500, 2048, 300, _lib.DDGEMM_VARIANT_INT8, 3),
-    (2100, 8192, 1100, _lib.DDGEMM_VARIANT_FP64, 3),
+    (4200, 2048, 300, _lib.DDGEMM_VARIANT_INT8_TC, 4),
+    (2500, 2048, 300, _lib.DDGEMM_VARIANT_INT8, 4),
+    (2100, 8192, 1100, _lib.DDGEMM_VARIANT_FP64, 4),
+    (1500, 4096, 300, _lib.DDGEMM_VARIANT_FP64, 2),
     (100, 70, 300, _lib.DDGEMM_VARIANT_FP64, 1),
     (100, 50, 0, _lib.DDGEMM_VARIANT_FP64, 1)])
 def test_host_buffer_size(m, n, k, variant, chunks):

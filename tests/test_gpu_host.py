@@ -98,8 +98,8 @@ def check_sampled_contract(a_hi, a_lo, b_hi, b_lo, c_hi, c_lo, seed=0, count=64)
 
 
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, True), (True, False)])
-def test_host_fp64_three_chunks(ops, ta, tb):
-    """2100 x 8192 x 300: chunks of 1024, 1024 and 52 rows of op(A)."""
+def test_host_fp64_four_chunks(ops, ta, tb):
+    """2100 x 8192 x 300: chunks of 640, 640, 640 and 180 rows of op(A)."""
     m, n, k = 2100, 8192, 300
     a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind="uniform", seed=11)
     c_hi, c_lo = run_host(ops, (a_hi, a_lo), (b_hi, b_lo), ta, tb, split_k=1)
@@ -136,14 +136,14 @@ def sample_rows_cols(m, n, mc, seed):
     return rows, cols
 
 
-@pytest.mark.parametrize("variant,m,n,mc,s,ta", [(INT8, 2500, 2048, 1024, 15, False),
-                                                (INT8, 2500, 2048, 1024, 13, True),
-                                                (INT8_TC, 4200, 2048, 2048, 16, False),
-                                                (INT8_TC, 4200, 2048, 2048, 14, True),
-                                                (INT8_TC8, 4200, 2048, 2048, 15, False)])
+@pytest.mark.parametrize("variant,m,n,mc,s,ta", [(INT8, 2500, 2048, 640, 15, False),
+                                                (INT8, 2500, 2048, 640, 13, True),
+                                                (INT8_TC, 4200, 2048, 1152, 16, False),
+                                                (INT8_TC, 4200, 2048, 1152, 14, True),
+                                                (INT8_TC8, 4200, 2048, 1152, 15, False)])
 def test_host_int8_forms(ops, variant, m, n, mc, s, ta):
-    """Three chunks of op(A)'s rows (1024/1024/452 for mma.sync,
-    2048/2048/104 for tcgen05): C is bit-identical to ddgemm() of the same
+    """Four chunks of op(A)'s rows (640/640/640/580 for mma.sync,
+    1152/1152/1152/744 for tcgen05): C is bit-identical to ddgemm() of the same
     form, and on the rows at every chunk boundary (and random ones) by 42
     columns bit-identical to the form's restatement.  Rows and columns of C
     are independent in the method (per-row and per-column scales), so the
