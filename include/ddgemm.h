@@ -304,16 +304,21 @@ size_t ddgemm_host_buffer_size(int m, int n, int k, const ddgemm_opts *opts);
  *
  *   - buffer: device memory of >= ddgemm_host_buffer_size() bytes, 256-byte
  *     aligned, owned by the caller; it holds the copies and the workspace.
- *   - The copies run on two streams of the library's own, ordered by eleven
- *     events: a call takes such a set from a per-device pool and returns
- *     it when it returns, so only the first call on a device (and a call
- *     that overlaps another one on the host) creates them; they live until
- *     the process exits (do not reset the device between calls).
- *     B is copied first, then op(A) in up to four chunks of rows: every
- *     chunk's split and products run on `stream` as soon as its rows have
- *     arrived, and its rows of C are copied back while the next chunk
- *     computes.  Chunks hold at least 1024 tiles of the form's kernel
- *     (about seven waves of the GPU), so small problems run as one chunk.
+ *   - The copies run on two streams of the library's own, ordered by
+ *     fifteen events: a call takes such a set from a per-device pool and
+ *     returns it when it returns, so only the first call on a device (and a
+ *     call that overlaps another one on the host) creates them; they live
+ *     until the process exits (do not reset the device between calls).
+ *     op(A) is copied in up to four chunks of rows: every chunk's split and
+ *     products run on `stream` as soon as its rows (and B) have arrived,
+ *     and its rows of C are copied back while the next chunk computes.
+ *     Chunks hold at least 1024 tiles of the form's kernel (about seven
+ *     waves of the GPU), so small problems run as one chunk.  The INT8
+ *     forms copy B whole first.  The FP64 forms, when there are several
+ *     chunks, copy the first chunk of A first and then B in up to four
+ *     parts of whole 256-entry k-blocks, and multiply the first chunk part
+ *     by part as the parts arrive (each part's product added into C in
+ *     k-block order, as ddgemm() does).
  *   - Each chunk computes exactly what ddgemm() computes for those rows:
  *     C is bit-identical to ddgemm() on device copies of the operands,
  *     except that the FP64 form may choose a different split-k grouping

@@ -259,7 +259,7 @@ cudaError_t split_a_into(const Carve &c, int mr, int k, const double *A_hi, cons
 // bins, the bins of the single k-block).
 cudaError_t products_into(const Carve &c, int mr, int n, int k, double *C_hi, double *C_lo,
                           int ldc, int *flags, double *bins, int split, char *ws, cudaStream_t s,
-                          const Parsed &p) {
+                          const Parsed &p, bool accumulate = false) {
     if (c.int8) {
         const Layout8 &L = c.L8;
         const int *e_a = reinterpret_cast<const int *>(ws + L.off_ea);
@@ -288,7 +288,7 @@ cudaError_t products_into(const Carve &c, int mr, int n, int k, double *C_hi, do
                         reinterpret_cast<const int *>(ws + L.off_ea),
                         reinterpret_cast<const int *>(ws + L.off_eb), C_hi, C_lo,
                         (long long)ldc, flags, p.status, bins, products, split, part, part_lo,
-                        p.wait};
+                        p.wait, accumulate};
     return ddg::launch_cascade_fp64(ca, s);
 }
 
@@ -329,13 +329,19 @@ size_t workspace_total(int m, int n, int k, const Parsed &p) {
 // ---- host buffers: ddgemm_host ---------------------------------------------
 //
 // The operands are copied in and C is copied out by two streams of the call's
-// own, so that the copies overlap the kernels on the caller's stream: B goes
-// first (every C entry needs all of it), then A in row chunks; each chunk's
-// split and products start as soon as its rows have arrived, and its rows of
-// C go back while the next chunk computes.  Exposed: the copy of B and of
-// the first chunk of A, the split of B, and the copy of the last chunk of C.
+// own, so that the copies overlap the kernels on the caller's stream: A in
+// row chunks, each split and multiplied as soon as its rows (and B) have
+// arrived, and its rows of C copied back while the next chunk computes.  B
+// is needed whole by every chunk; in the FP64 forms it comes in parts of
+// whole k-blocks after the first chunk of A, and that chunk is multiplied
+// part by part as they arrive (each part's product added into C in k-block
+// order, as one launch would), so that only the first part of B stays
+// exposed; B is then split whole for the other chunks.  The INT8 forms take
+// B whole first.  Exposed: the copy of the first chunk of A and of B (or of
+// its first part), their splits, and the copy of the last chunk of C.
 
 constexpr int HOST_MAX_CHUNKS = 4;
+constexpr int HOST_B_PARTS = 4;
 constexpr long long HOST_MIN_TILES = 1024;
 
 // Rows of op(A) per chunk: at least HOST_MIN_TILES tiles of the form's own
@@ -390,7 +396,7 @@ HostLayout host_layout(int m, int n, int k, const Parsed &p) {
 // call's copies after it (both wait for their own caller's stream anyway).
 // The sets live until the process exits.
 struct HostStreams {
-    static constexpr int MAX_EVENTS = 3 + 2 * HOST_MAX_CHUNKS;
+    static constexpr int MAX_EVENTS = 3 + 2 * HOST_MAX_CHUNKS + HOST_B_PARTS;
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t ev[MAX_EVENTS] = {};
     bool init() {
@@ -578,8 +584,10 @@ int ddgemm_host(int m, int n, int k, const double *A_hi, const double *A_lo, int
     PooledHostStreams pooled;
     if (!pooled.acquire()) return DDGEMM_ECUDA;
     HostStreams &hs = *pooled.h;
-    // event slots: the entry, B copied, chunk r of A copied, chunk r of C done
-    constexpr int E_ENTRY = 0, E_B = 1, E_A = 2, E_C = 2 + HOST_MAX_CHUNKS;
+    // event slots: the entry, B copied, chunk r of A copied, chunk r of C
+    // done, part q of B copied
+    constexpr int E_ENTRY = 0, E_B = 1, E_A = 2, E_C = 2 + HOST_MAX_CHUNKS,
+                  E_BP = 2 + 2 * HOST_MAX_CHUNKS;
     // nothing of this call starts before the work already on the caller's
     // stream (which may still be using the buffer)
     if (!after(hs.h2d, s, hs.ev[E_ENTRY]) ||
@@ -595,28 +603,90 @@ int ddgemm_host(int m, int n, int k, const double *A_hi, const double *A_lo, int
             return r;
         if (cudaEventRecord(hs.ev[E_C], s) != cudaSuccess) return DDGEMM_ECUDA;
     } else {
-        // B whole, then the chunks of A
         const long long bk = p.trans_b ? n : k, bn = p.trans_b ? k : n;  // stored shape
-        if (!copy2d(b_hi, bn, B_hi, ldb, bn, bk, hs.h2d) ||
-            !copy2d(b_lo, bn, B_lo, ldb, bn, bk, hs.h2d) || !after(s, hs.h2d, hs.ev[E_B]))
-            return DDGEMM_ECUDA;
         const Carve c = carve_for(H.mc, n, k, p);
-        if (split_b_into(c, n, k, b_hi, b_lo, (int)bn, ws, s, p) != cudaSuccess)
-            return DDGEMM_ECUDA;
         int sms = 0;
         if (!c.int8 && sm_count(sms) != DDGEMM_OK) return DDGEMM_ECUDA;
-        for (int r = 0; r < nchunks; ++r) {
-            const int r0 = r * H.mc, mr = std::min(H.mc, m - r0);
-            double *ah = a_hi + (size_t)r0 * k, *al = a_lo + (size_t)r0 * k;
+        // chunk r of A: its device rows and the copy of them
+        auto chunk_a = [&](int r, double *&ah, double *&al, int &mr, int &lda_c) {
+            const int r0 = r * H.mc;
+            mr = std::min(H.mc, m - r0);
+            ah = a_hi + (size_t)r0 * k;
+            al = a_lo + (size_t)r0 * k;
             // the chunk keeps A's stored orientation: rows r0.. of A, or
             // columns r0.. of the stored k x m matrix
-            const int lda_c = p.trans_a ? mr : k;
-            const bool ok =
-                p.trans_a ? copy2d(ah, mr, A_hi + r0, lda, mr, k, hs.h2d) &&
-                                copy2d(al, mr, A_lo + r0, lda, mr, k, hs.h2d)
-                          : copy2d(ah, k, A_hi + (size_t)r0 * lda, lda, k, mr, hs.h2d) &&
-                                copy2d(al, k, A_lo + (size_t)r0 * lda, lda, k, mr, hs.h2d);
-            if (!ok || !after(s, hs.h2d, hs.ev[E_A + r])) return DDGEMM_ECUDA;
+            lda_c = p.trans_a ? mr : k;
+            return p.trans_a ? copy2d(ah, mr, A_hi + r0, lda, mr, k, hs.h2d) &&
+                                   copy2d(al, mr, A_lo + r0, lda, mr, k, hs.h2d)
+                             : copy2d(ah, k, A_hi + (size_t)r0 * lda, lda, k, mr, hs.h2d) &&
+                                   copy2d(al, k, A_lo + (size_t)r0 * lda, lda, k, mr, hs.h2d);
+        };
+        // B in parts of whole k-blocks for the first chunk (FP64 forms, when
+        // there is a second chunk to hide it behind and the parts' workspace
+        // fits where B's pieces go later)
+        const int kblocks = (k + ddg::KC - 1) / ddg::KC;
+        int parts = 1, kpart = k;
+        Carve cp;
+        size_t cp_bytes = 0;
+        if (!c.int8 && nchunks > 1 && kblocks > 1) {
+            parts = std::min(HOST_B_PARTS, kblocks);
+            kpart = (kblocks + parts - 1) / parts * ddg::KC;
+            parts = (k + kpart - 1) / kpart;
+            cp = carve_for(H.mc, n, kpart, p);
+            cp_bytes = H.ws_bytes - c.L.off_b;
+            if (cp.base > cp_bytes) parts = 1;
+        }
+        int r_first = 0;
+        if (parts > 1) {
+            // copies: the first chunk of A, then B part by part
+            double *ah, *al;
+            int mr, lda_c;
+            if (!chunk_a(0, ah, al, mr, lda_c) || !after(s, hs.h2d, hs.ev[E_A])) return DDGEMM_ECUDA;
+            for (int q = 0; q < parts; ++q) {
+                const long long k0 = (long long)q * kpart, kq = std::min<long long>(kpart, k - k0);
+                const bool ok =
+                    p.trans_b ? copy2d(b_hi + k0, bn, B_hi + k0, ldb, kq, bk, hs.h2d) &&
+                                    copy2d(b_lo + k0, bn, B_lo + k0, ldb, kq, bk, hs.h2d)
+                              : copy2d(b_hi + k0 * bn, bn, B_hi + k0 * ldb, ldb, bn, kq, hs.h2d) &&
+                                    copy2d(b_lo + k0 * bn, bn, B_lo + k0 * ldb, ldb, bn, kq, hs.h2d);
+                if (!ok || cudaEventRecord(hs.ev[E_BP + q], hs.h2d) != cudaSuccess)
+                    return DDGEMM_ECUDA;
+            }
+            // the first chunk's products part by part, in the parts' own
+            // workspace (where B's pieces go later), each added into C
+            char *wp = ws + c.L.off_b;
+            for (int q = 0; q < parts; ++q) {
+                const int k0 = q * kpart, kq = std::min(kpart, k - k0);
+                const double *aph = p.trans_a ? ah + (size_t)k0 * mr : ah + k0;
+                const double *apl = p.trans_a ? al + (size_t)k0 * mr : al + k0;
+                const double *bph = p.trans_b ? b_hi + k0 : b_hi + (size_t)k0 * bn;
+                const double *bpl = p.trans_b ? b_lo + k0 : b_lo + (size_t)k0 * bn;
+                const int split = split_groups_in(mr, n, kq, sms, cp_bytes, cp, p);
+                if (cudaStreamWaitEvent(s, hs.ev[E_BP + q], 0) != cudaSuccess ||
+                    split_a_into(cp, mr, kq, aph, apl, lda_c, wp, s, p) != cudaSuccess ||
+                    split_b_into(cp, n, kq, bph, bpl, (int)bn, wp, s, p) != cudaSuccess ||
+                    products_into(cp, mr, n, kq, c_hi, c_lo, n, p.flags, nullptr, split, wp, s, p,
+                                  q > 0) != cudaSuccess)
+                    return DDGEMM_ECUDA;
+            }
+            if (cudaEventRecord(hs.ev[E_C], s) != cudaSuccess) return DDGEMM_ECUDA;
+            r_first = 1;
+        } else {
+            // B whole first
+            if (!copy2d(b_hi, bn, B_hi, ldb, bn, bk, hs.h2d) ||
+                !copy2d(b_lo, bn, B_lo, ldb, bn, bk, hs.h2d) || !after(s, hs.h2d, hs.ev[E_B]))
+                return DDGEMM_ECUDA;
+        }
+        // B split whole (all of it has arrived: the stream waited for its
+        // copy or for its last part) for the remaining chunks
+        if (r_first < nchunks && split_b_into(c, n, k, b_hi, b_lo, (int)bn, ws, s, p) != cudaSuccess)
+            return DDGEMM_ECUDA;
+        for (int r = r_first; r < nchunks; ++r) {
+            const int r0 = r * H.mc;
+            double *ah, *al;
+            int mr, lda_c;
+            if (!chunk_a(r, ah, al, mr, lda_c) || !after(s, hs.h2d, hs.ev[E_A + r]))
+                return DDGEMM_ECUDA;
             const int split = c.int8 ? 1 : split_groups_in(mr, n, k, sms, H.ws_bytes, c, p);
             if (split_a_into(c, mr, k, ah, al, lda_c, ws, s, p) != cudaSuccess ||
                 products_into(c, mr, n, k, c_hi + (size_t)r0 * n, c_lo + (size_t)r0 * n, n,

@@ -127,7 +127,10 @@ cascade_fp64_kernel(const __grid_constant__ CUtensorMap tm_a,
         const int ta = t0 + t;  // the k-step in the whole of k
         if ((ta + 1) % STEPS_PER_BLOCK == 0 || ta + 1 == total_steps) {
             const int p = ta / STEPS_PER_BLOCK;
-            epilogue<DUMP_BINS>(acc, p, p == kb_begin, m0 + wm * 16, n0 + wn * 32, lane, out);
+            // group 0's first k-block starts C from zero unless the launch
+            // continues an earlier product; the partials always start from zero
+            epilogue<DUMP_BINS>(acc, p, p == kb_begin && !(args.accumulate && part == 0),
+                                m0 + wm * 16, n0 + wn * 32, lane, out);
             if constexpr (DUMP_BINS) return;
         }
     }

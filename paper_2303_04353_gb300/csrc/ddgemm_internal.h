@@ -60,6 +60,10 @@ struct CascadeArgs {
     int split;               // k-block groups per tile (1: no split)
     double *part_hi, *part_lo;  // split > 1: partial C of groups 1..split-1, [split-1][m][n]
     WaitPlan wait{};
+    // add the k-blocks into C's (and the flags') current values instead of
+    // starting from zero: a product over a range of k that continues an
+    // earlier one, in the same k-block order as one launch over both
+    bool accumulate = false;
 };
 
 // Split-k over whole k-blocks: the number of groups for a grid of `tiles`

@@ -111,6 +111,21 @@ def test_host_fp64_four_chunks(ops, ta, tb):
     check_sampled_contract(a_hi, a_lo, b_hi, b_lo, c_hi, c_lo)
 
 
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, True), (False, True)])
+def test_host_fp64_first_chunk_by_parts_of_b(ops, ta, tb):
+    """2100 x 2048 x 1100: two chunks of op(A)'s rows (2048 and 52); B comes
+    in parts of 512, 512 and 76 entries of k, and the first chunk is
+    multiplied part by part, each part added into C.  With split_k = 1 the
+    k-blocks reach C in the same order as one launch: C is bit-identical to
+    ddgemm(), and the second chunk (B split whole) too."""
+    m, n, k = 2100, 2048, 1100
+    a_hi, a_lo, b_hi, b_lo = gemm_inputs(m, n, k, kind="wide", seed=13)
+    c_hi, c_lo = run_host(ops, (a_hi, a_lo), (b_hi, b_lo), ta, tb, split_k=1)
+    d_hi, d_lo = run_device(ops, (a_hi, a_lo), (b_hi, b_lo), ta, tb, split_k=1)
+    assert np.array_equal(c_hi, d_hi) and np.array_equal(c_lo, d_lo)
+    check_sampled_contract(a_hi, a_lo, b_hi, b_lo, c_hi, c_lo, seed=3)
+
+
 def test_host_fp64_split_k_chunks(ops):
     """The default split-k choice per chunk: within the reordering the FP64x2
     sum of k-block groups allows (8 (K_B + g) 2^-106 |A||B|, g <= 16)."""
