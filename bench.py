@@ -49,7 +49,7 @@ NOMINAL_BF16_TFLOPS = 2250.0
 # DRAM bytes per launch (read + write) of the dominant kernel, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
 # kernels at 4096^3; other workloads report null.
-TRAFFIC_4096 = {"cascade_fp64_kernel": 9.884234e9 + 0.286038e9,
+TRAFFIC_4096 = {"cascade_fp64_kernel": 9.881583e9 + 0.286808e9,
                 "cascade_int8_kernel<15>": 3.096227e9 + 0.268912e9,
                 "cascade_int8_tc_kernel<16>": 9.188401e9 + 0.287655e9}
 
