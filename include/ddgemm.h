@@ -278,8 +278,8 @@ size_t ddgemm_batched_workspace_size(int count, const ddgemm_problem *probs_host
  *               DDGEMM_ORIENT_FEWER_TILES, DDGEMM_PLANES_INTERLEAVED, 4}.
  *               Out-of-range fields: DDGEMM_EINVAL.
  * INT8_TC and INT8_TC8 (the INT8 form on the tcgen05 tensor cores, see
- * DDGEMM_VARIANT_INT8_TC): five launches, a plan, the exponents of every A
- * and of every B, the digits of all of them, and one persistent tcgen05
+ * DDGEMM_VARIANT_INT8_TC): four launches, a plan, the exponents of every A
+ * and of every B (one launch), the digits of all of them, and one persistent tcgen05
  * kernel over the (problem, 128 x 16 tile) items (tile grids over C or C^T
  * and the tile order as config says); each C_i is bit-identical to ddgemm()
  * with that variant.  The workspace size depends on opts (pass the same opts

@@ -1,8 +1,8 @@
 // Many FP64x2 GEMMs of uneven shapes with the INT8 form on the tcgen05
-// tensor cores, in five launches: a plan, the block exponents of every A
-// (one warp per row and k-block) and of every B (one CTA per 64 columns and
-// k-block), the tiled bf16 digits of every A and B (one CTA per 32 x 64
-// input tile), and one persistent tcgen05 kernel that walks the planned list
+// tensor cores, in four launches: a plan, the block exponents of every A
+// (one warp per row and k-block) and of every B (one CTA per 64 columns
+// and k-block) in one launch, the tiled bf16 digits of every A and B (one
+// CTA per 32 x 64 input tile), and one persistent tcgen05 kernel that walks the planned list
 // of (problem, 128 x 16 tile) items in the configured order (longest k
 // first unless ddgemm_batch_config says otherwise).  The paper has no
 // batched form; this is the tcgen05 INT8 form (cascade_int8_tc.cu) scheduled
@@ -16,6 +16,7 @@
 // so the call can be captured into a CUDA graph.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 
@@ -331,46 +332,47 @@ struct TcView {
     }
 };
 
-// Exponents of every A: one warp per (problem, row, k-block).  Neighbouring
-// warps take neighbouring chunks of units (a contiguous run per warp
-// measured slower: the runs differ in length of rows).
+// The exponents of every A and every B in one launch: CTAs [0, blocks_a)
+// take A's units, the others B's, so that the two latency-bound halves
+// overlap instead of running one after the other.
+//   A: one warp per (problem, row, k-block).  Neighbouring warps take
+//   neighbouring chunks of units (a contiguous run per warp measured
+//   slower: the runs differ in length of rows); a search of the unit prefix
+//   serves a chunk's units, mostly rows of one problem.
+//   B: one CTA per (problem, 64 columns, k-block).
 constexpr int EA_CHUNK = 8;
-__global__ void __launch_bounds__(256) tc_exps_a_kernel(const char *ws) {
-    const TcView V(ws);
-    const int count = V.hdr->count, lane = threadIdx.x & 31, kblk = V.hdr->kblk;
-    const long long total = V.hdr->total_ea;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    // chunks of EA_CHUNK consecutive units (mostly rows of one problem), so
-    // that a search of the unit prefix serves several units; the chunks are
-    // dealt out round robin for balance
-    int i = 0;
-    for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-         c * EA_CHUNK < total; c += nw) {
-        const long long u1 = c * EA_CHUNK + EA_CHUNK < total ? c * EA_CHUNK + EA_CHUNK : total;
-        for (long long u = c * EA_CHUNK; u < u1; ++u) {
-            i = advance_tc(V.ea_pre, count, u, i);
-            const TcEntry &e = V.ent[i];
-            const int local = (int)(u - V.ea_pre[i]);
-            const int row = e.kb8 == 1 ? local : local / e.kb8;
-            split8::exps_contig_unit(lane, row, local - row * e.kb8, e.m, e.k, kblk, e.a_hi,
-                                     e.lda, e.e_a);
-        }
-    }
-}
-
-// Exponents of every B: one CTA per (problem, 64 columns, k-block).
-__global__ void __launch_bounds__(256) tc_exps_b_kernel(const char *ws) {
+__global__ void __launch_bounds__(256) tc_exps_kernel(const char *ws, int blocks_a) {
     __shared__ unsigned long long part[4][64];
     const TcView V(ws);
-    const int count = V.hdr->count;
+    const int count = V.hdr->count, kblk = V.hdr->kblk;
     int i = 0;
-    for (long long u = blockIdx.x; u < V.hdr->total_eb; u += gridDim.x) {
-        i = advance_tc(V.eb_pre, count, u, i);
-        const TcEntry &e = V.ent[i];
-        const long long local = u - V.eb_pre[i];
-        const int vtiles = (e.n + 63) / 64;
-        split8::exps_strided_unit<4>((int)(local % vtiles), (int)(local / vtiles), e.n, e.k,
-                                  V.hdr->kblk, e.b_hi, e.ldb, e.e_b, part);
+    if ((int)blockIdx.x < blocks_a) {
+        const int lane = threadIdx.x & 31;
+        const long long total = V.hdr->total_ea;
+        const long long nw = ((long long)blocks_a * blockDim.x) >> 5;
+        for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+             c * EA_CHUNK < total; c += nw) {
+            const long long u1 =
+                c * EA_CHUNK + EA_CHUNK < total ? c * EA_CHUNK + EA_CHUNK : total;
+            for (long long u = c * EA_CHUNK; u < u1; ++u) {
+                i = advance_tc(V.ea_pre, count, u, i);
+                const TcEntry &e = V.ent[i];
+                const int local = (int)(u - V.ea_pre[i]);
+                const int row = e.kb8 == 1 ? local : local / e.kb8;
+                split8::exps_contig_unit(lane, row, local - row * e.kb8, e.m, e.k, kblk, e.a_hi,
+                                         e.lda, e.e_a);
+            }
+        }
+    } else {
+        const long long blocks_b = (long long)gridDim.x - blocks_a;
+        for (long long u = blockIdx.x - blocks_a; u < V.hdr->total_eb; u += blocks_b) {
+            i = advance_tc(V.eb_pre, count, u, i);
+            const TcEntry &e = V.ent[i];
+            const long long local = u - V.eb_pre[i];
+            const int vtiles = (e.n + 63) / 64;
+            split8::exps_strided_unit<4>((int)(local % vtiles), (int)(local / vtiles), e.n, e.k,
+                                         kblk, e.b_hi, e.ldb, e.e_b, part);
+        }
     }
 }
 
@@ -459,12 +461,9 @@ cudaError_t launch_batched_tc(char *ws, long long tiles, long long units_ea, lon
                               long long units_d, int sms, cudaStream_t s, int row_group,
                               const WaitPlan &wait, void *const *events) {
     const long long cap = 8LL * sms;
-    if (units_ea > 0) {
-        const long long blocks = (units_ea + 8 * EA_CHUNK - 1) / (8 * EA_CHUNK);
-        tc_exps_a_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(ws);
-    }
-    if (units_eb > 0)
-        tc_exps_b_kernel<<<(unsigned)(units_eb < cap ? units_eb : cap), 256, 0, s>>>(ws);
+    const long long ba = std::min(cap, (units_ea + 8 * EA_CHUNK - 1) / (8 * EA_CHUNK)),
+                    bb = std::min(cap, units_eb);
+    if (ba + bb > 0) tc_exps_kernel<<<(unsigned)(ba + bb), 256, 0, s>>>(ws, (int)ba);
     if (units_d > 0)
         tc_digits_kernel<S, BITS><<<(unsigned)(units_d < cap ? units_d : cap), 256, 0, s>>>(ws);
     cudaError_t e = cudaGetLastError();

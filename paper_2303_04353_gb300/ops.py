@@ -325,10 +325,11 @@ class Batch:
     ``problems`` is a list of (a_hi, a_lo, b_hi, b_lo, c_hi, c_lo) CUDA
     tensors (row-major, unit last stride).  The constructor uploads the
     problem descriptors and allocates the workspace (PyTorch memory), so
-    ``run()`` only enqueues the launches (four in the FP64 form, five in the
-    tcgen05 forms) and can be captured into a CUDA graph.  The tensors must stay alive and in place while the batch is
-    used, and the Batch itself (its workspace) until the work of its last
-    ``run()`` has completed on the stream it was enqueued on."""
+    ``run()`` only enqueues the launches (four in either form) and can be
+    captured into a CUDA graph.  The tensors must stay alive and in place
+    while the batch is used, and the Batch itself (its workspace) until the
+    work of its last ``run()`` has completed on the stream it was enqueued
+    on."""
 
     def __init__(self, problems, device=None, variant=_lib.DDGEMM_VARIANT_FP64, int8_slices=0):
         """variant: DDGEMM_VARIANT_FP64 (the persistent FP64 kernel),
