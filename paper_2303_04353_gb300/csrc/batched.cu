@@ -83,11 +83,11 @@ __device__ inline long long find(const long long *prefix, int count, long long u
     return lo;
 }
 
-// Ordering key for "longest k first": larger k, then larger m n, then index.
+// Ordering key for "longest k first": larger k, then larger m n, then index
+// (false for a = b).  Without branches: the lanes of the rank loop compare
+// different problems, and branching on the keys diverged.
 __device__ inline bool before(int ka, long long sa, int ia, int kb, long long sb, int ib) {
-    if (ka != kb) return ka > kb;
-    if (sa != sb) return sa > sb;
-    return ia < ib;
+    return (ka > kb) | ((ka == kb) & ((sa > sb) | ((sa == sb) & (ia < ib))));
 }
 
 // Problems whose ordering keys the plan kernel keeps in shared memory.
@@ -147,13 +147,11 @@ plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, int o
             const long long qmn = (long long)q.m * q.n;
             r = 0;
             if (keys_in_smem) {
-                for (int j = 0; j < count; ++j)
-                    if (j != i && before(key_k[j], key_mn[j], j, q.k, qmn, i)) ++r;
+#pragma unroll 4
+                for (int j = 0; j < count; ++j) r += before(key_k[j], key_mn[j], j, q.k, qmn, i);
             } else {
                 for (int j = 0; j < count; ++j)
-                    if (j != i && before(probs[j].k, (long long)probs[j].m * probs[j].n, j, q.k,
-                                         qmn, i))
-                        ++r;
+                    r += before(probs[j].k, (long long)probs[j].m * probs[j].n, j, q.k, qmn, i);
             }
         }
         order[r] = i;

@@ -137,11 +137,12 @@ __device__ inline int advance_tc(const long long *prefix, int count, long long u
     return lo;
 }
 
-// Longest k first, then larger m n, then index.
+// Longest k first, then larger m n, then index (false for a = b).  Without
+// branches: every lane of the plan's rank loop compares against another
+// problem, and branches on the keys diverged and made that loop the plan's
+// slowest phase.
 __device__ inline bool before_tc(int ka, long long sa, int ia, int kb, long long sb, int ib) {
-    if (ka != kb) return ka > kb;
-    if (sa != sb) return sa > sb;
-    return ia < ib;
+    return (ka > kb) | ((ka == kb) & ((sa > sb) | ((sa == sb) & (ia < ib))));
 }
 
 // Problems whose ordering keys the plan kernel keeps in shared memory.
@@ -196,13 +197,12 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
         if (order_rule == DDGEMM_ORDER_LONGEST_K_FIRST) {
             r = 0;
             if (keys_in_smem) {
+#pragma unroll 4
                 for (int j = 0; j < count; ++j)
-                    if (j != i && before_tc(key_k[j], key_mn[j], j, q.k, qmn, i)) ++r;
+                    r += before_tc(key_k[j], key_mn[j], j, q.k, qmn, i);
             } else {
                 for (int j = 0; j < count; ++j)
-                    if (j != i && before_tc(probs[j].k, (long long)probs[j].m * probs[j].n, j,
-                                            q.k, qmn, i))
-                        ++r;
+                    r += before_tc(probs[j].k, (long long)probs[j].m * probs[j].n, j, q.k, qmn, i);
             }
         }
         order[r] = i;
