@@ -57,6 +57,7 @@ struct TcHeader {
     int count;
     int kblk;                  // k-block of the digit width (8192 or 16384)
     unsigned int *status;
+    unsigned long long next_d;  // the digit kernel's unit counter (the plan zeroes it)
 };
 
 // Workspace: [header][entries][order][tile prefix][4 unit prefixes] | digits
@@ -310,6 +311,7 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
             hdr->count = count;
             hdr->kblk = kblk;
             hdr->status = status;
+            hdr->next_d = 0;
         }
     }
 }
@@ -377,6 +379,7 @@ __global__ void __launch_bounds__(256) tc_exps_kernel(const char *ws, int blocks
 }
 
 // Digits of every A, then of every B: one CTA per 32 x 64 input tile.
+constexpr int DIGIT_CHUNK = 4;
 template <int S, int BITS>
 __global__ void __launch_bounds__(256, 4) tc_digits_kernel(const char *ws) {
     __shared__ double sh[split8::TV][split8::TK + 1];
@@ -385,31 +388,44 @@ __global__ void __launch_bounds__(256, 4) tc_digits_kernel(const char *ws) {
     const int count = V.hdr->count;
     const long long total_a = V.da_pre[count];
     unsigned int *status = V.hdr->status;
-    // each CTA walks a contiguous run of units
-    const long long total = V.hdr->total_d, run = (total + gridDim.x - 1) / gridDim.x;
-    const long long u0 = (long long)blockIdx.x * run, u1 = u0 + run < total ? u0 + run : total;
+    // CTAs take chunks of DIGIT_CHUNK consecutive units from a counter, so
+    // that units of uneven cost (ragged tiles) do not leave some CTAs with
+    // the last of the work; chunks come in increasing order, so each CTA's
+    // problem lookups gallop forward
+    const long long total = V.hdr->total_d;
+    __shared__ long long s_next;
     int ia = 0, ib = 0;
-    for (long long u = u0; u < u1; ++u) {
-        __syncthreads();  // the previous unit is done with sh, sl
-        if (u < total_a) {
-            const int i = ia = advance_tc(V.da_pre, count, u, ia);
-            const TcEntry &e = V.ent[i];
-            const long long local = u - V.da_pre[i];
-            const int ktiles = (e.k + split8::TK - 1) / split8::TK;
-            split8::digits_unit<S, true, true, BITS>((int)(local / ktiles) * split8::TV,
-                                               (int)(local % ktiles) * split8::TK, e.m, e.k,
-                                               e.a_hi, e.a_lo, e.lda, e.a_tiles, 0,
-                                               tc_th_a(e.trans), e.e_a, status, sh, sl);
-        } else {
-            const long long ub = u - total_a;
-            const int i = ib = advance_tc(V.db_pre, count, ub, ib);
-            const TcEntry &e = V.ent[i];
-            const long long local = ub - V.db_pre[i];
-            const int ktiles = (e.k + split8::TK - 1) / split8::TK;
-            split8::digits_unit<S, false, true, BITS>((int)(local / ktiles) * split8::TV,
-                                                (int)(local % ktiles) * split8::TK, e.n, e.k,
-                                                e.b_hi, e.b_lo, e.ldb, e.b_tiles, 0,
-                                                tc_th_b(e.trans), e.e_b, status, sh, sl);
+    for (;;) {
+        __syncthreads();  // every thread has read s_next and is done with sh, sl
+        if (threadIdx.x == 0)
+            s_next = (long long)atomicAdd(const_cast<unsigned long long *>(&V.hdr->next_d),
+                                          (unsigned long long)DIGIT_CHUNK);
+        __syncthreads();
+        const long long u0 = s_next;
+        if (u0 >= total) break;
+        const long long u1 = u0 + DIGIT_CHUNK < total ? u0 + DIGIT_CHUNK : total;
+        for (long long u = u0; u < u1; ++u) {
+            if (u > u0) __syncthreads();  // the previous unit is done with sh, sl
+            if (u < total_a) {
+                const int i = ia = advance_tc(V.da_pre, count, u, ia);
+                const TcEntry &e = V.ent[i];
+                const long long local = u - V.da_pre[i];
+                const int ktiles = (e.k + split8::TK - 1) / split8::TK;
+                split8::digits_unit<S, true, true, BITS>((int)(local / ktiles) * split8::TV,
+                                                         (int)(local % ktiles) * split8::TK, e.m,
+                                                         e.k, e.a_hi, e.a_lo, e.lda, e.a_tiles, 0,
+                                                         tc_th_a(e.trans), e.e_a, status, sh, sl);
+            } else {
+                const long long ub = u - total_a;
+                const int i = ib = advance_tc(V.db_pre, count, ub, ib);
+                const TcEntry &e = V.ent[i];
+                const long long local = ub - V.db_pre[i];
+                const int ktiles = (e.k + split8::TK - 1) / split8::TK;
+                split8::digits_unit<S, false, true, BITS>((int)(local / ktiles) * split8::TV,
+                                                          (int)(local % ktiles) * split8::TK, e.n,
+                                                          e.k, e.b_hi, e.b_lo, e.ldb, e.b_tiles, 0,
+                                                          tc_th_b(e.trans), e.e_b, status, sh, sl);
+            }
         }
     }
 }
