@@ -57,7 +57,8 @@ struct TcHeader {
     int count;
     int kblk;                  // k-block of the digit width (8192 or 16384)
     unsigned int *status;
-    unsigned long long next_d;  // the digit kernel's unit counter (the plan zeroes it)
+    unsigned long long next_d;   // the digit kernel's unit counter (the plan zeroes it)
+    unsigned long long next_eb;  // the same for the exponents of B
 };
 
 // Workspace: [header][entries][order][tile prefix][4 unit prefixes] | digits
@@ -312,6 +313,7 @@ tc_plan_kernel(int count, const ddgemm_problem *__restrict__ probs, char *ws, in
             hdr->kblk = kblk;
             hdr->status = status;
             hdr->next_d = 0;
+            hdr->next_eb = 0;
         }
     }
 }
@@ -341,7 +343,7 @@ struct TcView {
 //   neighbouring chunks of units (a contiguous run per warp measured
 //   slower: the runs differ in length of rows); a search of the unit prefix
 //   serves a chunk's units, mostly rows of one problem.
-//   B: one CTA per (problem, 64 columns, k-block).
+//   B: one CTA per (problem, 64 columns, k-block), taken from a counter.
 constexpr int EA_CHUNK = 8;
 __global__ void __launch_bounds__(256) tc_exps_kernel(const char *ws, int blocks_a) {
     __shared__ unsigned long long part[4][64];
@@ -366,8 +368,16 @@ __global__ void __launch_bounds__(256) tc_exps_kernel(const char *ws, int blocks
             }
         }
     } else {
-        const long long blocks_b = (long long)gridDim.x - blocks_a;
-        for (long long u = blockIdx.x - blocks_a; u < V.hdr->total_eb; u += blocks_b) {
+        // B's units (of uneven size: k rows each) from a counter
+        __shared__ long long s_next;
+        for (;;) {
+            __syncthreads();  // every thread has read s_next
+            if (threadIdx.x == 0)
+                s_next = (long long)atomicAdd(const_cast<unsigned long long *>(&V.hdr->next_eb),
+                                              1ull);
+            __syncthreads();
+            const long long u = s_next;
+            if (u >= V.hdr->total_eb) break;
             i = advance_tc(V.eb_pre, count, u, i);
             const TcEntry &e = V.ent[i];
             const long long local = u - V.eb_pre[i];
